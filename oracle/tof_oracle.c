@@ -1,0 +1,1526 @@
+/*
+ * tof_oracle.c -- plain, slow FP64 CPU oracle of the ToF ReSTIR hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the cpu_baseline /
+ * reference legs of bench.py may load this library.  It shares no code, header, table or
+ * helper with the CUDA path; the two agree only through the seeded input arrays and the
+ * published definitions both restate (Philox4x32-10, Moller-Trumbore, the paper's equations).
+ *
+ * What it computes (Kim, Jarosz, Pediredla, "ToF ReSTIR", ACM TOG 45(4) 2026):
+ *   Sec. 3.1  time-of-flight path integral I(tau) = int W_tau(L(x)) f(x) dmu(x), with c = 1
+ *   Sec. 3.2  RIS (basic, MIS) and generalized RIS with shift maps and the generalized balance
+ *             heuristic (eq. GRIS_resampling_weight, eq. GRIS_MIS_weight)
+ *   Sec. 4.1  offset-path perturbation at the reconnection vertex of a hybrid shift
+ *   Sec. 4.2  2-D surface parameterisation xi of the reconnection vertex
+ *   Sec. 4.3  average-gradient gauge, Newton iteration with backtracking, shift Jacobian by
+ *             implicit differentiation, frame factor, gradient and Hessian of L
+ *   Sec. 4.5  transient histograms as independent per-bin gates; candidates deposited into
+ *             their own bin ("path reuse" of Jarabo 2014)
+ *   Sec. 5    reservoir stores the vertex after the reconnection vertex; delta light sources
+ *             (point light with NEE, collimated laser spot)
+ *
+ * Readings where the paper is silent, garbled or inconsistent are listed in the design doc; the ones
+ * that change arithmetic are repeated at the function that applies them.
+ *
+ * Everything is double precision.  Random numbers come from Philox4x32-10 (Salmon et al. 2011)
+ * keyed by (seed) and counted by (pixel, frame, stream, purpose), so the CUDA path and this
+ * oracle draw identical numbers.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdio.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OPI 3.14159265358979323846
+
+/* ============================================================================================
+ * small vector algebra
+ * ==========================================================================================*/
+typedef struct { double x, y, z; } v3;
+static v3 V(double x, double y, double z) { v3 r = {x, y, z}; return r; }
+static v3 vadd(v3 a, v3 b) { return V(a.x + b.x, a.y + b.y, a.z + b.z); }
+static v3 vsub(v3 a, v3 b) { return V(a.x - b.x, a.y - b.y, a.z - b.z); }
+static v3 vmul(v3 a, double s) { return V(a.x * s, a.y * s, a.z * s); }
+static double vdot(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static v3 vcross(v3 a, v3 b) { return V(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+static double vlen(v3 a) { return sqrt(vdot(a, a)); }
+static v3 vnorm(v3 a) { double l = vlen(a); return l > 0 ? vmul(a, 1.0 / l) : V(0, 0, 0); }
+static v3 vload(const double* p) { return V(p[0], p[1], p[2]); }
+
+/* ============================================================================================
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy as 1, 2, 3",
+ * SC 2011): 10 rounds of the 4x32 Philox S-box with multipliers 0xD2511F53 / 0xCD9E8D57 and
+ * Weyl key increments 0x9E3779B9 / 0xBB67AE85.
+ * ==========================================================================================*/
+void or_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* purposes (low byte of the 4th counter word) */
+enum { P_JITTER = 1, P_BSDF = 2, P_RIS = 3, P_NEIGHBOR = 4, P_MERGE = 5 };
+
+static double u01(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+static void rng4(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t out[4]) {
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    or_philox(ctr, key, out);
+}
+
+/* ============================================================================================
+ * materials and BSDFs (the paper uses diffuse, glossy and specular materials, Sec. 6; the
+ * microfacet model is Walter et al. 2007 GGX with the separable Smith shadowing term and a
+ * constant Fresnel equal to the albedo)
+ * ==========================================================================================*/
+enum { M_LAMBERT = 0, M_GGX = 1, M_MIRROR = 2 };
+enum { C_ROUGH = 0, C_GLOSSY = 1, C_DELTA = 2 };
+typedef struct { int type; double albedo, alpha; } omat;
+
+static int mat_class(const omat* m) {
+    if (m->type == M_MIRROR) return C_DELTA;
+    if (m->type == M_GGX && m->alpha < 0.2) return C_GLOSSY;
+    return C_ROUGH;
+}
+
+static double ggx_D(double nh, double a) {
+    double a2 = a * a, t = nh * nh * (a2 - 1.0) + 1.0;
+    return a2 / (OPI * t * t);
+}
+static double ggx_G1(double nv, double a) {
+    double a2 = a * a;
+    return 2.0 * nv / (nv + sqrt(a2 + (1.0 - a2) * nv * nv));
+}
+
+/* BSDF value f_s(wi, wo) for unit directions wi (toward the previous vertex) and wo (toward the
+ * next); n is the geometric normal of either orientation.  Reflection only; delta lobes give 0. */
+double or_bsdf_eval(int type, double albedo, double alpha, const double* nn, const double* wii, const double* woo) {
+    v3 n = vload(nn), wi = vload(wii), wo = vload(woo);
+    double ci = vdot(n, wi), co = vdot(n, wo);
+    if (ci * co <= 0.0) return 0.0;
+    if (ci < 0) { ci = -ci; co = -co; n = vmul(n, -1.0); }
+    if (type == M_LAMBERT) return albedo / OPI;
+    if (type == M_GGX) {
+        v3 h = vnorm(vadd(wi, wo));
+        double nh = vdot(n, h);
+        if (nh <= 0) return 0.0;
+        return albedo * ggx_D(nh, alpha) * ggx_G1(ci, alpha) * ggx_G1(co, alpha) / (4.0 * ci * co);
+    }
+    return 0.0;
+}
+static double bsdf_f(const omat* m, v3 n, v3 wi, v3 wo) {
+    double a[3] = {n.x, n.y, n.z}, b[3] = {wi.x, wi.y, wi.z}, c[3] = {wo.x, wo.y, wo.z};
+    return or_bsdf_eval(m->type, m->albedo, m->alpha, a, b, c);
+}
+
+/* solid-angle pdf of sampling wo at a surface with normal n, given wi */
+static double bsdf_pdf(const omat* m, v3 n, v3 wi, v3 wo) {
+    double ci = vdot(n, wi), co = vdot(n, wo);
+    if (ci * co <= 0.0) return 0.0;
+    if (ci < 0) { ci = -ci; co = -co; n = vmul(n, -1.0); }
+    if (m->type == M_LAMBERT) return co / OPI;
+    if (m->type == M_GGX) {
+        v3 h = vnorm(vadd(wi, wo));
+        double nh = vdot(n, h), oh = vdot(wo, h);
+        if (nh <= 0 || oh <= 0) return 0.0;
+        return ggx_D(nh, m->alpha) * nh / (4.0 * oh);
+    }
+    return 0.0;
+}
+
+/* orthonormal basis around a unit vector (Duff, Burgess, Christensen, Hery, Kensler, Liani,
+ * Villemin: "Building an Orthonormal Basis, Revisited", JCGT 6(1) 2017) */
+static void onb(v3 n, v3* t, v3* b) {
+    double sign = n.z >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sign + n.z);
+    double bb = n.x * n.y * a;
+    *t = V(1.0 + sign * n.x * n.x * a, sign * bb, -sign * n.x);
+    *b = V(bb, sign + n.y * n.y * a, -n.y);
+}
+
+/* sample wo given wi; returns 0 on failure.  *thr = f_s |cos_o| / pdf (albedo for delta). */
+static int bsdf_sample(const omat* m, v3 n, v3 wi, double u0, double u1, v3* wo, double* pdf, double* thr, int* delta) {
+    if (vdot(n, wi) < 0) n = vmul(n, -1.0);
+    *delta = 0;
+    if (m->type == M_MIRROR) {
+        *wo = vsub(vmul(n, 2.0 * vdot(wi, n)), wi);
+        *pdf = 1.0; *thr = m->albedo; *delta = 1;
+        return 1;
+    }
+    v3 t, b;
+    onb(n, &t, &b);
+    if (m->type == M_LAMBERT) {
+        double r = sqrt(u0), ph = 2.0 * OPI * u1;
+        double lz = sqrt(fmax(0.0, 1.0 - u0));
+        *wo = vadd(vadd(vmul(t, r * cos(ph)), vmul(b, r * sin(ph))), vmul(n, lz));
+    } else {
+        double a = m->alpha;
+        double tan2 = a * a * u0 / (1.0 - u0);
+        double ct = 1.0 / sqrt(1.0 + tan2), st = sqrt(fmax(0.0, 1.0 - ct * ct)), ph = 2.0 * OPI * u1;
+        v3 h = vadd(vadd(vmul(t, st * cos(ph)), vmul(b, st * sin(ph))), vmul(n, ct));
+        *wo = vsub(vmul(h, 2.0 * vdot(wi, h)), wi);
+    }
+    double co = vdot(n, *wo);
+    if (co <= 0.0) return 0;
+    *pdf = bsdf_pdf(m, n, wi, *wo);
+    double f = bsdf_f(m, n, wi, *wo);
+    if (!(*pdf > 0.0) || !(f > 0.0)) return 0;
+    *thr = f * co / *pdf;
+    return 1;
+}
+
+/* ============================================================================================
+ * scene geometry: world-space triangles (rigidly transformed per object), median-split BVH
+ * ==========================================================================================*/
+typedef struct { double lo[3], hi[3]; int left, right, start, count; } onode;
+typedef struct {
+    int nt, nobj, nmat;
+    double* tv;     /* nt*9 world corners */
+    int* tmat;      /* material per triangle */
+    omat* mats;
+    double* xf;     /* nobj*12, kept to decide whether two frames have identical geometry */
+    int nnodes;
+    onode* nodes;
+    int* prim;
+} ogeom;
+
+static const double* tri_v(const ogeom* g, int t) { return g->tv + 9 * (size_t)t; }
+
+static double* g_cent;    /* build-time scratch for the comparator (single-threaded build) */
+static int g_axis;
+static int cmp_prim(const void* a, const void* b) {
+    double ca = g_cent[3 * *(const int*)a + g_axis], cb = g_cent[3 * *(const int*)b + g_axis];
+    if (ca < cb) return -1;
+    if (ca > cb) return 1;
+    return (*(const int*)a) - (*(const int*)b);
+}
+
+static int bvh_build_rec(ogeom* g, double* cent, int start, int count) {
+    int id = g->nnodes++;
+    onode* nd = &g->nodes[id];
+    for (int k = 0; k < 3; ++k) { nd->lo[k] = 1e300; nd->hi[k] = -1e300; }
+    double clo[3] = {1e300, 1e300, 1e300}, chi[3] = {-1e300, -1e300, -1e300};
+    for (int i = start; i < start + count; ++i) {
+        const double* v = tri_v(g, g->prim[i]);
+        for (int c = 0; c < 3; ++c)
+            for (int k = 0; k < 3; ++k) {
+                if (v[3 * c + k] < nd->lo[k]) nd->lo[k] = v[3 * c + k];
+                if (v[3 * c + k] > nd->hi[k]) nd->hi[k] = v[3 * c + k];
+            }
+        for (int k = 0; k < 3; ++k) {
+            double c = cent[3 * g->prim[i] + k];
+            if (c < clo[k]) clo[k] = c;
+            if (c > chi[k]) chi[k] = c;
+        }
+    }
+    if (count <= 4) { nd->left = nd->right = -1; nd->start = start; nd->count = count; return id; }
+    int axis = 0;
+    for (int k = 1; k < 3; ++k) if (chi[k] - clo[k] > chi[axis] - clo[axis]) axis = k;
+    g_cent = cent; g_axis = axis;
+    qsort(g->prim + start, (size_t)count, sizeof(int), cmp_prim);
+    int half = count / 2;
+    int l = bvh_build_rec(g, cent, start, half);
+    int r = bvh_build_rec(g, cent, start + half, count - half);
+    nd = &g->nodes[id];
+    nd->left = l; nd->right = r; nd->start = start; nd->count = 0;
+    return id;
+}
+
+/* verts: object-local vertices; xforms: nobj row-major 3x4 object-to-world matrices */
+ogeom* or_geom_create(const double* verts, int nv, const uint32_t* tris, int nt, const uint32_t* tri_obj,
+                      const uint32_t* obj_mat, int nobj, const double* mats, int nmat, const double* xforms) {
+    (void)nv;
+    ogeom* g = (ogeom*)calloc(1, sizeof(ogeom));
+    g->nt = nt; g->nobj = nobj; g->nmat = nmat;
+    g->tv = (double*)malloc(sizeof(double) * 9 * (size_t)(nt > 0 ? nt : 1));
+    g->tmat = (int*)malloc(sizeof(int) * (size_t)(nt > 0 ? nt : 1));
+    g->mats = (omat*)malloc(sizeof(omat) * (size_t)(nmat > 0 ? nmat : 1));
+    g->xf = (double*)malloc(sizeof(double) * 12 * (size_t)(nobj > 0 ? nobj : 1));
+    memcpy(g->xf, xforms, sizeof(double) * 12 * (size_t)nobj);
+    for (int m = 0; m < nmat; ++m) { g->mats[m].type = (int)mats[3 * m]; g->mats[m].albedo = mats[3 * m + 1]; g->mats[m].alpha = mats[3 * m + 2]; }
+    for (int t = 0; t < nt; ++t) {
+        const double* M = xforms + 12 * (size_t)tri_obj[t];
+        for (int c = 0; c < 3; ++c) {
+            const double* p = verts + 3 * (size_t)tris[3 * t + c];
+            for (int r = 0; r < 3; ++r)
+                g->tv[9 * (size_t)t + 3 * c + r] = M[4 * r] * p[0] + M[4 * r + 1] * p[1] + M[4 * r + 2] * p[2] + M[4 * r + 3];
+        }
+        g->tmat[t] = (int)obj_mat[tri_obj[t]];
+    }
+    g->nodes = (onode*)malloc(sizeof(onode) * (size_t)(2 * (nt > 0 ? nt : 1)));
+    g->prim = (int*)malloc(sizeof(int) * (size_t)(nt > 0 ? nt : 1));
+    double* cent = (double*)malloc(sizeof(double) * 3 * (size_t)(nt > 0 ? nt : 1));
+    for (int t = 0; t < nt; ++t) {
+        g->prim[t] = t;
+        const double* v = tri_v(g, t);
+        for (int k = 0; k < 3; ++k) cent[3 * t + k] = (v[k] + v[3 + k] + v[6 + k]) / 3.0;
+    }
+    g->nnodes = 0;
+    if (nt > 0) bvh_build_rec(g, cent, 0, nt);
+    free(cent);
+    return g;
+}
+
+void or_geom_destroy(ogeom* g) {
+    if (!g) return;
+    free(g->tv); free(g->tmat); free(g->mats); free(g->xf); free(g->nodes); free(g->prim); free(g);
+}
+
+/* Moller-Trumbore ray/triangle test (Moller, Trumbore 1997); t in (tmin, tmax) */
+static int tri_hit(const double* v, v3 o, v3 d, double tmin, double tmax, double* t, double* b1, double* b2) {
+    v3 v0 = vload(v), e1 = vsub(vload(v + 3), v0), e2 = vsub(vload(v + 6), v0);
+    v3 pv = vcross(d, e2);
+    double det = vdot(e1, pv);
+    if (fabs(det) < 1e-14) return 0;
+    double inv = 1.0 / det;
+    v3 tv = vsub(o, v0);
+    double u = vdot(tv, pv) * inv;
+    if (u < 0.0 || u > 1.0) return 0;
+    v3 qv = vcross(tv, e1);
+    double w = vdot(d, qv) * inv;
+    if (w < 0.0 || u + w > 1.0) return 0;
+    double tt = vdot(e2, qv) * inv;
+    if (!(tt > tmin && tt < tmax)) return 0;
+    *t = tt; *b1 = u; *b2 = w;
+    return 1;
+}
+
+static int box_hit(const onode* nd, v3 o, v3 invd, double tmax) {
+    double t0 = 0.0, t1 = tmax;
+    double oo[3] = {o.x, o.y, o.z}, id[3] = {invd.x, invd.y, invd.z};
+    for (int k = 0; k < 3; ++k) {
+        double a = (nd->lo[k] - oo[k]) * id[k], b = (nd->hi[k] - oo[k]) * id[k];
+        if (a > b) { double s = a; a = b; b = s; }
+        if (a > t0) t0 = a;
+        if (b < t1) t1 = b;
+        if (t0 > t1) return 0;
+    }
+    return 1;
+}
+
+/* closest hit along o + t d, t in (0, tmax); any_hit = 1 returns on the first hit */
+static int trace(const ogeom* g, v3 o, v3 d, double tmax, int any_hit, int* tri, double* b1, double* b2, double* tout) {
+    if (g->nnodes == 0) return 0;
+    v3 invd = V(1.0 / d.x, 1.0 / d.y, 1.0 / d.z);
+    int stack[128], sp = 0, found = 0;
+    double best = tmax;
+    stack[sp++] = 0;
+    while (sp) {
+        const onode* nd = &g->nodes[stack[--sp]];
+        if (!box_hit(nd, o, invd, best)) continue;
+        if (nd->left < 0) {
+            for (int i = nd->start; i < nd->start + nd->count; ++i) {
+                double t, u, w;
+                if (tri_hit(tri_v(g, g->prim[i]), o, d, 0.0, best, &t, &u, &w)) {
+                    best = t; *tri = g->prim[i]; *b1 = u; *b2 = w; found = 1;
+                    if (any_hit) { *tout = t; return 1; }
+                }
+            }
+        } else {
+            stack[sp++] = nd->left;
+            stack[sp++] = nd->right;
+        }
+    }
+    if (found) *tout = best;
+    return found;
+}
+
+int or_geom_intersect(const ogeom* g, const double* o, const double* d, double tmax, int brute,
+                      double* t, int* tri, double* b1, double* b2) {
+    v3 oo = vload(o), dd = vload(d);
+    if (!brute) return trace(g, oo, dd, tmax, 0, tri, b1, b2, t);
+    int found = 0;
+    double best = tmax;
+    for (int i = 0; i < g->nt; ++i) {
+        double tt, u, w;
+        if (tri_hit(tri_v(g, i), oo, dd, 0.0, best, &tt, &u, &w)) { best = tt; *tri = i; *b1 = u; *b2 = w; found = 1; }
+    }
+    if (found) *t = best;
+    return found;
+}
+
+/* ============================================================================================
+ * surface points, ray offsets, visibility
+ * ==========================================================================================*/
+typedef struct { int tri; double b1, b2; v3 p, n; int mat; } osurf;
+
+static osurf surf_at(const ogeom* g, int tri, double b1, double b2) {
+    osurf s;
+    const double* v = tri_v(g, tri);
+    v3 v0 = vload(v), e1 = vsub(vload(v + 3), v0), e2 = vsub(vload(v + 6), v0);
+    s.tri = tri; s.b1 = b1; s.b2 = b2;
+    s.p = vadd(v0, vadd(vmul(e1, b1), vmul(e2, b2)));
+    s.n = vnorm(vcross(e1, e2));
+    s.mat = g->tmat[tri];
+    return s;
+}
+
+/* offset a surface point along its normal toward the side of direction dir */
+static v3 offset_point(v3 p, v3 n, v3 dir, double eps) {
+    return vdot(n, dir) >= 0.0 ? vadd(p, vmul(n, eps)) : vsub(p, vmul(n, eps));
+}
+
+/* closest hit of a ray leaving surface point s in unit direction d */
+static int trace_from(const ogeom* g, const osurf* s, v3 d, double eps, osurf* hit, double* t) {
+    v3 o = offset_point(s->p, s->n, d, eps);
+    int tri; double b1, b2;
+    if (!trace(g, o, d, 1e30, 0, &tri, &b1, &b2, t)) return 0;
+    *hit = surf_at(g, tri, b1, b2);
+    return 1;
+}
+
+/* mutual visibility of surface point a and either surface point b (bn != NULL) or point b */
+static int visible(const ogeom* g, v3 a, v3 an, v3 b, const v3* bn, double eps) {
+    v3 ao = offset_point(a, an, vsub(b, a), eps);
+    v3 bo = bn ? offset_point(b, *bn, vsub(a, b), eps) : b;
+    v3 d = vsub(bo, ao);
+    double dist = vlen(d);
+    if (!(dist > 0)) return 1;
+    d = vmul(d, 1.0 / dist);
+    int tri; double b1, b2, t;
+    return !trace(g, ao, d, dist, 1, &tri, &b1, &b2, &t);
+}
+
+/* ============================================================================================
+ * sensors, emitters, domains
+ * ==========================================================================================*/
+typedef struct {
+    int mode, W, H;
+    double pos[3], fwd[3], up[3], fov_y;
+    double wall_o[3], wall_u[3], wall_v[3];
+} osensor;
+typedef struct { int type; double pos[3], dir[3], power; } oemitter;
+typedef struct {
+    int depth, n_cand, n_spatial, radius, n_spatial_iters, temporal;
+    double m_cap;
+    int newton_max_iter;
+    double newton_tol_frac, jac_max, d_min, ray_eps;
+    uint32_t flags;
+} oparams;
+enum { F_DIRECT = 1, F_NAIVE = 2 };
+
+/* Sec. 5 "Light Source": a point light (direct NEE) or a collimated laser whose spot acts as a
+ * secondary emitter I(w) = P f_s(spot; to laser, w) |cos| (a light ray is traced first). */
+typedef struct {
+    int kind;        /* 0 none, 1 point, 2 spot */
+    v3 pos;
+    double I;        /* point intensity or laser power */
+    osurf s;         /* spot surface */
+    v3 to_origin;    /* unit direction from the spot toward the laser */
+    double emit_len; /* laser origin -> spot length, part of the optical path */
+} olight;
+
+static int light_same(const olight* a, const olight* b) {
+    if (a->kind != b->kind) return 0;
+    if (a->kind == 0) return 1;
+    if (a->pos.x != b->pos.x || a->pos.y != b->pos.y || a->pos.z != b->pos.z || a->I != b->I) return 0;
+    if (a->kind == 2) {
+        if (a->s.tri != b->s.tri || a->s.b1 != b->s.b1 || a->s.b2 != b->s.b2) return 0;
+        if (a->to_origin.x != b->to_origin.x || a->to_origin.y != b->to_origin.y || a->to_origin.z != b->to_origin.z) return 0;
+        if (a->emit_len != b->emit_len) return 0;
+    }
+    return 1;
+}
+
+/* intensity leaving the light toward point x, the light position and the extra path length */
+static double light_I(const ogeom* g, const olight* L, v3 x, v3* lpos) {
+    *lpos = L->kind == 2 ? L->s.p : L->pos;
+    if (L->kind == 1) return L->I;
+    if (L->kind == 2) {
+        v3 w = vnorm(vsub(x, L->s.p));
+        double f = bsdf_f(&g->mats[L->s.mat], L->s.n, L->to_origin, w);
+        return L->I * f * fabs(vdot(L->s.n, w));
+    }
+    return 0.0;
+}
+
+/* light factor of a path ending at vertex x: I_e(x) |cos_x| / d^2 (no BSDF, no visibility) */
+static double light_term(const ogeom* g, const olight* L, const osurf* x, v3* wl, double* seg) {
+    v3 lp;
+    double I = light_I(g, L, x->p, &lp);
+    v3 d = vsub(lp, x->p);
+    double dist = vlen(d);
+    if (!(dist > 0) || !(I > 0)) return 0.0;
+    *wl = vmul(d, 1.0 / dist);
+    *seg = dist + (L->kind == 2 ? L->emit_len : 0.0);
+    return I * fabs(vdot(x->n, *wl)) / (dist * dist);
+}
+
+static int light_visible(const ogeom* g, const olight* L, const osurf* x, double eps) {
+    if (L->kind == 2) return visible(g, x->p, x->n, L->s.p, &L->s.n, eps);
+    return visible(g, x->p, x->n, L->pos, NULL, eps);
+}
+
+/* G-buffer entry of one pixel */
+typedef struct { int valid; osurf s; double t; } ogb;
+
+/* A reservoir's domain: one pixel of one frame (Sec. 3.2: each pixel/time step is its own
+ * integration domain Omega_i with its own target function). */
+typedef struct {
+    const ogeom* g;
+    int valid;
+    v3 x0;          /* camera / device position */
+    osurf y1;       /* primary hit */
+    double o;       /* offset subtracted from L before gating (confocal convention) */
+    double L0, dL;  /* gate [L0, L0 + dL) of the gated variable tau = L - o */
+    olight light;
+} odomain;
+
+/* ============================================================================================
+ * path records (the reservoir sample, Sec. 5 "Reservoir Implementation": the reservoir follows
+ * ReSTIR PT and additionally stores the vertex after the reconnection vertex, with the
+ * reconnection radiance attached to that next vertex)
+ * ==========================================================================================*/
+#define MAXD 8
+typedef struct {
+    int valid;
+    double W, M, phat, tau;
+    uint32_t key_px, key_frame;
+    int tree, k, r;
+    int cls[MAXD];       /* classes of x_1..x_{r-1} (index 1..) */
+    v3 xprev;            /* x_{r-1}, world position in this record's own frame */
+    double pdf_pre;      /* product of area pdfs of x_2..x_{r-1} */
+    int p_tri; double p_b1, p_b2;
+    int ns;              /* number of suffix vertices x_{r+1}..x_k (k - r) */
+    int s_tri[4]; double s_b1[4], s_b2[4];
+    double Lsuf;         /* cached radiance factor of the suffix beyond x_{r+1} */
+} orec;
+
+static const orec EMPTY_REC = {0};
+
+/* ============================================================================================
+ * path-length derivatives (Sec. 4.3 "Gradient and Hessian Evaluation")
+ *   L(p) = |p1 - p| + |p2 - p|
+ *   grad_p L = -(d1 + d2) = -s,  hess_p L = A = (I - d1 d1^T)/|p1 - p| + (I - d2 d2^T)/|p2 - p|
+ *   grad_xi L = J^T(-s),  hess_xi L = J^T A J + Q with Q = 0 (exact on planar triangles)
+ * ==========================================================================================*/
+typedef struct { v3 o, t, b; } oframe2;     /* p(xi) = o + xi1 t + xi2 b, orthonormal t, b */
+
+static oframe2 tri_frame(const ogeom* g, int tri) {
+    const double* v = tri_v(g, tri);
+    v3 v0 = vload(v), e1 = vsub(vload(v + 3), v0), e2 = vsub(vload(v + 6), v0);
+    oframe2 f;
+    f.o = v0;
+    f.t = vnorm(e1);
+    v3 n = vnorm(vcross(e1, e2));
+    f.b = vcross(n, f.t);
+    return f;
+}
+static v3 frame_point(const oframe2* f, const double xi[2]) {
+    return vadd(f->o, vadd(vmul(f->t, xi[0]), vmul(f->b, xi[1])));
+}
+
+/* L, grad (2) and symmetric Hessian (h11, h12, h22) of L(xi) for neighbours p1, p2 */
+void or_length_derivs(const double* p1d, const double* p2d, const double* od, const double* td, const double* bd,
+                      const double xi[2], double* Lout, double g[2], double h[3]) {
+    oframe2 f = {vload(od), vload(td), vload(bd)};
+    v3 p1 = vload(p1d), p2 = vload(p2d), p = frame_point(&f, xi);
+    v3 a1 = vsub(p1, p), a2 = vsub(p2, p);
+    double l1 = vlen(a1), l2 = vlen(a2);
+    v3 d1 = vmul(a1, 1.0 / l1), d2 = vmul(a2, 1.0 / l2);
+    v3 s = vadd(d1, d2);
+    *Lout = l1 + l2;
+    g[0] = -vdot(f.t, s);
+    g[1] = -vdot(f.b, s);
+    /* J^T A J with A u = (u - d1 (d1.u))/l1 + (u - d2 (d2.u))/l2 */
+    double tt = (1.0 - vdot(d1, f.t) * vdot(d1, f.t)) / l1 + (1.0 - vdot(d2, f.t) * vdot(d2, f.t)) / l2;
+    double tb = (0.0 - vdot(d1, f.t) * vdot(d1, f.b)) / l1 + (0.0 - vdot(d2, f.t) * vdot(d2, f.b)) / l2;
+    double bb = (1.0 - vdot(d1, f.b) * vdot(d1, f.b)) / l1 + (1.0 - vdot(d2, f.b) * vdot(d2, f.b)) / l2;
+    h[0] = tt; h[1] = tb; h[2] = bb;
+}
+
+typedef struct {
+    v3 p1x, p2x; oframe2 fx;   /* base path: neighbours and frame of the reconnection vertex */
+    v3 p1y, p2y; oframe2 fy;   /* offset path: neighbours and frame (same triangle, its frame) */
+} onewton;
+
+static void derivs(v3 p1, v3 p2, const oframe2* f, const double xi[2], double* L, double g[2], double h[3]) {
+    double a[3] = {p1.x, p1.y, p1.z}, b[3] = {p2.x, p2.y, p2.z};
+    double o[3] = {f->o.x, f->o.y, f->o.z}, t[3] = {f->t.x, f->t.y, f->t.z}, bb[3] = {f->b.x, f->b.y, f->b.z};
+    or_length_derivs(a, b, o, t, bb, xi, L, g, h);
+}
+
+/* Sec. 4.3: F(xi, xi') = [ L_y(xi') - L_x(xi) - delta ; (R m)^T (xi' - xi) ],
+ * m = (grad L_x(xi) + grad L_y(xi')) / 2, R the 90-degree rotation (x, y) -> (-y, x).
+ * Each gradient is taken on its own path (base path x for xi, offset path y for xi'), which
+ * is what makes the gauge symmetric under swapping the two paths (the reversibility argument
+ * of the average-gradient gauge). */
+static void eval_F(const onewton* N, const double xi[2], double delta, const double xp[2],
+                   double gx[2], double hx[3], double Lx, double F[2], double gy[2], double hy[3], double m[2]) {
+    double Ly;
+    derivs(N->p1y, N->p2y, &N->fy, xp, &Ly, gy, hy);
+    m[0] = 0.5 * (gx[0] + gy[0]);
+    m[1] = 0.5 * (gx[1] + gy[1]);
+    double Rm[2] = {-m[1], m[0]};
+    F[0] = Ly - Lx - delta;
+    F[1] = Rm[0] * (xp[0] - xi[0]) + Rm[1] * (xp[1] - xi[1]);
+}
+
+/* rows of dF/dxi' (A) and dF/dxi (Bm), by differentiating F directly:
+ *   dF1/dxi' = grad L_y(xi'),  dF2/dxi' = R m - 0.5 H_y(xi') R (xi' - xi)
+ *   dF1/dxi  = -grad L_x(xi),  dF2/dxi  = -(R m + 0.5 H_x(xi) R (xi' - xi))
+ * (the printed dF/dxi' second row carries +0.5; the derivative of the stated F, using
+ *  R^T = -R, carries -0.5 -- the sign used here, pinned by finite differences in the tests) */
+static void jac_F(const double xi[2], const double xp[2], const double gx[2], const double hx[3],
+                  const double gy[2], const double hy[3], const double m[2], double A[4], double Bm[4]) {
+    double Rm[2] = {-m[1], m[0]};
+    double dd[2] = {xp[0] - xi[0], xp[1] - xi[1]};
+    double Rd[2] = {-dd[1], dd[0]};
+    double HyRd[2] = {hy[0] * Rd[0] + hy[1] * Rd[1], hy[1] * Rd[0] + hy[2] * Rd[1]};
+    double HxRd[2] = {hx[0] * Rd[0] + hx[1] * Rd[1], hx[1] * Rd[0] + hx[2] * Rd[1]};
+    A[0] = gy[0]; A[1] = gy[1];
+    A[2] = Rm[0] - 0.5 * HyRd[0]; A[3] = Rm[1] - 0.5 * HyRd[1];
+    Bm[0] = -gx[0]; Bm[1] = -gx[1];
+    Bm[2] = -(Rm[0] + 0.5 * HxRd[0]); Bm[3] = -(Rm[1] + 0.5 * HxRd[1]);
+}
+
+/* Newton iteration of Sec. 4.3 with backtracking (step halved up to 4 times when |F|_inf does
+ * not decrease).  Stops when |F|_inf <= tol_stop or after max_iter iterations.
+ * Success: |F|_inf <= tol_succ.  Returns 1 on success; xp = xi', *jdet = |det(dxi'/dxi)| =
+ * |det(dF/dxi)| / |det(dF/dxi')| (implicit differentiation), *iters = iterations used. */
+static int newton_solve(const onewton* N, const double xi[2], double delta, int max_iter, double tol_stop,
+                        double tol_succ, double xp[2], double* jdet, int* iters) {
+    double Lx, gx[2], hx[3];
+    derivs(N->p1x, N->p2x, &N->fx, xi, &Lx, gx, hx);
+    xp[0] = xi[0]; xp[1] = xi[1];
+    double F[2], gy[2], hy[3], m[2];
+    eval_F(N, xi, delta, xp, gx, hx, Lx, F, gy, hy, m);
+    int it = 0;
+    while (it < max_iter) {
+        double nF = fmax(fabs(F[0]), fabs(F[1]));
+        if (nF <= tol_stop) break;
+        double A[4], Bm[4];
+        jac_F(xi, xp, gx, hx, gy, hy, m, A, Bm);
+        double det = A[0] * A[3] - A[1] * A[2];
+        if (!(fabs(det) > 1e-300)) break;
+        double step[2] = {-(A[3] * F[0] - A[1] * F[1]) / det, -(-A[2] * F[0] + A[0] * F[1]) / det};
+        double lam = 1.0;
+        int accepted = 0;
+        for (int ls = 0; ls < 5; ++ls) {
+            double cand[2] = {xp[0] + lam * step[0], xp[1] + lam * step[1]};
+            double Fc[2], gyc[2], hyc[3], mc[2];
+            eval_F(N, xi, delta, cand, gx, hx, Lx, Fc, gyc, hyc, mc);
+            if (fmax(fabs(Fc[0]), fabs(Fc[1])) < nF) {
+                xp[0] = cand[0]; xp[1] = cand[1];
+                F[0] = Fc[0]; F[1] = Fc[1];
+                gy[0] = gyc[0]; gy[1] = gyc[1]; hy[0] = hyc[0]; hy[1] = hyc[1]; hy[2] = hyc[2];
+                m[0] = mc[0]; m[1] = mc[1];
+                accepted = 1;
+                break;
+            }
+            lam *= 0.5;
+        }
+        if (!accepted) break;
+        ++it;
+    }
+    *iters = it;
+    if (!(fmax(fabs(F[0]), fabs(F[1])) <= tol_succ)) return 0;
+    double A[4], Bm[4];
+    jac_F(xi, xp, gx, hx, gy, hy, m, A, Bm);
+    double dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
+    if (!(fabs(dA) > 0)) return 0;
+    *jdet = fabs(dB / dA);
+    return isfinite(*jdet);
+}
+
+/* exported for the pins: solve on explicit geometry (both frames given) */
+int or_newton(const double* p1x, const double* p2x, const double* fxo, const double* fxt, const double* fxb,
+              const double* p1y, const double* p2y, const double* fyo, const double* fyt, const double* fyb,
+              const double xi[2], double delta, int max_iter, double tol_stop, double tol_succ,
+              double xp[2], double* jdet, int* iters, double F_out[2]) {
+    onewton N;
+    N.p1x = vload(p1x); N.p2x = vload(p2x); N.fx.o = vload(fxo); N.fx.t = vload(fxt); N.fx.b = vload(fxb);
+    N.p1y = vload(p1y); N.p2y = vload(p2y); N.fy.o = vload(fyo); N.fy.t = vload(fyt); N.fy.b = vload(fyb);
+    *jdet = 0; *iters = 0;
+    int ok = newton_solve(&N, xi, delta, max_iter, tol_stop, tol_succ, xp, jdet, iters);
+    double Lx, gx[2], hx[3], gy[2], hy[3], m[2];
+    derivs(N.p1x, N.p2x, &N.fx, xi, &Lx, gx, hx);
+    eval_F(&N, xi, delta, xp, gx, hx, Lx, F_out, gy, hy, m);
+    return ok;
+}
+
+/* barycentrics (b1, b2) of in-plane coordinates xi on triangle tri */
+static void xi_to_bary(const ogeom* g, int tri, const oframe2* f, const double xi[2], double* b1, double* b2) {
+    const double* v = tri_v(g, tri);
+    v3 v0 = vload(v), e1 = vsub(vload(v + 3), v0), e2 = vsub(vload(v + 6), v0);
+    double e1t = vdot(e1, f->t), e2t = vdot(e2, f->t), e2b = vdot(e2, f->b);
+    *b2 = xi[1] / e2b;
+    *b1 = (xi[0] - *b2 * e2t) / e1t;
+}
+static void point_to_xi(const oframe2* f, v3 p, double xi[2]) {
+    v3 d = vsub(p, f->o);
+    xi[0] = vdot(d, f->t);
+    xi[1] = vdot(d, f->b);
+}
+
+/* ============================================================================================
+ * path evaluation helpers
+ * ==========================================================================================*/
+/* geometry term between two surface points (no visibility) */
+static double Gterm(const osurf* a, const osurf* b) {
+    v3 d = vsub(b->p, a->p);
+    double d2 = vdot(d, d);
+    if (!(d2 > 0)) return 0.0;
+    v3 w = vmul(d, 1.0 / sqrt(d2));
+    return fabs(vdot(a->n, w)) * fabs(vdot(b->n, w)) / d2;
+}
+static v3 dir_to(v3 from, v3 to) { return vnorm(vsub(to, from)); }
+
+/* reconnectability of vertex i on a path x_1..x_k (Sec. 4.1: reconnect at the first
+ * consecutive diffuse vertex; the path-length perturbation also re-evaluates the BSDF of the
+ * vertex after it, so that vertex must be rough as well, or be the light) */
+static int connectable(const int* cls, const v3* pos, int k, int i, double dmin) {
+    if (cls[i - 1] != C_ROUGH || cls[i] != C_ROUGH) return 0;
+    if (vlen(vsub(pos[i - 1], pos[i])) <= dmin) return 0;
+    if (i < k) {
+        if (cls[i + 1] != C_ROUGH) return 0;
+        if (vlen(vsub(pos[i], pos[i + 1])) <= dmin) return 0;
+    }
+    return 1;
+}
+static int find_r(const int* cls, const v3* pos, int k, double dmin) {
+    for (int i = 2; i <= k; ++i) if (connectable(cls, pos, k, i, dmin)) return i;
+    return 0;
+}
+
+/* ============================================================================================
+ * stats
+ * ==========================================================================================*/
+typedef struct { double newton_calls, newton_iters, newton_ok, shift_calls, shift_ok; } ostats;
+static void stat_add(double* a, double v) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+    *a += v;
+}
+
+/* ============================================================================================
+ * the shift map (Sec. 4.1-4.3): hybrid shift (random replay up to x_{r-1}, reconnection at
+ * p = x_r) followed by the path-length-aware perturbation of p, from domain Dj (the record's
+ * own) to domain Di.  Returns 1 on success with the offset path record, its target p_hat in Di
+ * and the Jacobian |dS/dx|.
+ * ==========================================================================================*/
+static int shift_rec(const orec* x, const odomain* Dj, const odomain* Di, const oparams* P, uint64_t seed,
+                     int geom_static, orec* y, double* phat_out, double* jac_out, ostats* st) {
+    if (!x->valid || x->r < 2 || !Di->valid || !Dj->valid) return 0;
+    const ogeom* gi = Di->g;
+    const ogeom* gj = Dj->g;
+    const int k = x->k, r = x->r;
+    const double eps = P->ray_eps;
+    if (st) stat_add(&st->shift_calls, 1);
+
+    /* (1) random replay of x_2..x_{r-1} from y_1 with the base path's random numbers */
+    osurf yv[MAXD + 1];
+    v3 ypos[MAXD + 2];
+    int ycls[MAXD + 2];
+    yv[1] = Di->y1;
+    double plen = vlen(vsub(Di->x0, yv[1].p));
+    double fpre = 1.0, pdf_pre_y = 1.0;
+    for (int j = 1; j <= r - 2; ++j) {
+        uint32_t u[4];
+        rng4(seed, x->key_px, x->key_frame, ((uint32_t)x->tree << 8) | (uint32_t)j, P_BSDF, u);
+        v3 wi = dir_to(yv[j].p, j == 1 ? Di->x0 : yv[j - 1].p);
+        const omat* m = &gi->mats[yv[j].mat];
+        if (mat_class(m) != x->cls[j]) return 0;
+        v3 wo; double pdf, thr; int delta;
+        if (!bsdf_sample(m, yv[j].n, wi, u01(u[0]), u01(u[1]), &wo, &pdf, &thr, &delta)) return 0;
+        double t;
+        if (!trace_from(gi, &yv[j], wo, eps, &yv[j + 1], &t)) return 0;
+        double seg = vlen(vsub(yv[j + 1].p, yv[j].p));
+        plen += seg;
+        if (delta) {
+            fpre *= m->albedo;
+        } else {
+            fpre *= bsdf_f(m, yv[j].n, wi, wo) * Gterm(&yv[j], &yv[j + 1]);
+            pdf_pre_y *= pdf * fabs(vdot(yv[j + 1].n, wo)) / (seg * seg);
+        }
+    }
+    if (mat_class(&gi->mats[yv[r - 1].mat]) != x->cls[r - 1]) return 0;
+
+    /* (2) suffix x_{r+1}..x_k and the light, evaluated in the target domain */
+    osurf sv[5];
+    for (int q = 0; q < x->ns; ++q) sv[q] = surf_at(gi, x->s_tri[q], x->s_b1[q], x->s_b2[q]);
+    const olight* Li = &Di->light;
+    if (Li->kind == 0) return 0;
+    v3 lpos_i = Li->kind == 2 ? Li->s.p : Li->pos;
+    double emit_i = Li->kind == 2 ? Li->emit_len : 0.0;
+    double slen = 0.0;
+    for (int q = 0; q + 1 < x->ns; ++q) slen += vlen(vsub(sv[q].p, sv[q + 1].p));
+    if (x->ns > 0) slen += vlen(vsub(sv[x->ns - 1].p, lpos_i)) + emit_i;
+    else slen += emit_i;
+    v3 p2y = x->ns > 0 ? sv[0].p : lpos_i;
+
+    /* (3) base-path quantities in the record's own frame */
+    oframe2 fx = tri_frame(gj, x->p_tri);
+    osurf pbase = surf_at(gj, x->p_tri, x->p_b1, x->p_b2);
+    v3 p2x;
+    if (x->ns > 0) p2x = surf_at(gj, x->s_tri[0], x->s_b1[0], x->s_b2[0]).p;
+    else p2x = Dj->light.kind == 2 ? Dj->light.s.p : Dj->light.pos;
+    double xi[2];
+    point_to_xi(&fx, pbase.p, xi);
+
+    /* (4) Newton solve for xi' (eq. path_length_constraint: L(y') = L(x) + delta, with delta
+     * chosen so the sample keeps its position inside the gate of the target domain) */
+    onewton N;
+    N.p1x = x->xprev; N.p2x = p2x; N.fx = fx;
+    N.p1y = yv[r - 1].p; N.p2y = p2y; N.fy = tri_frame(gi, x->p_tri);
+    double Lx_seg = vlen(vsub(x->xprev, pbase.p)) + vlen(vsub(p2x, pbase.p));
+    double ell = x->tau - Dj->L0 + Di->L0 + Di->o - plen - slen;   /* target for L_y(xi') */
+    double delta = ell - Lx_seg;
+    double xp[2], jnewton = 1.0;
+    int iters = 0;
+    if (P->flags & F_NAIVE) {
+        xp[0] = xi[0]; xp[1] = xi[1];
+    } else {
+        double tol_stop = 1e-6 * fabs(x->tau + Di->o + Di->L0 - Dj->L0);
+        double tol_succ = P->newton_tol_frac * Di->dL;
+        int ok = newton_solve(&N, xi, delta, P->newton_max_iter, tol_stop, tol_succ, xp, &jnewton, &iters);
+        if (st) { stat_add(&st->newton_calls, 1); stat_add(&st->newton_iters, iters); if (ok) stat_add(&st->newton_ok, 1); }
+        if (!ok) return 0;
+        if (!(jnewton >= 1.0 / P->jac_max && jnewton <= P->jac_max)) return 0;
+    }
+    double nb1, nb2;
+    xi_to_bary(gi, x->p_tri, &N.fy, xp, &nb1, &nb2);
+    if (!(nb1 >= 0.0 && nb2 >= 0.0 && nb1 + nb2 <= 1.0)) return 0;
+    osurf pp = surf_at(gi, x->p_tri, nb1, nb2);
+
+    /* (5) the offset path must reconnect at the same index (bijectivity of the hybrid shift) */
+    {
+        int cls[MAXD + 2];
+        v3 pos[MAXD + 2];
+        for (int j = 1; j <= r - 1; ++j) { cls[j] = mat_class(&gi->mats[yv[j].mat]); pos[j] = yv[j].p; }
+        cls[r] = mat_class(&gi->mats[pp.mat]); pos[r] = pp.p;
+        for (int q = 0; q < x->ns; ++q) { cls[r + 1 + q] = mat_class(&gi->mats[sv[q].mat]); pos[r + 1 + q] = sv[q].p; }
+        if (find_r(cls, pos, k, P->d_min) != r) return 0;
+        (void)ycls; (void)ypos;
+    }
+
+    /* (6) visibility of the two reconnection segments */
+    if (!visible(gi, yv[r - 1].p, yv[r - 1].n, pp.p, &pp.n, eps)) return 0;
+    if (x->ns > 0) { if (!visible(gi, pp.p, pp.n, sv[0].p, &sv[0].n, eps)) return 0; }
+    else if (!light_visible(gi, Li, &pp, eps)) return 0;
+
+    /* (7) target function of the offset path in domain Di */
+    v3 wprev = dir_to(yv[r - 1].p, r - 1 == 1 ? Di->x0 : yv[r - 2].p);
+    double f = fpre;
+    f *= bsdf_f(&gi->mats[yv[r - 1].mat], yv[r - 1].n, wprev, dir_to(yv[r - 1].p, pp.p));
+    f *= Gterm(&yv[r - 1], &pp);
+    double Lsuf_i = x->Lsuf;
+    if (x->ns == 0) {
+        v3 wl; double seg;
+        double lt = light_term(gi, Li, &pp, &wl, &seg);
+        f *= bsdf_f(&gi->mats[pp.mat], pp.n, dir_to(pp.p, yv[r - 1].p), wl) * lt;
+    } else {
+        f *= bsdf_f(&gi->mats[pp.mat], pp.n, dir_to(pp.p, yv[r - 1].p), dir_to(pp.p, sv[0].p));
+        f *= Gterm(&pp, &sv[0]);
+        v3 wnext;
+        if (x->ns > 1) wnext = dir_to(sv[0].p, sv[1].p);
+        else wnext = dir_to(sv[0].p, lpos_i);
+        f *= bsdf_f(&gi->mats[sv[0].mat], sv[0].n, dir_to(sv[0].p, pp.p), wnext);
+        int cache_ok = geom_static && light_same(&Dj->light, Li);
+        if (!cache_ok) {
+            /* Sec. 5: the reconnection information is re-evaluated when the scene or the light
+             * differs between the two domains */
+            double Ls = 1.0;
+            for (int q = 1; q < x->ns; ++q) {
+                const omat* mq = &gi->mats[sv[q].mat];
+                double gg = mat_class(&gi->mats[sv[q - 1].mat]) == C_DELTA ? 1.0 : Gterm(&sv[q - 1], &sv[q]);
+                if (mat_class(mq) == C_DELTA) {
+                    if (!geom_static) return 0;
+                    Ls *= gg * mq->albedo;
+                } else {
+                    v3 wn = q + 1 < x->ns ? dir_to(sv[q].p, sv[q + 1].p) : dir_to(sv[q].p, lpos_i);
+                    Ls *= gg * bsdf_f(mq, sv[q].n, dir_to(sv[q].p, sv[q - 1].p), wn);
+                }
+                if (!visible(gi, sv[q - 1].p, sv[q - 1].n, sv[q].p, &sv[q].n, eps)) return 0;
+            }
+            v3 wl; double seg;
+            Ls *= light_term(gi, Li, &sv[x->ns - 1], &wl, &seg);
+            if (!light_visible(gi, Li, &sv[x->ns - 1], eps)) return 0;
+            Lsuf_i = Ls;
+        }
+        f *= Lsuf_i;
+    }
+    double Lnew = plen + vlen(vsub(yv[r - 1].p, pp.p)) + vlen(vsub(pp.p, p2y)) + slen;
+    double tau = Lnew - Di->o;
+    if (!(tau >= Di->L0 && tau < Di->L0 + Di->dL)) return 0;
+    if (!(f > 0) || !isfinite(f)) return 0;
+
+    /* (8) Jacobian: replay pdf ratios (area measure) times the Newton determinant; the frame
+     * factor sqrt(det J'^T J') / sqrt(det J^T J) is 1 for the orthonormal in-plane frames */
+    double jac = (x->pdf_pre / pdf_pre_y) * jnewton;
+    if (!(jac > 0) || !isfinite(jac)) return 0;
+
+    *y = *x;
+    y->tau = tau;
+    y->xprev = yv[r - 1].p;
+    y->pdf_pre = pdf_pre_y;
+    y->p_b1 = nb1; y->p_b2 = nb2;
+    y->Lsuf = Lsuf_i;
+    y->phat = f;
+    *phat_out = f;
+    *jac_out = jac;
+    if (st) stat_add(&st->shift_ok, 1);
+    return 1;
+}
+
+/* ============================================================================================
+ * frame state
+ * ==========================================================================================*/
+typedef struct {
+    const ogeom* g;
+    osensor s; oemitter e;
+    double L0, dL; int B;
+    uint32_t frame;
+    olight laser;          /* resolved laser spot (emitter type 1) */
+    ogb* gb;               /* W*H */
+    orec* res;             /* W*H*Bn */
+    double* M;             /* W*H confidence per pixel, shared by all bins */
+    uint8_t* ok;           /* W*H : computed and untainted */
+} oframe;
+
+typedef struct {
+    int W, H, Bn;
+    int has_prev;
+    int cur;
+    oframe fr[2];
+    ostats st;
+} oview;
+
+oview* or_view_create(int W, int H, int B) {
+    oview* v = (oview*)calloc(1, sizeof(oview));
+    v->W = W; v->H = H; v->Bn = B > 0 ? B : 1;
+    for (int i = 0; i < 2; ++i) {
+        v->fr[i].gb = (ogb*)calloc((size_t)W * H, sizeof(ogb));
+        v->fr[i].res = (orec*)calloc((size_t)W * H * v->Bn, sizeof(orec));
+        v->fr[i].ok = (uint8_t*)calloc((size_t)W * H, 1);
+        v->fr[i].M = (double*)calloc((size_t)W * H, sizeof(double));
+    }
+    return v;
+}
+void or_view_destroy(oview* v) {
+    if (!v) return;
+    for (int i = 0; i < 2; ++i) { free(v->fr[i].gb); free(v->fr[i].res); free(v->fr[i].ok); free(v->fr[i].M); }
+    free(v);
+}
+void or_view_reset(oview* v) { v->has_prev = 0; }
+void or_view_stats(const oview* v, double out[5]) {
+    out[0] = v->st.newton_calls; out[1] = v->st.newton_iters; out[2] = v->st.newton_ok;
+    out[3] = v->st.shift_calls; out[4] = v->st.shift_ok;
+}
+
+/* pinhole / confocal primary ray of pixel (ix, iy) with sub-pixel jitter (u0, u1) */
+static void primary_ray(const osensor* s, int ix, int iy, double u0, double u1, v3* o, v3* d) {
+    *o = vload(s->pos);
+    if (s->mode == 1) {
+        v3 w = vadd(vload(s->wall_o), vadd(vmul(vload(s->wall_u), (ix + 0.5) / s->W), vmul(vload(s->wall_v), (iy + 0.5) / s->H)));
+        *d = vnorm(vsub(w, *o));
+        return;
+    }
+    v3 f = vnorm(vload(s->fwd));
+    v3 rt = vnorm(vcross(f, vload(s->up)));
+    v3 up = vcross(rt, f);
+    double th = tan(0.5 * s->fov_y), asp = (double)s->W / (double)s->H;
+    double sx = (2.0 * (ix + u0) / s->W - 1.0) * th * asp;
+    double sy = (1.0 - 2.0 * (iy + u1) / s->H) * th;
+    *d = vnorm(vadd(f, vadd(vmul(rt, sx), vmul(up, sy))));
+}
+
+/* pixel of a world point in a pinhole sensor (back-projection for temporal reuse) */
+static int project(const osensor* s, v3 p, int* ix, int* iy) {
+    v3 f = vnorm(vload(s->fwd));
+    v3 rt = vnorm(vcross(f, vload(s->up)));
+    v3 up = vcross(rt, f);
+    v3 d = vsub(p, vload(s->pos));
+    double z = vdot(d, f);
+    if (!(z > 0)) return 0;
+    double th = tan(0.5 * s->fov_y), asp = (double)s->W / (double)s->H;
+    double sx = vdot(d, rt) / z / (th * asp), sy = vdot(d, up) / z / th;
+    double fx = (sx + 1.0) * 0.5 * s->W, fy = (1.0 - sy) * 0.5 * s->H;
+    if (!(fx >= 0 && fy >= 0)) return 0;
+    int x = (int)floor(fx), y = (int)floor(fy);
+    if (x >= s->W || y >= s->H) return 0;
+    *ix = x; *iy = y;
+    return 1;
+}
+
+static odomain make_domain(const oframe* F, int pix, const oparams* P, double L0, double dL) {
+    odomain D;
+    memset(&D, 0, sizeof(D));
+    D.g = F->g;
+    D.x0 = vload(F->s.pos);
+    const ogb* gb = &F->gb[pix];
+    D.valid = gb->valid;
+    D.L0 = L0; D.dL = dL;
+    if (!gb->valid) return D;
+    D.y1 = gb->s;
+    D.o = F->s.mode == 1 ? 2.0 * gb->t : 0.0;
+    if (F->e.type == 0) { D.light.kind = 1; D.light.pos = vload(F->e.pos); D.light.I = F->e.power; }
+    else if (F->e.type == 1) D.light = F->laser;
+    else {
+        D.light.kind = 2; D.light.s = gb->s; D.light.I = F->e.power;
+        D.light.to_origin = vnorm(vsub(vload(F->e.pos), gb->s.p));
+        D.light.emit_len = vlen(vsub(vload(F->e.pos), gb->s.p));
+        D.light.pos = gb->s.p;
+    }
+    (void)P;
+    return D;
+}
+
+/* ============================================================================================
+ * initial candidates (Sec. 3.2 RIS, stage (1); Sec. 4.5 per-bin deposit for transients)
+ * Path trees: BSDF-sampled paths with NEE to the delta light at every vertex; the candidate of
+ * length k is the NEE path ending at x_k.  w = (1/N) p_hat / p with p_hat = f 1[tau in gate].
+ * ==========================================================================================*/
+typedef struct { osurf v[MAXD + 2]; double pdfA[MAXD + 2]; int cls[MAXD + 2]; } opathbuf;
+
+/* f(x) in area measure of the path x_1..x_k with NEE to the light (no visibility) */
+static double path_f(const ogeom* g, const odomain* D, const opathbuf* pb, int k) {
+    double f = 1.0;
+    for (int j = 1; j <= k; ++j) {
+        const omat* m = &g->mats[pb->v[j].mat];
+        v3 wi = dir_to(pb->v[j].p, j == 1 ? D->x0 : pb->v[j - 1].p);
+        if (j < k) {
+            if (mat_class(m) == C_DELTA) f *= m->albedo;
+            else f *= bsdf_f(m, pb->v[j].n, wi, dir_to(pb->v[j].p, pb->v[j + 1].p)) * Gterm(&pb->v[j], &pb->v[j + 1]);
+        } else {
+            v3 wl; double seg;
+            double lt = light_term(g, &D->light, &pb->v[k], &wl, &seg);
+            f *= bsdf_f(m, pb->v[k].n, wi, wl) * lt;
+        }
+    }
+    return f;
+}
+
+static void build_rec(const ogeom* g, const odomain* D, const opathbuf* pb, int k, int tree, uint32_t px,
+                      uint32_t frame, double tau, const oparams* P, orec* R) {
+    memset(R, 0, sizeof(*R));
+    R->valid = 1;
+    R->tau = tau;
+    R->key_px = px; R->key_frame = frame; R->tree = tree; R->k = k;
+    R->phat = path_f(g, D, pb, k);
+    v3 pos[MAXD + 2];
+    for (int j = 1; j <= k; ++j) pos[j] = pb->v[j].p;
+    int r = find_r(pb->cls, pos, k, P->d_min);
+    R->r = r;
+    if (r == 0) return;
+    for (int j = 1; j < r; ++j) R->cls[j] = pb->cls[j];
+    R->xprev = pb->v[r - 1].p;
+    R->pdf_pre = 1.0;
+    for (int j = 2; j <= r - 1; ++j) R->pdf_pre *= pb->pdfA[j];
+    R->p_tri = pb->v[r].tri; R->p_b1 = pb->v[r].b1; R->p_b2 = pb->v[r].b2;
+    R->ns = k - r;
+    for (int q = 0; q < R->ns; ++q) { R->s_tri[q] = pb->v[r + 1 + q].tri; R->s_b1[q] = pb->v[r + 1 + q].b1; R->s_b2[q] = pb->v[r + 1 + q].b2; }
+    /* suffix factor beyond x_{r+1}: prod_{j=r+2..k} G(x_{j-1}, x_j) f_s(x_j) * light term */
+    if (R->ns > 0) {
+        double Ls = 1.0;
+        for (int j = r + 2; j <= k; ++j) {
+            const omat* m = &g->mats[pb->v[j].mat];
+            const omat* mprev = &g->mats[pb->v[j - 1].mat];
+            double gg = mat_class(mprev) == C_DELTA ? 1.0 : Gterm(&pb->v[j - 1], &pb->v[j]);
+            if (mat_class(m) == C_DELTA) { Ls *= gg * m->albedo; continue; }
+            v3 wi = dir_to(pb->v[j].p, pb->v[j - 1].p);
+            v3 wo;
+            if (j < k) wo = dir_to(pb->v[j].p, pb->v[j + 1].p);
+            else { double seg; light_term(g, &D->light, &pb->v[k], &wo, &seg); }
+            Ls *= gg * bsdf_f(m, pb->v[j].n, wi, wo);
+        }
+        v3 wl; double seg;
+        Ls *= light_term(g, &D->light, &pb->v[k], &wl, &seg);
+        R->Lsuf = Ls;
+    }
+}
+
+/* One path tree; calls the candidate sink for every NEE path of length k in [kmin, depth].
+ * The sink receives (k, c = f/p without the gate, tau). */
+typedef void (*cand_sink)(void* ctx, int k, double c, double tau, const opathbuf* pb);
+
+static void trace_tree(const ogeom* g, const odomain* D, const oparams* P, uint64_t seed, uint32_t px, uint32_t frame,
+                       int tree, int gated_lo_hi, double glo, double ghi, cand_sink sink, void* ctx) {
+    opathbuf pb;
+    pb.v[1] = D->y1;
+    pb.cls[1] = mat_class(&g->mats[D->y1.mat]);
+    pb.pdfA[1] = 1.0;
+    double len = vlen(vsub(D->x0, D->y1.p));
+    double beta = 1.0;
+    int kmin = (P->flags & F_DIRECT) ? 1 : 2;
+    for (int d = 1; d <= P->depth; ++d) {
+        const osurf* x = &pb.v[d];
+        const omat* m = &g->mats[x->mat];
+        v3 wi = dir_to(x->p, d == 1 ? D->x0 : pb.v[d - 1].p);
+        if (d >= kmin && mat_class(m) != C_DELTA) {
+            v3 wl; double seg;
+            double lt = light_term(g, &D->light, x, &wl, &seg);
+            double fs = lt > 0 ? bsdf_f(m, x->n, wi, wl) : 0.0;
+            if (fs > 0) {
+                double tau = len + seg - D->o;
+                int in = gated_lo_hi ? (tau >= glo && tau < ghi) : 1;
+                if (in && light_visible(g, &D->light, x, P->ray_eps)) sink(ctx, d, beta * fs * lt, tau, &pb);
+            }
+        }
+        if (d == P->depth) break;
+        uint32_t u[4];
+        rng4(seed, px, frame, ((uint32_t)tree << 8) | (uint32_t)d, P_BSDF, u);
+        v3 wo; double pdf, thr; int delta;
+        if (!bsdf_sample(m, x->n, wi, u01(u[0]), u01(u[1]), &wo, &pdf, &thr, &delta)) break;
+        double t;
+        if (!trace_from(g, x, wo, P->ray_eps, &pb.v[d + 1], &t)) break;
+        double seg = vlen(vsub(pb.v[d + 1].p, x->p));
+        pb.cls[d + 1] = mat_class(&g->mats[pb.v[d + 1].mat]);
+        pb.pdfA[d + 1] = delta ? 1.0 : pdf * fabs(vdot(pb.v[d + 1].n, wo)) / (seg * seg);
+        len += seg;
+        beta *= thr;
+    }
+}
+
+typedef struct {
+    const ogeom* g; const odomain* D; const oparams* P; uint64_t seed; uint32_t px, frame; int tree;
+    int B; double t0, w;         /* transient: B bins of width w from t0; gated: B = 0 */
+    orec* out;                   /* gated: 1 record; transient: B records */
+    double* S;                   /* running weight sums (1 or B) */
+    double invN;
+} oinit_ctx;
+
+static void init_sink(void* vctx, int k, double c, double tau, const opathbuf* pb) {
+    oinit_ctx* C = (oinit_ctx*)vctx;
+    double w = C->invN * c;
+    if (!(w > 0)) return;
+    int b = 0;
+    if (C->B > 0) {
+        double fb = floor((tau - C->t0) / C->w);
+        if (!(fb >= 0 && fb < C->B)) return;
+        b = (int)fb;
+    }
+    uint32_t u[4];
+    rng4(C->seed, C->px, C->frame, ((uint32_t)C->tree << 8) | (uint32_t)k, P_RIS, u);
+    C->S[b] += w;
+    if (u01(u[0]) * C->S[b] < w)
+        build_rec(C->g, C->D, pb, k, C->tree, C->px, C->frame, tau, C->P, &C->out[b]);
+}
+
+/* ============================================================================================
+ * GRIS merge (Sec. 3.2: w_i = m_i(y_i) p_hat(y_i) W_i |dS_i/dx_i|, generalized balance
+ * heuristic m_i(y_i) = M_i p_hat_{<-i}(y_i) / sum_j M_j p_hat_{<-j}(y_i), with the denominator
+ * evaluated at the same y_i for every j, and p_hat_{<-i}(y_i) = p_hat_i(x_i) / |dS_i/dx_i|).
+ * Slot 0 is the canonical sample.  Selection streams over the slots with one uniform each.
+ * ==========================================================================================*/
+typedef struct { const odomain* D; const orec* x; double M; int geom_static; } oslot;
+
+static double merge(const oslot* sl, int n, const oparams* P, uint64_t seed, uint32_t px, uint32_t frame, int pass,
+                    int bin, orec* out, ostats* st) {
+    orec y[16];
+    double py[16], J[16], w[16];
+    int ok[16];
+    double Msum = 0.0;
+    for (int s = 0; s < n; ++s) {
+        Msum += sl[s].M;
+        ok[s] = 0; w[s] = 0.0;
+        if (!sl[s].x->valid) continue;
+        if (s == 0) { y[0] = *sl[0].x; py[0] = sl[0].x->phat; J[0] = 1.0; ok[0] = py[0] > 0; continue; }
+        ok[s] = shift_rec(sl[s].x, sl[s].D, sl[0].D, P, seed, sl[s].geom_static, &y[s], &py[s], &J[s], st);
+    }
+    for (int s = 0; s < n; ++s) {
+        if (!ok[s]) continue;
+        double num = s == 0 ? sl[0].M * py[0] : sl[s].M * sl[s].x->phat / J[s];
+        double den = sl[0].M * py[s];
+        for (int j = 1; j < n; ++j) {
+            if (j == s) { den += sl[s].M * sl[s].x->phat / J[s]; continue; }
+            orec tmp; double pj, Jj;
+            if (shift_rec(&y[s], sl[0].D, sl[j].D, P, seed, sl[j].geom_static, &tmp, &pj, &Jj, NULL))
+                den += sl[j].M * pj * Jj;
+        }
+        double m = den > 0 ? num / den : 0.0;
+        w[s] = m * py[s] * sl[s].x->W * J[s];
+        if (!(w[s] > 0) || !isfinite(w[s])) w[s] = 0.0;
+    }
+    double S = 0.0;
+    int sel = -1;
+    for (int s = 0; s < n; ++s) {
+        if (!(w[s] > 0)) continue;
+        uint32_t u[4];
+        rng4(seed, px, frame, ((uint32_t)pass << 8) | (uint32_t)s, P_MERGE | ((uint32_t)bin << 8), u);
+        S += w[s];
+        if (u01(u[0]) * S < w[s]) sel = s;
+    }
+    if (sel >= 0) {
+        *out = y[sel];
+        out->valid = 1;
+        out->W = S / py[sel];
+    } else {
+        *out = EMPTY_REC;
+    }
+    out->M = Msum;
+    return S;
+}
+
+/* spatial neighbour of slot s in pass `pass`: uniform integer offset in the disk of radius R
+ * (excluding the centre) by rejection from the square, up to 8 tries; -1 if none / off-image */
+static int pick_neighbor(uint64_t seed, uint32_t px, uint32_t frame, int pass, int slot, int W, int H, int R) {
+    int ix = (int)(px % (uint32_t)W), iy = (int)(px / (uint32_t)W);
+    uint32_t side = 2u * (uint32_t)R + 1u;
+    for (int a = 0; a < 4; ++a) {
+        uint32_t u[4];
+        rng4(seed, px, frame, ((uint32_t)pass << 8) | (uint32_t)slot, P_NEIGHBOR | ((uint32_t)a << 8), u);
+        for (int h = 0; h < 2; ++h) {
+            int dx = (int)(u[2 * h] % side) - R, dy = (int)(u[2 * h + 1] % side) - R;
+            if (dx * dx + dy * dy > R * R || (dx == 0 && dy == 0)) continue;
+            int nx = ix + dx, ny = iy + dy;
+            if (nx < 0 || ny < 0 || nx >= W || ny >= H) return -1;
+            return ny * W + nx;
+        }
+    }
+    return -1;
+}
+
+static int xf_equal(const ogeom* a, const ogeom* b) {
+    if (a == b) return 1;
+    if (a->nobj != b->nobj) return 0;
+    return memcmp(a->xf, b->xf, sizeof(double) * 12 * (size_t)a->nobj) == 0;
+}
+
+/* ============================================================================================
+ * one frame of the pipeline (Sec. 3.2 stages (1)-(4)).  Gated when B == 0 (gate [L0, L0+dL)),
+ * transient with B bins [L0 + b dL, L0 + (b+1) dL) otherwise.  Pixels outside the region of
+ * interest [x0, x1) x [y0, y1) are not computed; any result that depends on one of them is
+ * marked not-ok in ok_out.
+ * ==========================================================================================*/
+int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* e, double L0, double dL, int B,
+                    const oparams* P, uint64_t seed, uint32_t frame, int x0, int y0, int x1, int y1,
+                    double* out, uint8_t* ok_out, int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    const int W = v->W, H = v->H;
+    const int Bn = B > 0 ? B : 1;
+    if (Bn != v->Bn || s->W != W || s->H != H) return -1;
+    if (P->depth < 1 || P->depth > MAXD - 2 || P->n_cand < 1 || P->n_spatial > 15) return -1;
+    int prev = v->cur;
+    int cur = v->has_prev ? 1 - v->cur : v->cur;
+    oframe* F = &v->fr[cur];
+    oframe* Fp = &v->fr[prev];
+    const int have_prev = v->has_prev && P->temporal;
+    F->g = g; F->s = *s; F->e = *e; F->L0 = L0; F->dL = dL; F->B = B; F->frame = frame;
+    memset(&F->laser, 0, sizeof(F->laser));
+    if (e->type == 1) {
+        osurf dummy; memset(&dummy, 0, sizeof(dummy));
+        v3 o = vload(e->pos), d = vnorm(vload(e->dir));
+        int tri; double b1, b2, t;
+        if (trace(g, o, d, 1e30, 0, &tri, &b1, &b2, &t)) {
+            F->laser.kind = 2; F->laser.s = surf_at(g, tri, b1, b2); F->laser.I = e->power;
+            F->laser.to_origin = vmul(d, -1.0); F->laser.emit_len = t; F->laser.pos = F->laser.s.p;
+        }
+    }
+    const int geom_static = have_prev ? xf_equal(Fp->g, g) : 1;
+
+    /* G-buffer */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int pix = 0; pix < W * H; ++pix) {
+        int ix = pix % W, iy = pix / W;
+        F->ok[pix] = (ix >= x0 && ix < x1 && iy >= y0 && iy < y1);
+        F->gb[pix].valid = 0;
+        if (!F->ok[pix]) continue;
+        uint32_t u[4];
+        rng4(seed, (uint32_t)pix, frame, 0, P_JITTER, u);
+        v3 o, d;
+        primary_ray(s, ix, iy, u01(u[0]), u01(u[1]), &o, &d);
+        int tri; double b1, b2, t;
+        if (trace(g, o, d, 1e30, 0, &tri, &b1, &b2, &t)) {
+            F->gb[pix].valid = 1;
+            F->gb[pix].s = surf_at(g, tri, b1, b2);
+            F->gb[pix].t = vlen(vsub(F->gb[pix].s.p, o));
+        }
+    }
+
+    /* initial candidates */
+    orec* R0 = (orec*)calloc((size_t)W * H * Bn, sizeof(orec));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int pix = 0; pix < W * H; ++pix) {
+        orec* rr = &R0[(size_t)pix * Bn];
+        for (int b = 0; b < Bn; ++b) { rr[b] = EMPTY_REC; rr[b].M = P->n_cand; }
+        if (!F->ok[pix] || !F->gb[pix].valid) continue;
+        odomain D = make_domain(F, pix, P, L0, dL);
+        double* S = (double*)calloc((size_t)Bn, sizeof(double));
+        oinit_ctx C = {g, &D, P, seed, (uint32_t)pix, frame, 0, B, L0, dL, rr, S, 1.0 / P->n_cand};
+        for (int t = 0; t < P->n_cand; ++t) {
+            C.tree = t;
+            if (B > 0) trace_tree(g, &D, P, seed, (uint32_t)pix, frame, t, 1, L0, L0 + B * dL, init_sink, &C);
+            else trace_tree(g, &D, P, seed, (uint32_t)pix, frame, t, 1, L0, L0 + dL, init_sink, &C);
+        }
+        for (int b = 0; b < Bn; ++b) {
+            if (rr[b].valid && rr[b].phat > 0) { rr[b].W = S[b] / rr[b].phat; rr[b].M = P->n_cand; }
+            else { rr[b] = EMPTY_REC; rr[b].M = P->n_cand; }
+        }
+        free(S);
+    }
+
+    /* bin gate of bin b */
+#define GATE_L0(b) (B > 0 ? L0 + (b) * dL : L0)
+    /* temporal reuse (stage (2)): previous reservoir at the back-projected pixel */
+    /* Confidence weights are per pixel and shared by every bin: they follow from the reuse
+     * structure alone (N after the initial stage, then sums of capped inputs), never from whether
+     * a reservoir happens to hold a sample -- a sample-dependent M would bias the generalized
+     * balance heuristic. */
+    double* Mc = (double*)malloc(sizeof(double) * (size_t)W * H);
+    for (int pix = 0; pix < W * H; ++pix) Mc[pix] = P->n_cand;
+    orec* R1 = R0;
+    uint8_t* ok1 = (uint8_t*)malloc((size_t)W * H);
+    memcpy(ok1, F->ok, (size_t)W * H);
+    if (have_prev) {
+        double* Mt = (double*)malloc(sizeof(double) * (size_t)W * H);
+        R1 = (orec*)calloc((size_t)W * H * Bn, sizeof(orec));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+        for (int pix = 0; pix < W * H; ++pix) {
+            orec* dst = &R1[(size_t)pix * Bn];
+            memcpy(dst, &R0[(size_t)pix * Bn], sizeof(orec) * Bn);
+            Mt[pix] = Mc[pix];
+            if (!F->ok[pix] || !F->gb[pix].valid) continue;
+            int q = -1;
+            if (s->mode == 1) q = pix;
+            else {
+                osurf sp = surf_at(Fp->g, F->gb[pix].s.tri, F->gb[pix].s.b1, F->gb[pix].s.b2);
+                int qx, qy;
+                if (project(&Fp->s, sp.p, &qx, &qy)) q = qy * W + qx;
+            }
+            if (q < 0) continue;
+            if (!Fp->ok[q]) { ok1[pix] = 0; continue; }
+            double Mprev = fmin(Fp->M[q], P->m_cap);
+            Mt[pix] = Mc[pix] + Mprev;
+            for (int b = 0; b < Bn; ++b) {
+                const orec* xc = &R0[(size_t)pix * Bn + b];
+                const orec* xt = &Fp->res[(size_t)q * Bn + b];
+                if (B > 0 && !xc->valid && !xt->valid) continue;
+                odomain Dc = make_domain(F, pix, P, GATE_L0(b), dL);
+                odomain Dt = make_domain(Fp, q, P, Fp->B > 0 ? Fp->L0 + b * Fp->dL : Fp->L0, Fp->dL);
+                oslot sl[2];
+                sl[0].D = &Dc; sl[0].x = xc; sl[0].M = Mc[pix]; sl[0].geom_static = 1;
+                sl[1].D = &Dt; sl[1].x = xt; sl[1].M = Mprev; sl[1].geom_static = geom_static;
+                merge(sl, 2, P, seed, (uint32_t)pix, frame, 0, b, &dst[b], &v->st);
+            }
+        }
+        free(Mc);
+        Mc = Mt;
+    }
+
+    /* spatial reuse (stage (3)) */
+    orec* Rcur = R1;
+    uint8_t* okc = ok1;
+    for (int it = 0; it < P->n_spatial_iters && P->n_spatial > 0; ++it) {
+        orec* Rn = (orec*)calloc((size_t)W * H * Bn, sizeof(orec));
+        uint8_t* okn = (uint8_t*)malloc((size_t)W * H);
+        double* Mn = (double*)malloc(sizeof(double) * (size_t)W * H);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+        for (int pix = 0; pix < W * H; ++pix) {
+            orec* dst = &Rn[(size_t)pix * Bn];
+            memcpy(dst, &Rcur[(size_t)pix * Bn], sizeof(orec) * Bn);
+            okn[pix] = okc[pix];
+            Mn[pix] = Mc[pix];
+            if (!okc[pix] || !F->gb[pix].valid) continue;
+            int nb[16], nn = 0;
+            for (int sI = 1; sI <= P->n_spatial; ++sI) {
+                int q = pick_neighbor(seed, (uint32_t)pix, frame, 1 + it, sI, W, H, P->radius);
+                if (q < 0) continue;
+                if (!okc[q]) { okn[pix] = 0; }
+                nb[nn++] = q;
+            }
+            if (!okn[pix]) continue;
+            for (int a = 0; a < nn; ++a) Mn[pix] += fmin(Mc[nb[a]], P->m_cap);
+            for (int b = 0; b < Bn; ++b) {
+                const orec* xc = &Rcur[(size_t)pix * Bn + b];
+                if (B > 0) {
+                    int any = xc->valid;
+                    for (int a = 0; a < nn; ++a) any |= Rcur[(size_t)nb[a] * Bn + b].valid;
+                    if (!any) continue;
+                }
+                odomain Dc = make_domain(F, pix, P, GATE_L0(b), dL);
+                odomain Dn[16];
+                oslot sl[16];
+                sl[0].D = &Dc; sl[0].x = xc; sl[0].M = Mc[pix]; sl[0].geom_static = 1;
+                for (int a = 0; a < nn; ++a) {
+                    Dn[a] = make_domain(F, nb[a], P, GATE_L0(b), dL);
+                    sl[1 + a].D = &Dn[a];
+                    sl[1 + a].x = &Rcur[(size_t)nb[a] * Bn + b];
+                    sl[1 + a].M = fmin(Mc[nb[a]], P->m_cap);
+                    sl[1 + a].geom_static = 1;
+                }
+                merge(sl, 1 + nn, P, seed, (uint32_t)pix, frame, 1 + it, b, &dst[b], &v->st);
+            }
+        }
+        if (Rcur != R0 && Rcur != R1) free(Rcur);
+        if (okc != ok1) free(okc);
+        Rcur = Rn;
+        okc = okn;
+        free(Mc);
+        Mc = Mn;
+    }
+
+    /* final shading (stage (4)): f(y) W_y (= the merge's weight sum for a box gate) */
+    for (int pix = 0; pix < W * H; ++pix) {
+        for (int b = 0; b < Bn; ++b) {
+            const orec* rr = &Rcur[(size_t)pix * Bn + b];
+            out[(size_t)pix * Bn + b] = (rr->valid && okc[pix]) ? rr->phat * rr->W : 0.0;
+        }
+        ok_out[pix] = okc[pix];
+    }
+    memcpy(F->res, Rcur, sizeof(orec) * (size_t)W * H * Bn);
+    memcpy(F->ok, okc, (size_t)W * H);
+    memcpy(F->M, Mc, sizeof(double) * (size_t)W * H);
+    free(Mc);
+    if (Rcur != R0) free(Rcur);
+    if (R1 != R0 && R1 != Rcur) free(R1);
+    free(R0);
+    if (okc != ok1) free(okc);
+    free(ok1);
+    v->cur = cur;
+    v->has_prev = 1;
+    return 0;
+#undef GATE_L0
+}
+
+/* ============================================================================================
+ * plain path tracing (the "path tracing without any reuse" comparison of Sec. 6): spp paths
+ * per pixel, each with its own jitter, every NEE path of length kmin..depth splatted with
+ * f / p into the gate (B == 0) or its bin.
+ * ==========================================================================================*/
+typedef struct { int B; double t0, w; double* acc; double scale; } opt_ctx;
+static void pt_sink(void* vctx, int k, double c, double tau, const opathbuf* pb) {
+    (void)k; (void)pb;
+    opt_ctx* C = (opt_ctx*)vctx;
+    if (C->B > 0) {
+        double fb = floor((tau - C->t0) / C->w);
+        if (!(fb >= 0 && fb < C->B)) return;
+        C->acc[(int)fb] += C->scale * c;
+    } else {
+        C->acc[0] += C->scale * c;
+    }
+}
+
+int or_render_pt(const ogeom* g, const osensor* s, const oemitter* e, double L0, double dL, int B, const oparams* P,
+                 uint64_t seed, uint32_t frame, int spp, int x0, int y0, int x1, int y1, double* out, int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    const int W = s->W, H = s->H, Bn = B > 0 ? B : 1;
+    olight laser; memset(&laser, 0, sizeof(laser));
+    if (e->type == 1) {
+        v3 o = vload(e->pos), d = vnorm(vload(e->dir));
+        int tri; double b1, b2, t;
+        if (trace(g, o, d, 1e30, 0, &tri, &b1, &b2, &t)) {
+            laser.kind = 2; laser.s = surf_at(g, tri, b1, b2); laser.I = e->power;
+            laser.to_origin = vmul(d, -1.0); laser.emit_len = t; laser.pos = laser.s.p;
+        }
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int pix = 0; pix < W * H; ++pix) {
+        double* acc = &out[(size_t)pix * Bn];
+        for (int b = 0; b < Bn; ++b) acc[b] = 0.0;
+        int ix = pix % W, iy = pix / W;
+        if (!(ix >= x0 && ix < x1 && iy >= y0 && iy < y1)) continue;
+        for (int sm = 0; sm < spp; ++sm) {
+            uint32_t u[4];
+            rng4(seed, (uint32_t)pix, frame, (uint32_t)sm, P_JITTER, u);
+            v3 o, d;
+            primary_ray(s, ix, iy, u01(u[0]), u01(u[1]), &o, &d);
+            int tri; double b1, b2, t;
+            if (!trace(g, o, d, 1e30, 0, &tri, &b1, &b2, &t)) continue;
+            odomain D; memset(&D, 0, sizeof(D));
+            D.g = g; D.valid = 1; D.x0 = o; D.y1 = surf_at(g, tri, b1, b2);
+            double tp = vlen(vsub(D.y1.p, o));
+            D.o = s->mode == 1 ? 2.0 * tp : 0.0;
+            if (e->type == 0) { D.light.kind = 1; D.light.pos = vload(e->pos); D.light.I = e->power; }
+            else if (e->type == 1) D.light = laser;
+            else {
+                D.light.kind = 2; D.light.s = D.y1; D.light.I = e->power;
+                D.light.to_origin = vnorm(vsub(vload(e->pos), D.y1.p));
+                D.light.emit_len = vlen(vsub(vload(e->pos), D.y1.p)); D.light.pos = D.y1.p;
+            }
+            opt_ctx C = {B, L0, dL, acc, 1.0 / spp};
+            if (B > 0) trace_tree(g, &D, P, seed, (uint32_t)pix, frame, sm, 1, L0, L0 + B * dL, pt_sink, &C);
+            else trace_tree(g, &D, P, seed, (uint32_t)pix, frame, sm, 1, L0, L0 + dL, pt_sink, &C);
+        }
+    }
+    return 0;
+}
+
+/* ============================================================================================
+ * small exported hooks for the pins (tests call these on explicit inputs)
+ * ==========================================================================================*/
+/* streaming selection over n weights with uniforms u: returns the selected index or -1 */
+int or_stream_select(const double* w, const double* u, int n, double* S_out) {
+    double S = 0.0;
+    int sel = -1;
+    for (int i = 0; i < n; ++i) {
+        if (!(w[i] > 0)) continue;
+        S += w[i];
+        if (u[i] * S < w[i]) sel = i;
+    }
+    *S_out = S;
+    return sel;
+}
+
+/* BSDF sampling hook: returns ok; wo[3], pdf, thr */
+int or_bsdf_sample(int type, double albedo, double alpha, const double* n, const double* wi, double u0, double u1,
+                   double* wo, double* pdf, double* thr) {
+    omat m = {type, albedo, alpha};
+    v3 w; int delta;
+    int ok = bsdf_sample(&m, vload(n), vload(wi), u0, u1, &w, pdf, thr, &delta);
+    wo[0] = w.x; wo[1] = w.y; wo[2] = w.z;
+    return ok;
+}
+double or_bsdf_pdf(int type, double albedo, double alpha, const double* n, const double* wi, const double* wo) {
+    omat m = {type, albedo, alpha};
+    return bsdf_pdf(&m, vload(n), vload(wi), vload(wo));
+}
+
+/* read a stored reservoir (for record-level tests): fills W, M, phat, tau, k, r, valid */
+int or_view_reservoir(const oview* v, int pix, int b, double out[4], int iout[3]) {
+    const orec* r = &v->fr[v->cur].res[(size_t)pix * v->Bn + b];
+    out[0] = r->W; out[1] = r->M; out[2] = r->phat; out[3] = r->tau;
+    iout[0] = r->k; iout[1] = r->r; iout[2] = r->valid;
+    return 0;
+}
+
+/* exercise the full shift on a stored reservoir: shift the record of pixel `src` (current
+ * frame) into the domain of pixel `dst` and back.  Returns 1 if both succeed; outputs the
+ * forward and inverse Jacobians and the round-trip barycentric error. */
+int or_shift_roundtrip(const oview* v, const oparams* P, uint64_t seed, int src, int dst, double out[6]) {
+    const oframe* F = &v->fr[v->cur];
+    const orec* x = &F->res[(size_t)src * v->Bn];
+    odomain Ds = make_domain(F, src, P, F->L0, F->dL);
+    odomain Dd = make_domain(F, dst, P, F->L0, F->dL);
+    orec y, z;
+    double py, J, pz, Jz;
+    for (int i = 0; i < 6; ++i) out[i] = 0;
+    if (!shift_rec(x, &Ds, &Dd, P, seed, 1, &y, &py, &J, NULL)) return 0;
+    if (!shift_rec(&y, &Dd, &Ds, P, seed, 1, &z, &pz, &Jz, NULL)) return -1;
+    out[0] = J; out[1] = Jz; out[2] = fabs(z.p_b1 - x->p_b1) + fabs(z.p_b2 - x->p_b2);
+    out[3] = py; out[4] = pz; out[5] = x->phat;
+    return 1;
+}
