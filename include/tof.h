@@ -1,0 +1,171 @@
+/*
+ * tof.h -- C ABI of the GB300 ToF ReSTIR library (libtof.so).
+ *
+ * The library renders time-gated images and transient histograms with the ToF ReSTIR method
+ * (Kim, Jarosz, Pediredla, "ToF ReSTIR: Time-of-Flight Rendering with Spatio-temporal Reservoir
+ * Resampling", ACM TOG 45(4), 2026): per-pixel RIS reservoirs of light paths under an optical
+ * path-length gate, initial path-tree candidates, temporal and spatial reuse through the
+ * path-length-aware shift mapping (Newton solve on the reconnection vertex with the
+ * average-gradient gauge and its Jacobian), and the splat into a gated image or a transient
+ * histogram.  Every stage runs as hand-written CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions for every entry point
+ *   - Return value: TOF_OK (0) or a negative tof_status; never aborts.  tof_last_error() gives a
+ *     one-line message for the last failure on that context.
+ *   - Host pointers (const T*) are read during the call only and stay owned by the caller.
+ *   - Device pointers (out_*_dev) are caller-owned device memory on the context's GPU, written
+ *     asynchronously on `stream` (a cudaStream_t passed as void*, NULL = legacy default stream);
+ *     they are valid once the stream has been synchronised.
+ *   - Scenes and views are library-owned device state named by integer handles; they persist
+ *     until destroyed (or the context is destroyed).
+ *   - Units are metres, optical path length uses c = 1 and refractive index 1 (Sec. 3.1).
+ *   - Thread safety: one context per host thread, or external locking.
+ */
+#ifndef TOF_H
+#define TOF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tof_status;
+#define TOF_OK 0
+#define TOF_EINVAL (-1)   /* invalid argument (sizes, ids, NaN geometry, unsupported option) */
+#define TOF_ENOMEM (-2)   /* device allocation failed */
+#define TOF_EBUDGET (-3)  /* request exceeds the context's HBM budget */
+#define TOF_ECUDA (-4)    /* a CUDA runtime call or kernel launch failed */
+#define TOF_ETIMEOUT (-5) /* a bounded device-side wait gave up */
+#define TOF_ESTATE (-6)   /* call out of order (e.g. render before tof_bvh_build) */
+
+typedef struct tof_ctx tof_ctx;
+typedef int32_t tof_scene;
+typedef int32_t tof_view;
+
+/* material types (Sec. 6: diffuse, glossy and specular surfaces) */
+#define TOF_LAMBERT 0
+#define TOF_GGX 1      /* Walter et al. 2007 microfacet, Smith G1*G1, Fresnel = albedo */
+#define TOF_MIRROR 2   /* perfect specular reflection */
+typedef struct {
+    int32_t type;
+    float albedo;      /* in [0, 1] */
+    float alpha;       /* GGX roughness; ignored otherwise */
+} tof_material;
+
+/* sensor: pinhole camera, or confocal scan of a planar wall (one pixel per scanned wall point;
+ * the path length of each pixel is measured minus 2 |device - wall point|) */
+#define TOF_PINHOLE 0
+#define TOF_CONFOCAL 1
+typedef struct {
+    int32_t mode;
+    int32_t W, H;
+    float pos[3];      /* camera / device position */
+    float fwd[3], up[3];
+    float fov_y;       /* radians, pinhole only */
+    float wall_o[3], wall_u[3], wall_v[3]; /* confocal only: wall point (i,j) = o + (i+.5)/W u + (j+.5)/H v */
+} tof_sensor;
+
+/* emitters (Sec. 5 "Light Source"): delta lights only */
+#define TOF_EMIT_POINT 0     /* isotropic point light of intensity `power` at pos, NEE */
+#define TOF_EMIT_LASER 1     /* collimated laser from pos along dir; its first hit is a secondary
+                                emitter of intensity power * f_s * |cos| (a light ray is traced first) */
+#define TOF_EMIT_CONFOCAL 2  /* laser from pos aimed at each pixel's own primary hit */
+typedef struct {
+    int32_t type;
+    float pos[3];
+    float dir[3];
+    float power;
+} tof_emitter;
+
+/* gate [L0, L0 + dL) on tau = L - offset (Sec. 3.1 W_tau, a box; Sec. 6) */
+typedef struct { float L0, dL; } tof_gate;
+
+/* transient bins: bin b covers [t0 + b*width, t0 + (b+1)*width) (Sec. 3.1, Sec. 4.5) */
+typedef struct { float t0, width; int32_t B; } tof_bins;
+
+/* flags */
+#define TOF_FLAG_DIRECT 1u       /* include length-1 (direct) paths; the paper reports indirect only */
+#define TOF_FLAG_NAIVE_SHIFT 2u  /* hybrid shift without the path-length correction (comparison) */
+
+/* reuse / sampling parameters (Sec. 6: path depth, candidates, neighbours, radius, M-cap;
+ * Newton tolerance 1 % of the gate width with at most 5 iterations) */
+typedef struct {
+    int32_t depth;            /* max surface vertices per path, 1..5 */
+    int32_t n_cand;           /* path trees per pixel, 1..64 */
+    int32_t n_spatial;        /* spatial neighbours per pass, 0..8 */
+    int32_t radius;           /* spatial radius in pixels, 1..255 */
+    int32_t n_spatial_iters;  /* spatial passes, 0..4 */
+    int32_t temporal;         /* temporal reuse on (1) / off (0) */
+    float m_cap;              /* confidence cap for reused reservoirs */
+    int32_t newton_max_iter;  /* <= 16 */
+    float newton_tol_frac;    /* success threshold as a fraction of the gate width */
+    float jac_max;            /* reject shifts with |det| outside [1/jac_max, jac_max] */
+    float d_min;              /* minimum reconnection segment length */
+    float ray_eps;            /* ray origin offset along the normal */
+    uint32_t flags;
+} tof_params;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
+ * context may allocate for scenes and views (0 = no bound); allocations beyond it fail with
+ * TOF_EBUDGET. */
+tof_status tof_create(tof_ctx** out, int device, uint64_t hbm_budget_bytes);
+tof_status tof_destroy(tof_ctx* ctx);
+const char* tof_last_error(tof_ctx* ctx);
+/* bytes currently allocated on the device by this context */
+uint64_t tof_device_bytes(tof_ctx* ctx);
+
+/* Upload a triangle scene (Sec. 6 scenes: triangle meshes with per-object materials).
+ *   verts  [nv*3] object-local positions; tris [nt*3] vertex indices; tri_object [nt] object id;
+ *   mats [nmat]; object_material [nobj] material id per object.
+ * Host arrays are copied.  Rejects non-finite vertices, out-of-range ids, nt == 0. */
+tof_status tof_scene_upload(tof_ctx* ctx, const float* verts, uint32_t nv, const uint32_t* tris, uint32_t nt,
+                            const uint32_t* tri_object, const tof_material* mats, uint32_t nmat,
+                            const uint32_t* object_material, uint32_t nobj, tof_scene* out);
+tof_status tof_scene_destroy(tof_ctx* ctx, tof_scene scene);
+
+/* Place the objects (row-major 3x4 object-to-world matrices, nobj*12 floats) and build the GPU
+ * LBVH (Morton codes, radix sort, hierarchy, bounds).  refit_only = 1 keeps the hierarchy and
+ * refits bounds after rigid motion.  Call once per frame before rendering it: the library keeps
+ * the geometry of the previous call resident for temporal reuse (an exact inverse shift into the
+ * previous frame needs the previous scene).  Transforms identical to the current ones are a
+ * no-op (the scene is static between the two frames). */
+tof_status tof_bvh_build(tof_ctx* ctx, tof_scene scene, const float* object_xforms, int refit_only, void* stream);
+
+/* Per-view device state (reservoirs of the current and previous frame, G-buffers, confidence)
+ * for a W x H sensor; B = 0 for gated rendering, else the number of transient bins. */
+tof_status tof_view_create(tof_ctx* ctx, tof_scene scene, int32_t W, int32_t H, int32_t B, tof_view* out);
+tof_status tof_view_destroy(tof_ctx* ctx, tof_view view);
+
+/* Render one time-gated frame (Sec. 3.2 stages (1)-(4)): G-buffer, initial path-tree RIS,
+ * temporal reuse against the view's previous frame (params->temporal), params->n_spatial_iters
+ * spatial passes, and the gated image out_image_dev[H*W] (row-major, float32) = f(y) W_y.
+ * `frame` keys the random streams together with `seed`. */
+tof_status tof_render_gated(tof_ctx* ctx, tof_scene scene, tof_view view, const tof_sensor* sensor,
+                            const tof_emitter* emitter, const tof_gate* gate, const tof_params* params,
+                            uint64_t seed, uint32_t frame, float* out_image_dev, void* stream);
+
+/* Render one transient frame (Sec. 4.5): per-bin reservoirs, per-bin temporal / spatial reuse,
+ * and the histogram out_hist_dev[H*W*B] (bin fastest, float32). */
+tof_status tof_render_transient(tof_ctx* ctx, tof_scene scene, tof_view view, const tof_sensor* sensor,
+                                const tof_emitter* emitter, const tof_bins* bins, const tof_params* params,
+                                uint64_t seed, uint32_t frame, float* out_hist_dev, void* stream);
+
+/* Plain gated (bins == NULL) or transient path tracing without reuse, spp paths per pixel each
+ * with its own jitter (the comparison method of Sec. 6).  Output layout as above. */
+tof_status tof_render_pt(tof_ctx* ctx, tof_scene scene, const tof_sensor* sensor, const tof_emitter* emitter,
+                         const tof_gate* gate, const tof_bins* bins, const tof_params* params, uint64_t seed,
+                         uint32_t frame, int32_t spp, float* out_dev, void* stream);
+
+/* Forget the view's history (the next frame renders without temporal reuse). */
+tof_status tof_reservoirs_reset(tof_ctx* ctx, tof_view view);
+
+/* Shift statistics accumulated by the view since creation or reset (Table "Newton statistics",
+ * Sec. 6): out[0] Newton solves, out[1] Newton iterations, out[2] Newton successes, out[3]
+ * shift attempts, out[4] successful shifts.  Synchronises the view's last stream. */
+tof_status tof_view_stats(tof_ctx* ctx, tof_view view, double out[5]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOF_H */

@@ -142,14 +142,18 @@ static double bsdf_pdf(const omat* m, v3 n, v3 wi, v3 wo) {
     return 0.0;
 }
 
-/* orthonormal basis around a unit vector (Duff, Burgess, Christensen, Hery, Kensler, Liani,
- * Villemin: "Building an Orthonormal Basis, Revisited", JCGT 6(1) 2017) */
+/* orthonormal tangent frame (t, b, n) around a unit normal: t = normalize(a x n), b = n x t, with
+ * the reference axis a one of two fixed generic unit vectors (a1, and a2 perpendicular to it,
+ * used when |n.a1| >= 0.6).  The frame must be a deterministic function of n, and any such frame
+ * is discontinuous somewhere on the sphere; this one puts the switch on a cone around a generic
+ * direction that mesh normals (axis-aligned walls, symmetric tessellations) do not meet exactly,
+ * so float and double evaluations of the same normal pick the same branch. */
 static void onb(v3 n, v3* t, v3* b) {
-    double sign = n.z >= 0.0 ? 1.0 : -1.0;
-    double a = -1.0 / (sign + n.z);
-    double bb = n.x * n.y * a;
-    *t = V(1.0 + sign * n.x * n.x * a, sign * bb, -sign * n.x);
-    *b = V(bb, sign + n.y * n.y * a, -n.y);
+    const v3 a1 = {0.4140355211239282, 0.731736150464251, 0.5414210869105452};
+    const v3 a2 = {0.0, 0.5947978113475719, -0.8038753408434284};
+    v3 a = fabs(vdot(n, a1)) < 0.6 ? a1 : a2;
+    *t = vnorm(vcross(a, n));
+    *b = vcross(n, *t);
 }
 
 /* sample wo given wi; returns 0 on failure.  *thr = f_s |cos_o| / pdf (albedo for delta). */

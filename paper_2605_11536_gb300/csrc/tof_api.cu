@@ -1,0 +1,544 @@
+// tof_api.cu -- host runtime behind the C ABI of include/tof.h.
+//
+// Owns the device state (scenes with double-buffered world geometry and LBVH, views with the
+// reservoirs / G-buffers / confidence of the current and previous frame), validates arguments,
+// accounts device memory against the context's HBM budget and orders the per-frame stages of
+// the ToF ReSTIR pipeline on the caller's stream (Sec. 3.2 stages (1)-(4)).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tof.h"
+#include "tof_internal.h"
+
+namespace tof {
+cudaError_t launch_gbuffer(const GbufArgs& a, cudaStream_t s);
+cudaError_t launch_initial(const InitArgs& a, int* err, cudaStream_t s);
+cudaError_t launch_reuse(const ReuseArgs& a, cudaStream_t s);
+cudaError_t launch_splat(const SplatArgs& a, cudaStream_t s);
+cudaError_t launch_pt(const PtArgs& a, cudaStream_t s);
+cudaError_t launch_laser(const GeomDev& g, float3 o, float3 d, float power, LightDev* out, cudaStream_t s);
+cudaError_t launch_xform(int nt, const float* vloc, const uint32_t* tris, const uint32_t* triobj, const uint32_t* objmat,
+                         const float* xf, float4* tri_out, float4* cent, cudaStream_t s);
+cudaError_t launch_build_topology(int n, const float4* cent, uint32_t* bb, uint32_t* keys, uint32_t* vals, uint32_t* keys2,
+                                  uint32_t* vals2, uint32_t* hist, int* child, int* parent_int, int* parent_leaf,
+                                  uint32_t** prim_out, cudaStream_t s);
+cudaError_t launch_refit(int n, const uint32_t* prim, const float4* tri, float4* leaf, float4* nodes, const int* child,
+                         const int* parent_int, const int* parent_leaf, uint32_t* counter, cudaStream_t s);
+}  // namespace tof
+
+using namespace tof;
+
+namespace {
+
+struct DevAlloc {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct SceneH {
+    bool alive = false;
+    int nv = 0, nt = 0, nobj = 0, nmat = 0;
+    float* vloc = nullptr;
+    uint32_t *tris = nullptr, *triobj = nullptr, *objmat = nullptr;
+    float4* mats = nullptr;
+    float* xf = nullptr;
+    float4* cent = nullptr;
+    uint32_t *keys = nullptr, *vals = nullptr, *keys2 = nullptr, *vals2 = nullptr, *hist = nullptr, *bb = nullptr;
+    uint32_t* prim = nullptr;   // points into vals after a build
+    int *child = nullptr, *parent_int = nullptr, *parent_leaf = nullptr;
+    uint32_t* counter = nullptr;
+    float4* tri[2] = {nullptr, nullptr};
+    float4* leaf[2] = {nullptr, nullptr};
+    float4* nodes[2] = {nullptr, nullptr};
+    uint32_t version[2] = {0, 0};
+    std::vector<float> xfh[2];
+    int cur = 0;
+    bool built = false;
+};
+
+struct ResH {
+    float4* planes = nullptr;
+    float* M = nullptr;
+    uint32_t* occ = nullptr;
+    size_t stride = 0;
+    int words = 1;
+    ResDev dev() const {
+        ResDev r;
+        r.planes = planes; r.stride = stride; r.M = M; r.occ = occ; r.words = words;
+        return r;
+    }
+};
+
+struct ViewH {
+    bool alive = false;
+    int scene = -1, W = 0, H = 0, B = 0;
+    float4* gb[2] = {nullptr, nullptr};
+    LightDev* laser[2] = {nullptr, nullptr};
+    ResH res[3];
+    FrameDev fd[2];
+    int geom_slot[2] = {0, 0};
+    uint32_t geom_version[2] = {0, 0};
+    int cur = 0;
+    int prev_final = -1;
+    bool has_prev = false;
+    StatsDev* stats = nullptr;
+    cudaStream_t last_stream = nullptr;
+};
+
+}  // namespace
+
+struct tof_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    std::string err;
+    std::vector<SceneH> scenes;
+    std::vector<ViewH> views;
+    std::vector<DevAlloc> allocs;
+    uint32_t version_counter = 0;
+    int* d_err = nullptr;
+    float* d_scratch = nullptr;  // scratch image for plain PT temporaries
+};
+
+static tof_status fail(tof_ctx* c, tof_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+template <class T>
+static tof_status dalloc(tof_ctx* c, T** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(c, TOF_EBUDGET, "%s: %zu bytes exceed the HBM budget (%llu of %llu used)", what, bytes,
+                    (unsigned long long)c->used, (unsigned long long)c->budget);
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, TOF_ENOMEM, "%s: cudaMalloc(%zu) failed: %s", what, bytes, cudaGetErrorString(e));
+    }
+    c->used += bytes;
+    DevAlloc a;
+    a.p = q; a.bytes = bytes;
+    c->allocs.push_back(a);
+    *p = (T*)q;
+    return TOF_OK;
+}
+static void dfree(tof_ctx* c, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < c->allocs.size(); ++i)
+        if (c->allocs[i].p == p) {
+            c->used -= c->allocs[i].bytes;
+            c->allocs.erase(c->allocs.begin() + (long)i);
+            break;
+        }
+    cudaFree(p);
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t _e = (call);                                                                     \
+        if (_e != cudaSuccess) return fail(c, TOF_ECUDA, "%s: %s", #call, cudaGetErrorString(_e));   \
+    } while (0)
+#define TRY(call)                          \
+    do {                                   \
+        tof_status _s = (call);            \
+        if (_s != TOF_OK) return _s;       \
+    } while (0)
+
+static float3 v3f(const float* p) { return make_float3(p[0], p[1], p[2]); }
+
+static ParamsDev to_dev(const tof_params* p, uint64_t seed) {
+    ParamsDev d;
+    d.depth = p->depth; d.n_cand = p->n_cand; d.n_spatial = p->n_spatial; d.radius = p->radius;
+    d.n_spatial_iters = p->n_spatial_iters; d.temporal = p->temporal; d.m_cap = p->m_cap;
+    d.newton_max_iter = p->newton_max_iter; d.newton_tol_frac = p->newton_tol_frac; d.jac_max = p->jac_max;
+    d.d_min = p->d_min; d.ray_eps = p->ray_eps; d.flags = p->flags; d.seed = seed;
+    return d;
+}
+
+static tof_status check_params(tof_ctx* c, const tof_params* p, int transient) {
+    if (!p) return fail(c, TOF_EINVAL, "params is NULL");
+    if (p->depth < 1 || p->depth > kMaxDepth) return fail(c, TOF_EINVAL, "depth %d outside [1, %d]", p->depth, kMaxDepth);
+    if (p->n_cand < 1 || p->n_cand > kMaxCand) return fail(c, TOF_EINVAL, "n_cand %d outside [1, %d]", p->n_cand, kMaxCand);
+    if (p->n_spatial < 0 || p->n_spatial > kMaxNb) return fail(c, TOF_EINVAL, "n_spatial %d outside [0, %d]", p->n_spatial, kMaxNb);
+    if (p->radius < 1 || p->radius > 255) return fail(c, TOF_EINVAL, "radius %d outside [1, 255]", p->radius);
+    if (p->n_spatial_iters < 0 || p->n_spatial_iters > 4) return fail(c, TOF_EINVAL, "n_spatial_iters outside [0, 4]");
+    if (p->newton_max_iter < 0 || p->newton_max_iter > 16) return fail(c, TOF_EINVAL, "newton_max_iter outside [0, 16]");
+    if (!(p->m_cap > 0) || !(p->jac_max >= 1) || !(p->newton_tol_frac > 0) || !(p->ray_eps > 0) || !(p->d_min >= 0))
+        return fail(c, TOF_EINVAL, "m_cap, jac_max, newton_tol_frac, ray_eps must be positive, d_min >= 0");
+    if (transient) {
+        int kmin = (p->flags & TOF_FLAG_DIRECT) ? 1 : 2;
+        int lengths = p->depth - kmin + 1;
+        if (lengths > 0 && p->n_cand * lengths > kMaxBinsPerPixel)
+            return fail(c, TOF_EINVAL, "transient: n_cand * path lengths = %d exceeds %d candidates per pixel",
+                        p->n_cand * lengths, kMaxBinsPerPixel);
+    }
+    return TOF_OK;
+}
+
+static tof_status check_sensor(tof_ctx* c, const tof_sensor* s, int W, int H) {
+    if (!s) return fail(c, TOF_EINVAL, "sensor is NULL");
+    if (s->W != W || s->H != H) return fail(c, TOF_EINVAL, "sensor %dx%d does not match the view %dx%d", s->W, s->H, W, H);
+    if (s->mode != TOF_PINHOLE && s->mode != TOF_CONFOCAL) return fail(c, TOF_EINVAL, "unknown sensor mode %d", s->mode);
+    if (s->mode == TOF_PINHOLE && !(s->fov_y > 0 && s->fov_y < 3.1f)) return fail(c, TOF_EINVAL, "fov_y out of range");
+    return TOF_OK;
+}
+
+static FrameDev make_frame(const SceneH& S, int slot, const tof_sensor* s, const tof_emitter* e, float L0, float dL, int B,
+                           uint32_t frame, float4* gb, LightDev* laser) {
+    FrameDev F;
+    memset(&F, 0, sizeof(F));
+    F.g.tri = S.tri[slot]; F.g.leaf = S.leaf[slot]; F.g.nodes = S.nodes[slot]; F.g.mats = S.mats; F.g.nt = S.nt;
+    F.g.version = S.version[slot];
+    F.mode = s->mode; F.W = s->W; F.H = s->H;
+    F.pos = v3f(s->pos); F.fwd = v3f(s->fwd); F.up = v3f(s->up); F.fov_y = s->fov_y;
+    F.wall_o = v3f(s->wall_o); F.wall_u = v3f(s->wall_u); F.wall_v = v3f(s->wall_v);
+    F.etype = e->type; F.epos = v3f(e->pos); F.edir = v3f(e->dir); F.epower = e->power;
+    F.laser = laser;
+    F.L0 = L0; F.dL = dL; F.B = B;
+    F.frame = frame;
+    F.gb = gb;
+    return F;
+}
+
+extern "C" {
+
+tof_status tof_create(tof_ctx** out, int device, uint64_t hbm_budget_bytes) {
+    if (!out) return TOF_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return TOF_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return TOF_ECUDA;
+    tof_ctx* c = new tof_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    if (dalloc(c, &c->d_err, 64, "error word") != TOF_OK) { delete c; return TOF_ENOMEM; }
+    cudaMemset(c->d_err, 0, 64);
+    *out = c;
+    return TOF_OK;
+}
+
+tof_status tof_destroy(tof_ctx* c) {
+    if (!c) return TOF_EINVAL;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto& a : c->allocs) cudaFree(a.p);
+    delete c;
+    return TOF_OK;
+}
+
+const char* tof_last_error(tof_ctx* c) { return c ? c->err.c_str() : "no context"; }
+uint64_t tof_device_bytes(tof_ctx* c) { return c ? c->used : 0; }
+
+tof_status tof_scene_upload(tof_ctx* c, const float* verts, uint32_t nv, const uint32_t* tris, uint32_t nt,
+                            const uint32_t* tri_object, const tof_material* mats, uint32_t nmat,
+                            const uint32_t* object_material, uint32_t nobj, tof_scene* out) {
+    if (!c || !out) return TOF_EINVAL;
+    if (!verts || !tris || !tri_object || !mats || !object_material) return fail(c, TOF_EINVAL, "NULL scene array");
+    if (nt == 0 || nv == 0 || nobj == 0 || nmat == 0) return fail(c, TOF_EINVAL, "empty scene");
+    if (nt > (1u << 26)) return fail(c, TOF_EINVAL, "too many triangles");
+    for (uint64_t i = 0; i < 3ull * nv; ++i)
+        if (!std::isfinite(verts[i])) return fail(c, TOF_EINVAL, "non-finite vertex coordinate at %llu", (unsigned long long)i);
+    for (uint64_t i = 0; i < 3ull * nt; ++i)
+        if (tris[i] >= nv) return fail(c, TOF_EINVAL, "triangle index out of range");
+    for (uint32_t i = 0; i < nt; ++i)
+        if (tri_object[i] >= nobj) return fail(c, TOF_EINVAL, "tri_object out of range");
+    for (uint32_t i = 0; i < nobj; ++i)
+        if (object_material[i] >= nmat) return fail(c, TOF_EINVAL, "object_material out of range");
+    std::vector<float4> mh(nmat);
+    for (uint32_t i = 0; i < nmat; ++i) {
+        if (mats[i].type < 0 || mats[i].type > 2 || !(mats[i].albedo >= 0 && mats[i].albedo <= 1))
+            return fail(c, TOF_EINVAL, "material %u invalid", i);
+        if (mats[i].type == TOF_GGX && !(mats[i].alpha > 0 && mats[i].alpha <= 1))
+            return fail(c, TOF_EINVAL, "material %u: GGX alpha must be in (0, 1]", i);
+        mh[i] = make_float4((float)mats[i].type, mats[i].albedo, mats[i].alpha, 0.f);
+    }
+    cudaSetDevice(c->device);
+    SceneH S;
+    S.nv = (int)nv; S.nt = (int)nt; S.nobj = (int)nobj; S.nmat = (int)nmat;
+    TRY(dalloc(c, &S.vloc, sizeof(float) * 3 * nv, "vertices"));
+    TRY(dalloc(c, &S.tris, sizeof(uint32_t) * 3 * nt, "triangles"));
+    TRY(dalloc(c, &S.triobj, sizeof(uint32_t) * nt, "tri_object"));
+    TRY(dalloc(c, &S.objmat, sizeof(uint32_t) * nobj, "object_material"));
+    TRY(dalloc(c, &S.mats, sizeof(float4) * nmat, "materials"));
+    TRY(dalloc(c, &S.xf, sizeof(float) * 12 * nobj, "transforms"));
+    TRY(dalloc(c, &S.cent, sizeof(float4) * nt, "centroids"));
+    TRY(dalloc(c, &S.keys, sizeof(uint32_t) * nt, "keys"));
+    TRY(dalloc(c, &S.vals, sizeof(uint32_t) * nt, "vals"));
+    TRY(dalloc(c, &S.keys2, sizeof(uint32_t) * nt, "keys2"));
+    TRY(dalloc(c, &S.vals2, sizeof(uint32_t) * nt, "vals2"));
+    int ntiles = ((int)nt + 2047) / 2048;
+    TRY(dalloc(c, &S.hist, sizeof(uint32_t) * 256 * (size_t)ntiles, "histogram"));
+    TRY(dalloc(c, &S.bb, sizeof(uint32_t) * 8, "bounds"));
+    TRY(dalloc(c, &S.child, sizeof(int) * 2 * nt, "children"));
+    TRY(dalloc(c, &S.parent_int, sizeof(int) * nt, "parents"));
+    TRY(dalloc(c, &S.parent_leaf, sizeof(int) * nt, "leaf parents"));
+    TRY(dalloc(c, &S.counter, sizeof(uint32_t) * nt, "refit counters"));
+    for (int k = 0; k < 2; ++k) {
+        TRY(dalloc(c, &S.tri[k], sizeof(float4) * 3 * nt, "triangle records"));
+        TRY(dalloc(c, &S.leaf[k], sizeof(float4) * 3 * nt, "leaf records"));
+        TRY(dalloc(c, &S.nodes[k], sizeof(float4) * 4 * (size_t)(nt > 1 ? nt - 1 : 1), "nodes"));
+    }
+    CK(cudaMemcpy(S.vloc, verts, sizeof(float) * 3 * nv, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.tris, tris, sizeof(uint32_t) * 3 * nt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.triobj, tri_object, sizeof(uint32_t) * nt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.objmat, object_material, sizeof(uint32_t) * nobj, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.mats, mh.data(), sizeof(float4) * nmat, cudaMemcpyHostToDevice));
+    S.alive = true;
+    c->scenes.push_back(S);
+    *out = (tof_scene)(c->scenes.size() - 1);
+    return TOF_OK;
+}
+
+tof_status tof_scene_destroy(tof_ctx* c, tof_scene id) {
+    if (!c || id < 0 || id >= (int)c->scenes.size() || !c->scenes[id].alive) return c ? fail(c, TOF_EINVAL, "bad scene") : TOF_EINVAL;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    SceneH& S = c->scenes[id];
+    void* ps[] = {S.vloc, S.tris, S.triobj, S.objmat, S.mats, S.xf, S.cent, S.keys, S.vals, S.keys2, S.vals2, S.hist, S.bb,
+                  S.child, S.parent_int, S.parent_leaf, S.counter, S.tri[0], S.tri[1], S.leaf[0], S.leaf[1], S.nodes[0], S.nodes[1]};
+    for (void* p : ps) dfree(c, p);
+    S = SceneH();
+    return TOF_OK;
+}
+
+tof_status tof_bvh_build(tof_ctx* c, tof_scene id, const float* xf, int refit_only, void* stream) {
+    if (!c) return TOF_EINVAL;
+    if (id < 0 || id >= (int)c->scenes.size() || !c->scenes[id].alive) return fail(c, TOF_EINVAL, "bad scene handle %d", id);
+    if (!xf) return fail(c, TOF_EINVAL, "object_xforms is NULL");
+    SceneH& S = c->scenes[id];
+    for (int i = 0; i < 12 * S.nobj; ++i)
+        if (!std::isfinite(xf[i])) return fail(c, TOF_EINVAL, "non-finite transform entry %d", i);
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<float> xv(xf, xf + 12 * S.nobj);
+    if (S.built && S.xfh[S.cur] == xv) return TOF_OK;   // static between frames
+    int slot = S.built ? 1 - S.cur : 0;
+    CK(cudaMemcpyAsync(S.xf, xf, sizeof(float) * 12 * S.nobj, cudaMemcpyHostToDevice, s));
+    CK(launch_xform(S.nt, S.vloc, S.tris, S.triobj, S.objmat, S.xf, S.tri[slot], S.cent, s));
+    if (!S.built || !refit_only) {
+        CK(launch_build_topology(S.nt, S.cent, S.bb, S.keys, S.vals, S.keys2, S.vals2, S.hist, S.child, S.parent_int,
+                                 S.parent_leaf, &S.prim, s));
+    }
+    CK(launch_refit(S.nt, S.prim, S.tri[slot], S.leaf[slot], S.nodes[slot], S.child, S.parent_int, S.parent_leaf, S.counter, s));
+    S.version[slot] = ++c->version_counter;
+    S.xfh[slot] = xv;
+    S.cur = slot;
+    S.built = true;
+    return TOF_OK;
+}
+
+tof_status tof_view_create(tof_ctx* c, tof_scene scene, int32_t W, int32_t H, int32_t B, tof_view* out) {
+    if (!c || !out) return TOF_EINVAL;
+    if (scene < 0 || scene >= (int)c->scenes.size() || !c->scenes[scene].alive) return fail(c, TOF_EINVAL, "bad scene handle");
+    if (W < 1 || H < 1 || W > 16384 || H > 16384 || B < 0 || B > 65536) return fail(c, TOF_EINVAL, "bad view size %dx%dx%d", W, H, B);
+    cudaSetDevice(c->device);
+    ViewH V;
+    V.scene = scene; V.W = W; V.H = H; V.B = B;
+    size_t npix = (size_t)W * H, Bn = B > 0 ? (size_t)B : 1;
+    int words = (int)((Bn + 31) / 32);
+    for (int k = 0; k < 2; ++k) {
+        TRY(dalloc(c, &V.gb[k], sizeof(float4) * npix, "G-buffer"));
+        TRY(dalloc(c, &V.laser[k], sizeof(LightDev), "laser spot"));
+    }
+    for (int k = 0; k < 3; ++k) {
+        ResH& R = V.res[k];
+        R.stride = npix * Bn;
+        R.words = words;
+        TRY(dalloc(c, &R.planes, sizeof(float4) * 6 * R.stride, "reservoirs"));
+        TRY(dalloc(c, &R.M, sizeof(float) * npix, "confidence"));
+        TRY(dalloc(c, &R.occ, sizeof(uint32_t) * npix * words, "occupancy"));
+        CK(cudaMemset(R.occ, 0, sizeof(uint32_t) * npix * words));
+    }
+    TRY(dalloc(c, &V.stats, sizeof(StatsDev), "stats"));
+    CK(cudaMemset(V.stats, 0, sizeof(StatsDev)));
+    V.alive = true;
+    c->views.push_back(V);
+    *out = (tof_view)(c->views.size() - 1);
+    return TOF_OK;
+}
+
+tof_status tof_view_destroy(tof_ctx* c, tof_view id) {
+    if (!c || id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return c ? fail(c, TOF_EINVAL, "bad view") : TOF_EINVAL;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    ViewH& V = c->views[id];
+    for (int k = 0; k < 2; ++k) { dfree(c, V.gb[k]); dfree(c, V.laser[k]); }
+    for (int k = 0; k < 3; ++k) { dfree(c, V.res[k].planes); dfree(c, V.res[k].M); dfree(c, V.res[k].occ); }
+    dfree(c, V.stats);
+    V = ViewH();
+    return TOF_OK;
+}
+
+tof_status tof_reservoirs_reset(tof_ctx* c, tof_view id) {
+    if (!c || id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return c ? fail(c, TOF_EINVAL, "bad view") : TOF_EINVAL;
+    ViewH& V = c->views[id];
+    V.has_prev = false;
+    V.prev_final = -1;
+    return TOF_OK;
+}
+
+tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[5]) {
+    if (!c || !out || id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return c ? fail(c, TOF_EINVAL, "bad view") : TOF_EINVAL;
+    cudaSetDevice(c->device);
+    ViewH& V = c->views[id];
+    StatsDev h;
+    CK(cudaStreamSynchronize(V.last_stream));
+    CK(cudaMemcpy(&h, V.stats, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 5; ++i) out[i] = (double)h.v[i];
+    return TOF_OK;
+}
+
+static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_sensor* sensor, const tof_emitter* emitter,
+                         float L0, float dL, int B, const tof_params* params, uint64_t seed, uint32_t frame, float* out,
+                         void* stream) {
+    if (!c) return TOF_EINVAL;
+    if (scene < 0 || scene >= (int)c->scenes.size() || !c->scenes[scene].alive) return fail(c, TOF_EINVAL, "bad scene handle");
+    if (vid < 0 || vid >= (int)c->views.size() || !c->views[vid].alive) return fail(c, TOF_EINVAL, "bad view handle");
+    ViewH& V = c->views[vid];
+    SceneH& S = c->scenes[scene];
+    if (V.scene != scene) return fail(c, TOF_EINVAL, "view %d belongs to scene %d", vid, V.scene);
+    if (!S.built) return fail(c, TOF_ESTATE, "tof_bvh_build has not been called for scene %d", scene);
+    if ((B > 0) != (V.B > 0) || (B > 0 && B != V.B)) return fail(c, TOF_EINVAL, "bins %d do not match the view (%d)", B, V.B);
+    TRY(check_sensor(c, sensor, V.W, V.H));
+    TRY(check_params(c, params, B > 0));
+    if (!emitter || emitter->type < 0 || emitter->type > 2 || !(emitter->power >= 0))
+        return fail(c, TOF_EINVAL, "bad emitter");
+    if (!(dL > 0) || !std::isfinite(L0)) return fail(c, TOF_EINVAL, "gate / bin width must be positive and finite");
+    if (!out) return fail(c, TOF_EINVAL, "output pointer is NULL");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    V.last_stream = s;
+
+    const int fc = V.has_prev ? 1 - V.cur : V.cur;
+    FrameDev F = make_frame(S, S.cur, sensor, emitter, L0, dL, B, frame, V.gb[fc], V.laser[fc]);
+    ParamsDev P = to_dev(params, seed);
+    if (emitter->type == TOF_EMIT_LASER) CK(launch_laser(F.g, v3f(emitter->pos), v3f(emitter->dir), emitter->power, V.laser[fc], s));
+    GbufArgs ga;
+    ga.F = F; ga.gb = V.gb[fc]; ga.P = P;
+    CK(launch_gbuffer(ga, s));
+
+    // temporal reuse needs the previous frame's geometry still resident
+    bool temporal = params->temporal && V.has_prev && V.prev_final >= 0 &&
+                    S.version[V.geom_slot[1 - fc]] == V.geom_version[1 - fc];
+    int stages = 1 + (temporal ? 1 : 0) + (params->n_spatial > 0 ? params->n_spatial_iters : 0);
+    int bufs[2], nb = 0;
+    for (int k = 0; k < 3 && nb < 2; ++k)
+        if (k != V.prev_final) bufs[nb++] = k;
+    // stage i writes bufs[(i + off) % 2] so that the last stage lands in bufs[1]
+    int off = (stages % 2 == 0) ? 0 : 1;
+    auto out_of = [&](int st) { return bufs[(st + off) % 2]; };
+    int stage = 0;
+    InitArgs ia;
+    ia.F = F; ia.dst = V.res[out_of(stage)].dev(); ia.P = P;
+    ia.out = (stage == stages - 1 && B == 0) ? out : nullptr;
+    CK(launch_initial(ia, c->d_err, s));
+    int src = out_of(stage);
+    ++stage;
+    ReuseArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.cur = F; ra.P = P; ra.stats = V.stats;
+    if (temporal) {
+        ra.prev = V.fd[1 - fc];
+        ra.src = V.res[src].dev();
+        ra.prv = V.res[V.prev_final].dev();
+        ra.dst = V.res[out_of(stage)].dev();
+        ra.temporal = 1; ra.pass = 0;
+        ra.geom_static = V.geom_version[1 - fc] == S.version[S.cur];
+        ra.out = (stage == stages - 1 && B == 0) ? out : nullptr;
+        CK(launch_reuse(ra, s));
+        src = out_of(stage);
+        ++stage;
+    }
+    if (params->n_spatial > 0) {
+        for (int it = 0; it < params->n_spatial_iters; ++it) {
+            ra.prev = F;
+            ra.src = V.res[src].dev();
+            ra.prv = ra.src;
+            ra.dst = V.res[out_of(stage)].dev();
+            ra.temporal = 0; ra.pass = 1 + it; ra.geom_static = 1;
+            ra.out = (stage == stages - 1 && B == 0) ? out : nullptr;
+            CK(launch_reuse(ra, s));
+            src = out_of(stage);
+            ++stage;
+        }
+    }
+    if (B > 0) {
+        SplatArgs sa;
+        sa.src = V.res[src].dev(); sa.npix = V.W * V.H; sa.B = B; sa.out = out;
+        CK(launch_splat(sa, s));
+    }
+    V.fd[fc] = F;
+    V.geom_slot[fc] = S.cur;
+    V.geom_version[fc] = S.version[S.cur];
+    V.cur = fc;
+    V.prev_final = src;
+    V.has_prev = true;
+    return TOF_OK;
+}
+
+tof_status tof_render_gated(tof_ctx* c, tof_scene scene, tof_view view, const tof_sensor* sensor, const tof_emitter* emitter,
+                            const tof_gate* gate, const tof_params* params, uint64_t seed, uint32_t frame, float* out_image_dev,
+                            void* stream) {
+    if (!c) return TOF_EINVAL;
+    if (!gate) return fail(c, TOF_EINVAL, "gate is NULL");
+    return render(c, scene, view, sensor, emitter, gate->L0, gate->dL, 0, params, seed, frame, out_image_dev, stream);
+}
+
+tof_status tof_render_transient(tof_ctx* c, tof_scene scene, tof_view view, const tof_sensor* sensor,
+                                const tof_emitter* emitter, const tof_bins* bins, const tof_params* params, uint64_t seed,
+                                uint32_t frame, float* out_hist_dev, void* stream) {
+    if (!c) return TOF_EINVAL;
+    if (!bins || bins->B < 1) return fail(c, TOF_EINVAL, "bins missing or B < 1");
+    return render(c, scene, view, sensor, emitter, bins->t0, bins->width, bins->B, params, seed, frame, out_hist_dev, stream);
+}
+
+tof_status tof_render_pt(tof_ctx* c, tof_scene scene, const tof_sensor* sensor, const tof_emitter* emitter, const tof_gate* gate,
+                         const tof_bins* bins, const tof_params* params, uint64_t seed, uint32_t frame, int32_t spp,
+                         float* out_dev, void* stream) {
+    if (!c) return TOF_EINVAL;
+    if (scene < 0 || scene >= (int)c->scenes.size() || !c->scenes[scene].alive) return fail(c, TOF_EINVAL, "bad scene handle");
+    SceneH& S = c->scenes[scene];
+    if (!S.built) return fail(c, TOF_ESTATE, "tof_bvh_build has not been called");
+    if (!sensor) return fail(c, TOF_EINVAL, "sensor is NULL");
+    TRY(check_sensor(c, sensor, sensor->W, sensor->H));
+    TRY(check_params(c, params, 0));
+    if (!emitter || emitter->type < 0 || emitter->type > 2) return fail(c, TOF_EINVAL, "bad emitter");
+    if (spp < 1) return fail(c, TOF_EINVAL, "spp must be >= 1");
+    if (!out_dev) return fail(c, TOF_EINVAL, "output pointer is NULL");
+    if (!gate && !bins) return fail(c, TOF_EINVAL, "gate or bins required");
+    float L0 = bins ? bins->t0 : gate->L0, dL = bins ? bins->width : gate->dL;
+    int B = bins ? bins->B : 0;
+    if (bins && B < 1) return fail(c, TOF_EINVAL, "B < 1");
+    if (!(dL > 0)) return fail(c, TOF_EINVAL, "gate / bin width must be positive");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    LightDev* laser = nullptr;
+    if (emitter->type == TOF_EMIT_LASER) {
+        if (!c->d_scratch) TRY(dalloc(c, &c->d_scratch, 256, "laser scratch"));
+        laser = (LightDev*)c->d_scratch;
+    }
+    FrameDev F = make_frame(S, S.cur, sensor, emitter, L0, dL, B, frame, nullptr, laser);
+    ParamsDev P = to_dev(params, seed);
+    if (laser) CK(launch_laser(F.g, v3f(emitter->pos), v3f(emitter->dir), emitter->power, laser, s));
+    PtArgs pa;
+    pa.F = F; pa.P = P; pa.spp = spp; pa.out = out_dev;
+    CK(launch_pt(pa, s));
+    return TOF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+// tof_bvh.cu -- GPU LBVH for the ToF ReSTIR hot path (sm_103a).
+//
+// The paper traces rays with DXR hardware BVHs (Sec. 6, Falcor on an RTX 3090); GB300 has no
+// RT cores, so visibility runs on a software LBVH built here:
+//   xform_kernel    rigid 3x4 object transform of every triangle corner, per frame
+//   bounds / morton 30-bit Morton codes of triangle centroids in the centroid bounds
+//   radix sort      4 stable 8-bit LSD passes (tile histograms, one scan, ranked scatter)
+//   karras_kernel   binary radix tree over the sorted codes (Karras, HPG 2012), ties broken by index
+//   refit_kernel    leaf records in leaf order and bottom-up child boxes (one atomic per node;
+//                   the second arriving thread continues, no thread waits)
+#include <cstdio>
+
+#include "tof_internal.h"
+
+namespace tof {
+
+__device__ __forceinline__ float3 fx3(const float* M, float3 p, int r) {
+    (void)r;
+    return make_float3(M[0] * p.x + M[1] * p.y + M[2] * p.z + M[3], M[4] * p.x + M[5] * p.y + M[6] * p.z + M[7],
+                       M[8] * p.x + M[9] * p.y + M[10] * p.z + M[11]);
+}
+
+// per triangle: world corners -> (v0, mat), (e1), (e2); centroid
+__global__ void xform_kernel(int nt, const float* __restrict__ vloc, const uint32_t* __restrict__ tris,
+                             const uint32_t* __restrict__ triobj, const uint32_t* __restrict__ objmat,
+                             const float* __restrict__ xf, float4* __restrict__ tri_out, float4* __restrict__ cent) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    uint32_t o = triobj[t];
+    const float* M = xf + 12 * (size_t)o;
+    float3 v[3];
+    for (int c = 0; c < 3; ++c) {
+        uint32_t vi = tris[3 * (size_t)t + c];
+        float3 p = make_float3(vloc[3 * (size_t)vi], vloc[3 * (size_t)vi + 1], vloc[3 * (size_t)vi + 2]);
+        v[c] = fx3(M, p, 0);
+    }
+    float3 e1 = make_float3(v[1].x - v[0].x, v[1].y - v[0].y, v[1].z - v[0].z);
+    float3 e2 = make_float3(v[2].x - v[0].x, v[2].y - v[0].y, v[2].z - v[0].z);
+    tri_out[3 * (size_t)t] = make_float4(v[0].x, v[0].y, v[0].z, __int_as_float((int)objmat[o]));
+    tri_out[3 * (size_t)t + 1] = make_float4(e1.x, e1.y, e1.z, 0.f);
+    tri_out[3 * (size_t)t + 2] = make_float4(e2.x, e2.y, e2.z, 0.f);
+    if (cent) cent[t] = make_float4((v[0].x + v[1].x + v[2].x) / 3.0f, (v[0].y + v[1].y + v[2].y) / 3.0f,
+                                    (v[0].z + v[1].z + v[2].z) / 3.0f, 0.f);
+}
+
+// order-preserving float <-> uint for atomic min / max
+__device__ __forceinline__ uint32_t fenc(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fdec(uint32_t u) { return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u); }
+
+__global__ void bounds_kernel(int n, const float4* __restrict__ cent, uint32_t* __restrict__ bb) {
+    __shared__ uint32_t s[6];
+    if (threadIdx.x < 3) s[threadIdx.x] = 0xFFFFFFFFu;
+    else if (threadIdx.x < 6) s[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 c = cent[i];
+        atomicMin(&s[0], fenc(c.x)); atomicMin(&s[1], fenc(c.y)); atomicMin(&s[2], fenc(c.z));
+        atomicMax(&s[3], fenc(c.x)); atomicMax(&s[4], fenc(c.y)); atomicMax(&s[5], fenc(c.z));
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) atomicMin(&bb[threadIdx.x], s[threadIdx.x]);
+    else if (threadIdx.x < 6) atomicMax(&bb[threadIdx.x], s[threadIdx.x]);
+}
+
+__device__ __forceinline__ uint32_t expand10(uint32_t v) {
+    v = (v * 0x00010001u) & 0xFF0000FFu;
+    v = (v * 0x00000101u) & 0x0F00F00Fu;
+    v = (v * 0x00000011u) & 0xC30C30C3u;
+    v = (v * 0x00000005u) & 0x49249249u;
+    return v;
+}
+
+__global__ void morton_kernel(int n, const float4* __restrict__ cent, const uint32_t* __restrict__ bb,
+                              uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float lo[3] = {fdec(bb[0]), fdec(bb[1]), fdec(bb[2])}, hi[3] = {fdec(bb[3]), fdec(bb[4]), fdec(bb[5])};
+    float4 c = cent[i];
+    float cc[3] = {c.x, c.y, c.z};
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+        float ext = fmaxf(hi[k] - lo[k], 1e-20f);
+        float t = (cc[k] - lo[k]) / ext * 1024.0f;
+        q[k] = (uint32_t)fminf(fmaxf(t, 0.f), 1023.f);
+    }
+    keys[i] = (expand10(q[0]) << 2) | (expand10(q[1]) << 1) | expand10(q[2]);
+    vals[i] = (uint32_t)i;
+}
+
+// ---- radix sort: 2048-key tiles --------------------------------------------------------------
+constexpr int kTile = 2048;
+
+__global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t* __restrict__ keys, int n, int shift,
+                                                         uint32_t* __restrict__ hist, int ntiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0u;
+    __syncthreads();
+    int base = blockIdx.x * kTile;
+    for (int i = threadIdx.x; i < kTile; i += 256) {
+        int g = base + i;
+        if (g < n) atomicAdd(&h[(keys[g] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of n words in place (single block of 1024 threads)
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ data, int n) {
+    __shared__ uint32_t part[1024];
+    int per = (n + 1023) / 1024;
+    int b = threadIdx.x * per, e = min(n, b + per);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += data[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int i = b; i < e; ++i) { uint32_t v = data[i]; data[i] = run; run += v; }
+}
+
+__global__ void __launch_bounds__(256) radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int n,
+                                                            int shift, const uint32_t* __restrict__ offs, int ntiles) {
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wc[8][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    base[tid] = offs[tid * ntiles + blockIdx.x];
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int r = 0; r < kTile / 256; ++r) {
+        for (int k = 0; k < 8; ++k) wc[k][tid] = 0u;
+        __syncthreads();
+        int i = blockIdx.x * kTile + r * 256 + tid;
+        bool valid = i < n;
+        uint32_t key = valid ? kin[i] : 0u;
+        uint32_t dg = (key >> shift) & 255u;
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, valid ? dg : 256u + (uint32_t)lane);
+        uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) wc[warp][dg] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t off = base[dg] + rank;
+            for (int w = 0; w < warp; ++w) off += wc[w][dg];
+            kout[off] = key;
+            vout[off] = vin[i];
+        }
+        __syncthreads();
+        uint32_t tot = 0;
+        for (int w = 0; w < 8; ++w) tot += wc[w][tid];
+        base[tid] += tot;
+        __syncthreads();
+    }
+}
+
+// ---- Karras 2012 hierarchy --------------------------------------------------------------------
+__device__ __forceinline__ int delta(const uint32_t* __restrict__ k, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    uint32_t a = k[i], b = k[j];
+    if (a == b) return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+    return __clz(a ^ b);
+}
+
+__global__ void karras_kernel(int n, const uint32_t* __restrict__ keys, int* __restrict__ child, int* __restrict__ parent_int,
+                              int* __restrict__ parent_leaf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(keys, n, i, i - d);
+    int lmax = 2;
+    while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta(keys, n, i, j);
+    int s = 0;
+    int div = 2;
+    int t = (l + div - 1) / div;
+    while (true) {
+        if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t == 1) break;
+        div <<= 1;
+        t = (l + div - 1) / div;
+    }
+    int g = i + s * d + (d < 0 ? -1 : 0);
+    int left = min(i, j) == g ? ~g : g;
+    int right = max(i, j) == g + 1 ? ~(g + 1) : g + 1;
+    child[2 * i] = left;
+    child[2 * i + 1] = right;
+    if (left < 0) parent_leaf[~left] = i; else parent_int[left] = i;
+    if (right < 0) parent_leaf[~right] = i; else parent_int[right] = i;
+    if (i == 0) parent_int[0] = -1;
+}
+
+struct Box { float lo[3], hi[3]; };
+
+__device__ __forceinline__ Box tri_box(const float4* __restrict__ tri, int t) {
+    float4 a = tri[3 * (size_t)t], e1 = tri[3 * (size_t)t + 1], e2 = tri[3 * (size_t)t + 2];
+    float v[3][3] = {{a.x, a.y, a.z}, {a.x + e1.x, a.y + e1.y, a.z + e1.z}, {a.x + e2.x, a.y + e2.y, a.z + e2.z}};
+    Box b;
+    for (int k = 0; k < 3; ++k) {
+        float lo = fminf(v[0][k], fminf(v[1][k], v[2][k])), hi = fmaxf(v[0][k], fmaxf(v[1][k], v[2][k]));
+        float pad = 1e-6f * fmaxf(fabsf(lo), fabsf(hi)) + 1e-6f;   // conservative against rounding
+        b.lo[k] = lo - pad; b.hi[k] = hi + pad;
+    }
+    return b;
+}
+__device__ __forceinline__ Box node_box(const float4* N) {
+    float4 n0 = __ldcg(N), n1 = __ldcg(N + 1), n2 = __ldcg(N + 2);
+    Box b;
+    b.lo[0] = fminf(n0.x, n1.x); b.hi[0] = fmaxf(n0.y, n1.y);
+    b.lo[1] = fminf(n0.z, n1.z); b.hi[1] = fmaxf(n0.w, n1.w);
+    b.lo[2] = fminf(n2.x, n2.z); b.hi[2] = fmaxf(n2.y, n2.w);
+    return b;
+}
+
+__global__ void refit_kernel(int n, const uint32_t* __restrict__ prim, const float4* __restrict__ tri, float4* __restrict__ leaf,
+                             float4* nodes, const int* __restrict__ child, const int* __restrict__ parent_int,
+                             const int* __restrict__ parent_leaf, uint32_t* __restrict__ counter) {
+    int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= n) return;
+    int t = (int)prim[L];
+    float4 a = tri[3 * (size_t)t];
+    leaf[3 * (size_t)L] = make_float4(a.x, a.y, a.z, __int_as_float(t));
+    leaf[3 * (size_t)L + 1] = tri[3 * (size_t)t + 1];
+    leaf[3 * (size_t)L + 2] = tri[3 * (size_t)t + 2];
+    if (n == 1) return;
+    int p = parent_leaf[L];
+    __threadfence();
+    int guard = n;   // depth of a valid hierarchy is below n
+    while (p >= 0 && --guard >= 0) {
+        if (atomicAdd(&counter[p], 1u) == 0u) return;   // first arrival: the sibling finishes p
+        __threadfence();
+        int c[2] = {child[2 * p], child[2 * p + 1]};
+        Box b[2];
+        for (int k = 0; k < 2; ++k) b[k] = c[k] < 0 ? tri_box(tri, (int)prim[~c[k]]) : node_box(nodes + 4 * (size_t)c[k]);
+        float4* N = nodes + 4 * (size_t)p;
+        N[0] = make_float4(b[0].lo[0], b[0].hi[0], b[0].lo[1], b[0].hi[1]);
+        N[1] = make_float4(b[1].lo[0], b[1].hi[0], b[1].lo[1], b[1].hi[1]);
+        N[2] = make_float4(b[0].lo[2], b[0].hi[2], b[1].lo[2], b[1].hi[2]);
+        N[3] = make_float4(__int_as_float(c[0]), __int_as_float(c[1]), 0.f, 0.f);
+        __threadfence();
+        p = parent_int[p];
+    }
+}
+
+// ---- host launchers --------------------------------------------------------------------------
+static inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_xform(int nt, const float* vloc, const uint32_t* tris, const uint32_t* triobj, const uint32_t* objmat,
+                         const float* xf, float4* tri_out, float4* cent, cudaStream_t s) {
+    xform_kernel<<<blocks(nt, 256), 256, 0, s>>>(nt, vloc, tris, triobj, objmat, xf, tri_out, cent);
+    return cudaGetLastError();
+}
+
+// full build of the hierarchy (prim order, children, parents) from the centroids
+cudaError_t launch_build_topology(int n, const float4* cent, uint32_t* bb, uint32_t* keys, uint32_t* vals, uint32_t* keys2,
+                                  uint32_t* vals2, uint32_t* hist, int* child, int* parent_int, int* parent_leaf,
+                                  uint32_t** prim_out, cudaStream_t s) {
+    uint32_t init[6] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u};
+    cudaError_t e = cudaMemcpyAsync(bb, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    bounds_kernel<<<min(1024u, blocks(n, 256)), 256, 0, s>>>(n, cent, bb);
+    morton_kernel<<<blocks(n, 256), 256, 0, s>>>(n, cent, bb, keys, vals);
+    int ntiles = (n + kTile - 1) / kTile;
+    uint32_t *ki = keys, *vi = vals, *ko = keys2, *vo = vals2;
+    for (int shift = 0; shift < 32; shift += 8) {
+        radix_hist_kernel<<<ntiles, 256, 0, s>>>(ki, n, shift, hist, ntiles);
+        scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * ntiles);
+        radix_scatter_kernel<<<ntiles, 256, 0, s>>>(ki, vi, ko, vo, n, shift, hist, ntiles);
+        uint32_t* t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    // after 4 passes the sorted keys / prims are back in keys / vals
+    if (n > 1) karras_kernel<<<blocks(n - 1, 256), 256, 0, s>>>(n, ki, child, parent_int, parent_leaf);
+    *prim_out = vi;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refit(int n, const uint32_t* prim, const float4* tri, float4* leaf, float4* nodes, const int* child,
+                         const int* parent_int, const int* parent_leaf, uint32_t* counter, cudaStream_t s) {
+    if (n > 1) {
+        cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t) * (size_t)(n - 1), s);
+        if (e != cudaSuccess) return e;
+    }
+    refit_kernel<<<blocks(n, 256), 256, 0, s>>>(n, prim, tri, leaf, nodes, child, parent_int, parent_leaf, counter);
+    return cudaGetLastError();
+}
+
+}  // namespace tof

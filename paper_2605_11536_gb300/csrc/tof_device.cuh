@@ -1,0 +1,839 @@
+// tof_device.cuh -- device functions of the ToF ReSTIR hot path (sm_103a, FP32).
+//
+// Layering: float3 algebra -> Philox streams -> BSDFs -> LBVH traversal -> domains and lights ->
+// path trees (initial candidates) -> path-length-aware shift -> GRIS merge.
+// The method follows Kim, Jarosz, Pediredla, "ToF ReSTIR" (ACM TOG 45(4), 2026); each function
+// names the section or equation it implements.
+#pragma once
+#include <stdint.h>
+
+#include "tof_internal.h"
+
+namespace tof {
+
+// ============================================================================================
+// float3 algebra
+// ============================================================================================
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float len3(float3 a) { return sqrtf(dot3(a, a)); }
+__device__ __forceinline__ float3 norm3(float3 a) {
+    float l = len3(a);
+    return l > 0.f ? a * (1.0f / l) : f3(0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 dir_to(float3 from, float3 to) { return norm3(to - from); }
+
+// ============================================================================================
+// Philox4x32-10 (Salmon et al., SC 2011) counter-based streams.  Key = 64-bit seed; counter =
+// (pixel, frame, stream word, purpose word).  Uniform u = (x >> 8) * 2^-24.
+// ============================================================================================
+enum : uint32_t { P_JITTER = 1, P_BSDF = 2, P_RIS = 3, P_NEIGHBOR = 4, P_MERGE = 5 };
+
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t seed) {
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// ============================================================================================
+// materials (Sec. 6: diffuse, glossy, specular).  Class: rough (Lambert, GGX alpha >= 0.2),
+// glossy (GGX alpha < 0.2), delta (mirror).
+// ============================================================================================
+enum { M_LAMBERT = 0, M_GGX = 1, M_MIRROR = 2 };
+enum { C_ROUGH = 0, C_GLOSSY = 1, C_DELTA = 2 };
+constexpr float kPi = 3.14159265358979323846f;
+
+struct Mat { int type; float albedo, alpha; };
+__device__ __forceinline__ Mat load_mat(const GeomDev& g, int id) {
+    float4 m = __ldg(&g.mats[id]);
+    Mat r; r.type = (int)m.x; r.albedo = m.y; r.alpha = m.z;
+    return r;
+}
+__device__ __forceinline__ int mat_class(const Mat& m) {
+    if (m.type == M_MIRROR) return C_DELTA;
+    if (m.type == M_GGX && m.alpha < 0.2f) return C_GLOSSY;
+    return C_ROUGH;
+}
+__device__ __forceinline__ float ggx_D(float nh, float a) {
+    float a2 = a * a, t = nh * nh * (a2 - 1.0f) + 1.0f;
+    return a2 / (kPi * t * t);
+}
+__device__ __forceinline__ float ggx_G1(float nv, float a) {
+    float a2 = a * a;
+    return 2.0f * nv / (nv + sqrtf(a2 + (1.0f - a2) * nv * nv));
+}
+// f_s(wi, wo): wi toward the previous vertex, wo toward the next; reflection only
+__device__ float bsdf_f(const Mat& m, float3 n, float3 wi, float3 wo) {
+    float ci = dot3(n, wi), co = dot3(n, wo);
+    if (ci * co <= 0.f) return 0.f;
+    if (ci < 0.f) { ci = -ci; co = -co; n = n * -1.0f; }
+    if (m.type == M_LAMBERT) return m.albedo / kPi;
+    if (m.type == M_GGX) {
+        float3 h = norm3(wi + wo);
+        float nh = dot3(n, h);
+        if (nh <= 0.f) return 0.f;
+        return m.albedo * ggx_D(nh, m.alpha) * ggx_G1(ci, m.alpha) * ggx_G1(co, m.alpha) / (4.0f * ci * co);
+    }
+    return 0.f;
+}
+__device__ float bsdf_pdf(const Mat& m, float3 n, float3 wi, float3 wo) {
+    float ci = dot3(n, wi), co = dot3(n, wo);
+    if (ci * co <= 0.f) return 0.f;
+    if (ci < 0.f) { co = -co; n = n * -1.0f; }
+    if (m.type == M_LAMBERT) return co / kPi;
+    if (m.type == M_GGX) {
+        float3 h = norm3(wi + wo);
+        float nh = dot3(n, h), oh = dot3(wo, h);
+        if (nh <= 0.f || oh <= 0.f) return 0.f;
+        return ggx_D(nh, m.alpha) * nh / (4.0f * oh);
+    }
+    return 0.f;
+}
+// tangent frame (t, b, n): t = normalize(a x n), b = n x t, with the reference axis a one of two
+// fixed generic unit vectors (a2 perpendicular to a1, used when |n.a1| >= 0.6); the frame's
+// unavoidable discontinuity sits on a cone that axis-aligned or symmetric mesh normals do not
+// meet exactly, so the branch taken does not depend on rounding
+__device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
+    const float3 a1 = f3(0.4140355211239282f, 0.731736150464251f, 0.5414210869105452f);
+    const float3 a2 = f3(0.0f, 0.5947978113475719f, -0.8038753408434284f);
+    float3 a = fabsf(dot3(n, a1)) < 0.6f ? a1 : a2;
+    t = norm3(cross3(a, n));
+    b = cross3(n, t);
+}
+// sample wo given wi; thr = f_s |cos_o| / pdf (albedo for the mirror)
+__device__ bool bsdf_sample(const Mat& m, float3 n, float3 wi, float u0, float u1, float3& wo, float& pdf,
+                            float& thr, bool& delta) {
+    if (dot3(n, wi) < 0.f) n = n * -1.0f;
+    delta = false;
+    if (m.type == M_MIRROR) {
+        wo = n * (2.0f * dot3(wi, n)) - wi;
+        pdf = 1.0f; thr = m.albedo; delta = true;
+        return true;
+    }
+    float3 t, b;
+    onb(n, t, b);
+    if (m.type == M_LAMBERT) {
+        float r = sqrtf(u0), ph = 2.0f * kPi * u1;
+        float lz = sqrtf(fmaxf(0.f, 1.0f - u0));
+        float s, c;
+        sincosf(ph, &s, &c);
+        wo = t * (r * c) + b * (r * s) + n * lz;
+    } else {
+        float a = m.alpha;
+        float tan2 = a * a * u0 / (1.0f - u0);
+        float ct = 1.0f / sqrtf(1.0f + tan2), st = sqrtf(fmaxf(0.f, 1.0f - ct * ct)), ph = 2.0f * kPi * u1;
+        float s, c;
+        sincosf(ph, &s, &c);
+        float3 h = t * (st * c) + b * (st * s) + n * ct;
+        wo = h * (2.0f * dot3(wi, h)) - wi;
+    }
+    float co = dot3(n, wo);
+    if (co <= 0.f) return false;
+    pdf = bsdf_pdf(m, n, wi, wo);
+    float f = bsdf_f(m, n, wi, wo);
+    if (!(pdf > 0.f) || !(f > 0.f)) return false;
+    thr = f * co / pdf;
+    return true;
+}
+
+// ============================================================================================
+// geometry: surface points, Moller-Trumbore, LBVH traversal, visibility
+// ============================================================================================
+struct Surf { int tri; float b1, b2; float3 p, n; int mat; };
+
+__device__ __forceinline__ Surf surf_at(const GeomDev& g, int tri, float b1, float b2) {
+    float4 a = __ldg(&g.tri[3 * tri]), e1 = __ldg(&g.tri[3 * tri + 1]), e2 = __ldg(&g.tri[3 * tri + 2]);
+    Surf s;
+    s.tri = tri; s.b1 = b1; s.b2 = b2;
+    float3 E1 = xyz(e1), E2 = xyz(e2);
+    s.p = xyz(a) + (E1 * b1 + E2 * b2);
+    s.n = norm3(cross3(E1, E2));
+    s.mat = __float_as_int(a.w);
+    return s;
+}
+__device__ __forceinline__ float3 offset_point(float3 p, float3 n, float3 dir, float eps) {
+    return dot3(n, dir) >= 0.f ? p + n * eps : p - n * eps;
+}
+
+__device__ __forceinline__ bool tri_test(const float4* __restrict__ L, int leaf, float3 o, float3 d, float tmax, float& t,
+                                         float& b1, float& b2, int& orig) {
+    float4 a = __ldg(&L[3 * leaf]), e1v = __ldg(&L[3 * leaf + 1]), e2v = __ldg(&L[3 * leaf + 2]);
+    float3 e1 = xyz(e1v), e2 = xyz(e2v);
+    float3 pv = cross3(d, e2);
+    float det = dot3(e1, pv);
+    if (fabsf(det) < 1e-20f) return false;
+    float inv = 1.0f / det;
+    float3 tv = o - xyz(a);
+    float u = dot3(tv, pv) * inv;
+    if (u < 0.f || u > 1.f) return false;
+    float3 qv = cross3(tv, e1);
+    float w = dot3(d, qv) * inv;
+    if (w < 0.f || u + w > 1.f) return false;
+    float tt = dot3(e2, qv) * inv;
+    if (!(tt > 0.f && tt < tmax)) return false;
+    t = tt; b1 = u; b2 = w; orig = __float_as_int(a.w);
+    return true;
+}
+
+// closest hit (any_hit = false) or first hit (any_hit = true) of o + t d, t in (0, tmax)
+template <bool kAny>
+__device__ bool traverse(const GeomDev& g, float3 o, float3 d, float tmax, int& tri, float& b1, float& b2, float& tout) {
+    if (g.nt <= 0) return false;
+    bool found = false;
+    float best = tmax;
+    if (g.nt == 1) {
+        int orig;
+        if (tri_test(g.leaf, 0, o, d, best, tout, b1, b2, orig)) { tri = orig; return true; }
+        return false;
+    }
+    float3 id = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    float3 ood = f3(o.x * id.x, o.y * id.y, o.z * id.z);
+    int stack[kStack];
+    int sp = 0;
+    int node = 0;
+    // a valid hierarchy visits each of its nt - 1 internal nodes at most once per ray; the cap
+    // only guards against a malformed one
+    int budget = g.nt + 64;
+    while (true) {
+        if (--budget < 0) break;
+        const float4* N = g.nodes + 4 * node;
+        float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
+        float a0 = n0.x * id.x - ood.x, a1 = n0.y * id.x - ood.x;
+        float b0 = n0.z * id.y - ood.y, bb1 = n0.w * id.y - ood.y;
+        float c0 = n2.x * id.z - ood.z, c1 = n2.y * id.z - ood.z;
+        float lo0 = fmaxf(fmaxf(fminf(a0, a1), fminf(b0, bb1)), fmaxf(fminf(c0, c1), 0.f));
+        float hi0 = fminf(fminf(fmaxf(a0, a1), fmaxf(b0, bb1)), fminf(fmaxf(c0, c1), best));
+        float d0 = n1.x * id.x - ood.x, d1 = n1.y * id.x - ood.x;
+        float e0 = n1.z * id.y - ood.y, e1 = n1.w * id.y - ood.y;
+        float f0 = n2.z * id.z - ood.z, f1 = n2.w * id.z - ood.z;
+        float lo1 = fmaxf(fmaxf(fminf(d0, d1), fminf(e0, e1)), fmaxf(fminf(f0, f1), 0.f));
+        float hi1 = fminf(fminf(fmaxf(d0, d1), fmaxf(e0, e1)), fminf(fmaxf(f0, f1), best));
+        bool h0 = lo0 <= hi0, h1 = lo1 <= hi1;
+        int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
+        if (h0 && ch0 < 0) {
+            float t, u, w; int orig;
+            if (tri_test(g.leaf, ~ch0, o, d, best, t, u, w, orig)) {
+                best = t; tri = orig; b1 = u; b2 = w; found = true;
+                if (kAny) { tout = t; return true; }
+            }
+            h0 = false;
+        }
+        if (h1 && ch1 < 0) {
+            float t, u, w; int orig;
+            if (tri_test(g.leaf, ~ch1, o, d, best, t, u, w, orig)) {
+                best = t; tri = orig; b1 = u; b2 = w; found = true;
+                if (kAny) { tout = t; return true; }
+            }
+            h1 = false;
+        }
+        if (h0 && h1) {
+            int nearc = lo0 <= lo1 ? ch0 : ch1, farc = lo0 <= lo1 ? ch1 : ch0;
+            if (sp < kStack) stack[sp++] = farc;
+            node = nearc;
+        } else if (h0) {
+            node = ch0;
+        } else if (h1) {
+            node = ch1;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    if (found) tout = best;
+    return found;
+}
+
+__device__ __forceinline__ bool trace_from(const GeomDev& g, const Surf& s, float3 d, float eps, Surf& hit) {
+    float3 o = offset_point(s.p, s.n, d, eps);
+    int tri; float b1, b2, t;
+    if (!traverse<false>(g, o, d, 3.0e38f, tri, b1, b2, t)) return false;
+    hit = surf_at(g, tri, b1, b2);
+    return true;
+}
+// mutual visibility of surface point a and surface point b (bsurf) or point b
+__device__ bool visible(const GeomDev& g, float3 a, float3 an, float3 b, const float3* bn, float eps) {
+    float3 ao = offset_point(a, an, b - a, eps);
+    float3 bo = bn ? offset_point(b, *bn, a - b, eps) : b;
+    float3 d = bo - ao;
+    float dist = len3(d);
+    if (!(dist > 0.f)) return true;
+    d = d * (1.0f / dist);
+    int tri; float b1, b2, t;
+    return !traverse<true>(g, ao, d, dist, tri, b1, b2, t);
+}
+
+// ============================================================================================
+// sensor rays and back-projection
+// ============================================================================================
+__device__ void primary_ray(const FrameDev& F, int ix, int iy, float u0, float u1, float3& o, float3& d) {
+    o = F.pos;
+    if (F.mode == 1) {
+        float3 w = F.wall_o + (F.wall_u * ((ix + 0.5f) / F.W) + F.wall_v * ((iy + 0.5f) / F.H));
+        d = norm3(w - o);
+        return;
+    }
+    float3 f = norm3(F.fwd);
+    float3 rt = norm3(cross3(f, F.up));
+    float3 up = cross3(rt, f);
+    float th = tanf(0.5f * F.fov_y), asp = (float)F.W / (float)F.H;
+    float sx = (2.0f * (ix + u0) / F.W - 1.0f) * th * asp;
+    float sy = (1.0f - 2.0f * (iy + u1) / F.H) * th;
+    d = norm3(f + (rt * sx + up * sy));
+}
+__device__ bool project(const FrameDev& F, float3 p, int& ix, int& iy) {
+    float3 f = norm3(F.fwd);
+    float3 rt = norm3(cross3(f, F.up));
+    float3 up = cross3(rt, f);
+    float3 d = p - F.pos;
+    float z = dot3(d, f);
+    if (!(z > 0.f)) return false;
+    float th = tanf(0.5f * F.fov_y), asp = (float)F.W / (float)F.H;
+    float sx = dot3(d, rt) / z / (th * asp), sy = dot3(d, up) / z / th;
+    float fx = (sx + 1.0f) * 0.5f * F.W, fy = (1.0f - sy) * 0.5f * F.H;
+    if (!(fx >= 0.f && fy >= 0.f)) return false;
+    int x = (int)floorf(fx), y = (int)floorf(fy);
+    if (x >= F.W || y >= F.H) return false;
+    ix = x; iy = y;
+    return true;
+}
+
+// ============================================================================================
+// domains and lights (Sec. 3.2: each pixel of each frame is an integration domain with its own
+// target; Sec. 5: point light with NEE, laser spot as a secondary emitter)
+// ============================================================================================
+struct Domain {
+    const FrameDev* F;
+    bool valid;
+    float3 x0;
+    Surf y1;
+    float o, L0, dL;
+    LightDev light;
+    float3 spot_n;   // spot surface normal (kind 2)
+    int spot_mat;
+};
+
+__device__ void resolve_spot(const GeomDev& g, LightDev& L, float3& sn, int& smat) {
+    Surf s = surf_at(g, L.s_tri, L.s_b1, L.s_b2);
+    L.pos = s.p; sn = s.n; smat = s.mat;
+}
+
+__device__ Domain make_domain(const FrameDev* F, int pix, float L0, float dL) {
+    Domain D;
+    D.F = F;
+    D.x0 = F->pos;
+    D.L0 = L0; D.dL = dL;
+    D.light.kind = 0;
+    float4 gb = __ldg(&F->gb[pix]);
+    uint32_t tri = __float_as_uint(gb.x);
+    D.valid = tri != kNoHit;
+    D.o = 0.f;
+    D.spot_n = f3(0.f, 0.f, 1.f);
+    D.spot_mat = 0;
+    if (!D.valid) return D;
+    D.y1 = surf_at(F->g, (int)tri, gb.y, gb.z);
+    D.o = F->mode == 1 ? 2.0f * gb.w : 0.f;
+    if (F->etype == 0) {
+        D.light.kind = 1; D.light.pos = F->epos; D.light.I = F->epower;
+    } else if (F->etype == 1) {
+        D.light = *F->laser;
+        if (D.light.kind == 2) resolve_spot(F->g, D.light, D.spot_n, D.spot_mat);
+    } else {
+        D.light.kind = 2; D.light.s_tri = D.y1.tri; D.light.s_b1 = D.y1.b1; D.light.s_b2 = D.y1.b2;
+        D.light.I = F->epower;
+        D.light.to_origin = dir_to(D.y1.p, F->epos);
+        D.light.emit_len = len3(F->epos - D.y1.p);
+        D.light.pos = D.y1.p;
+        D.spot_n = D.y1.n; D.spot_mat = D.y1.mat;
+    }
+    return D;
+}
+
+__device__ __forceinline__ bool light_same(const LightDev& a, const LightDev& b) {
+    if (a.kind != b.kind) return false;
+    if (a.kind == 0) return true;
+    if (a.pos.x != b.pos.x || a.pos.y != b.pos.y || a.pos.z != b.pos.z || a.I != b.I) return false;
+    if (a.kind == 2) {
+        if (a.s_tri != b.s_tri || a.s_b1 != b.s_b1 || a.s_b2 != b.s_b2) return false;
+        if (a.to_origin.x != b.to_origin.x || a.to_origin.y != b.to_origin.y || a.to_origin.z != b.to_origin.z) return false;
+        if (a.emit_len != b.emit_len) return false;
+    }
+    return true;
+}
+
+// light factor I_e |cos_x| / d^2 of a path ending at x (no BSDF, no visibility); wl, seg out
+__device__ float light_term(const Domain& D, const Surf& x, float3& wl, float& seg) {
+    const LightDev& L = D.light;
+    float3 lp = L.pos;
+    float I = 0.f;
+    if (L.kind == 1) I = L.I;
+    else if (L.kind == 2) {
+        float3 w = dir_to(L.pos, x.p);
+        Mat sm = load_mat(D.F->g, D.spot_mat);
+        I = L.I * bsdf_f(sm, D.spot_n, L.to_origin, w) * fabsf(dot3(D.spot_n, w));
+    }
+    float3 dd = lp - x.p;
+    float dist = len3(dd);
+    if (!(dist > 0.f) || !(I > 0.f)) return 0.f;
+    wl = dd * (1.0f / dist);
+    seg = dist + (L.kind == 2 ? L.emit_len : 0.f);
+    return I * fabsf(dot3(x.n, wl)) / (dist * dist);
+}
+__device__ __forceinline__ bool light_visible(const Domain& D, const GeomDev& g, const Surf& x, float eps) {
+    if (D.light.kind == 2) return visible(g, x.p, x.n, D.light.pos, &D.spot_n, eps);
+    return visible(g, x.p, x.n, D.light.pos, nullptr, eps);
+}
+
+__device__ __forceinline__ float Gterm(const Surf& a, const Surf& b) {
+    float3 d = b.p - a.p;
+    float d2 = dot3(d, d);
+    if (!(d2 > 0.f)) return 0.f;
+    float3 w = d * (1.0f / sqrtf(d2));
+    return fabsf(dot3(a.n, w)) * fabsf(dot3(b.n, w)) / d2;
+}
+
+// ============================================================================================
+// reservoir records: decoded form and the 6-plane float4 encoding
+//   P0 (W, phat, tau, Lsuf)   P1 (key_px, key_frame, meta, pdf_pre)   P2 (xprev.xyz, p_tri)
+//   P3 (p_b1, p_b2, s0_tri, s0_b1)   P4 (s0_b2, s1_tri, s1_b1, s1_b2)   P5 (s2_tri, s2_b1, s2_b2, 0)
+//   meta: tree [0,8) | k [8,11) | r [11,14) | ns [14,16) | class of x_1..x_4, 2 bits each [16,24)
+// (Sec. 5: the reservoir stores the vertex after the reconnection vertex; the reconnection
+//  radiance Lsuf is attached to it)
+// ============================================================================================
+struct Rec {
+    float W, phat, tau, Lsuf;
+    uint32_t key_px, key_frame, meta;
+    float pdf_pre;
+    float3 xprev;
+    int p_tri;
+    float p_b1, p_b2;
+    int s_tri[3];
+    float s_b1[3], s_b2[3];
+};
+__device__ __forceinline__ int rec_tree(const Rec& r) { return (int)(r.meta & 0xFFu); }
+__device__ __forceinline__ int rec_k(const Rec& r) { return (int)((r.meta >> 8) & 7u); }
+__device__ __forceinline__ int rec_r(const Rec& r) { return (int)((r.meta >> 11) & 7u); }
+__device__ __forceinline__ int rec_ns(const Rec& r) { return (int)((r.meta >> 14) & 3u); }
+__device__ __forceinline__ int rec_cls(const Rec& r, int j) { return (int)((r.meta >> (16 + 2 * (j - 1))) & 3u); }
+
+__device__ __forceinline__ void rec_store(const ResDev& R, size_t idx, const Rec& r) {
+    float4* P = R.planes;
+    const size_t s = R.stride;
+    P[idx] = make_float4(r.W, r.phat, r.tau, r.Lsuf);
+    P[s + idx] = make_float4(__uint_as_float(r.key_px), __uint_as_float(r.key_frame), __uint_as_float(r.meta), r.pdf_pre);
+    if (rec_r(r) >= 2) {
+        P[2 * s + idx] = make_float4(r.xprev.x, r.xprev.y, r.xprev.z, __int_as_float(r.p_tri));
+        P[3 * s + idx] = make_float4(r.p_b1, r.p_b2, __int_as_float(r.s_tri[0]), r.s_b1[0]);
+        int ns = rec_ns(r);
+        if (ns >= 2) P[4 * s + idx] = make_float4(r.s_b2[0], __int_as_float(r.s_tri[1]), r.s_b1[1], r.s_b2[1]);
+        else if (ns == 1) P[4 * s + idx] = make_float4(r.s_b2[0], 0.f, 0.f, 0.f);
+        if (ns >= 3) P[5 * s + idx] = make_float4(__int_as_float(r.s_tri[2]), r.s_b1[2], r.s_b2[2], 0.f);
+    }
+}
+__device__ __forceinline__ void rec_load(const ResDev& R, size_t idx, Rec& r) {
+    const float4* P = R.planes;
+    const size_t s = R.stride;
+    float4 a = P[idx], b = P[s + idx];
+    r.W = a.x; r.phat = a.y; r.tau = a.z; r.Lsuf = a.w;
+    r.key_px = __float_as_uint(b.x); r.key_frame = __float_as_uint(b.y); r.meta = __float_as_uint(b.z); r.pdf_pre = b.w;
+    if (rec_r(r) >= 2) {
+        float4 c = P[2 * s + idx], d = P[3 * s + idx];
+        r.xprev = f3(c.x, c.y, c.z); r.p_tri = __float_as_int(c.w);
+        r.p_b1 = d.x; r.p_b2 = d.y; r.s_tri[0] = __float_as_int(d.z); r.s_b1[0] = d.w;
+        int ns = rec_ns(r);
+        if (ns >= 1) {
+            float4 e = P[4 * s + idx];
+            r.s_b2[0] = e.x; r.s_tri[1] = __float_as_int(e.y); r.s_b1[1] = e.z; r.s_b2[1] = e.w;
+        }
+        if (ns >= 3) {
+            float4 f = P[5 * s + idx];
+            r.s_tri[2] = __float_as_int(f.x); r.s_b1[2] = f.y; r.s_b2[2] = f.z;
+        }
+    }
+}
+__device__ __forceinline__ bool occ_get(const ResDev& R, int pix, int b) {
+    return (R.occ[(size_t)pix * R.words + (b >> 5)] >> (b & 31)) & 1u;
+}
+
+// ============================================================================================
+// path trees (Sec. 3.2 stage (1); Sec. 5 light source): BSDF-sampled paths with NEE to the
+// delta light at every vertex; the candidate of length k is the NEE path ending at x_k.
+// ============================================================================================
+struct TreeVerts {
+    Surf v[kMaxDepth + 1];     // v[1..depth]
+    float pdfA[kMaxDepth + 1];
+    int cls[kMaxDepth + 1];
+};
+
+// reconnectability of vertex i of x_1..x_k (Sec. 4.1: first consecutive diffuse pair; the
+// perturbation re-evaluates the BSDF after p, so that vertex must be rough or be the light)
+__device__ __forceinline__ bool connectable(const int* cls, const float3* pos, int k, int i, float dmin) {
+    if (cls[i - 1] != C_ROUGH || cls[i] != C_ROUGH) return false;
+    if (len3(pos[i - 1] - pos[i]) <= dmin) return false;
+    if (i < k) {
+        if (cls[i + 1] != C_ROUGH) return false;
+        if (len3(pos[i] - pos[i + 1]) <= dmin) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ int find_r(const int* cls, const float3* pos, int k, float dmin) {
+    for (int i = 2; i <= k; ++i)
+        if (connectable(cls, pos, k, i, dmin)) return i;
+    return 0;
+}
+
+// f(x) in area measure of the NEE path x_1..x_k (no visibility)
+__device__ float path_f(const Domain& D, const TreeVerts& T, int k) {
+    const GeomDev& g = D.F->g;
+    float f = 1.0f;
+    for (int j = 1; j <= k; ++j) {
+        Mat m = load_mat(g, T.v[j].mat);
+        float3 wi = dir_to(T.v[j].p, j == 1 ? D.x0 : T.v[j - 1].p);
+        if (j < k) {
+            if (mat_class(m) == C_DELTA) f *= m.albedo;
+            else f *= bsdf_f(m, T.v[j].n, wi, dir_to(T.v[j].p, T.v[j + 1].p)) * Gterm(T.v[j], T.v[j + 1]);
+        } else {
+            float3 wl; float seg;
+            float lt = light_term(D, T.v[k], wl, seg);
+            f *= bsdf_f(m, T.v[k].n, wi, wl) * lt;
+        }
+    }
+    return f;
+}
+
+// reservoir record of the candidate of length k from tree `tree` (P0's W is filled later)
+__device__ void build_rec(const Domain& D, const TreeVerts& T, int k, int tree, uint32_t px, uint32_t frame, float tau,
+                          const ParamsDev& P, Rec& R) {
+    const GeomDev& g = D.F->g;
+    R.W = 0.f;
+    R.tau = tau;
+    R.key_px = px; R.key_frame = frame;
+    R.phat = path_f(D, T, k);
+    R.Lsuf = 0.f;
+    R.pdf_pre = 1.0f;
+    float3 pos[kMaxDepth + 1];
+    for (int j = 1; j <= k; ++j) pos[j] = T.v[j].p;
+    int r = find_r(T.cls, pos, k, P.d_min);
+    uint32_t meta = (uint32_t)tree | ((uint32_t)k << 8) | ((uint32_t)r << 11);
+    if (r == 0) { R.meta = meta; return; }
+    for (int j = 1; j < r; ++j) meta |= (uint32_t)T.cls[j] << (16 + 2 * (j - 1));
+    int ns = k - r;
+    meta |= (uint32_t)ns << 14;
+    R.meta = meta;
+    R.xprev = T.v[r - 1].p;
+    for (int j = 2; j <= r - 1; ++j) R.pdf_pre *= T.pdfA[j];
+    R.p_tri = T.v[r].tri; R.p_b1 = T.v[r].b1; R.p_b2 = T.v[r].b2;
+    for (int q = 0; q < 3; ++q) { R.s_tri[q] = 0; R.s_b1[q] = 0.f; R.s_b2[q] = 0.f; }
+    for (int q = 0; q < ns; ++q) { R.s_tri[q] = T.v[r + 1 + q].tri; R.s_b1[q] = T.v[r + 1 + q].b1; R.s_b2[q] = T.v[r + 1 + q].b2; }
+    if (ns > 0) {
+        float Ls = 1.0f;
+        for (int j = r + 2; j <= k; ++j) {
+            Mat m = load_mat(g, T.v[j].mat);
+            float gg = T.cls[j - 1] == C_DELTA ? 1.0f : Gterm(T.v[j - 1], T.v[j]);
+            if (mat_class(m) == C_DELTA) { Ls *= gg * m.albedo; continue; }
+            float3 wi = dir_to(T.v[j].p, T.v[j - 1].p);
+            float3 wo;
+            if (j < k) wo = dir_to(T.v[j].p, T.v[j + 1].p);
+            else { float seg; light_term(D, T.v[k], wo, seg); }
+            Ls *= gg * bsdf_f(m, T.v[j].n, wi, wo);
+        }
+        float3 wl; float seg;
+        Ls *= light_term(D, T.v[k], wl, seg);
+        R.Lsuf = Ls;
+    }
+}
+
+// ============================================================================================
+// path-length derivatives (Sec. 4.3 "Gradient and Hessian Evaluation"):
+//   L(p) = |p1 - p| + |p2 - p|, grad_p L = -(d1 + d2), hess_p L = A = sum (I - d d^T)/|p_i - p|,
+//   grad_xi L = J^T grad_p L, hess_xi L = J^T A J (Q = 0 on flat triangles)
+// ============================================================================================
+struct Frame2 { float3 o, t, b; };
+__device__ __forceinline__ Frame2 tri_frame(const GeomDev& g, int tri) {
+    float4 a = __ldg(&g.tri[3 * tri]), e1 = __ldg(&g.tri[3 * tri + 1]), e2 = __ldg(&g.tri[3 * tri + 2]);
+    Frame2 f;
+    f.o = xyz(a);
+    f.t = norm3(xyz(e1));
+    float3 n = norm3(cross3(xyz(e1), xyz(e2)));
+    f.b = cross3(n, f.t);
+    return f;
+}
+__device__ __forceinline__ float3 frame_point(const Frame2& f, float x0, float x1) { return f.o + (f.t * x0 + f.b * x1); }
+
+__device__ __forceinline__ void length_derivs(float3 p1, float3 p2, const Frame2& f, float x0, float x1, float& L,
+                                              float g[2], float h[3]) {
+    float3 p = frame_point(f, x0, x1);
+    float3 a1 = p1 - p, a2 = p2 - p;
+    float l1 = len3(a1), l2 = len3(a2);
+    float3 d1 = a1 * (1.0f / l1), d2 = a2 * (1.0f / l2);
+    float3 s = d1 + d2;
+    L = l1 + l2;
+    g[0] = -dot3(f.t, s);
+    g[1] = -dot3(f.b, s);
+    float d1t = dot3(d1, f.t), d1b = dot3(d1, f.b), d2t = dot3(d2, f.t), d2b = dot3(d2, f.b);
+    h[0] = (1.0f - d1t * d1t) / l1 + (1.0f - d2t * d2t) / l2;
+    h[1] = (-d1t * d1b) / l1 + (-d2t * d2b) / l2;
+    h[2] = (1.0f - d1b * d1b) / l1 + (1.0f - d2b * d2b) / l2;
+}
+
+struct NewtonGeo { float3 p1x, p2x; Frame2 fx; float3 p1y, p2y; Frame2 fy; };
+
+// F(xi, xi') = [L_y(xi') - L_x(xi) - delta ; (R m)^T (xi' - xi)], m = (grad L_x(xi) + grad L_y(xi'))/2,
+// R = 90-degree rotation; each gradient on its own path (Sec. 4.3, average-gradient gauge)
+__device__ __forceinline__ void newton_F(const NewtonGeo& N, const float xi[2], float Lx, const float gx[2], float delta,
+                                         const float xp[2], float F[2], float gy[2], float hy[3], float m[2]) {
+    float Ly;
+    length_derivs(N.p1y, N.p2y, N.fy, xp[0], xp[1], Ly, gy, hy);
+    m[0] = 0.5f * (gx[0] + gy[0]);
+    m[1] = 0.5f * (gx[1] + gy[1]);
+    F[0] = Ly - Lx - delta;
+    F[1] = -m[1] * (xp[0] - xi[0]) + m[0] * (xp[1] - xi[1]);
+}
+// dF/dxi' rows: (grad L_y(xi'), R m - 0.5 H_y R (xi' - xi)); dF/dxi rows: (-grad L_x(xi), -(R m + 0.5 H_x R (xi' - xi)))
+__device__ __forceinline__ void newton_J(const float xi[2], const float xp[2], const float gx[2], const float hx[3],
+                                         const float gy[2], const float hy[3], const float m[2], float A[4], float Bm[4]) {
+    float Rm0 = -m[1], Rm1 = m[0];
+    float dd0 = xp[0] - xi[0], dd1 = xp[1] - xi[1];
+    float Rd0 = -dd1, Rd1 = dd0;
+    float HyRd0 = hy[0] * Rd0 + hy[1] * Rd1, HyRd1 = hy[1] * Rd0 + hy[2] * Rd1;
+    float HxRd0 = hx[0] * Rd0 + hx[1] * Rd1, HxRd1 = hx[1] * Rd0 + hx[2] * Rd1;
+    A[0] = gy[0]; A[1] = gy[1]; A[2] = Rm0 - 0.5f * HyRd0; A[3] = Rm1 - 0.5f * HyRd1;
+    Bm[0] = -gx[0]; Bm[1] = -gx[1]; Bm[2] = -(Rm0 + 0.5f * HxRd0); Bm[3] = -(Rm1 + 0.5f * HxRd1);
+}
+
+// Newton iteration with backtracking (Sec. 4.3); returns success, xi', |det(dxi'/dxi)| and the
+// iteration count.  Stops at |F|_inf <= tol_stop or after max_iter; success if |F|_inf <= tol_succ.
+__device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float delta, int max_iter, float tol_stop,
+                             float tol_succ, float xp[2], float& jdet, int& iters) {
+    float Lx, gx[2], hx[3];
+    length_derivs(N.p1x, N.p2x, N.fx, xi[0], xi[1], Lx, gx, hx);
+    xp[0] = xi[0]; xp[1] = xi[1];
+    float F[2], gy[2], hy[3], m[2];
+    newton_F(N, xi, Lx, gx, delta, xp, F, gy, hy, m);
+    int it = 0;
+    while (it < max_iter) {
+        float nF = fmaxf(fabsf(F[0]), fabsf(F[1]));
+        if (nF <= tol_stop) break;
+        float A[4], Bm[4];
+        newton_J(xi, xp, gx, hx, gy, hy, m, A, Bm);
+        float det = A[0] * A[3] - A[1] * A[2];
+        if (!(fabsf(det) > 1e-30f)) break;
+        float s0 = -(A[3] * F[0] - A[1] * F[1]) / det, s1 = -(-A[2] * F[0] + A[0] * F[1]) / det;
+        float lam = 1.0f;
+        bool accepted = false;
+        for (int ls = 0; ls < 5; ++ls) {
+            float c[2] = {xp[0] + lam * s0, xp[1] + lam * s1};
+            float Fc[2], gyc[2], hyc[3], mc[2];
+            newton_F(N, xi, Lx, gx, delta, c, Fc, gyc, hyc, mc);
+            if (fmaxf(fabsf(Fc[0]), fabsf(Fc[1])) < nF) {
+                xp[0] = c[0]; xp[1] = c[1];
+                F[0] = Fc[0]; F[1] = Fc[1];
+                gy[0] = gyc[0]; gy[1] = gyc[1]; hy[0] = hyc[0]; hy[1] = hyc[1]; hy[2] = hyc[2];
+                m[0] = mc[0]; m[1] = mc[1];
+                accepted = true;
+                break;
+            }
+            lam *= 0.5f;
+        }
+        if (!accepted) break;
+        ++it;
+    }
+    iters = it;
+    if (!(fmaxf(fabsf(F[0]), fabsf(F[1])) <= tol_succ)) return false;
+    float A[4], Bm[4];
+    newton_J(xi, xp, gx, hx, gy, hy, m, A, Bm);
+    float dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
+    if (!(fabsf(dA) > 0.f)) return false;
+    jdet = fabsf(dB / dA);
+    return isfinite(jdet);
+}
+
+// ============================================================================================
+// the shift map (Sec. 4.1-4.3): hybrid shift of the record x from domain Dj to domain Di --
+// random replay of x_2..x_{r-1} from y_1, reconnection at p = x_r, path-length-aware
+// perturbation of p on its triangle -- returning the offset record, its target in Di and the
+// Jacobian |dS/dx| (replay pdf ratios times the Newton determinant; the in-plane frames are
+// orthonormal, so the frame factor is 1).
+// ============================================================================================
+struct ShiftStats { uint32_t newton_calls, newton_iters, newton_ok, shift_calls, shift_ok; };
+
+__device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& Di, const ParamsDev& P, bool geom_static, Rec& y,
+                          float& phat_out, float& jac_out, ShiftStats* st) {
+    const int r = rec_r(x);
+    if (r < 2 || !Di.valid || !Dj.valid) return false;
+    const GeomDev& gi = Di.F->g;
+    const GeomDev& gj = Dj.F->g;
+    const int k = rec_k(x), ns = rec_ns(x), tree = rec_tree(x);
+    const float eps = P.ray_eps;
+    if (st) st->shift_calls++;
+
+    // (1) random replay with the base path's random numbers
+    Surf yv[kMaxDepth];
+    yv[1] = Di.y1;
+    float plen = len3(Di.x0 - yv[1].p);
+    float fpre = 1.0f, pdfy = 1.0f;
+    for (int j = 1; j <= r - 2; ++j) {
+        uint4 u = philox(x.key_px, x.key_frame, ((uint32_t)tree << 8) | (uint32_t)j, P_BSDF, P.seed);
+        float3 wi = dir_to(yv[j].p, j == 1 ? Di.x0 : yv[j - 1].p);
+        Mat m = load_mat(gi, yv[j].mat);
+        if (mat_class(m) != rec_cls(x, j)) return false;
+        float3 wo; float pdf, thr; bool delta;
+        if (!bsdf_sample(m, yv[j].n, wi, u01(u.x), u01(u.y), wo, pdf, thr, delta)) return false;
+        if (!trace_from(gi, yv[j], wo, eps, yv[j + 1])) return false;
+        float seg = len3(yv[j + 1].p - yv[j].p);
+        plen += seg;
+        if (delta) fpre *= m.albedo;
+        else {
+            fpre *= bsdf_f(m, yv[j].n, wi, wo) * Gterm(yv[j], yv[j + 1]);
+            pdfy *= pdf * fabsf(dot3(yv[j + 1].n, wo)) / (seg * seg);
+        }
+    }
+    if (mat_class(load_mat(gi, yv[r - 1].mat)) != rec_cls(x, r - 1)) return false;
+
+    // (2) suffix and light in the target domain
+    Surf sv[3];
+    for (int q = 0; q < ns; ++q) sv[q] = surf_at(gi, x.s_tri[q], x.s_b1[q], x.s_b2[q]);
+    if (Di.light.kind == 0) return false;
+    float3 lpos_i = Di.light.pos;
+    float emit_i = Di.light.kind == 2 ? Di.light.emit_len : 0.f;
+    float slen = 0.f;
+    for (int q = 0; q + 1 < ns; ++q) slen += len3(sv[q].p - sv[q + 1].p);
+    if (ns > 0) slen += len3(sv[ns - 1].p - lpos_i) + emit_i;
+    else slen += emit_i;
+    float3 p2y = ns > 0 ? sv[0].p : lpos_i;
+
+    // (3) base-path quantities in the record's own frame
+    NewtonGeo N;
+    N.fx = tri_frame(gj, x.p_tri);
+    Surf pbase = surf_at(gj, x.p_tri, x.p_b1, x.p_b2);
+    float3 p2x = ns > 0 ? surf_at(gj, x.s_tri[0], x.s_b1[0], x.s_b2[0]).p : Dj.light.pos;
+    float xi[2];
+    {
+        float3 dd = pbase.p - N.fx.o;
+        xi[0] = dot3(dd, N.fx.t);
+        xi[1] = dot3(dd, N.fx.b);
+    }
+    N.p1x = x.xprev; N.p2x = p2x;
+    N.p1y = yv[r - 1].p; N.p2y = p2y; N.fy = tri_frame(gi, x.p_tri);
+
+    // (4) Newton solve of L(y') = L(x) + delta (eq. path_length_constraint), delta keeping the
+    // sample at the same position inside the target gate
+    float Lx_seg = len3(x.xprev - pbase.p) + len3(p2x - pbase.p);
+    float ell = x.tau - Dj.L0 + Di.L0 + Di.o - plen - slen;
+    float delta = ell - Lx_seg;
+    float xp[2];
+    float jn = 1.0f;
+    if (P.flags & 2u) {
+        xp[0] = xi[0]; xp[1] = xi[1];
+    } else {
+        int iters = 0;
+        float tol_stop = 1e-6f * fabsf(x.tau + Di.o + Di.L0 - Dj.L0);
+        float tol_succ = P.newton_tol_frac * Di.dL;
+        bool ok = newton_solve(N, xi, delta, P.newton_max_iter, tol_stop, tol_succ, xp, jn, iters);
+        if (st) { st->newton_calls++; st->newton_iters += iters; if (ok) st->newton_ok++; }
+        if (!ok) return false;
+        if (!(jn >= 1.0f / P.jac_max && jn <= P.jac_max)) return false;
+    }
+    float nb1, nb2;
+    {
+        float4 a = __ldg(&gi.tri[3 * x.p_tri]), e1v = __ldg(&gi.tri[3 * x.p_tri + 1]), e2v = __ldg(&gi.tri[3 * x.p_tri + 2]);
+        (void)a;
+        float3 e1 = xyz(e1v), e2 = xyz(e2v);
+        float e1t = dot3(e1, N.fy.t), e2t = dot3(e2, N.fy.t), e2b = dot3(e2, N.fy.b);
+        nb2 = xp[1] / e2b;
+        nb1 = (xp[0] - nb2 * e2t) / e1t;
+    }
+    if (!(nb1 >= 0.f && nb2 >= 0.f && nb1 + nb2 <= 1.0f)) return false;
+    Surf pp = surf_at(gi, x.p_tri, nb1, nb2);
+
+    // (5) the offset path must reconnect at the same index
+    {
+        int cls[kMaxDepth + 2];
+        float3 pos[kMaxDepth + 2];
+        for (int j = 1; j <= r - 1; ++j) { cls[j] = mat_class(load_mat(gi, yv[j].mat)); pos[j] = yv[j].p; }
+        cls[r] = mat_class(load_mat(gi, pp.mat)); pos[r] = pp.p;
+        for (int q = 0; q < ns; ++q) { cls[r + 1 + q] = mat_class(load_mat(gi, sv[q].mat)); pos[r + 1 + q] = sv[q].p; }
+        if (find_r(cls, pos, k, P.d_min) != r) return false;
+    }
+
+    // (6) visibility of the two reconnection segments
+    if (!visible(gi, yv[r - 1].p, yv[r - 1].n, pp.p, &pp.n, eps)) return false;
+    if (ns > 0) { if (!visible(gi, pp.p, pp.n, sv[0].p, &sv[0].n, eps)) return false; }
+    else if (!light_visible(Di, gi, pp, eps)) return false;
+
+    // (7) target function in Di
+    float3 wprev = dir_to(yv[r - 1].p, r - 1 == 1 ? Di.x0 : yv[r - 2].p);
+    float f = fpre;
+    f *= bsdf_f(load_mat(gi, yv[r - 1].mat), yv[r - 1].n, wprev, dir_to(yv[r - 1].p, pp.p));
+    f *= Gterm(yv[r - 1], pp);
+    float Lsuf_i = x.Lsuf;
+    Mat mp = load_mat(gi, pp.mat);
+    if (ns == 0) {
+        float3 wl; float seg;
+        float lt = light_term(Di, pp, wl, seg);
+        f *= bsdf_f(mp, pp.n, dir_to(pp.p, yv[r - 1].p), wl) * lt;
+    } else {
+        f *= bsdf_f(mp, pp.n, dir_to(pp.p, yv[r - 1].p), dir_to(pp.p, sv[0].p));
+        f *= Gterm(pp, sv[0]);
+        float3 wnext = ns > 1 ? dir_to(sv[0].p, sv[1].p) : dir_to(sv[0].p, lpos_i);
+        f *= bsdf_f(load_mat(gi, sv[0].mat), sv[0].n, dir_to(sv[0].p, pp.p), wnext);
+        bool cache_ok = geom_static && light_same(Dj.light, Di.light);
+        if (!cache_ok) {
+            // Sec. 5: re-evaluate the reconnection information when the scene or light differs
+            float Ls = 1.0f;
+            for (int q = 1; q < ns; ++q) {
+                Mat mq = load_mat(gi, sv[q].mat);
+                float gg = mat_class(load_mat(gi, sv[q - 1].mat)) == C_DELTA ? 1.0f : Gterm(sv[q - 1], sv[q]);
+                if (mat_class(mq) == C_DELTA) {
+                    if (!geom_static) return false;
+                    Ls *= gg * mq.albedo;
+                } else {
+                    float3 wn = q + 1 < ns ? dir_to(sv[q].p, sv[q + 1].p) : dir_to(sv[q].p, lpos_i);
+                    Ls *= gg * bsdf_f(mq, sv[q].n, dir_to(sv[q].p, sv[q - 1].p), wn);
+                }
+                if (!visible(gi, sv[q - 1].p, sv[q - 1].n, sv[q].p, &sv[q].n, eps)) return false;
+            }
+            float3 wl; float seg;
+            Ls *= light_term(Di, sv[ns - 1], wl, seg);
+            if (!light_visible(Di, gi, sv[ns - 1], eps)) return false;
+            Lsuf_i = Ls;
+        }
+        f *= Lsuf_i;
+    }
+    float Lnew = plen + len3(yv[r - 1].p - pp.p) + len3(pp.p - p2y) + slen;
+    float tau = Lnew - Di.o;
+    if (!(tau >= Di.L0 && tau < Di.L0 + Di.dL)) return false;
+    if (!(f > 0.f) || !isfinite(f)) return false;
+
+    // (8) Jacobian
+    float jac = (x.pdf_pre / pdfy) * jn;
+    if (!(jac > 0.f) || !isfinite(jac)) return false;
+
+    y = x;
+    y.tau = tau;
+    y.xprev = yv[r - 1].p;
+    y.pdf_pre = pdfy;
+    y.p_b1 = nb1; y.p_b2 = nb2;
+    y.Lsuf = Lsuf_i;
+    y.phat = f;
+    phat_out = f;
+    jac_out = jac;
+    if (st) st->shift_ok++;
+    return true;
+}
+
+}  // namespace tof

@@ -1,0 +1,123 @@
+// tof_internal.h -- device-visible data layouts shared by the kernels and the host runtime of
+// libtof.so (not part of the public C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tof {
+
+constexpr int kMaxDepth = 5;        // surface vertices per path
+constexpr int kMaxCand = 64;        // path trees per pixel
+constexpr int kMaxNb = 8;           // spatial neighbours per pass
+constexpr int kMaxSlots = 1 + kMaxNb;
+constexpr int kStack = 64;          // BVH traversal stack
+constexpr int kMaxBinsPerPixel = 32;  // distinct transient bins a pixel's initial candidates may hit
+constexpr uint32_t kNoHit = 0xFFFFFFFFu;
+
+// material record: (type, albedo, alpha, unused)
+// triangle record (original order): 3 float4 = (v0.xyz, material id bits), (e1.xyz, 0), (e2.xyz, 0)
+// triangle record (leaf order):     3 float4 = (v0.xyz, original id bits), (e1.xyz, 0), (e2.xyz, 0)
+// internal node: 4 float4 = (c0 lo.x, hi.x, lo.y, hi.y), (c1 lo.x, hi.x, lo.y, hi.y),
+//                           (c0 lo.z, hi.z, c1 lo.z, hi.z), (child0 bits, child1 bits, 0, 0)
+//                child >= 0: internal node, child < 0: leaf ~child.
+struct GeomDev {
+    const float4* tri;
+    const float4* leaf;
+    const float4* nodes;
+    const float4* mats;
+    int nt;
+    uint32_t version;
+};
+
+// resolved light of one domain (Sec. 5 "Light Source")
+struct LightDev {
+    int kind;          // 0 none, 1 point, 2 spot (laser / confocal)
+    float3 pos;        // point position or spot position
+    float I;           // intensity (point) or laser power (spot)
+    int s_tri;         // spot surface
+    float s_b1, s_b2;
+    float3 to_origin;  // spot -> laser origin
+    float emit_len;    // laser origin -> spot
+};
+
+// one frame of one view: geometry, sensor, emitter, gate, G-buffer
+struct FrameDev {
+    GeomDev g;
+    int mode, W, H;
+    float3 pos, fwd, up;
+    float fov_y;
+    float3 wall_o, wall_u, wall_v;
+    int etype;
+    float3 epos, edir;
+    float epower;
+    const LightDev* laser;   // resolved laser spot (etype == 1)
+    float L0, dL;            // gate, or (t0, width) of the bins
+    int B;                   // 0 gated, else bins
+    uint32_t frame;
+    const float4* gb;        // (tri bits, b1, b2, t) per pixel
+};
+
+// reservoir buffer: 6 planes of float4 with `stride` entries each, per-pixel confidence M and
+// one occupancy bit per (pixel, bin)
+struct ResDev {
+    float4* planes;          // plane k at planes + k * stride
+    size_t stride;           // W*H*max(B,1)
+    float* M;                // W*H
+    uint32_t* occ;           // W*H*words, words = ceil(max(B,1)/32)
+    int words;
+};
+
+struct ParamsDev {
+    int depth, n_cand, n_spatial, radius, n_spatial_iters, temporal;
+    float m_cap;
+    int newton_max_iter;
+    float newton_tol_frac, jac_max, d_min, ray_eps;
+    uint32_t flags;
+    uint64_t seed;
+};
+
+// shift statistics (device, accumulated): newton calls, iterations, successes, shift calls, ok
+struct StatsDev {
+    unsigned long long v[5];
+};
+
+struct GbufArgs {
+    FrameDev F;
+    float4* gb;
+    ParamsDev P;
+};
+
+struct InitArgs {
+    FrameDev F;
+    ResDev dst;
+    ParamsDev P;
+    float* out;              // gated image if this is the last stage (else null)
+};
+
+struct ReuseArgs {
+    FrameDev cur, prev;
+    ResDev src;              // canonical reservoirs (current frame)
+    ResDev prv;              // previous frame's final reservoirs (temporal)
+    ResDev dst;
+    ParamsDev P;
+    int temporal;            // 1: temporal pass, 0: spatial pass
+    int pass;                // 0 temporal, 1.. spatial
+    int geom_static;         // previous and current geometry identical
+    float* out;              // gated image if last stage
+    StatsDev* stats;
+};
+
+struct SplatArgs {
+    ResDev src;
+    int npix, B;
+    float* out;
+};
+
+struct PtArgs {
+    FrameDev F;
+    ParamsDev P;
+    int spp;
+    float* out;
+};
+
+}  // namespace tof
