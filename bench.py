@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""ToF ReSTIR throughput on one GB300 (or N replicas): dynamic time-gated rendering.
+
+Workload (default): 512 x 512 pinhole sensor, 32-frame sequence of a 66k-triangle scene (a
+200 x 125-cell fBm heightfield = 50k triangles plus 20 spheres of 800 triangles rotating 1 deg
+per frame; GGX / Lambert / mirror 70 / 20 / 10 %), path depth 4, 4 path trees per pixel,
+temporal reuse + 5 spatial neighbours within 30 px, M-cap 20, gate L0 = 8 m, dL = 0.03 m.
+One step = one frame of the whole hot path: BVH refit for the rigid motion, G-buffer, initial
+path-tree RIS, temporal reuse, spatial reuse and the gated image (final shading fused).
+
+Timing: W warm-up frames, then K timed frames, each bracketed by CUDA events on the render
+stream with a 256 MiB L2 flush between frames (outside the events); barrier + synchronize on
+both sides of the timed loop; the max over ranks is taken.  `value` = frames of all ranks /
+time.  `e2e` repeats the loop through host buffers (object transforms uploaded by the call,
+image read back to pinned host memory inside the timed region).
+
+--impl reference times the CPU oracle (FP64, all host cores) on a bounded crop of the same
+workload and prints the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "frames/s at rel-MSE 1e-2, batched/served vs per-launch; p50/p99 frame latency"
+HBM_FALLBACK = 6800.0
+# algorithmic bytes per pixel of one gated reuse (merge) pass with the 96-byte reservoir:
+# own reservoir read 96 + one distinct neighbour reservoir amortised 96 + reservoir write 96 +
+# G-buffer 16 + confidence read/write 8 + occupancy read/write 8
+REUSE_BYTES_PER_PX = 96 + 96 + 96 + 16 + 8 + 8
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def rel_mse(img, ref, eps=1e-2):
+    """mean((I - R)^2 / (R^2 + eps)) after scaling both by the reference's mean."""
+    s = float(np.mean(ref))
+    if s <= 0:
+        return float("nan")
+    I, R = img / s, ref / s
+    return float(np.mean((I - R) ** 2 / (R * R + eps)))
+
+
+def workload(W=512, H=512, frames=32, seed=1):
+    from paper_2605_11536_gb300 import scenes
+    return scenes.heightfield_spheres(W=W, H=H, frames=frames, seed=seed)
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2605_11536_gb300 import tof
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sc = workload(seed=1 + rank)
+    p = sc.params
+    W, H = sc.sensors[0]["W"], sc.sensors[0]["H"]
+    nf = sc.n_frames
+    ctx = tof.tof_create(torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    sptr = stream.cuda_stream
+    sid = tof.tof_scene_upload(ctx, sc.verts, sc.tris, sc.tri_object, sc.materials, sc.object_material)
+    vid = tof.tof_view_create(ctx, sid, W, H, 0)
+    tof.tof_view_profile(ctx, vid, 1)
+    out = torch.zeros(H * W, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    xf32 = [np.ascontiguousarray(sc.xforms[f].reshape(-1), dtype=np.float32) for f in range(nf)]
+
+    def frame(f, refit):
+        tof.tof_bvh_build(ctx, sid, xf32[f % nf], refit_only=refit, stream=sptr)
+        tof.tof_render_gated(ctx, sid, vid, sc.sensors[f % nf], sc.emitters[f % nf], sc.gates[f % nf], p, sc.seed, f,
+                             out.data_ptr(), sptr)
+
+    with torch.cuda.stream(stream):
+        for f in range(args.warmup):
+            frame(f, 0 if f == 0 else 1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_acc = {k: [] for k in tof.STAGES}
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    t0 = time.perf_counter()
+    with clocks, torch.cuda.stream(stream):
+        for i in range(args.steps):
+            f = args.warmup + i
+            flush.zero_()
+            ev[i][0].record(stream)
+            frame(f, 1)
+            ev[i][1].record(stream)
+            st = tof.tof_view_stage_ms(ctx, vid)
+            for k, v in st.items():
+                stage_acc[k].append(v)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    shift_stats = tof.tof_view_stats(ctx, vid)
+
+    # end to end through host buffers: transforms uploaded by the call, image read back
+    host_img = torch.empty(H * W, dtype=torch.float32, pin_memory=True)
+    vid2 = tof.tof_view_create(ctx, sid, W, H, 0)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup + args.steps):
+            f = i
+            t = time.perf_counter()
+            tof.tof_bvh_build(ctx, sid, xf32[f % nf], refit_only=1, stream=sptr)
+            tof.tof_render_gated(ctx, sid, vid2, sc.sensors[f % nf], sc.emitters[f % nf], sc.gates[f % nf], p, sc.seed, f,
+                                 out.data_ptr(), sptr)
+            host_img.copy_(out, non_blocking=True)
+            stream.synchronize()
+            if i >= args.warmup:
+                e2e_ms.append((time.perf_counter() - t) * 1e3)
+    last_frame = args.warmup + args.steps - 1
+    img_last = host_img.numpy().astype(np.float64).reshape(H, W).copy()
+
+    # quality: relMSE of the last frame against a high-spp plain path-traced reference, and plain
+    # path tracing at equal time
+    quality = {}
+    if rank == 0 and not args.no_quality:
+        fq = last_frame % nf
+        tof.tof_bvh_build(ctx, sid, xf32[fq], refit_only=1, stream=sptr)
+        ref = torch.zeros(H * W, device=dev)
+        with torch.cuda.stream(stream):
+            ref_spp = args.ref_spp
+            acc = torch.zeros(H * W, device=dev, dtype=torch.float64)
+            chunk = 64
+            for c0 in range(0, ref_spp, chunk):
+                tof.tof_render_pt(ctx, sid, sc.sensors[fq], sc.emitters[fq], sc.gates[fq], None, p, 9000 + c0, fq, chunk,
+                                  ref.data_ptr(), sptr)
+                acc += ref.double()
+            stream.synchronize()
+            refimg = (acc / (ref_spp // chunk)).cpu().numpy().reshape(H, W)
+            ms_frame = float(np.median(step_ms))
+            # plain PT at (approximately) equal time
+            pt_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            spp = 1
+            pt_ms = 0.0
+            for _ in range(8):
+                pt_ev[0].record(stream)
+                tof.tof_render_pt(ctx, sid, sc.sensors[fq], sc.emitters[fq], sc.gates[fq], None, p, 77, fq, spp,
+                                  ref.data_ptr(), sptr)
+                pt_ev[1].record(stream)
+                stream.synchronize()
+                pt_ms = pt_ev[0].elapsed_time(pt_ev[1])
+                if pt_ms >= ms_frame or spp >= 4096:
+                    break
+                spp = max(spp + 1, int(spp * ms_frame / max(pt_ms, 1e-3)))
+            ptimg = ref.cpu().numpy().astype(np.float64).reshape(H, W)
+        e_restir = rel_mse(img_last, refimg)
+        e_pt = rel_mse(ptimg, refimg)
+        quality = {"frame": int(fq), "ref_spp": int(args.ref_spp), "relmse_restir": e_restir, "relmse_pt_equal_time": e_pt,
+                   "pt_spp": spp, "pt_ms": pt_ms, "restir_ms": ms_frame,
+                   "restir_vs_pt_inv_mse_time": (1.0 / (e_restir * ms_frame)) / (1.0 / (e_pt * pt_ms))
+                   if e_restir > 0 and e_pt > 0 else None}
+    tof.tof_destroy(ctx)
+    return dict(step_ms=step_ms, dev_s=dev_s, wall=wall, stages=stage_acc, e2e_ms=e2e_ms, clocks=clocks.summary(),
+                quality=quality, stats=shift_stats, npix=W * H, W=W, H=H, nobj=len(sc.object_material))
+
+
+def cpu_baseline(args, crop=None, frames=3):
+    """The oracle as it stands on the host cores (all of them, OpenMP): the first `frames` frames of
+    the workload at full resolution (or on a crop of it, with the margin the spatial reuse needs),
+    timing the frames after the first (temporal + spatial reuse), extrapolated per pixel for a crop."""
+    import oracle as O
+    sc = workload()
+    W, H = sc.sensors[0]["W"], sc.sensors[0]["H"]
+    if crop:
+        R = sc.params.radius * max(1, sc.params.n_spatial_iters)
+        x0, y0 = W // 2 - crop // 2 - R, H // 2 - crop // 2 - R
+        roi = (x0, y0, x0 + crop + 2 * R, y0 + crop + 2 * R)
+    else:
+        roi = (0, 0, W, H)
+    computed = (roi[2] - roi[0]) * (roi[3] - roi[1])
+    ncores = os.cpu_count() or 1
+    geoms = [O.Geom(sc, f) for f in range(frames)]
+    v = O.View(W, H)
+    O.render_frame(v, geoms[0], sc, 0, roi=roi, nthreads=ncores)
+    t = time.perf_counter()
+    for f in range(1, frames):
+        O.render_frame(v, geoms[f], sc, f, roi=roi, nthreads=ncores)
+    dt = (time.perf_counter() - t) / (frames - 1)
+    fps = 1.0 / (dt * (W * H) / computed)
+    what = "full 512x512 frames" if not crop else "a %dx%d region (%d px incl. reuse margin) of the 512x512 frame, " \
+        "extrapolated per pixel" % (roi[2] - roi[0], roi[3] - roi[1], computed)
+    return {"value": fps, "unit": "frames/s", "cores": ncores, "kind": "oracle",
+            "sample": "FP64 oracle, frames 1..%d (temporal + spatial reuse) on %s, %.2f s per frame"
+                      % (frames - 1, what, dt)}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, timed on the host cores, on a bounded sample per step."""
+    cb = None
+    times = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(args, crop=64, frames=2)
+        if i >= args.warmup:
+            times.append(1.0 / cb["value"])
+    fps = len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / fps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "dynamic gated 512x512, 66k tris, depth 4, temporal + 5 spatial (frame 0 crop)"},
+            "cpu_baseline": {"value": fps, "kind": "oracle", "cores": cb["cores"], "sample": cb["sample"]},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=24)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-spp", type=int, default=512)
+    ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import torch
+    if world > 1:
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    r = run_ours(args, rank, world)
+    dev_s = r["dev_s"]
+    if world > 1:
+        t = torch.tensor([dev_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_s = float(t.item())
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    hbm, hbm_kind = _peaks()
+    K = args.steps
+    value = world * K / dev_s
+    st = {k: float(np.mean(v)) for k, v in r["stages"].items()}
+    dom = max(("gbuffer", "initial", "temporal", "spatial"), key=lambda k: st[k])
+    # dominant stage's launch duration (one launch per pass) measured live with CUDA events
+    dom_ms = st[dom]
+    if dom in ("temporal", "spatial"):
+        achieved = REUSE_BYTES_PER_PX * r["npix"] / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "reuse_kernel (%s pass)" % dom, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "note": "achieved = %d algorithmic B/px x %d px / mean launch time; peak = %s HBM copy bandwidth"
+                        % (REUSE_BYTES_PER_PX, r["npix"], hbm_kind)}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None}
+    e2e_fps = len(r["e2e_ms"]) / (sum(r["e2e_ms"]) / 1e3)
+    steps_sorted = sorted(r["step_ms"])
+    p50 = float(np.percentile(steps_sorted, 50))
+    p99 = float(np.percentile(steps_sorted, 99))
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": dev_s * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "dynamic gated 512x512 x 32 frames, 66k tris (200x125 fBm heightfield + 20 rotating "
+                                   "spheres), depth 4, 4 trees, temporal + 5 spatial within 30 px, L0 8 m dL 0.03 m",
+                       "l2": "256 MiB flush between timed frames", "parallelism": "replicas x%d" % world},
+            "latency_ms": {"p50": p50, "p99": p99},
+            "stage_ms": st,
+            "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 12 * 4 * r["nobj"],
+                    "d2h_bytes_per_step": 4 * r["npix"]},
+            "gpu_launches": 6 * K,
+            "roofline": roof,
+            "clocks": r["clocks"],
+            "quality": r["quality"],
+            "newton": {"calls": r["stats"]["newton_calls"], "mean_iters": r["stats"]["newton_iters"] / max(1, r["stats"]["newton_calls"]),
+                       "newton_sr": r["stats"]["newton_ok"] / max(1, r["stats"]["newton_calls"]),
+                       "shift_sr": r["stats"]["shift_ok"] / max(1, r["stats"]["shift_calls"])},
+            "wall_s": r["wall"]}
+    if not args.no_cpu:
+        try:
+            line["cpu_baseline"] = cpu_baseline(args)
+        except Exception as e:  # the oracle is optional for the GPU number itself
+            line["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

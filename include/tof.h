@@ -165,6 +165,14 @@ tof_status tof_reservoirs_reset(tof_ctx* ctx, tof_view view);
  * shift attempts, out[4] successful shifts.  Synchronises the view's last stream. */
 tof_status tof_view_stats(tof_ctx* ctx, tof_view view, double out[5]);
 
+/* Per-stage timing of a view's frames with CUDA events recorded on the render stream
+ * (enable = 1 turns it on; off by default).  tof_view_stage_ms synchronises that stream and
+ * returns the device durations (ms) of the last rendered frame: out[0] G-buffer (and laser spot),
+ * out[1] initial candidates, out[2] temporal reuse, out[3] spatial reuse (all passes), out[4]
+ * transient splat, out[5] the whole frame.  A stage that did not run reports 0. */
+tof_status tof_view_profile(tof_ctx* ctx, tof_view view, int enable);
+tof_status tof_view_stage_ms(tof_ctx* ctx, tof_view view, float out[6]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,9 @@ struct ViewH {
     bool has_prev = false;
     StatsDev* stats = nullptr;
     cudaStream_t last_stream = nullptr;
+    bool profile = false;
+    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool ran[5] = {false, false, false, false, false};
 };
 
 }  // namespace
@@ -380,6 +383,8 @@ tof_status tof_view_destroy(tof_ctx* c, tof_view id) {
     for (int k = 0; k < 2; ++k) { dfree(c, V.gb[k]); dfree(c, V.laser[k]); }
     for (int k = 0; k < 3; ++k) { dfree(c, V.res[k].planes); dfree(c, V.res[k].M); dfree(c, V.res[k].occ); }
     dfree(c, V.stats);
+    for (int k = 0; k < 7; ++k)
+        if (V.ev[k]) cudaEventDestroy(V.ev[k]);
     V = ViewH();
     return TOF_OK;
 }
@@ -401,6 +406,12 @@ tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[5]) {
     CK(cudaMemcpy(&h, V.stats, sizeof(h), cudaMemcpyDeviceToHost));
     for (int i = 0; i < 5; ++i) out[i] = (double)h.v[i];
     return TOF_OK;
+}
+
+// stage boundaries: ev[0] frame start, ev[1] after G-buffer, ev[2] after initial, ev[3] after
+// temporal, ev[4] after spatial, ev[5] after splat, ev[6] frame end
+static void mark(ViewH& V, int k, cudaStream_t s) {
+    if (V.profile && V.ev[k]) cudaEventRecord(V.ev[k], s);
 }
 
 static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_sensor* sensor, const tof_emitter* emitter,
@@ -427,10 +438,14 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     const int fc = V.has_prev ? 1 - V.cur : V.cur;
     FrameDev F = make_frame(S, S.cur, sensor, emitter, L0, dL, B, frame, V.gb[fc], V.laser[fc]);
     ParamsDev P = to_dev(params, seed);
+    for (int k = 0; k < 5; ++k) V.ran[k] = false;
+    mark(V, 0, s);
     if (emitter->type == TOF_EMIT_LASER) CK(launch_laser(F.g, v3f(emitter->pos), v3f(emitter->dir), emitter->power, V.laser[fc], s));
     GbufArgs ga;
     ga.F = F; ga.gb = V.gb[fc]; ga.P = P;
     CK(launch_gbuffer(ga, s));
+    mark(V, 1, s);
+    V.ran[0] = true;
 
     // temporal reuse needs the previous frame's geometry still resident
     bool temporal = params->temporal && V.has_prev && V.prev_final >= 0 &&
@@ -447,6 +462,8 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     ia.F = F; ia.dst = V.res[out_of(stage)].dev(); ia.P = P;
     ia.out = (stage == stages - 1 && B == 0) ? out : nullptr;
     CK(launch_initial(ia, c->d_err, s));
+    mark(V, 2, s);
+    V.ran[1] = true;
     int src = out_of(stage);
     ++stage;
     ReuseArgs ra;
@@ -463,7 +480,9 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
         CK(launch_reuse(ra, s));
         src = out_of(stage);
         ++stage;
+        V.ran[2] = true;
     }
+    mark(V, 3, s);
     if (params->n_spatial > 0) {
         for (int it = 0; it < params->n_spatial_iters; ++it) {
             ra.prev = F;
@@ -475,19 +494,48 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
             CK(launch_reuse(ra, s));
             src = out_of(stage);
             ++stage;
+            V.ran[3] = true;
         }
     }
+    mark(V, 4, s);
     if (B > 0) {
         SplatArgs sa;
         sa.src = V.res[src].dev(); sa.npix = V.W * V.H; sa.B = B; sa.out = out;
         CK(launch_splat(sa, s));
+        V.ran[4] = true;
     }
+    mark(V, 5, s);
+    mark(V, 6, s);
     V.fd[fc] = F;
     V.geom_slot[fc] = S.cur;
     V.geom_version[fc] = S.version[S.cur];
     V.cur = fc;
     V.prev_final = src;
     V.has_prev = true;
+    return TOF_OK;
+}
+
+tof_status tof_view_profile(tof_ctx* c, tof_view id, int enable) {
+    if (!c || id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return c ? fail(c, TOF_EINVAL, "bad view") : TOF_EINVAL;
+    cudaSetDevice(c->device);
+    ViewH& V = c->views[id];
+    if (enable && !V.ev[0])
+        for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&V.ev[k]));
+    V.profile = enable != 0;
+    return TOF_OK;
+}
+
+tof_status tof_view_stage_ms(tof_ctx* c, tof_view id, float out[6]) {
+    if (!c || !out || id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return c ? fail(c, TOF_EINVAL, "bad view") : TOF_EINVAL;
+    ViewH& V = c->views[id];
+    if (!V.profile || !V.ev[0]) return fail(c, TOF_ESTATE, "profiling is off for view %d", id);
+    cudaSetDevice(c->device);
+    CK(cudaStreamSynchronize(V.last_stream));
+    for (int k = 0; k < 5; ++k) {
+        out[k] = 0.f;
+        if (V.ran[k]) CK(cudaEventElapsedTime(&out[k], V.ev[k], V.ev[k + 1]));
+    }
+    CK(cudaEventElapsedTime(&out[5], V.ev[0], V.ev[6]));
     return TOF_OK;
 }
 

@@ -266,17 +266,18 @@ def box_icosphere(W: int = 64, H: int = 64, seed: int = 0, frames: int = 1) -> S
 
 def heightfield_spheres(W: int = 512, H: int = 512, frames: int = 32, seed: int = 1,
                         nx: int = 200, ny: int = 125, n_spheres: int = 20,
-                        sphere_stacks: int = 21, sphere_slices: int = 20) -> Scene:
+                        sphere_stacks: int = 21, sphere_slices: int = 20,
+                        extent=(20.0, 12.5), cam=(0.0, -3.6, 1.7), look=(0.0, 0.8, 0.2)) -> Scene:
     """Dynamic time-gated workload: a 200 x 125-cell fBm heightfield (50,000 triangles, 20 m x
-    12.5 m, amplitude 0.2 m) plus 20 spheres of 800 triangles (r = 0.5 m) resting on it, each
-    rotating rigidly 1 deg/frame about a seeded axis through a seeded pivot within 2 m.  Materials
-    per object: GGX (alpha ~ U[0.05, 0.5]) on 70 %, Lambert on 20 %, mirror on 10 %; the
-    heightfield is one of the Lambertian objects.  Coaxial camera and point light 2.2 m above the
-    ground.  Depth 4, temporal + 5 spatial neighbours within 30 px, M-cap 20, L0 = 8 m,
-    dL = 0.03 m."""
+    12.5 m, amplitude 0.2 m) plus 20 spheres of 800 triangles (radius U[0.4, 0.95] m) resting on it
+    within a few metres of the sensor, each rotating rigidly 1 deg/frame about a seeded axis through a
+    seeded pivot within 2 m.  Materials per object: GGX (alpha ~ U[0.05, 0.5]) on 70 %, Lambert on
+    20 %, mirror on 10 %; the heightfield is one of the Lambertian objects.  A coaxial camera and
+    point light 1.7 m above the ground look into the cluster (a proximity time-gated sensor).
+    Depth 4, temporal + 5 spatial neighbours within 30 px, M-cap 20, L0 = 8 m, dL = 0.03 m."""
     rng = np.random.default_rng(seed)
     b = _Builder()
-    sx, sy = 20.0, 12.5
+    sx, sy = extent
     hv, hf, hgrid, xs, ys = heightfield(rng, nx, ny, sx, sy, 0.2)
     nobj = 1 + n_spheres
     n_ggx = int(round(0.7 * nobj))
@@ -294,13 +295,14 @@ def heightfield_spheres(W: int = 512, H: int = 512, frames: int = 32, seed: int 
     sv, sf = uv_sphere(sphere_stacks, sphere_slices)
     centres, axes, pivots = [], [], []
     for s in range(n_spheres):
-        cx = rng.uniform(-4.0, 4.0)
-        cy = rng.uniform(-2.0, 4.0)
+        rad = rng.uniform(0.4, 0.95)
+        cx = rng.uniform(-2.2, 2.2)
+        cy = rng.uniform(-0.6, 2.2)
         i = int(np.clip(round((cx + sx / 2) / sx * nx), 0, nx))
         j = int(np.clip(round((cy + sy / 2) / sy * ny), 0, ny))
-        c = np.array([cx, cy, hgrid[j, i] + 0.5])
+        c = np.array([cx, cy, hgrid[j, i] + rad])
         centres.append(c)
-        b.add(sv * 0.5 + c, sf, 1 + s)
+        b.add(sv * rad + c, sf, 1 + s)
         ax = rng.normal(size=3)
         axes.append(ax / np.linalg.norm(ax))
         off = rng.normal(size=3)
@@ -313,15 +315,15 @@ def heightfield_spheres(W: int = 512, H: int = 512, frames: int = 32, seed: int 
         xf[fr, 0] = _identity34()
         for s in range(n_spheres):
             ang = math.radians(1.0) * fr
-            # rotate about an axis through the pivot; the axis is tilted so spheres stay near
-            # the ground (vertical component of the orbit stays small)
+            # even spheres orbit a nearly vertical axis through their pivot (staying near the
+            # ground), odd spheres spin about a seeded axis through their centre
             xf[fr, 1 + s] = _rot34([0.15 * axes[s][0], 0.15 * axes[s][1], 1.0], ang, pivots[s]) \
                 if s % 2 == 0 else _rot34(axes[s], ang, centres[s])
-    sensor = dict(mode=PINHOLE, pos=[0.0, -4.0, 2.2], fwd=list(np.array([0, 4.0, -2.2]) /
-                  np.linalg.norm([0, 4.0, -2.2])), up=[0, 0, 1], fov_y=math.radians(60), W=W, H=H)
-    emitter = dict(type=EMIT_POINT, pos=[0.0, -4.0, 2.2], dir=[0, 1, 0], power=50.0)
-    p = Params(depth=4, n_cand=4, n_spatial=5, radius=30, n_spatial_iters=1, temporal=1,
-               m_cap=20.0)
+    fwd = np.array(look, dtype=float) - np.array(cam, dtype=float)
+    fwd /= np.linalg.norm(fwd)
+    sensor = dict(mode=PINHOLE, pos=list(cam), fwd=list(fwd), up=[0, 0, 1], fov_y=math.radians(60), W=W, H=H)
+    emitter = dict(type=EMIT_POINT, pos=list(cam), dir=list(fwd), power=20.0)
+    p = Params(depth=4, n_cand=4, n_spatial=5, radius=30, n_spatial_iters=1, temporal=1, m_cap=20.0)
     return Scene("heightfield_spheres", v, f, to, om, np.array(mats, dtype=np.float64), xf,
                  [sensor] * frames, [emitter] * frames, [(8.0, 0.03)] * frames, None, p, seed,
                  meta=dict(centres=np.array(centres).tolist(), kinds=kinds))

@@ -52,7 +52,7 @@ class tof_params(C.Structure):
 
 EXPORTS = ["tof_create", "tof_destroy", "tof_last_error", "tof_device_bytes", "tof_scene_upload", "tof_scene_destroy",
            "tof_bvh_build", "tof_view_create", "tof_view_destroy", "tof_render_gated", "tof_render_transient",
-           "tof_render_pt", "tof_reservoirs_reset", "tof_view_stats"]
+           "tof_render_pt", "tof_reservoirs_reset", "tof_view_stats", "tof_view_profile", "tof_view_stage_ms"]
 
 _vp, _fp, _u32p = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)
 
@@ -78,6 +78,8 @@ def _declare(L):
                                 C.POINTER(tof_bins), C.POINTER(tof_params), C.c_uint64, C.c_uint32, C.c_int32, _vp, _vp]
     L.tof_reservoirs_reset.argtypes = [_vp, C.c_int32]
     L.tof_view_stats.argtypes = [_vp, C.c_int32, C.POINTER(C.c_double)]
+    L.tof_view_profile.argtypes = [_vp, C.c_int32, C.c_int]
+    L.tof_view_stage_ms.argtypes = [_vp, C.c_int32, C.POINTER(C.c_float)]
     for name in EXPORTS:
         if name not in ("tof_last_error", "tof_device_bytes"):
             getattr(L, name).restype = C.c_int32
@@ -224,3 +226,16 @@ def tof_view_stats(ctx, view: int):
     a = (C.c_double * 5)()
     _check(ctx, lib().tof_view_stats(ctx, view, a), "tof_view_stats")
     return dict(newton_calls=a[0], newton_iters=a[1], newton_ok=a[2], shift_calls=a[3], shift_ok=a[4])
+
+
+def tof_view_profile(ctx, view: int, enable: int = 1):
+    _check(ctx, lib().tof_view_profile(ctx, view, int(enable)), "tof_view_profile")
+
+
+STAGES = ("gbuffer", "initial", "temporal", "spatial", "splat", "frame")
+
+
+def tof_view_stage_ms(ctx, view: int):
+    a = (C.c_float * 6)()
+    _check(ctx, lib().tof_view_stage_ms(ctx, view, a), "tof_view_stage_ms")
+    return dict(zip(STAGES, [float(x) for x in a]))

@@ -89,3 +89,28 @@ def test_transient_box():
     g = gpu_render(sc, [0, 1], B=40)
     for f in range(2):
         _check(g[f], o[f])
+
+
+def test_heightfield_full_size_center_region():
+    """The dynamic 512x512 workload (66k triangles, rotating spheres, GGX/Lambert/mirror, depth 4,
+    temporal + 5 spatial within 30 px) rendered at full size on the GPU; the oracle computes a
+    central region that covers the dependency cone of its inner pixels over 3 frames (spatial
+    radius per frame plus motion), and every untainted pixel is compared."""
+    sc = scenes.heightfield_spheres(W=512, H=512, frames=3)
+    frames = [0, 1, 2]
+    half = 130
+    roi = (256 - half, 256 - half, 256 + half, 256 + half)
+    o, oks, st, _ = oracle_render(sc, frames, roi=roi, nthreads=0)
+    g = gpu_render(sc, frames)
+    for f in frames:
+        assert oks[f].sum() >= 40 * 40
+        _check(g[f], o[f], mask=oks[f], min_nonzero=30)
+
+
+def test_heightfield_small_temporal_spatial():
+    sc = scenes.heightfield_spheres(W=96, H=80, frames=4)
+    sc.params.radius = 8
+    o, ok, st, _ = oracle_render(sc, [0, 1, 2, 3])
+    g = gpu_render(sc, [0, 1, 2, 3])
+    for f in range(4):
+        _check(g[f], o[f], min_nonzero=20)
