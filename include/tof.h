@@ -160,18 +160,22 @@ tof_status tof_render_pt(tof_ctx* ctx, tof_scene scene, const tof_sensor* sensor
 /* Forget the view's history (the next frame renders without temporal reuse). */
 tof_status tof_reservoirs_reset(tof_ctx* ctx, tof_view view);
 
-/* Shift statistics accumulated by the view since creation or reset (Table "Newton statistics",
- * Sec. 6): out[0] Newton solves, out[1] Newton iterations, out[2] Newton successes, out[3]
- * shift attempts, out[4] successful shifts.  Synchronises the view's last stream. */
-tof_status tof_view_stats(tof_ctx* ctx, tof_view view, double out[5]);
+/* Shift statistics accumulated by the view since creation (Table "Newton statistics", Sec. 6):
+ * out[0] Newton solves, out[1] Newton iterations, out[2] Newton successes, out[3] forward shift
+ * attempts, out[4] successful forward shifts (these five over forward shifts of every reuse
+ * pass), out[5] inverse (MIS) shift attempts of every pass, out[6] forward and out[7] inverse
+ * shift attempts of the spatial passes alone.  Synchronises the view's last stream. */
+tof_status tof_view_stats(tof_ctx* ctx, tof_view view, double out[8]);
 
 /* Per-stage timing of a view's frames with CUDA events recorded on the render stream
  * (enable = 1 turns it on; off by default).  tof_view_stage_ms synchronises that stream and
  * returns the device durations (ms) of the last rendered frame: out[0] G-buffer (and laser spot),
  * out[1] initial candidates, out[2] temporal reuse, out[3] spatial reuse (all passes), out[4]
- * transient splat, out[5] the whole frame.  A stage that did not run reports 0. */
+ * transient splat, out[5] the whole frame, and the spatial passes' kernels summed over passes:
+ * out[6] setup (slots, units, tasks), out[7] forward shifts, out[8] inverse (MIS) shifts,
+ * out[9] merge.  A stage that did not run reports 0. */
 tof_status tof_view_profile(tof_ctx* ctx, tof_view view, int enable);
-tof_status tof_view_stage_ms(tof_ctx* ctx, tof_view view, float out[6]);
+tof_status tof_view_stage_ms(tof_ctx* ctx, tof_view view, float out[10]);
 
 #ifdef __cplusplus
 }

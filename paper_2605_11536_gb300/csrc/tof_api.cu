@@ -11,13 +11,14 @@
 #include <string>
 #include <vector>
 
-#include "../../include/tof.h"
+#include "tof.h"
 #include "tof_internal.h"
 
 namespace tof {
 cudaError_t launch_gbuffer(const GbufArgs& a, cudaStream_t s);
 cudaError_t launch_initial(const InitArgs& a, int* err, cudaStream_t s);
-cudaError_t launch_reuse(const ReuseArgs& a, cudaStream_t s);
+cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, cudaEvent_t* ev, cudaStream_t s);
+cudaError_t reuse_persist_blocks(int* out);
 cudaError_t launch_splat(const SplatArgs& a, cudaStream_t s);
 cudaError_t launch_pt(const PtArgs& a, cudaStream_t s);
 cudaError_t launch_laser(const GeomDev& g, float3 o, float3 d, float power, LightDev* out, cudaStream_t s);
@@ -90,6 +91,12 @@ struct ViewH {
     bool profile = false;
     cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool ran[5] = {false, false, false, false, false};
+    // wavefront scratch of the reuse passes (sized on first use)
+    WaveDev wave;
+    int wave_slots = 0, wave_cap = 0;
+    std::vector<cudaEvent_t> kev;   // 5 events per timed spatial launch group
+    size_t kev_used = 0;
+    void* wave_ptrs[12] = {nullptr};
 };
 
 }  // namespace
@@ -104,7 +111,8 @@ struct tof_ctx {
     std::vector<DevAlloc> allocs;
     uint32_t version_counter = 0;
     int* d_err = nullptr;
-    float* d_scratch = nullptr;  // scratch image for plain PT temporaries
+    float* d_scratch = nullptr;  // laser spot of plain PT renders
+    int persist_blocks = 0;      // resident blocks of the persistent reuse kernels
 };
 
 static tof_status fail(tof_ctx* c, tof_status st, const char* fmt, ...) {
@@ -382,9 +390,11 @@ tof_status tof_view_destroy(tof_ctx* c, tof_view id) {
     ViewH& V = c->views[id];
     for (int k = 0; k < 2; ++k) { dfree(c, V.gb[k]); dfree(c, V.laser[k]); }
     for (int k = 0; k < 3; ++k) { dfree(c, V.res[k].planes); dfree(c, V.res[k].M); dfree(c, V.res[k].occ); }
+    for (void* p : V.wave_ptrs) dfree(c, p);
     dfree(c, V.stats);
     for (int k = 0; k < 7; ++k)
         if (V.ev[k]) cudaEventDestroy(V.ev[k]);
+    for (cudaEvent_t e : V.kev) cudaEventDestroy(e);
     V = ViewH();
     return TOF_OK;
 }
@@ -397,14 +407,73 @@ tof_status tof_reservoirs_reset(tof_ctx* c, tof_view id) {
     return TOF_OK;
 }
 
-tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[5]) {
+tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[8]) {
     if (!c || !out || id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return c ? fail(c, TOF_EINVAL, "bad view") : TOF_EINVAL;
     cudaSetDevice(c->device);
     ViewH& V = c->views[id];
     StatsDev h;
     CK(cudaStreamSynchronize(V.last_stream));
     CK(cudaMemcpy(&h, V.stats, sizeof(h), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < 5; ++i) out[i] = (double)h.v[i];
+    for (int i = 0; i < 8; ++i) out[i] = (double)h.v[i];
+    return TOF_OK;
+}
+
+// (re)allocate the view's wavefront scratch for S slots per pixel and cap merge units
+static tof_status ensure_wave(tof_ctx* c, ViewH& V, int S, int cap) {
+    if (V.wave_slots >= S && V.wave_cap >= cap) return TOF_OK;
+    for (void*& p : V.wave_ptrs) { dfree(c, p); p = nullptr; }
+    S = S > V.wave_slots ? S : V.wave_slots;
+    cap = cap > V.wave_cap ? cap : V.wave_cap;
+    size_t npix = (size_t)V.W * V.H, U = (size_t)cap;
+    WaveDev& w = V.wave;
+    w.slots = S; w.cap_units = cap;
+    TRY(dalloc(c, &w.slot_pix, sizeof(int) * npix * S, "reuse slots"));
+    TRY(dalloc(c, &w.slot_M, sizeof(float) * npix * S, "reuse confidences"));
+    TRY(dalloc(c, &w.nslot, npix, "reuse slot counts"));
+    TRY(dalloc(c, &w.units, sizeof(int2) * U, "merge units"));
+    TRY(dalloc(c, &w.fwd, sizeof(uint32_t) * U * (S - 1), "forward shift tasks"));
+    TRY(dalloc(c, &w.inv, sizeof(uint32_t) * U * S * (S - 1), "inverse shift tasks"));
+    TRY(dalloc(c, &w.yrec, sizeof(float4) * 6 * U * (S - 1), "shifted records"));
+    TRY(dalloc(c, &w.py, sizeof(float) * U * S, "shifted targets"));
+    TRY(dalloc(c, &w.jac, sizeof(float) * U * S, "shift Jacobians"));
+    TRY(dalloc(c, &w.terms, sizeof(float) * U * S * S, "MIS terms"));
+    TRY(dalloc(c, &w.counters, sizeof(uint32_t) * 4, "task counters"));
+    void* ps[12] = {w.slot_pix, w.slot_M, w.nslot, w.units, w.fwd, w.inv, w.yrec, w.py, w.jac, w.terms, w.counters, nullptr};
+    for (int k = 0; k < 12; ++k) V.wave_ptrs[k] = ps[k];
+    V.wave_slots = S; V.wave_cap = cap;
+    return TOF_OK;
+}
+
+// one reuse pass as a wavefront; transient passes run in pixel chunks so that a chunk's merge
+// units (at most B per pixel) never exceed the scratch capacity
+static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, cudaStream_t s) {
+    const int S = ra.temporal ? 2 : 1 + ra.P.n_spatial;
+    const size_t npix = (size_t)V.W * V.H;
+    const size_t Bn = V.B > 0 ? (size_t)V.B : 1;
+    const size_t kMaxUnits = (size_t)1 << 22;
+    size_t cap = npix * Bn < kMaxUnits ? npix * Bn : kMaxUnits;
+    if (cap < npix && V.B == 0) cap = npix;
+    TRY(ensure_wave(c, V, S, (int)cap));
+    if (!c->persist_blocks) CK(reuse_persist_blocks(&c->persist_blocks));
+    WaveDev w = V.wave;
+    w.slots = S;
+    w.cap_units = V.wave_cap;
+    size_t chunk = V.B > 0 ? (size_t)V.wave_cap / Bn : npix;
+    if (chunk < 1) chunk = 1;
+    for (size_t p0 = 0; p0 < npix; p0 += chunk) {
+        size_t p1 = p0 + chunk < npix ? p0 + chunk : npix;
+        cudaEvent_t* ev = nullptr;
+        if (V.profile && !ra.temporal) {
+            while (V.kev.size() < V.kev_used + 5) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                V.kev.push_back(e);
+            }
+            ev = &V.kev[V.kev_used];
+            V.kev_used += 5;
+        }
+        CK(launch_reuse_wave(ra, w, (int)p0, (int)p1, c->persist_blocks, ev, s));
+    }
     return TOF_OK;
 }
 
@@ -439,6 +508,7 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     FrameDev F = make_frame(S, S.cur, sensor, emitter, L0, dL, B, frame, V.gb[fc], V.laser[fc]);
     ParamsDev P = to_dev(params, seed);
     for (int k = 0; k < 5; ++k) V.ran[k] = false;
+    V.kev_used = 0;
     mark(V, 0, s);
     if (emitter->type == TOF_EMIT_LASER) CK(launch_laser(F.g, v3f(emitter->pos), v3f(emitter->dir), emitter->power, V.laser[fc], s));
     GbufArgs ga;
@@ -477,7 +547,7 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
         ra.temporal = 1; ra.pass = 0;
         ra.geom_static = V.geom_version[1 - fc] == S.version[S.cur];
         ra.out = (stage == stages - 1 && B == 0) ? out : nullptr;
-        CK(launch_reuse(ra, s));
+        TRY(reuse_pass(c, V, ra, s));
         src = out_of(stage);
         ++stage;
         V.ran[2] = true;
@@ -491,7 +561,7 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
             ra.dst = V.res[out_of(stage)].dev();
             ra.temporal = 0; ra.pass = 1 + it; ra.geom_static = 1;
             ra.out = (stage == stages - 1 && B == 0) ? out : nullptr;
-            CK(launch_reuse(ra, s));
+            TRY(reuse_pass(c, V, ra, s));
             src = out_of(stage);
             ++stage;
             V.ran[3] = true;
@@ -525,7 +595,7 @@ tof_status tof_view_profile(tof_ctx* c, tof_view id, int enable) {
     return TOF_OK;
 }
 
-tof_status tof_view_stage_ms(tof_ctx* c, tof_view id, float out[6]) {
+tof_status tof_view_stage_ms(tof_ctx* c, tof_view id, float out[10]) {
     if (!c || !out || id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return c ? fail(c, TOF_EINVAL, "bad view") : TOF_EINVAL;
     ViewH& V = c->views[id];
     if (!V.profile || !V.ev[0]) return fail(c, TOF_ESTATE, "profiling is off for view %d", id);
@@ -536,6 +606,13 @@ tof_status tof_view_stage_ms(tof_ctx* c, tof_view id, float out[6]) {
         if (V.ran[k]) CK(cudaEventElapsedTime(&out[k], V.ev[k], V.ev[k + 1]));
     }
     CK(cudaEventElapsedTime(&out[5], V.ev[0], V.ev[6]));
+    for (int k = 6; k < 10; ++k) out[k] = 0.f;
+    for (size_t g = 0; g + 5 <= V.kev_used; g += 5)
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, V.kev[g + k], V.kev[g + k + 1]));
+            out[6 + k] += ms;
+        }
     return TOF_OK;
 }
 

@@ -14,21 +14,21 @@ namespace tof {
 // ============================================================================================
 // float3 algebra
 // ============================================================================================
-__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
-__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+static __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+static __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+static __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+static __device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+static __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
     return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
-__device__ __forceinline__ float len3(float3 a) { return sqrtf(dot3(a, a)); }
-__device__ __forceinline__ float3 norm3(float3 a) {
+static __device__ __forceinline__ float len3(float3 a) { return sqrtf(dot3(a, a)); }
+static __device__ __forceinline__ float3 norm3(float3 a) {
     float l = len3(a);
     return l > 0.f ? a * (1.0f / l) : f3(0.f, 0.f, 0.f);
 }
-__device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
-__device__ __forceinline__ float3 dir_to(float3 from, float3 to) { return norm3(to - from); }
+static __device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
+static __device__ __forceinline__ float3 dir_to(float3 from, float3 to) { return norm3(to - from); }
 
 // ============================================================================================
 // Philox4x32-10 (Salmon et al., SC 2011) counter-based streams.  Key = 64-bit seed; counter =
@@ -36,7 +36,7 @@ __device__ __forceinline__ float3 dir_to(float3 from, float3 to) { return norm3(
 // ============================================================================================
 enum : uint32_t { P_JITTER = 1, P_BSDF = 2, P_RIS = 3, P_NEIGHBOR = 4, P_MERGE = 5 };
 
-__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t seed) {
+static __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t seed) {
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -48,7 +48,7 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     }
     return make_uint4(c0, c1, c2, c3);
 }
-__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+static __device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
 
 // ============================================================================================
 // materials (Sec. 6: diffuse, glossy, specular).  Class: rough (Lambert, GGX alpha >= 0.2),
@@ -59,26 +59,26 @@ enum { C_ROUGH = 0, C_GLOSSY = 1, C_DELTA = 2 };
 constexpr float kPi = 3.14159265358979323846f;
 
 struct Mat { int type; float albedo, alpha; };
-__device__ __forceinline__ Mat load_mat(const GeomDev& g, int id) {
+static __device__ __forceinline__ Mat load_mat(const GeomDev& g, int id) {
     float4 m = __ldg(&g.mats[id]);
     Mat r; r.type = (int)m.x; r.albedo = m.y; r.alpha = m.z;
     return r;
 }
-__device__ __forceinline__ int mat_class(const Mat& m) {
+static __device__ __forceinline__ int mat_class(const Mat& m) {
     if (m.type == M_MIRROR) return C_DELTA;
     if (m.type == M_GGX && m.alpha < 0.2f) return C_GLOSSY;
     return C_ROUGH;
 }
-__device__ __forceinline__ float ggx_D(float nh, float a) {
+static __device__ __forceinline__ float ggx_D(float nh, float a) {
     float a2 = a * a, t = nh * nh * (a2 - 1.0f) + 1.0f;
     return a2 / (kPi * t * t);
 }
-__device__ __forceinline__ float ggx_G1(float nv, float a) {
+static __device__ __forceinline__ float ggx_G1(float nv, float a) {
     float a2 = a * a;
     return 2.0f * nv / (nv + sqrtf(a2 + (1.0f - a2) * nv * nv));
 }
 // f_s(wi, wo): wi toward the previous vertex, wo toward the next; reflection only
-__device__ float bsdf_f(const Mat& m, float3 n, float3 wi, float3 wo) {
+static __device__ float bsdf_f(const Mat& m, float3 n, float3 wi, float3 wo) {
     float ci = dot3(n, wi), co = dot3(n, wo);
     if (ci * co <= 0.f) return 0.f;
     if (ci < 0.f) { ci = -ci; co = -co; n = n * -1.0f; }
@@ -91,7 +91,7 @@ __device__ float bsdf_f(const Mat& m, float3 n, float3 wi, float3 wo) {
     }
     return 0.f;
 }
-__device__ float bsdf_pdf(const Mat& m, float3 n, float3 wi, float3 wo) {
+static __device__ float bsdf_pdf(const Mat& m, float3 n, float3 wi, float3 wo) {
     float ci = dot3(n, wi), co = dot3(n, wo);
     if (ci * co <= 0.f) return 0.f;
     if (ci < 0.f) { co = -co; n = n * -1.0f; }
@@ -108,7 +108,7 @@ __device__ float bsdf_pdf(const Mat& m, float3 n, float3 wi, float3 wo) {
 // fixed generic unit vectors (a2 perpendicular to a1, used when |n.a1| >= 0.6); the frame's
 // unavoidable discontinuity sits on a cone that axis-aligned or symmetric mesh normals do not
 // meet exactly, so the branch taken does not depend on rounding
-__device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
+static __device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
     const float3 a1 = f3(0.4140355211239282f, 0.731736150464251f, 0.5414210869105452f);
     const float3 a2 = f3(0.0f, 0.5947978113475719f, -0.8038753408434284f);
     float3 a = fabsf(dot3(n, a1)) < 0.6f ? a1 : a2;
@@ -116,7 +116,7 @@ __device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
     b = cross3(n, t);
 }
 // sample wo given wi; thr = f_s |cos_o| / pdf (albedo for the mirror)
-__device__ bool bsdf_sample(const Mat& m, float3 n, float3 wi, float u0, float u1, float3& wo, float& pdf,
+static __device__ bool bsdf_sample(const Mat& m, float3 n, float3 wi, float u0, float u1, float3& wo, float& pdf,
                             float& thr, bool& delta) {
     if (dot3(n, wi) < 0.f) n = n * -1.0f;
     delta = false;
@@ -156,7 +156,7 @@ __device__ bool bsdf_sample(const Mat& m, float3 n, float3 wi, float u0, float u
 // ============================================================================================
 struct Surf { int tri; float b1, b2; float3 p, n; int mat; };
 
-__device__ __forceinline__ Surf surf_at(const GeomDev& g, int tri, float b1, float b2) {
+static __device__ __forceinline__ Surf surf_at(const GeomDev& g, int tri, float b1, float b2) {
     float4 a = __ldg(&g.tri[3 * tri]), e1 = __ldg(&g.tri[3 * tri + 1]), e2 = __ldg(&g.tri[3 * tri + 2]);
     Surf s;
     s.tri = tri; s.b1 = b1; s.b2 = b2;
@@ -166,11 +166,11 @@ __device__ __forceinline__ Surf surf_at(const GeomDev& g, int tri, float b1, flo
     s.mat = __float_as_int(a.w);
     return s;
 }
-__device__ __forceinline__ float3 offset_point(float3 p, float3 n, float3 dir, float eps) {
+static __device__ __forceinline__ float3 offset_point(float3 p, float3 n, float3 dir, float eps) {
     return dot3(n, dir) >= 0.f ? p + n * eps : p - n * eps;
 }
 
-__device__ __forceinline__ bool tri_test(const float4* __restrict__ L, int leaf, float3 o, float3 d, float tmax, float& t,
+static __device__ __forceinline__ bool tri_test(const float4* __restrict__ L, int leaf, float3 o, float3 d, float tmax, float& t,
                                          float& b1, float& b2, int& orig) {
     float4 a = __ldg(&L[3 * leaf]), e1v = __ldg(&L[3 * leaf + 1]), e2v = __ldg(&L[3 * leaf + 2]);
     float3 e1 = xyz(e1v), e2 = xyz(e2v);
@@ -190,9 +190,11 @@ __device__ __forceinline__ bool tri_test(const float4* __restrict__ L, int leaf,
     return true;
 }
 
-// closest hit (any_hit = false) or first hit (any_hit = true) of o + t d, t in (0, tmax)
+// closest hit (any_hit = false) or first hit (any_hit = true) of o + t d, t in (0, tmax).
+// Kept out of line: one copy of the loop serves every call site (replay, visibility, NEE), which
+// keeps the shift kernels' code small and lets lanes from different call sites share it.
 template <bool kAny>
-__device__ bool traverse(const GeomDev& g, float3 o, float3 d, float tmax, int& tri, float& b1, float& b2, float& tout) {
+static __device__ __noinline__ bool traverse(const GeomDev& g, float3 o, float3 d, float tmax, int& tri, float& b1, float& b2, float& tout) {
     if (g.nt <= 0) return false;
     bool found = false;
     float best = tmax;
@@ -258,7 +260,7 @@ __device__ bool traverse(const GeomDev& g, float3 o, float3 d, float tmax, int& 
     return found;
 }
 
-__device__ __forceinline__ bool trace_from(const GeomDev& g, const Surf& s, float3 d, float eps, Surf& hit) {
+static __device__ __forceinline__ bool trace_from(const GeomDev& g, const Surf& s, float3 d, float eps, Surf& hit) {
     float3 o = offset_point(s.p, s.n, d, eps);
     int tri; float b1, b2, t;
     if (!traverse<false>(g, o, d, 3.0e38f, tri, b1, b2, t)) return false;
@@ -266,7 +268,7 @@ __device__ __forceinline__ bool trace_from(const GeomDev& g, const Surf& s, floa
     return true;
 }
 // mutual visibility of surface point a and surface point b (bsurf) or point b
-__device__ bool visible(const GeomDev& g, float3 a, float3 an, float3 b, const float3* bn, float eps) {
+static __device__ bool visible(const GeomDev& g, float3 a, float3 an, float3 b, const float3* bn, float eps) {
     float3 ao = offset_point(a, an, b - a, eps);
     float3 bo = bn ? offset_point(b, *bn, a - b, eps) : b;
     float3 d = bo - ao;
@@ -280,7 +282,7 @@ __device__ bool visible(const GeomDev& g, float3 a, float3 an, float3 b, const f
 // ============================================================================================
 // sensor rays and back-projection
 // ============================================================================================
-__device__ void primary_ray(const FrameDev& F, int ix, int iy, float u0, float u1, float3& o, float3& d) {
+static __device__ void primary_ray(const FrameDev& F, int ix, int iy, float u0, float u1, float3& o, float3& d) {
     o = F.pos;
     if (F.mode == 1) {
         float3 w = F.wall_o + (F.wall_u * ((ix + 0.5f) / F.W) + F.wall_v * ((iy + 0.5f) / F.H));
@@ -295,7 +297,7 @@ __device__ void primary_ray(const FrameDev& F, int ix, int iy, float u0, float u
     float sy = (1.0f - 2.0f * (iy + u1) / F.H) * th;
     d = norm3(f + (rt * sx + up * sy));
 }
-__device__ bool project(const FrameDev& F, float3 p, int& ix, int& iy) {
+static __device__ bool project(const FrameDev& F, float3 p, int& ix, int& iy) {
     float3 f = norm3(F.fwd);
     float3 rt = norm3(cross3(f, F.up));
     float3 up = cross3(rt, f);
@@ -327,12 +329,12 @@ struct Domain {
     int spot_mat;
 };
 
-__device__ void resolve_spot(const GeomDev& g, LightDev& L, float3& sn, int& smat) {
+static __device__ void resolve_spot(const GeomDev& g, LightDev& L, float3& sn, int& smat) {
     Surf s = surf_at(g, L.s_tri, L.s_b1, L.s_b2);
     L.pos = s.p; sn = s.n; smat = s.mat;
 }
 
-__device__ Domain make_domain(const FrameDev* F, int pix, float L0, float dL) {
+static __device__ Domain make_domain(const FrameDev* F, int pix, float L0, float dL) {
     Domain D;
     D.F = F;
     D.x0 = F->pos;
@@ -363,7 +365,37 @@ __device__ Domain make_domain(const FrameDev* F, int pix, float L0, float dL) {
     return D;
 }
 
-__device__ __forceinline__ bool light_same(const LightDev& a, const LightDev& b) {
+// domain of a pixel whose primary hit is (tri, b1, b2) at distance t from the sensor
+static __device__ __forceinline__ Domain make_domain_hit(const FrameDev* F, bool valid, int tri, float b1, float b2, float t, float L0, float dL) {
+    Domain D;
+    D.F = F;
+    D.x0 = F->pos;
+    D.L0 = L0; D.dL = dL;
+    D.light.kind = 0;
+    D.valid = valid;
+    D.o = 0.f;
+    D.spot_n = f3(0.f, 0.f, 1.f);
+    D.spot_mat = 0;
+    if (!valid) return D;
+    D.y1 = surf_at(F->g, tri, b1, b2);
+    D.o = F->mode == 1 ? 2.0f * t : 0.f;
+    if (F->etype == 0) {
+        D.light.kind = 1; D.light.pos = F->epos; D.light.I = F->epower;
+    } else if (F->etype == 1) {
+        D.light = *F->laser;
+        if (D.light.kind == 2) resolve_spot(F->g, D.light, D.spot_n, D.spot_mat);
+    } else {
+        D.light.kind = 2; D.light.s_tri = D.y1.tri; D.light.s_b1 = D.y1.b1; D.light.s_b2 = D.y1.b2;
+        D.light.I = F->epower;
+        D.light.to_origin = dir_to(D.y1.p, F->epos);
+        D.light.emit_len = len3(F->epos - D.y1.p);
+        D.light.pos = D.y1.p;
+        D.spot_n = D.y1.n; D.spot_mat = D.y1.mat;
+    }
+    return D;
+}
+
+static __device__ __forceinline__ bool light_same(const LightDev& a, const LightDev& b) {
     if (a.kind != b.kind) return false;
     if (a.kind == 0) return true;
     if (a.pos.x != b.pos.x || a.pos.y != b.pos.y || a.pos.z != b.pos.z || a.I != b.I) return false;
@@ -376,7 +408,7 @@ __device__ __forceinline__ bool light_same(const LightDev& a, const LightDev& b)
 }
 
 // light factor I_e |cos_x| / d^2 of a path ending at x (no BSDF, no visibility); wl, seg out
-__device__ float light_term(const Domain& D, const Surf& x, float3& wl, float& seg) {
+static __device__ float light_term(const Domain& D, const Surf& x, float3& wl, float& seg) {
     const LightDev& L = D.light;
     float3 lp = L.pos;
     float I = 0.f;
@@ -393,12 +425,12 @@ __device__ float light_term(const Domain& D, const Surf& x, float3& wl, float& s
     seg = dist + (L.kind == 2 ? L.emit_len : 0.f);
     return I * fabsf(dot3(x.n, wl)) / (dist * dist);
 }
-__device__ __forceinline__ bool light_visible(const Domain& D, const GeomDev& g, const Surf& x, float eps) {
+static __device__ __forceinline__ bool light_visible(const Domain& D, const GeomDev& g, const Surf& x, float eps) {
     if (D.light.kind == 2) return visible(g, x.p, x.n, D.light.pos, &D.spot_n, eps);
     return visible(g, x.p, x.n, D.light.pos, nullptr, eps);
 }
 
-__device__ __forceinline__ float Gterm(const Surf& a, const Surf& b) {
+static __device__ __forceinline__ float Gterm(const Surf& a, const Surf& b) {
     float3 d = b.p - a.p;
     float d2 = dot3(d, d);
     if (!(d2 > 0.f)) return 0.f;
@@ -424,13 +456,13 @@ struct Rec {
     int s_tri[3];
     float s_b1[3], s_b2[3];
 };
-__device__ __forceinline__ int rec_tree(const Rec& r) { return (int)(r.meta & 0xFFu); }
-__device__ __forceinline__ int rec_k(const Rec& r) { return (int)((r.meta >> 8) & 7u); }
-__device__ __forceinline__ int rec_r(const Rec& r) { return (int)((r.meta >> 11) & 7u); }
-__device__ __forceinline__ int rec_ns(const Rec& r) { return (int)((r.meta >> 14) & 3u); }
-__device__ __forceinline__ int rec_cls(const Rec& r, int j) { return (int)((r.meta >> (16 + 2 * (j - 1))) & 3u); }
+static __device__ __forceinline__ int rec_tree(const Rec& r) { return (int)(r.meta & 0xFFu); }
+static __device__ __forceinline__ int rec_k(const Rec& r) { return (int)((r.meta >> 8) & 7u); }
+static __device__ __forceinline__ int rec_r(const Rec& r) { return (int)((r.meta >> 11) & 7u); }
+static __device__ __forceinline__ int rec_ns(const Rec& r) { return (int)((r.meta >> 14) & 3u); }
+static __device__ __forceinline__ int rec_cls(const Rec& r, int j) { return (int)((r.meta >> (16 + 2 * (j - 1))) & 3u); }
 
-__device__ __forceinline__ void rec_store(const ResDev& R, size_t idx, const Rec& r) {
+static __device__ __forceinline__ void rec_store(const ResDev& R, size_t idx, const Rec& r) {
     float4* P = R.planes;
     const size_t s = R.stride;
     P[idx] = make_float4(r.W, r.phat, r.tau, r.Lsuf);
@@ -444,7 +476,7 @@ __device__ __forceinline__ void rec_store(const ResDev& R, size_t idx, const Rec
         if (ns >= 3) P[5 * s + idx] = make_float4(__int_as_float(r.s_tri[2]), r.s_b1[2], r.s_b2[2], 0.f);
     }
 }
-__device__ __forceinline__ void rec_load(const ResDev& R, size_t idx, Rec& r) {
+static __device__ __forceinline__ void rec_load(const ResDev& R, size_t idx, Rec& r) {
     const float4* P = R.planes;
     const size_t s = R.stride;
     float4 a = P[idx], b = P[s + idx];
@@ -465,7 +497,7 @@ __device__ __forceinline__ void rec_load(const ResDev& R, size_t idx, Rec& r) {
         }
     }
 }
-__device__ __forceinline__ bool occ_get(const ResDev& R, int pix, int b) {
+static __device__ __forceinline__ bool occ_get(const ResDev& R, int pix, int b) {
     return (R.occ[(size_t)pix * R.words + (b >> 5)] >> (b & 31)) & 1u;
 }
 
@@ -481,7 +513,7 @@ struct TreeVerts {
 
 // reconnectability of vertex i of x_1..x_k (Sec. 4.1: first consecutive diffuse pair; the
 // perturbation re-evaluates the BSDF after p, so that vertex must be rough or be the light)
-__device__ __forceinline__ bool connectable(const int* cls, const float3* pos, int k, int i, float dmin) {
+static __device__ __forceinline__ bool connectable(const int* cls, const float3* pos, int k, int i, float dmin) {
     if (cls[i - 1] != C_ROUGH || cls[i] != C_ROUGH) return false;
     if (len3(pos[i - 1] - pos[i]) <= dmin) return false;
     if (i < k) {
@@ -490,14 +522,14 @@ __device__ __forceinline__ bool connectable(const int* cls, const float3* pos, i
     }
     return true;
 }
-__device__ __forceinline__ int find_r(const int* cls, const float3* pos, int k, float dmin) {
+static __device__ __forceinline__ int find_r(const int* cls, const float3* pos, int k, float dmin) {
     for (int i = 2; i <= k; ++i)
         if (connectable(cls, pos, k, i, dmin)) return i;
     return 0;
 }
 
 // f(x) in area measure of the NEE path x_1..x_k (no visibility)
-__device__ float path_f(const Domain& D, const TreeVerts& T, int k) {
+static __device__ float path_f(const Domain& D, const TreeVerts& T, int k) {
     const GeomDev& g = D.F->g;
     float f = 1.0f;
     for (int j = 1; j <= k; ++j) {
@@ -516,7 +548,7 @@ __device__ float path_f(const Domain& D, const TreeVerts& T, int k) {
 }
 
 // reservoir record of the candidate of length k from tree `tree` (P0's W is filled later)
-__device__ void build_rec(const Domain& D, const TreeVerts& T, int k, int tree, uint32_t px, uint32_t frame, float tau,
+static __device__ void build_rec(const Domain& D, const TreeVerts& T, int k, int tree, uint32_t px, uint32_t frame, float tau,
                           const ParamsDev& P, Rec& R) {
     const GeomDev& g = D.F->g;
     R.W = 0.f;
@@ -563,7 +595,7 @@ __device__ void build_rec(const Domain& D, const TreeVerts& T, int k, int tree, 
 //   grad_xi L = J^T grad_p L, hess_xi L = J^T A J (Q = 0 on flat triangles)
 // ============================================================================================
 struct Frame2 { float3 o, t, b; };
-__device__ __forceinline__ Frame2 tri_frame(const GeomDev& g, int tri) {
+static __device__ __forceinline__ Frame2 tri_frame(const GeomDev& g, int tri) {
     float4 a = __ldg(&g.tri[3 * tri]), e1 = __ldg(&g.tri[3 * tri + 1]), e2 = __ldg(&g.tri[3 * tri + 2]);
     Frame2 f;
     f.o = xyz(a);
@@ -572,9 +604,9 @@ __device__ __forceinline__ Frame2 tri_frame(const GeomDev& g, int tri) {
     f.b = cross3(n, f.t);
     return f;
 }
-__device__ __forceinline__ float3 frame_point(const Frame2& f, float x0, float x1) { return f.o + (f.t * x0 + f.b * x1); }
+static __device__ __forceinline__ float3 frame_point(const Frame2& f, float x0, float x1) { return f.o + (f.t * x0 + f.b * x1); }
 
-__device__ __forceinline__ void length_derivs(float3 p1, float3 p2, const Frame2& f, float x0, float x1, float& L,
+static __device__ __forceinline__ void length_derivs(float3 p1, float3 p2, const Frame2& f, float x0, float x1, float& L,
                                               float g[2], float h[3]) {
     float3 p = frame_point(f, x0, x1);
     float3 a1 = p1 - p, a2 = p2 - p;
@@ -594,7 +626,7 @@ struct NewtonGeo { float3 p1x, p2x; Frame2 fx; float3 p1y, p2y; Frame2 fy; };
 
 // F(xi, xi') = [L_y(xi') - L_x(xi) - delta ; (R m)^T (xi' - xi)], m = (grad L_x(xi) + grad L_y(xi'))/2,
 // R = 90-degree rotation; each gradient on its own path (Sec. 4.3, average-gradient gauge)
-__device__ __forceinline__ void newton_F(const NewtonGeo& N, const float xi[2], float Lx, const float gx[2], float delta,
+static __device__ __forceinline__ void newton_F(const NewtonGeo& N, const float xi[2], float Lx, const float gx[2], float delta,
                                          const float xp[2], float F[2], float gy[2], float hy[3], float m[2]) {
     float Ly;
     length_derivs(N.p1y, N.p2y, N.fy, xp[0], xp[1], Ly, gy, hy);
@@ -604,7 +636,7 @@ __device__ __forceinline__ void newton_F(const NewtonGeo& N, const float xi[2], 
     F[1] = -m[1] * (xp[0] - xi[0]) + m[0] * (xp[1] - xi[1]);
 }
 // dF/dxi' rows: (grad L_y(xi'), R m - 0.5 H_y R (xi' - xi)); dF/dxi rows: (-grad L_x(xi), -(R m + 0.5 H_x R (xi' - xi)))
-__device__ __forceinline__ void newton_J(const float xi[2], const float xp[2], const float gx[2], const float hx[3],
+static __device__ __forceinline__ void newton_J(const float xi[2], const float xp[2], const float gx[2], const float hx[3],
                                          const float gy[2], const float hy[3], const float m[2], float A[4], float Bm[4]) {
     float Rm0 = -m[1], Rm1 = m[0];
     float dd0 = xp[0] - xi[0], dd1 = xp[1] - xi[1];
@@ -617,7 +649,7 @@ __device__ __forceinline__ void newton_J(const float xi[2], const float xp[2], c
 
 // Newton iteration with backtracking (Sec. 4.3); returns success, xi', |det(dxi'/dxi)| and the
 // iteration count.  Stops at |F|_inf <= tol_stop or after max_iter; success if |F|_inf <= tol_succ.
-__device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float delta, int max_iter, float tol_stop,
+static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float delta, int max_iter, float tol_stop,
                              float tol_succ, float xp[2], float& jdet, int& iters) {
     float Lx, gx[2], hx[3];
     length_derivs(N.p1x, N.p2x, N.fx, xi[0], xi[1], Lx, gx, hx);
@@ -671,7 +703,7 @@ __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float delta,
 // ============================================================================================
 struct ShiftStats { uint32_t newton_calls, newton_iters, newton_ok, shift_calls, shift_ok; };
 
-__device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& Di, const ParamsDev& P, bool geom_static, Rec& y,
+static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& Di, const ParamsDev& P, bool geom_static, Rec& y,
                           float& phat_out, float& jac_out, ShiftStats* st) {
     const int r = rec_r(x);
     if (r < 2 || !Di.valid || !Dj.valid) return false;

@@ -76,9 +76,10 @@ struct ParamsDev {
     uint64_t seed;
 };
 
-// shift statistics (device, accumulated): newton calls, iterations, successes, shift calls, ok
+// shift statistics (device, accumulated): newton calls, iterations, successes, forward shift
+// calls, forward successes, inverse shift calls, spatial forward calls, spatial inverse calls
 struct StatsDev {
-    unsigned long long v[5];
+    unsigned long long v[8];
 };
 
 struct GbufArgs {
@@ -105,6 +106,23 @@ struct ReuseArgs {
     int geom_static;         // previous and current geometry identical
     float* out;              // gated image if last stage
     StatsDev* stats;
+};
+
+// wavefront scratch of one reuse pass (tof_reuse.cu); S = slots per pixel (1 canonical + reused)
+struct WaveDev {
+    int slots;              // S
+    int cap_units;          // merge units (pixel, bin) per launch
+    int* slot_pix;          // npix * S
+    float* slot_M;          // npix * S
+    uint8_t* nslot;         // npix
+    int2* units;            // cap_units
+    uint32_t* fwd;          // cap_units * (S - 1)   forward tasks (unit << 4 | slot)
+    uint32_t* inv;          // cap_units * S * (S-1) inverse tasks (unit << 8 | s << 4 | j)
+    float4* yrec;           // 6 planes of cap_units * (S - 1) shifted records
+    float* py;              // cap_units * S
+    float* jac;             // cap_units * S
+    float* terms;           // cap_units * S * S
+    uint32_t* counters;     // units, forward tasks, inverse tasks, overflow
 };
 
 struct SplatArgs {

@@ -2,11 +2,11 @@
 //
 //   gbuffer_kernel   primary visibility, one jittered ray per pixel            (Sec. 3.2 setup)
 //   initial_kernel   path trees with NEE, streaming RIS into per-bin reservoirs (stage (1), Sec. 4.5)
-//   reuse_kernel     temporal or spatial GRIS merge through the path-length shift (stages (2), (3))
+//   (temporal and spatial reuse, stages (2) and (3), are in tof_reuse.cu)
 //   splat_kernel     transient histogram H[px, b] = f(y_b) W_b                  (stage (4), Sec. 4.5)
 //   pt_kernel        plain gated / transient path tracing (the comparison of Sec. 6)
 //   laser_kernel     resolves the collimated laser's spot (Sec. 5 "Light Source")
-// The gated image is written by the last stage's kernel (final shading fused into it).
+// The gated image is written by the last stage's kernels (final shading fused into them).
 #include "tof_device.cuh"
 
 namespace tof {
@@ -14,35 +14,6 @@ namespace tof {
 // --------------------------------------------------------------------------------------------
 // shared helpers
 // --------------------------------------------------------------------------------------------
-__device__ Domain make_domain_hit(const FrameDev* F, bool valid, int tri, float b1, float b2, float t, float L0, float dL) {
-    Domain D;
-    D.F = F;
-    D.x0 = F->pos;
-    D.L0 = L0; D.dL = dL;
-    D.light.kind = 0;
-    D.valid = valid;
-    D.o = 0.f;
-    D.spot_n = f3(0.f, 0.f, 1.f);
-    D.spot_mat = 0;
-    if (!valid) return D;
-    D.y1 = surf_at(F->g, tri, b1, b2);
-    D.o = F->mode == 1 ? 2.0f * t : 0.f;
-    if (F->etype == 0) {
-        D.light.kind = 1; D.light.pos = F->epos; D.light.I = F->epower;
-    } else if (F->etype == 1) {
-        D.light = *F->laser;
-        if (D.light.kind == 2) resolve_spot(F->g, D.light, D.spot_n, D.spot_mat);
-    } else {
-        D.light.kind = 2; D.light.s_tri = D.y1.tri; D.light.s_b1 = D.y1.b1; D.light.s_b2 = D.y1.b2;
-        D.light.I = F->epower;
-        D.light.to_origin = dir_to(D.y1.p, F->epos);
-        D.light.emit_len = len3(F->epos - D.y1.p);
-        D.light.pos = D.y1.p;
-        D.spot_n = D.y1.n; D.spot_mat = D.y1.mat;
-    }
-    return D;
-}
-
 __device__ __forceinline__ float gate_L0(const FrameDev& F, int b) { return F.B > 0 ? F.L0 + b * F.dL : F.L0; }
 
 // One path tree; Sink(k, c, tau, T) receives each NEE candidate of length k in [kmin, depth]
@@ -210,181 +181,6 @@ __global__ void __launch_bounds__(128) initial_kernel(const __grid_constant__ In
 }
 
 // --------------------------------------------------------------------------------------------
-// reuse (stages (2) and (3)): GRIS merge (eq. GRIS_resampling_weight) with the generalized
-// balance heuristic (eq. GRIS_MIS_weight, denominators evaluated at the same y_i for every
-// domain, p_hat_{<-i}(y_i) = p_hat_i(x_i) / |dS_i/dx_i|); slot 0 is the canonical sample.
-// Confidence weights are per pixel and shared by every bin.
-// --------------------------------------------------------------------------------------------
-struct Slot {
-    const FrameDev* F;
-    const ResDev* R;
-    int pix;
-    float M;
-    bool geom_static;
-};
-
-__device__ __forceinline__ int pick_neighbor(uint64_t seed, uint32_t px, uint32_t frame, int pass, int slot, int W, int H, int R) {
-    int ix = (int)(px % (uint32_t)W), iy = (int)(px / (uint32_t)W);
-    uint32_t side = 2u * (uint32_t)R + 1u;
-    for (int a = 0; a < 4; ++a) {
-        uint4 u = philox(px, frame, ((uint32_t)pass << 8) | (uint32_t)slot, P_NEIGHBOR | ((uint32_t)a << 8), seed);
-        uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-        for (int h = 0; h < 2; ++h) {
-            int dx = (int)(uu[2 * h] % side) - R, dy = (int)(uu[2 * h + 1] % side) - R;
-            if (dx * dx + dy * dy > R * R || (dx == 0 && dy == 0)) continue;
-            int nx = ix + dx, ny = iy + dy;
-            if (nx < 0 || ny < 0 || nx >= W || ny >= H) return -1;
-            return ny * W + nx;
-        }
-    }
-    return -1;
-}
-
-__device__ __forceinline__ Domain slot_domain(const Slot& s, int b) {
-    float4 gb = __ldg(&s.F->gb[s.pix]);
-    uint32_t tri = __float_as_uint(gb.x);
-    return make_domain_hit(s.F, tri != kNoHit, (int)tri, gb.y, gb.z, gb.w, gate_L0(*s.F, b), s.F->dL);
-}
-
-// merge of bin b over n slots; returns true and the merged record if any candidate survives
-__device__ bool merge_bin(const ReuseArgs& a, const Slot* sl, int n, int b, uint32_t pix, Rec& out, ShiftStats& st) {
-    const ParamsDev& P = a.P;
-    const int Bn0 = sl[0].F->B > 0 ? sl[0].F->B : 1;
-    Rec y[kMaxSlots];
-    float py[kMaxSlots], J[kMaxSlots], ph[kMaxSlots], Wx[kMaxSlots], w[kMaxSlots];
-    bool ok[kMaxSlots];
-    Domain D0 = slot_domain(sl[0], b);
-    for (int s = 0; s < n; ++s) {
-        ok[s] = false; w[s] = 0.f;
-        int Bs = sl[s].F->B > 0 ? sl[s].F->B : 1;
-        if (!occ_get(*sl[s].R, sl[s].pix, b)) continue;
-        size_t idx = (size_t)sl[s].pix * Bs + b;
-        if (s == 0) {
-            rec_load(*sl[0].R, idx, y[0]);
-            py[0] = y[0].phat; J[0] = 1.0f; ph[0] = y[0].phat; Wx[0] = y[0].W;
-            ok[0] = py[0] > 0.f;
-            continue;
-        }
-        Rec x;
-        rec_load(*sl[s].R, idx, x);
-        ph[s] = x.phat; Wx[s] = x.W;
-        Domain Ds = slot_domain(sl[s], b);
-        ok[s] = shift_rec(x, Ds, D0, P, sl[s].geom_static, y[s], py[s], J[s], &st);
-    }
-    (void)Bn0;
-    for (int s = 0; s < n; ++s) {
-        if (!ok[s]) continue;
-        float num = s == 0 ? sl[0].M * py[0] : sl[s].M * ph[s] / J[s];
-        float den = sl[0].M * py[s];
-        for (int j = 1; j < n; ++j) {
-            if (j == s) { den += sl[s].M * ph[s] / J[s]; continue; }
-            Domain Dj = slot_domain(sl[j], b);
-            Rec tmp; float pj, Jj;
-            if (shift_rec(y[s], D0, Dj, P, sl[j].geom_static, tmp, pj, Jj, nullptr)) den += sl[j].M * pj * Jj;
-        }
-        float m = den > 0.f ? num / den : 0.f;
-        w[s] = m * py[s] * Wx[s] * J[s];
-        if (!(w[s] > 0.f) || !isfinite(w[s])) w[s] = 0.f;
-    }
-    float S = 0.f;
-    int sel = -1;
-    for (int s = 0; s < n; ++s) {
-        if (!(w[s] > 0.f)) continue;
-        uint4 u = philox(pix, sl[0].F->frame, ((uint32_t)a.pass << 8) | (uint32_t)s, P_MERGE | ((uint32_t)b << 8), P.seed);
-        S += w[s];
-        if (u01(u.x) * S < w[s]) sel = s;
-    }
-    if (sel < 0) return false;
-    out = y[sel];
-    out.W = S / py[sel];
-    return true;
-}
-
-__global__ void __launch_bounds__(128) reuse_kernel(const __grid_constant__ ReuseArgs a) {
-    const FrameDev& C = a.cur;
-    int ix = blockIdx.x * 16 + (threadIdx.x & 15), iy = blockIdx.y * 8 + (threadIdx.x >> 4);
-    ShiftStats st = {0, 0, 0, 0, 0};
-    bool active = ix < C.W && iy < C.H;
-    if (active) {
-        const int pix = iy * C.W + ix;
-        const ParamsDev& P = a.P;
-        const int Bn = C.B > 0 ? C.B : 1;
-        const int words = a.dst.words;
-        uint32_t* docc = a.dst.occ + (size_t)pix * words;
-        const uint32_t* socc = a.src.occ + (size_t)pix * words;
-        Slot sl[kMaxSlots];
-        int n = 1;
-        sl[0].F = &a.cur; sl[0].R = &a.src; sl[0].pix = pix; sl[0].M = a.src.M[pix]; sl[0].geom_static = true;
-        bool gb_valid = __float_as_uint(C.gb[pix].x) != kNoHit;
-        if (gb_valid) {
-            if (a.temporal) {
-                int q = -1;
-                if (C.mode == 1) q = pix;
-                else {
-                    float4 gb = C.gb[pix];
-                    Surf sp = surf_at(a.prev.g, __float_as_int(gb.x), gb.y, gb.z);
-                    int qx, qy;
-                    if (project(a.prev, sp.p, qx, qy)) q = qy * C.W + qx;
-                }
-                if (q >= 0) {
-                    sl[1].F = &a.prev; sl[1].R = &a.prv; sl[1].pix = q; sl[1].M = fminf(a.prv.M[q], P.m_cap);
-                    sl[1].geom_static = a.geom_static != 0;
-                    n = 2;
-                }
-            } else {
-                for (int s = 1; s <= P.n_spatial; ++s) {
-                    int q = pick_neighbor(P.seed, (uint32_t)pix, C.frame, a.pass, s, C.W, C.H, P.radius);
-                    if (q < 0) continue;
-                    sl[n].F = &a.cur; sl[n].R = &a.src; sl[n].pix = q; sl[n].M = fminf(a.src.M[q], P.m_cap);
-                    sl[n].geom_static = true;
-                    ++n;
-                }
-            }
-        }
-        float Msum = 0.f;
-        for (int s = 0; s < n; ++s) Msum += sl[s].M;
-        a.dst.M[pix] = Msum;
-        float outv = 0.f;
-        if (n == 1) {
-            // no reuse candidate: the canonical reservoir carries over unchanged
-            for (int w = 0; w < words; ++w) {
-                uint32_t m = socc[w];
-                docc[w] = m;
-                while (m) {
-                    int bit = __ffs(m) - 1;
-                    m &= m - 1;
-                    size_t idx = (size_t)pix * Bn + (w << 5) + bit;
-                    for (int k = 0; k < 6; ++k) a.dst.planes[k * a.dst.stride + idx] = a.src.planes[k * a.src.stride + idx];
-                    if (C.B == 0) { float4 p0 = a.src.planes[idx]; outv = p0.y * p0.x; }
-                }
-            }
-        } else {
-            for (int w = 0; w < words; ++w) {
-                uint32_t m = 0u;
-                for (int s = 0; s < n; ++s) m |= sl[s].R->occ[(size_t)sl[s].pix * sl[s].R->words + w];
-                uint32_t res = 0u;
-                while (m) {
-                    int bit = __ffs(m) - 1;
-                    m &= m - 1;
-                    int b = (w << 5) + bit;
-                    if (b >= Bn) break;
-                    Rec r;
-                    if (merge_bin(a, sl, n, b, (uint32_t)pix, r, st)) {
-                        size_t idx = (size_t)pix * Bn + b;
-                        rec_store(a.dst, idx, r);
-                        res |= 1u << bit;
-                        if (C.B == 0) outv = r.phat * r.W;
-                    }
-                }
-                docc[w] = res;
-            }
-        }
-        if (a.out) a.out[pix] = outv;
-    }
-    stats_flush(a.stats, st);
-}
-
-// --------------------------------------------------------------------------------------------
 // transient splat (stage (4)): H[px, b] = f(y_b) W_b for occupied bins, 0 elsewhere; one warp
 // per pixel so that the histogram row is written with coalesced stores
 // --------------------------------------------------------------------------------------------
@@ -481,10 +277,6 @@ cudaError_t launch_gbuffer(const GbufArgs& a, cudaStream_t s) {
 }
 cudaError_t launch_initial(const InitArgs& a, int* err, cudaStream_t s) {
     initial_kernel<<<pix_grid(a.F.W, a.F.H), 128, 0, s>>>(a, err);
-    return cudaGetLastError();
-}
-cudaError_t launch_reuse(const ReuseArgs& a, cudaStream_t s) {
-    reuse_kernel<<<pix_grid(a.cur.W, a.cur.H), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_splat(const SplatArgs& a, cudaStream_t s) {

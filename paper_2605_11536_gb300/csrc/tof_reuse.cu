@@ -1,0 +1,377 @@
+// tof_reuse.cu -- temporal and spatial reuse (Sec. 3.2 stages (2) and (3)) as a wavefront of
+// shift tasks.
+//
+// One GRIS merge (eq. GRIS_resampling_weight with the generalized balance heuristic of
+// eq. GRIS_MIS_weight) needs, for a pixel's (or a pixel-bin's) canonical sample and k reused
+// samples, k forward shifts into the pixel's domain and, for every surviving candidate, one
+// inverse shift into each other reused domain.  Run as one thread per pixel, the shifts of the
+// few pixels that hold samples serialise while the rest of the warp idles, so the pass is split:
+//   reuse_setup_kernel   per pixel: slots (neighbours or the back-projected previous pixel),
+//                        capped confidences, merge units (pixel, bin), forward-shift tasks and
+//                        the canonical sample's inverse-shift tasks
+//   shift_fwd_kernel     persistent over forward tasks: shift slot s's sample into the unit's
+//                        domain; emit the inverse-shift tasks of the shifted candidate
+//   shift_inv_kernel     persistent over inverse tasks: shift candidate s's offset path into
+//                        domain j -> the term M_j p_hat_j(S_j^-1(y_s)) |dS_j^-1/dy_s|
+//   reuse_merge_kernel   persistent over units: MIS weights, streaming selection, output
+// Task lists are compacted with atomics, read by the next kernel in stream order; no kernel
+// waits on another's progress.
+#include "tof_device.cuh"
+
+namespace tof {
+
+__device__ __forceinline__ float gate_L0r(const FrameDev& F, int b) { return F.B > 0 ? F.L0 + b * F.dL : F.L0; }
+
+__device__ __forceinline__ const FrameDev* slot_frame(const ReuseArgs& a, int s) {
+    return (a.temporal && s == 1) ? &a.prev : &a.cur;
+}
+__device__ __forceinline__ const ResDev* slot_res(const ReuseArgs& a, int s) {
+    return (a.temporal && s == 1) ? &a.prv : &a.src;
+}
+
+__device__ __forceinline__ Domain pix_domain(const FrameDev* F, int pix, int b) {
+    float4 gb = __ldg(&F->gb[pix]);
+    uint32_t tri = __float_as_uint(gb.x);
+    return make_domain_hit(F, tri != kNoHit, (int)tri, gb.y, gb.z, gb.w, gate_L0r(*F, b), F->dL);
+}
+
+__device__ __forceinline__ int pick_nb(uint64_t seed, uint32_t px, uint32_t frame, int pass, int slot, int W, int H, int R) {
+    int ix = (int)(px % (uint32_t)W), iy = (int)(px / (uint32_t)W);
+    uint32_t side = 2u * (uint32_t)R + 1u;
+    for (int a = 0; a < 4; ++a) {
+        uint4 u = philox(px, frame, ((uint32_t)pass << 8) | (uint32_t)slot, P_NEIGHBOR | ((uint32_t)a << 8), seed);
+        uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+        for (int h = 0; h < 2; ++h) {
+            int dx = (int)(uu[2 * h] % side) - R, dy = (int)(uu[2 * h + 1] % side) - R;
+            if (dx * dx + dy * dy > R * R || (dx == 0 && dy == 0)) continue;
+            int nx = ix + dx, ny = iy + dy;
+            if (nx < 0 || ny < 0 || nx >= W || ny >= H) return -1;
+            return ny * W + nx;
+        }
+    }
+    return -1;
+}
+
+// warp-aggregated reservation of `n` consecutive slots in a counter
+__device__ __forceinline__ uint32_t reserve(uint32_t* counter, uint32_t n) {
+    const uint32_t mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t v = __shfl_up_sync(mask, incl, o);
+        if (lane >= o && ((mask >> (lane - o)) & 1u)) incl += v;
+    }
+    // the highest active lane holds the warp total only if all lanes are active; fall back to a
+    // per-thread atomic for partially active warps
+    if (mask != 0xFFFFFFFFu) return n ? atomicAdd(counter, n) : 0u;
+    uint32_t total = __shfl_sync(mask, incl, 31);
+    uint32_t base = 0;
+    if (lane == 31) base = total ? atomicAdd(counter, total) : 0u;
+    base = __shfl_sync(mask, base, 31);
+    return base + incl - n;
+}
+
+__device__ __forceinline__ void store_rec(float4* P, size_t stride, size_t idx, const Rec& r) {
+    ResDev R;
+    R.planes = P; R.stride = stride;
+    rec_store(R, idx, r);
+}
+
+// --------------------------------------------------------------------------------------------
+// per pixel: slots, confidence, units and tasks
+// --------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) reuse_setup_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w,
+                                                          int p0, int p1) {
+    const FrameDev& C = a.cur;
+    const int pix = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = pix < p1;
+    const ParamsDev& P = a.P;
+    const int Bn = C.B > 0 ? C.B : 1;
+    const int words = a.dst.words;
+    int n = 1;
+    int sp[kMaxSlots];
+    float sM[kMaxSlots];
+    if (active) {
+        sp[0] = pix;
+        sM[0] = a.src.M[pix];
+        bool gb_valid = __float_as_uint(C.gb[pix].x) != kNoHit;
+        if (gb_valid) {
+            if (a.temporal) {
+                int q = -1;
+                if (C.mode == 1) q = pix;
+                else {
+                    float4 gb = C.gb[pix];
+                    Surf sp0 = surf_at(a.prev.g, __float_as_int(gb.x), gb.y, gb.z);
+                    int qx, qy;
+                    if (project(a.prev, sp0.p, qx, qy)) q = qy * C.W + qx;
+                }
+                if (q >= 0) { sp[1] = q; sM[1] = fminf(a.prv.M[q], P.m_cap); n = 2; }
+            } else {
+                for (int s = 1; s <= P.n_spatial; ++s) {
+                    int q = pick_nb(P.seed, (uint32_t)pix, C.frame, a.pass, s, C.W, C.H, P.radius);
+                    if (q < 0) continue;
+                    sp[n] = q; sM[n] = fminf(a.src.M[q], P.m_cap); ++n;
+                }
+            }
+        }
+        float Msum = 0.f;
+        for (int s = 0; s < n; ++s) Msum += sM[s];
+        a.dst.M[pix] = Msum;
+        const int S = w.slots;
+        w.nslot[pix] = (uint8_t)n;
+        for (int s = 0; s < n; ++s) { w.slot_pix[(size_t)pix * S + s] = sp[s]; w.slot_M[(size_t)pix * S + s] = sM[s]; }
+    }
+    // units: one per bin that any slot occupies (pixels without reuse candidates copy through)
+    uint32_t* docc = active ? a.dst.occ + (size_t)pix * words : nullptr;
+    const uint32_t* socc = active ? a.src.occ + (size_t)pix * words : nullptr;
+    float outv = 0.f;
+    for (int wd = 0; wd < words; ++wd) {
+        uint32_t m = 0u;
+        if (active) {
+            if (n == 1) {
+                m = socc[wd];
+                docc[wd] = m;
+                while (m) {
+                    int bit = __ffs(m) - 1;
+                    m &= m - 1;
+                    size_t idx = (size_t)pix * Bn + (wd << 5) + bit;
+                    for (int k = 0; k < 6; ++k) a.dst.planes[k * a.dst.stride + idx] = a.src.planes[k * a.src.stride + idx];
+                    if (C.B == 0) { float4 p0v = a.src.planes[idx]; outv = p0v.y * p0v.x; }
+                }
+                m = 0u;
+            } else {
+                docc[wd] = 0u;
+                for (int s = 0; s < n; ++s) {
+                    const ResDev* R = slot_res(a, s);
+                    m |= R->occ[(size_t)sp[s] * R->words + wd];
+                }
+            }
+        }
+        // one unit per set bit; reserve units, forward tasks and canonical inverse tasks
+        uint32_t nu = __popc(m);
+        uint32_t ubase = reserve(&w.counters[0], nu);
+        uint32_t k = 0;
+        while (m) {
+            int bit = __ffs(m) - 1;
+            m &= m - 1;
+            int b = (wd << 5) + bit;
+            uint32_t u = ubase + k++;
+            if (u >= (uint32_t)w.cap_units) { atomicOr(&w.counters[3], 1u); continue; }
+            w.units[u] = make_int2(pix, b);
+            uint32_t nf = 0;
+            for (int s = 1; s < n; ++s) {
+                const ResDev* R = slot_res(a, s);
+                if (occ_get(*R, sp[s], b)) ++nf;
+            }
+            bool canon = occ_get(a.src, pix, b);
+            uint32_t fb = nf ? atomicAdd(&w.counters[1], nf) : 0u;
+            uint32_t i = 0;
+            for (int s = 1; s < n; ++s) {
+                const ResDev* R = slot_res(a, s);
+                if (occ_get(*R, sp[s], b)) w.fwd[fb + i++] = (u << 4) | (uint32_t)s;
+            }
+            if (canon && n > 1) {
+                uint32_t ib = atomicAdd(&w.counters[2], (uint32_t)(n - 1));
+                for (int j = 1; j < n; ++j) w.inv[ib + j - 1] = (u << 8) | (uint32_t)j;
+            }
+        }
+    }
+    // gated: pixels that form a unit get their value from the merge (which runs after this kernel)
+    if (active && a.out) a.out[pix] = n == 1 ? outv : 0.f;
+}
+
+// --------------------------------------------------------------------------------------------
+// forward shifts: slot s's sample into the unit's domain
+// --------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128, 4) shift_fwd_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+    ShiftStats st = {0, 0, 0, 0, 0};
+    const uint32_t ntask = min(w.counters[1], (uint32_t)w.cap_units * (uint32_t)(w.slots - 1));
+    const int S = w.slots;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
+        uint32_t task = w.fwd[t];
+        uint32_t u = task >> 4;
+        int s = (int)(task & 15u);
+        int2 ub = w.units[u];
+        int pix = ub.x, b = ub.y;
+        int q = w.slot_pix[(size_t)pix * S + s];
+        const FrameDev* Fs = slot_frame(a, s);
+        const ResDev* Rs = slot_res(a, s);
+        int Bs = Fs->B > 0 ? Fs->B : 1;
+        Rec x;
+        rec_load(*Rs, (size_t)q * Bs + b, x);
+        Domain Ds = pix_domain(Fs, q, b);
+        Domain D0 = pix_domain(&a.cur, pix, b);
+        Rec y;
+        float py = 0.f, J = 1.f;
+        bool geom_static = (a.temporal && s == 1) ? a.geom_static != 0 : true;
+        bool ok = shift_rec(x, Ds, D0, a.P, geom_static, y, py, J, &st);
+        size_t ui = (size_t)u * S + s;
+        w.py[ui] = ok ? py : 0.f;
+        w.jac[ui] = ok ? J : 1.f;
+        if (ok) {
+            store_rec(w.yrec, (size_t)w.cap_units * (S - 1), (size_t)u * (S - 1) + (s - 1), y);
+            int n = w.nslot[pix];
+            if (n > 2) {
+                uint32_t ib = atomicAdd(&w.counters[2], (uint32_t)(n - 2));
+                uint32_t i = 0;
+                for (int j = 1; j < n; ++j)
+                    if (j != s) w.inv[ib + i++] = (u << 8) | ((uint32_t)s << 4) | (uint32_t)j;
+            }
+        }
+    }
+    // warp-level flush of the shift statistics
+    if (a.stats) {
+        // counters 0..4 and 6 (spatial forward calls); counter 5 belongs to the inverse kernel
+        unsigned long long v[7] = {st.newton_calls, st.newton_iters, st.newton_ok, st.shift_calls, st.shift_ok, 0ull,
+                                   a.temporal ? 0ull : (unsigned long long)st.shift_calls};
+        for (int i = 0; i < 7; ++i) {
+            unsigned long long x = v[i];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+            if ((threadIdx.x & 31) == 0 && x) atomicAdd(&a.stats->v[i], x);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------------------------
+// inverse shifts: candidate s's offset path (in the unit's domain) into domain j
+// --------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128, 4) shift_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+    const uint32_t cap = (uint32_t)w.cap_units * (uint32_t)w.slots * (uint32_t)(w.slots - 1);
+    const uint32_t ntask = min(w.counters[2], cap);
+    const int S = w.slots;
+    const int Bn = a.cur.B > 0 ? a.cur.B : 1;
+    unsigned long long ninv = 0;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
+        ++ninv;
+        uint32_t task = w.inv[t];
+        uint32_t u = task >> 8;
+        int s = (int)((task >> 4) & 15u), j = (int)(task & 15u);
+        int2 ub = w.units[u];
+        int pix = ub.x, b = ub.y;
+        Rec y;
+        if (s == 0) {
+            rec_load(a.src, (size_t)pix * Bn + b, y);
+        } else {
+            ResDev R;
+            R.planes = w.yrec; R.stride = (size_t)w.cap_units * (S - 1);
+            rec_load(R, (size_t)u * (S - 1) + (s - 1), y);
+        }
+        int q = w.slot_pix[(size_t)pix * S + j];
+        Domain D0 = pix_domain(&a.cur, pix, b);
+        Domain Dj = pix_domain(slot_frame(a, j), q, b);
+        bool geom_static = (a.temporal && j == 1) ? a.geom_static != 0 : true;
+        Rec tmp;
+        float pj = 0.f, Jj = 1.f;
+        float term = 0.f;
+        if (shift_rec(y, D0, Dj, a.P, geom_static, tmp, pj, Jj, nullptr)) term = w.slot_M[(size_t)pix * S + j] * pj * Jj;
+        w.terms[((size_t)u * S + s) * S + j] = term;
+    }
+    if (a.stats) {
+        unsigned long long x = ninv;
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if ((threadIdx.x & 31) == 0 && x) {
+            atomicAdd(&a.stats->v[5], x);
+            if (!a.temporal) atomicAdd(&a.stats->v[7], x);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------------------------
+// merge: MIS weights, streaming selection, output record
+// --------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+    const uint32_t nunits = min(w.counters[0], (uint32_t)w.cap_units);
+    const int S = w.slots;
+    const FrameDev& C = a.cur;
+    const int Bn = C.B > 0 ? C.B : 1;
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nunits; u += gridDim.x * blockDim.x) {
+        int2 ub = w.units[u];
+        int pix = ub.x, b = ub.y;
+        int n = w.nslot[pix];
+        float py[kMaxSlots], J[kMaxSlots], ph[kMaxSlots], Wx[kMaxSlots], M[kMaxSlots], wv[kMaxSlots];
+        bool ok[kMaxSlots];
+        for (int s = 0; s < n; ++s) {
+            M[s] = w.slot_M[(size_t)pix * S + s];
+            ok[s] = false;
+            wv[s] = 0.f;
+            const ResDev* R = slot_res(a, s);
+            int q = w.slot_pix[(size_t)pix * S + s];
+            if (!occ_get(*R, q, b)) continue;
+            const FrameDev* Fs = slot_frame(a, s);
+            int Bs = Fs->B > 0 ? Fs->B : 1;
+            float4 p0 = R->planes[(size_t)q * Bs + b];
+            ph[s] = p0.y; Wx[s] = p0.x;
+            if (s == 0) { py[0] = p0.y; J[0] = 1.f; ok[0] = py[0] > 0.f; }
+            else { py[s] = w.py[(size_t)u * S + s]; J[s] = w.jac[(size_t)u * S + s]; ok[s] = py[s] > 0.f; }
+        }
+        for (int s = 0; s < n; ++s) {
+            if (!ok[s]) continue;
+            float num = s == 0 ? M[0] * py[0] : M[s] * ph[s] / J[s];
+            float den = M[0] * py[s];
+            for (int j = 1; j < n; ++j) den += (j == s) ? M[s] * ph[s] / J[s] : w.terms[((size_t)u * S + s) * S + j];
+            float m = den > 0.f ? num / den : 0.f;
+            wv[s] = m * py[s] * Wx[s] * J[s];
+            if (!(wv[s] > 0.f) || !isfinite(wv[s])) wv[s] = 0.f;
+        }
+        float Ssum = 0.f;
+        int sel = -1;
+        for (int s = 0; s < n; ++s) {
+            if (!(wv[s] > 0.f)) continue;
+            uint4 r = philox((uint32_t)pix, C.frame, ((uint32_t)a.pass << 8) | (uint32_t)s, P_MERGE | ((uint32_t)b << 8), a.P.seed);
+            Ssum += wv[s];
+            if (u01(r.x) * Ssum < wv[s]) sel = s;
+        }
+        float outv = 0.f;
+        if (sel >= 0) {
+            Rec y;
+            if (sel == 0) rec_load(a.src, (size_t)pix * Bn + b, y);
+            else {
+                ResDev R;
+                R.planes = w.yrec; R.stride = (size_t)w.cap_units * (S - 1);
+                rec_load(R, (size_t)u * (S - 1) + (sel - 1), y);
+            }
+            y.W = Ssum / py[sel];
+            y.phat = py[sel];
+            rec_store(a.dst, (size_t)pix * Bn + b, y);
+            atomicOr(&a.dst.occ[(size_t)pix * a.dst.words + (b >> 5)], 1u << (b & 31));
+            outv = y.phat * y.W;
+        }
+        if (a.out) a.out[pix] = outv;
+    }
+}
+
+// ev (optional): 5 events recorded around the four kernels for per-kernel timing
+cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, cudaEvent_t* ev,
+                              cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(w.counters, 0, 4 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    int np = p1 - p0;
+    if (np <= 0) return cudaSuccess;
+    if (ev) cudaEventRecord(ev[0], s);
+    reuse_setup_kernel<<<(np + 127) / 128, 128, 0, s>>>(a, w, p0, p1);
+    if (ev) cudaEventRecord(ev[1], s);
+    shift_fwd_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    if (ev) cudaEventRecord(ev[2], s);
+    shift_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    if (ev) cudaEventRecord(ev[3], s);
+    reuse_merge_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    if (ev) cudaEventRecord(ev[4], s);
+    return cudaGetLastError();
+}
+
+cudaError_t reuse_persist_blocks(int* out) {
+    int dev = 0, sms = 0, b1 = 0, b2 = 0, b3 = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, shift_fwd_kernel, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, shift_inv_kernel, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, reuse_merge_kernel, 128, 0);
+    int b = b1;
+    if (b2 < b) b = b2;
+    if (b3 < b) b = b3;
+    *out = sms * (b > 0 ? b : 1);
+    return cudaGetLastError();
+}
+
+}  // namespace tof

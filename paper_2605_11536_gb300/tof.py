@@ -223,19 +223,21 @@ def tof_reservoirs_reset(ctx, view: int):
 
 
 def tof_view_stats(ctx, view: int):
-    a = (C.c_double * 5)()
+    a = (C.c_double * 8)()
     _check(ctx, lib().tof_view_stats(ctx, view, a), "tof_view_stats")
-    return dict(newton_calls=a[0], newton_iters=a[1], newton_ok=a[2], shift_calls=a[3], shift_ok=a[4])
+    return dict(newton_calls=a[0], newton_iters=a[1], newton_ok=a[2], shift_calls=a[3], shift_ok=a[4], inv_calls=a[5],
+                spatial_fwd_calls=a[6], spatial_inv_calls=a[7])
 
 
 def tof_view_profile(ctx, view: int, enable: int = 1):
     _check(ctx, lib().tof_view_profile(ctx, view, int(enable)), "tof_view_profile")
 
 
-STAGES = ("gbuffer", "initial", "temporal", "spatial", "splat", "frame")
+STAGES = ("gbuffer", "initial", "temporal", "spatial", "splat", "frame", "spatial_setup", "spatial_fwd_shift",
+          "spatial_inv_shift", "spatial_merge")
 
 
 def tof_view_stage_ms(ctx, view: int):
-    a = (C.c_float * 6)()
+    a = (C.c_float * 10)()
     _check(ctx, lib().tof_view_stage_ms(ctx, view, a), "tof_view_stage_ms")
     return dict(zip(STAGES, [float(x) for x in a]))
