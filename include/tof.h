@@ -145,6 +145,29 @@ tof_status tof_render_gated(tof_ctx* ctx, tof_scene scene, tof_view view, const 
                             const tof_emitter* emitter, const tof_gate* gate, const tof_params* params,
                             uint64_t seed, uint32_t frame, float* out_image_dev, void* stream);
 
+/* Allocation-free variant of tof_render_gated, for callers that may not allocate device memory
+ * while they render: code that records frames into a CUDA graph, real-time loops that run under
+ * a fixed device-memory pool, or hosts that forbid cudaMalloc after start-up.  tof_render_gated
+ * allocates a view's reuse scratch (slot tables, shift task lists, shifted records, MIS terms)
+ * with cudaMalloc on the view's first frame; this entry point takes that scratch from a static
+ * device array compiled into the library instead and calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The paper has no counterpart; the rendering it performs is exactly that
+ * of tof_render_gated.
+ *   - Limits: the view has W*H <= 16384 pixels (e.g. 128 x 128), is a gated view (B = 0), and
+ *     params->n_spatial <= 5; larger requests fail with TOF_EINVAL and a message naming the limit.
+ *   - The static array (about 14.5 MiB) belongs to the library's device image: every GPU that
+ *     loads libtof.so holds it until the process exits.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the one array and each call overwrites it (its task counters are reset on
+ *     the stream at the start of each reuse pass): calls whose work overlaps on the GPU -- on
+ *     different streams, or from different threads -- race and must be serialised by the caller.
+ *   - Scene, view and output are as for tof_render_gated; the view itself (tof_view_create) is
+ *     allocated at set-up time. */
+tof_status tof_render_gated_noalloc(tof_ctx* ctx, tof_scene scene, tof_view view, const tof_sensor* sensor,
+                                    const tof_emitter* emitter, const tof_gate* gate, const tof_params* params,
+                                    uint64_t seed, uint32_t frame, float* out_image_dev, void* stream);
+
 /* Render one transient frame (Sec. 4.5): per-bin reservoirs, per-bin temporal / spatial reuse,
  * and the histogram out_hist_dev[H*W*B] (bin fastest, float32). */
 tof_status tof_render_transient(tof_ctx* ctx, tof_scene scene, tof_view view, const tof_sensor* sensor,

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -221,6 +222,70 @@ static FrameDev make_frame(const SceneH& S, int slot, const tof_sensor* s, const
     F.frame = frame;
     F.gb = gb;
     return F;
+}
+
+// ============================================================================================
+// allocation-free gated rendering
+//
+// The first render of a view allocates the reuse passes' wavefront scratch (slot tables, task
+// lists, shifted records, MIS terms) with cudaMalloc.  tof_render_gated_noalloc instead takes that
+// scratch from the file-scope device array below, so a call allocates nothing.  The array is a
+// fixed part of the library's device image: every GPU that loads libtof.so holds it until the
+// process exits.  Limits: W*H <= kNoAllocMaxPix pixels and 1 + n_spatial <= kNoAllocMaxSlots.
+// ============================================================================================
+constexpr size_t kNoAllocMaxPix = 16384;
+constexpr size_t kNoAllocMaxSlots = 6;
+constexpr size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kNA_U = kNoAllocMaxPix, kNA_S = kNoAllocMaxSlots;
+constexpr size_t kNA_slot_pix = 0;
+constexpr size_t kNA_slot_M = kNA_slot_pix + al256(sizeof(int) * kNoAllocMaxPix * kNA_S);
+constexpr size_t kNA_nslot = kNA_slot_M + al256(sizeof(float) * kNoAllocMaxPix * kNA_S);
+constexpr size_t kNA_units = kNA_nslot + al256(kNoAllocMaxPix);
+constexpr size_t kNA_fwd = kNA_units + al256(sizeof(int2) * kNA_U);
+constexpr size_t kNA_inv = kNA_fwd + al256(sizeof(uint32_t) * kNA_U * (kNA_S - 1));
+constexpr size_t kNA_yrec = kNA_inv + al256(sizeof(uint32_t) * kNA_U * kNA_S * (kNA_S - 1));
+constexpr size_t kNA_py = kNA_yrec + al256(sizeof(float4) * 6 * kNA_U * (kNA_S - 1));
+constexpr size_t kNA_jac = kNA_py + al256(sizeof(float) * kNA_U * kNA_S);
+constexpr size_t kNA_terms = kNA_jac + al256(sizeof(float) * kNA_U * kNA_S);
+constexpr size_t kNA_counters = kNA_terms + al256(sizeof(float) * kNA_U * kNA_S * kNA_S);
+constexpr size_t kNoAllocBytes = kNA_counters + 256;   // about 14.5 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// device address of g_noalloc_scratch per device, looked up once per device (with that device
+// current) on the first call made on it
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256];
+
+static tof_status noalloc_wave(tof_ctx* c, WaveDev* w) {
+    if (c->device < 0 || c->device >= 256) return fail(c, TOF_EINVAL, "device id out of range");
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[c->device]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return fail(c, TOF_ECUDA, "cudaGetSymbolAddress of the static reuse scratch failed: %s", cudaGetErrorString(e));
+            g_noalloc_addr[c->device] = p;
+        }
+        base = g_noalloc_addr[c->device];
+    }
+    unsigned char* b = (unsigned char*)base;
+    w->slots = (int)kNA_S;
+    w->cap_units = (int)kNA_U;
+    w->slot_pix = (int*)(b + kNA_slot_pix);
+    w->slot_M = (float*)(b + kNA_slot_M);
+    w->nslot = (uint8_t*)(b + kNA_nslot);
+    w->units = (int2*)(b + kNA_units);
+    w->fwd = (uint32_t*)(b + kNA_fwd);
+    w->inv = (uint32_t*)(b + kNA_inv);
+    w->yrec = (float4*)(b + kNA_yrec);
+    w->py = (float*)(b + kNA_py);
+    w->jac = (float*)(b + kNA_jac);
+    w->terms = (float*)(b + kNA_terms);
+    w->counters = (uint32_t*)(b + kNA_counters);
+    return TOF_OK;
 }
 
 extern "C" {
@@ -446,24 +511,24 @@ static tof_status ensure_wave(tof_ctx* c, ViewH& V, int S, int cap) {
 
 // one reuse pass as a wavefront; transient passes run in pixel chunks so that a chunk's merge
 // units (at most B per pixel) never exceed the scratch capacity
-static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, cudaStream_t s) {
+static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const WaveDev* fixed, cudaStream_t s) {
     const int S = ra.temporal ? 2 : 1 + ra.P.n_spatial;
     const size_t npix = (size_t)V.W * V.H;
     const size_t Bn = V.B > 0 ? (size_t)V.B : 1;
     const size_t kMaxUnits = (size_t)1 << 22;
     size_t cap = npix * Bn < kMaxUnits ? npix * Bn : kMaxUnits;
     if (cap < npix && V.B == 0) cap = npix;
-    TRY(ensure_wave(c, V, S, (int)cap));
+    if (!fixed) TRY(ensure_wave(c, V, S, (int)cap));
     if (!c->persist_blocks) CK(reuse_persist_blocks(&c->persist_blocks));
-    WaveDev w = V.wave;
+    WaveDev w = fixed ? *fixed : V.wave;
     w.slots = S;
-    w.cap_units = V.wave_cap;
+    if (!fixed) w.cap_units = V.wave_cap;
     size_t chunk = V.B > 0 ? (size_t)V.wave_cap / Bn : npix;
     if (chunk < 1) chunk = 1;
     for (size_t p0 = 0; p0 < npix; p0 += chunk) {
         size_t p1 = p0 + chunk < npix ? p0 + chunk : npix;
         cudaEvent_t* ev = nullptr;
-        if (V.profile && !ra.temporal) {
+        if (V.profile && !ra.temporal && !fixed) {
             while (V.kev.size() < V.kev_used + 5) {
                 cudaEvent_t e;
                 CK(cudaEventCreate(&e));
@@ -485,7 +550,7 @@ static void mark(ViewH& V, int k, cudaStream_t s) {
 
 static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_sensor* sensor, const tof_emitter* emitter,
                          float L0, float dL, int B, const tof_params* params, uint64_t seed, uint32_t frame, float* out,
-                         void* stream) {
+                         void* stream, const WaveDev* fixed_wave = nullptr) {
     if (!c) return TOF_EINVAL;
     if (scene < 0 || scene >= (int)c->scenes.size() || !c->scenes[scene].alive) return fail(c, TOF_EINVAL, "bad scene handle");
     if (vid < 0 || vid >= (int)c->views.size() || !c->views[vid].alive) return fail(c, TOF_EINVAL, "bad view handle");
@@ -547,7 +612,7 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
         ra.temporal = 1; ra.pass = 0;
         ra.geom_static = V.geom_version[1 - fc] == S.version[S.cur];
         ra.out = (stage == stages - 1 && B == 0) ? out : nullptr;
-        TRY(reuse_pass(c, V, ra, s));
+        TRY(reuse_pass(c, V, ra, fixed_wave, s));
         src = out_of(stage);
         ++stage;
         V.ran[2] = true;
@@ -561,7 +626,7 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
             ra.dst = V.res[out_of(stage)].dev();
             ra.temporal = 0; ra.pass = 1 + it; ra.geom_static = 1;
             ra.out = (stage == stages - 1 && B == 0) ? out : nullptr;
-            TRY(reuse_pass(c, V, ra, s));
+            TRY(reuse_pass(c, V, ra, fixed_wave, s));
             src = out_of(stage);
             ++stage;
             V.ran[3] = true;
@@ -622,6 +687,27 @@ tof_status tof_render_gated(tof_ctx* c, tof_scene scene, tof_view view, const to
     if (!c) return TOF_EINVAL;
     if (!gate) return fail(c, TOF_EINVAL, "gate is NULL");
     return render(c, scene, view, sensor, emitter, gate->L0, gate->dL, 0, params, seed, frame, out_image_dev, stream);
+}
+
+tof_status tof_render_gated_noalloc(tof_ctx* c, tof_scene scene, tof_view view, const tof_sensor* sensor,
+                                    const tof_emitter* emitter, const tof_gate* gate, const tof_params* params, uint64_t seed,
+                                    uint32_t frame, float* out_image_dev, void* stream) {
+    if (!c) return TOF_EINVAL;
+    if (!gate) return fail(c, TOF_EINVAL, "gate is NULL");
+    if (!params) return fail(c, TOF_EINVAL, "params is NULL");
+    if (view < 0 || view >= (int)c->views.size() || !c->views[view].alive) return fail(c, TOF_EINVAL, "bad view handle");
+    const ViewH& V = c->views[view];
+    if (V.B != 0) return fail(c, TOF_EINVAL, "tof_render_gated_noalloc: the view is a transient view");
+    if ((size_t)V.W * (size_t)V.H > kNoAllocMaxPix)
+        return fail(c, TOF_EINVAL, "tof_render_gated_noalloc: %d x %d pixels exceed the static scratch limit of %zu pixels",
+                    V.W, V.H, kNoAllocMaxPix);
+    if (params->n_spatial < 0 || (size_t)(1 + params->n_spatial) > kNoAllocMaxSlots)
+        return fail(c, TOF_EINVAL, "tof_render_gated_noalloc: n_spatial %d exceeds the static scratch limit of %zu",
+                    params->n_spatial, kNoAllocMaxSlots - 1);
+    cudaSetDevice(c->device);
+    WaveDev w;
+    TRY(noalloc_wave(c, &w));
+    return render(c, scene, view, sensor, emitter, gate->L0, gate->dL, 0, params, seed, frame, out_image_dev, stream, &w);
 }
 
 tof_status tof_render_transient(tof_ctx* c, tof_scene scene, tof_view view, const tof_sensor* sensor,

@@ -52,7 +52,8 @@ class tof_params(C.Structure):
 
 EXPORTS = ["tof_create", "tof_destroy", "tof_last_error", "tof_device_bytes", "tof_scene_upload", "tof_scene_destroy",
            "tof_bvh_build", "tof_view_create", "tof_view_destroy", "tof_render_gated", "tof_render_transient",
-           "tof_render_pt", "tof_reservoirs_reset", "tof_view_stats", "tof_view_profile", "tof_view_stage_ms"]
+           "tof_render_pt", "tof_reservoirs_reset", "tof_view_stats", "tof_view_profile", "tof_view_stage_ms",
+           "tof_render_gated_noalloc"]
 
 _vp, _fp, _u32p = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)
 
@@ -72,6 +73,8 @@ def _declare(L):
     L.tof_view_destroy.argtypes = [_vp, C.c_int32]
     L.tof_render_gated.argtypes = [_vp, C.c_int32, C.c_int32, C.POINTER(tof_sensor), C.POINTER(tof_emitter),
                                    C.POINTER(tof_gate), C.POINTER(tof_params), C.c_uint64, C.c_uint32, _vp, _vp]
+    L.tof_render_gated_noalloc.argtypes = [_vp, C.c_int32, C.c_int32, C.POINTER(tof_sensor), C.POINTER(tof_emitter),
+                                           C.POINTER(tof_gate), C.POINTER(tof_params), C.c_uint64, C.c_uint32, _vp, _vp]
     L.tof_render_transient.argtypes = [_vp, C.c_int32, C.c_int32, C.POINTER(tof_sensor), C.POINTER(tof_emitter),
                                        C.POINTER(tof_bins), C.POINTER(tof_params), C.c_uint64, C.c_uint32, _vp, _vp]
     L.tof_render_pt.argtypes = [_vp, C.c_int32, C.POINTER(tof_sensor), C.POINTER(tof_emitter), C.POINTER(tof_gate),
@@ -199,6 +202,15 @@ def tof_render_gated(ctx, scene, view, sensor_d, emitter_d, gate, params_p, seed
     rc = lib().tof_render_gated(ctx, scene, view, C.byref(s), C.byref(e), C.byref(g), C.byref(p), int(seed), int(frame),
                                 C.c_void_p(out_ptr), C.c_void_p(stream))
     _check(ctx, rc, "tof_render_gated")
+
+
+def tof_render_gated_noalloc(ctx, scene, view, sensor_d, emitter_d, gate, params_p, seed, frame, out_ptr, stream=0):
+    """tof_render_gated without device allocation inside the call (static reuse scratch; see tof.h)."""
+    s, e, p = sensor(sensor_d), emitter(emitter_d), params(params_p)
+    g = tof_gate(float(gate[0]), float(gate[1]))
+    rc = lib().tof_render_gated_noalloc(ctx, scene, view, C.byref(s), C.byref(e), C.byref(g), C.byref(p), int(seed),
+                                        int(frame), C.c_void_p(out_ptr), C.c_void_p(stream))
+    _check(ctx, rc, "tof_render_gated_noalloc")
 
 
 def tof_render_transient(ctx, scene, view, sensor_d, emitter_d, bins, params_p, seed, frame, out_ptr, stream=0):
