@@ -284,7 +284,10 @@ void or_geom_destroy(ogeom* g) {
     free(g->tv); free(g->tmat); free(g->mats); free(g->xf); free(g->nodes); free(g->prim); free(g);
 }
 
-/* Moller-Trumbore ray/triangle test (Moller, Trumbore 1997); t in (tmin, tmax) */
+/* Moller-Trumbore ray/triangle test (Moller, Trumbore 1997); t in (tmin, tmax).  The barycentric
+ * tests accept BARY_EPS outside the triangle so that a ray through an edge shared by two triangles
+ * hits at least one of them whatever the rounding (no cracks on tessellated surfaces). */
+#define BARY_EPS 1e-6
 static int tri_hit(const double* v, v3 o, v3 d, double tmin, double tmax, double* t, double* b1, double* b2) {
     v3 v0 = vload(v), e1 = vsub(vload(v + 3), v0), e2 = vsub(vload(v + 6), v0);
     v3 pv = vcross(d, e2);
@@ -293,10 +296,10 @@ static int tri_hit(const double* v, v3 o, v3 d, double tmin, double tmax, double
     double inv = 1.0 / det;
     v3 tv = vsub(o, v0);
     double u = vdot(tv, pv) * inv;
-    if (u < 0.0 || u > 1.0) return 0;
+    if (u < -BARY_EPS || u > 1.0 + BARY_EPS) return 0;
     v3 qv = vcross(tv, e1);
     double w = vdot(d, qv) * inv;
-    if (w < 0.0 || u + w > 1.0) return 0;
+    if (w < -BARY_EPS || u + w > 1.0 + BARY_EPS) return 0;
     double tt = vdot(e2, qv) * inv;
     if (!(tt > tmin && tt < tmax)) return 0;
     *t = tt; *b1 = u; *b2 = w;
@@ -329,7 +332,9 @@ static int trace(const ogeom* g, v3 o, v3 d, double tmax, int any_hit, int* tri,
         if (nd->left < 0) {
             for (int i = nd->start; i < nd->start + nd->count; ++i) {
                 double t, u, w;
-                if (tri_hit(tri_v(g, g->prim[i]), o, d, 0.0, best, &t, &u, &w)) {
+                /* closest hit; at equal distance the lower triangle index wins (order-independent) */
+                if (tri_hit(tri_v(g, g->prim[i]), o, d, 0.0, found ? best * (1.0 + 1e-12) + 1e-300 : best, &t, &u, &w) &&
+                    (!found || t < best || (t == best && g->prim[i] < *tri))) {
                     best = t; *tri = g->prim[i]; *b1 = u; *b2 = w; found = 1;
                     if (any_hit) { *tout = t; return 1; }
                 }
@@ -351,7 +356,8 @@ int or_geom_intersect(const ogeom* g, const double* o, const double* d, double t
     double best = tmax;
     for (int i = 0; i < g->nt; ++i) {
         double tt, u, w;
-        if (tri_hit(tri_v(g, i), oo, dd, 0.0, best, &tt, &u, &w)) { best = tt; *tri = i; *b1 = u; *b2 = w; found = 1; }
+        if (tri_hit(tri_v(g, i), oo, dd, 0.0, found ? best * (1.0 + 1e-12) + 1e-300 : best, &tt, &u, &w) &&
+            (!found || tt < best || (tt == best && i < *tri))) { best = tt; *tri = i; *b1 = u; *b2 = w; found = 1; }
     }
     if (found) *t = best;
     return found;
@@ -799,7 +805,7 @@ static int shift_rec(const orec* x, const odomain* Dj, const odomain* Di, const 
     }
     double nb1, nb2;
     xi_to_bary(gi, x->p_tri, &N.fy, xp, &nb1, &nb2);
-    if (!(nb1 >= 0.0 && nb2 >= 0.0 && nb1 + nb2 <= 1.0)) return 0;
+    if (!(nb1 >= -BARY_EPS && nb2 >= -BARY_EPS && nb1 + nb2 <= 1.0 + BARY_EPS)) return 0;
     osurf pp = surf_at(gi, x->p_tri, nb1, nb2);
 
     /* (5) the offset path must reconnect at the same index (bijectivity of the hybrid shift) */

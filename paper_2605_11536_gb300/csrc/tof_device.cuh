@@ -170,6 +170,9 @@ static __device__ __forceinline__ float3 offset_point(float3 p, float3 n, float3
     return dot3(n, dir) >= 0.f ? p + n * eps : p - n * eps;
 }
 
+// Moller-Trumbore with barycentric tests inclusive by kBaryEps, so that a ray through an edge
+// shared by two triangles hits at least one of them whatever the rounding (no cracks)
+constexpr float kBaryEps = 1e-6f;
 static __device__ __forceinline__ bool tri_test(const float4* __restrict__ L, int leaf, float3 o, float3 d, float tmax, float& t,
                                          float& b1, float& b2, int& orig) {
     float4 a = __ldg(&L[3 * leaf]), e1v = __ldg(&L[3 * leaf + 1]), e2v = __ldg(&L[3 * leaf + 2]);
@@ -180,14 +183,18 @@ static __device__ __forceinline__ bool tri_test(const float4* __restrict__ L, in
     float inv = 1.0f / det;
     float3 tv = o - xyz(a);
     float u = dot3(tv, pv) * inv;
-    if (u < 0.f || u > 1.f) return false;
+    if (u < -kBaryEps || u > 1.f + kBaryEps) return false;
     float3 qv = cross3(tv, e1);
     float w = dot3(d, qv) * inv;
-    if (w < 0.f || u + w > 1.f) return false;
+    if (w < -kBaryEps || u + w > 1.f + kBaryEps) return false;
     float tt = dot3(e2, qv) * inv;
-    if (!(tt > 0.f && tt < tmax)) return false;
+    if (!(tt > 0.f && tt <= tmax)) return false;
     t = tt; b1 = u; b2 = w; orig = __float_as_int(a.w);
     return true;
+}
+// closest-hit acceptance: nearer, or equally near with a lower triangle id (order-independent)
+static __device__ __forceinline__ bool closer(bool found, float t, int id, float best, int best_id) {
+    return !found || t < best || (t == best && id < best_id);
 }
 
 // closest hit (any_hit = false) or first hit (any_hit = true) of o + t d, t in (0, tmax).
@@ -200,7 +207,7 @@ static __device__ __noinline__ bool traverse(const GeomDev& g, float3 o, float3 
     float best = tmax;
     if (g.nt == 1) {
         int orig;
-        if (tri_test(g.leaf, 0, o, d, best, tout, b1, b2, orig)) { tri = orig; return true; }
+        if (tri_test(g.leaf, 0, o, d, best, tout, b1, b2, orig) && tout < tmax) { tri = orig; return true; }
         return false;
     }
     float3 id = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
@@ -229,7 +236,7 @@ static __device__ __noinline__ bool traverse(const GeomDev& g, float3 o, float3 
         int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
         if (h0 && ch0 < 0) {
             float t, u, w; int orig;
-            if (tri_test(g.leaf, ~ch0, o, d, best, t, u, w, orig)) {
+            if (tri_test(g.leaf, ~ch0, o, d, best, t, u, w, orig) && (found || t < tmax) && closer(found, t, orig, best, tri)) {
                 best = t; tri = orig; b1 = u; b2 = w; found = true;
                 if (kAny) { tout = t; return true; }
             }
@@ -237,7 +244,7 @@ static __device__ __noinline__ bool traverse(const GeomDev& g, float3 o, float3 
         }
         if (h1 && ch1 < 0) {
             float t, u, w; int orig;
-            if (tri_test(g.leaf, ~ch1, o, d, best, t, u, w, orig)) {
+            if (tri_test(g.leaf, ~ch1, o, d, best, t, u, w, orig) && (found || t < tmax) && closer(found, t, orig, best, tri)) {
                 best = t; tri = orig; b1 = u; b2 = w; found = true;
                 if (kAny) { tout = t; return true; }
             }
@@ -789,7 +796,7 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
         nb2 = xp[1] / e2b;
         nb1 = (xp[0] - nb2 * e2t) / e1t;
     }
-    if (!(nb1 >= 0.f && nb2 >= 0.f && nb1 + nb2 <= 1.0f)) return false;
+    if (!(nb1 >= -kBaryEps && nb2 >= -kBaryEps && nb1 + nb2 <= 1.0f + kBaryEps)) return false;
     Surf pp = surf_at(gi, x.p_tri, nb1, nb2);
 
     // (5) the offset path must reconnect at the same index
