@@ -249,6 +249,76 @@ def run_ours(args, rank, world):
                 nobj=len(sc.object_material))
 
 
+def batch_workload(n=64, seed=3):
+    """64 instances over 4 scenes built like the dynamic workload (10k..200k triangles), resolutions
+    log-uniform in [64, 1024], gate widths U[0.01, 0.1] m, depths U{2..5}."""
+    from paper_2605_11536_gb300 import scenes
+    shapes = [(50, 40, 10), (100, 100, 20), (200, 150, 40), (300, 250, 60)]   # nx, ny, spheres -> 12k..198k tris
+    sc = [scenes.heightfield_spheres(W=64, H=64, frames=8, seed=10 + i, nx=nx, ny=ny, n_spheres=ns)
+          for i, (nx, ny, ns) in enumerate(shapes)]
+    inst = scenes.batch_instances(n=n, seed=seed)
+    return sc, inst
+
+
+def run_batched(args, steps=6, warmup=2):
+    """Batched form: all instances in one tof_render_batch graph launch, against one
+    tof_render_gated launch per instance on one stream (same jobs, same frames)."""
+    import torch
+    from paper_2605_11536_gb300 import tof
+    scs, inst = batch_workload()
+    ctx = tof.tof_create(torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    try:
+        sids = [tof.tof_scene_upload(ctx, s.verts, s.tris, s.tri_object, s.materials, s.object_material) for s in scs]
+        res = {}
+        for mode in ("per_launch", "batched"):
+            views, bufs, params = [], [], []
+            for it in inst:
+                views.append(tof.tof_view_create(ctx, sids[it["scene"]], it["W"], it["H"], 0))
+                bufs.append(torch.zeros(it["W"] * it["H"], device="cuda"))
+                sc = scs[it["scene"]]
+                p = type(sc.params)(**vars(sc.params))
+                p.depth = it["depth"]
+                params.append(p)
+            times = []
+            for f in range(warmup + steps):
+                for k, s in enumerate(scs):
+                    tof.tof_bvh_build(ctx, sids[k], s.xforms[f % s.n_frames].reshape(-1), refit_only=0 if f == 0 else 1,
+                                      stream=sptr)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                jobs = []
+                for i, it in enumerate(inst):
+                    sc = scs[it["scene"]]
+                    sens = dict(sc.sensors[f % sc.n_frames], W=it["W"], H=it["H"])
+                    gate = (sc.gates[0][0], it["dL"])
+                    if mode == "batched":
+                        jobs.append(tof.job(sids[it["scene"]], views[i], sens, sc.emitters[0], params[i], it["seed"], f,
+                                            bufs[i].data_ptr(), gate=gate))
+                    else:
+                        tof.tof_render_gated(ctx, sids[it["scene"]], views[i], sens, sc.emitters[0], gate, params[i],
+                                             it["seed"], f, bufs[i].data_ptr(), sptr)
+                if mode == "batched":
+                    tof.tof_render_batch(ctx, jobs, sptr)
+                e1.record(stream)
+                stream.synchronize()
+                if f >= warmup:
+                    times.append(e0.elapsed_time(e1))
+            res[mode] = float(np.mean(times))
+            for v in views:
+                tof.tof_view_destroy(ctx, v)
+    finally:
+        tof.tof_destroy(ctx)
+    npx = sum(it["W"] * it["H"] for it in inst)
+    return {"instances": len(inst), "pixels": npx, "scene_tris": [int(s.nt) for s in scs],
+            "batched_ms": res["batched"], "per_launch_ms": res["per_launch"],
+            "batched_instances_per_s": len(inst) / (res["batched"] / 1e3),
+            "per_launch_instances_per_s": len(inst) / (res["per_launch"] / 1e3),
+            "speedup": res["per_launch"] / res["batched"], "frames_timed": steps}
+
+
 def cpu_baseline(args, crop=None, frames=3):
     """The oracle as it stands on the host cores (all of them, OpenMP): the first `frames` frames of
     the workload at full resolution (or on a crop of it, with the margin the spatial reuse needs),
@@ -303,9 +373,10 @@ def main():
     ap.add_argument("--steps", type=int, default=240)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-spp", type=int, default=512)
+    ap.add_argument("--ref-spp", type=int, default=4096)
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -377,6 +448,11 @@ def main():
             "shifts_per_frame": {"spatial_forward": pf["spatial_fwd_calls"], "spatial_inverse": pf["spatial_inv_calls"],
                                  "all_forward": pf["shift_calls"], "all_inverse": pf["inv_calls"]},
             "wall_s": r["wall"]}
+    if not args.no_batch:
+        try:
+            line["batched"] = run_batched(args)
+        except Exception as e:
+            line["batched"] = {"error": str(e)[:300]}
     if not args.no_cpu:
         try:
             line["cpu_baseline"] = cpu_baseline(args)

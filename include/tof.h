@@ -174,6 +174,28 @@ tof_status tof_render_transient(tof_ctx* ctx, tof_scene scene, tof_view view, co
                                 const tof_emitter* emitter, const tof_bins* bins, const tof_params* params,
                                 uint64_t seed, uint32_t frame, float* out_hist_dev, void* stream);
 
+/* One render job of a batch (configs[3]-style batched rendering): a gated (transient == 0) or
+ * transient frame of one view, exactly as tof_render_gated / tof_render_transient would render it. */
+typedef struct {
+    tof_scene scene;
+    tof_view view;
+    tof_sensor sensor;
+    tof_emitter emitter;
+    tof_gate gate;            /* used when transient == 0 */
+    tof_bins bins;            /* used when transient != 0 */
+    int32_t transient;
+    tof_params params;
+    uint64_t seed;
+    uint32_t frame;
+    float* out_dev;           /* H*W (gated) or H*W*B (transient) floats, caller-owned device memory */
+} tof_job;
+
+/* Render n independent jobs as one CUDA graph launched on `stream`: every job's stage kernels form
+ * their own branch of the graph, so small instances run concurrently and the whole batch costs one
+ * launch.  Jobs must use distinct views.  Results equal those of rendering each job on its own.
+ * Scratch for every view is allocated before the graph is captured (first use of a view). */
+tof_status tof_render_batch(tof_ctx* ctx, const tof_job* jobs, uint32_t n, void* stream);
+
 /* Plain gated (bins == NULL) or transient path tracing without reuse, spp paths per pixel each
  * with its own jitter (the comparison method of Sec. 6).  Output layout as above. */
 tof_status tof_render_pt(tof_ctx* ctx, tof_scene scene, const tof_sensor* sensor, const tof_emitter* emitter,

@@ -114,6 +114,13 @@ struct tof_ctx {
     int* d_err = nullptr;
     float* d_scratch = nullptr;  // laser spot of plain PT renders
     int persist_blocks = 0;      // resident blocks of the persistent reuse kernels
+    // batched rendering: stream pool, fork / join events, and the instantiated graph
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t capture = nullptr;
+    cudaGraphExec_t batch_exec = nullptr;
+    bool in_batch = false;
 };
 
 static tof_status fail(tof_ctx* c, tof_status st, const char* fmt, ...) {
@@ -312,6 +319,11 @@ tof_status tof_destroy(tof_ctx* c) {
     if (!c) return TOF_EINVAL;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+    for (cudaStream_t q : c->pool) cudaStreamDestroy(q);
+    for (cudaEvent_t e : c->join) cudaEventDestroy(e);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->capture) cudaStreamDestroy(c->capture);
     for (auto& a : c->allocs) cudaFree(a.p);
     delete c;
     return TOF_OK;
@@ -483,6 +495,8 @@ tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[8]) {
     return TOF_OK;
 }
 
+static bool g_no_marks = false;   // set while a batch is being captured (no profiling events)
+
 // (re)allocate the view's wavefront scratch for S slots per pixel and cap merge units
 static tof_status ensure_wave(tof_ctx* c, ViewH& V, int S, int cap) {
     if (V.wave_slots >= S && V.wave_cap >= cap) return TOF_OK;
@@ -528,7 +542,7 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
     for (size_t p0 = 0; p0 < npix; p0 += chunk) {
         size_t p1 = p0 + chunk < npix ? p0 + chunk : npix;
         cudaEvent_t* ev = nullptr;
-        if (V.profile && !ra.temporal && !fixed) {
+        if (V.profile && !ra.temporal && !fixed && !g_no_marks) {
             while (V.kev.size() < V.kev_used + 5) {
                 cudaEvent_t e;
                 CK(cudaEventCreate(&e));
@@ -545,7 +559,7 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
 // stage boundaries: ev[0] frame start, ev[1] after G-buffer, ev[2] after initial, ev[3] after
 // temporal, ev[4] after spatial, ev[5] after splat, ev[6] frame end
 static void mark(ViewH& V, int k, cudaStream_t s) {
-    if (V.profile && V.ev[k]) cudaEventRecord(V.ev[k], s);
+    if (V.profile && V.ev[k] && !g_no_marks) cudaEventRecord(V.ev[k], s);
 }
 
 static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_sensor* sensor, const tof_emitter* emitter,
@@ -716,6 +730,105 @@ tof_status tof_render_transient(tof_ctx* c, tof_scene scene, tof_view view, cons
     if (!c) return TOF_EINVAL;
     if (!bins || bins->B < 1) return fail(c, TOF_EINVAL, "bins missing or B < 1");
     return render(c, scene, view, sensor, emitter, bins->t0, bins->width, bins->B, params, seed, frame, out_hist_dev, stream);
+}
+
+tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* stream) {
+    if (!c) return TOF_EINVAL;
+    if (!jobs || n == 0) return fail(c, TOF_EINVAL, "empty batch");
+    if (c->in_batch) return fail(c, TOF_ESTATE, "tof_render_batch is not re-entrant");
+    cudaSetDevice(c->device);
+    // validate and prepare every job outside the capture (allocation is not allowed inside it)
+    std::vector<int> seen;
+    for (uint32_t i = 0; i < n; ++i) {
+        const tof_job& J = jobs[i];
+        if (J.view < 0 || J.view >= (int)c->views.size() || !c->views[J.view].alive)
+            return fail(c, TOF_EINVAL, "job %u: bad view handle", i);
+        for (int v : seen)
+            if (v == J.view) return fail(c, TOF_EINVAL, "job %u: view %d used by two jobs of one batch", i, J.view);
+        seen.push_back(J.view);
+        if (J.scene < 0 || J.scene >= (int)c->scenes.size() || !c->scenes[J.scene].alive)
+            return fail(c, TOF_EINVAL, "job %u: bad scene handle", i);
+        if (!c->scenes[J.scene].built) return fail(c, TOF_ESTATE, "job %u: scene %d has no BVH", i, J.scene);
+        ViewH& V = c->views[J.view];
+        TRY(check_params(c, &J.params, J.transient != 0));
+        TRY(check_sensor(c, &J.sensor, V.W, V.H));
+        if (!J.out_dev) return fail(c, TOF_EINVAL, "job %u: output pointer is NULL", i);
+        const size_t npix = (size_t)V.W * V.H, Bn = V.B > 0 ? (size_t)V.B : 1;
+        size_t cap = npix * Bn < ((size_t)1 << 22) ? npix * Bn : ((size_t)1 << 22);
+        if (cap < npix && V.B == 0) cap = npix;
+        int S = 1 + J.params.n_spatial > 2 ? 1 + J.params.n_spatial : 2;
+        TRY(ensure_wave(c, V, S, (int)cap));
+    }
+    if (!c->persist_blocks) CK(reuse_persist_blocks(&c->persist_blocks));
+    const uint32_t P = n < 16 ? n : 16;
+    while (c->pool.size() < P) {
+        cudaStream_t q;
+        cudaEvent_t e;
+        CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->pool.push_back(q);
+        c->join.push_back(e);
+    }
+    if (!c->fork) CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    if (!c->capture) CK(cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+    // capture: fork onto the pool, one branch per stream, join
+    c->in_batch = true;
+    g_no_marks = true;
+    tof_status st = TOF_OK;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEventRecord(c->fork, c->capture);
+        for (uint32_t p = 0; p < P; ++p) cudaStreamWaitEvent(c->pool[p], c->fork, 0);
+        for (uint32_t i = 0; i < n && st == TOF_OK; ++i) {
+            const tof_job& J = jobs[i];
+            cudaStream_t q = c->pool[i % P];
+            if (J.transient)
+                st = render(c, J.scene, J.view, &J.sensor, &J.emitter, J.bins.t0, J.bins.width, J.bins.B, &J.params, J.seed,
+                            J.frame, J.out_dev, q);
+            else
+                st = render(c, J.scene, J.view, &J.sensor, &J.emitter, J.gate.L0, J.gate.dL, 0, &J.params, J.seed, J.frame,
+                            J.out_dev, q);
+        }
+        for (uint32_t p = 0; p < P; ++p) {
+            cudaEventRecord(c->join[p], c->pool[p]);
+            cudaStreamWaitEvent(c->capture, c->join[p], 0);
+        }
+        e = cudaStreamEndCapture(c->capture, &graph);
+    }
+    g_no_marks = false;
+    c->in_batch = false;
+    if (st != TOF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess || !graph) {
+        cudaGetLastError();
+        return fail(c, TOF_ECUDA, "batch capture failed: %s", cudaGetErrorString(e));
+    }
+    // reuse the instantiated graph when only node parameters changed
+    bool updated = false;
+    if (c->batch_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->batch_exec, graph, &info) == cudaSuccess) updated = true;
+        else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->batch_exec);
+            c->batch_exec = nullptr;
+        }
+    }
+    if (!updated) {
+        e = cudaGraphInstantiate(&c->batch_exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            c->batch_exec = nullptr;
+            return fail(c, TOF_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaGraphDestroy(graph);
+    CK(cudaGraphLaunch(c->batch_exec, (cudaStream_t)stream));
+    for (uint32_t i = 0; i < n; ++i) c->views[jobs[i].view].last_stream = (cudaStream_t)stream;
+    return TOF_OK;
 }
 
 tof_status tof_render_pt(tof_ctx* c, tof_scene scene, const tof_sensor* sensor, const tof_emitter* emitter, const tof_gate* gate,

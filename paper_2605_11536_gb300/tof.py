@@ -50,12 +50,20 @@ class tof_params(C.Structure):
                 ("d_min", C.c_float), ("ray_eps", C.c_float), ("flags", C.c_uint32)]
 
 
+class tof_job(C.Structure):
+    pass
+
+
 EXPORTS = ["tof_create", "tof_destroy", "tof_last_error", "tof_device_bytes", "tof_scene_upload", "tof_scene_destroy",
            "tof_bvh_build", "tof_view_create", "tof_view_destroy", "tof_render_gated", "tof_render_transient",
            "tof_render_pt", "tof_reservoirs_reset", "tof_view_stats", "tof_view_profile", "tof_view_stage_ms",
-           "tof_render_gated_noalloc"]
+           "tof_render_gated_noalloc", "tof_render_batch"]
 
 _vp, _fp, _u32p = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)
+
+tof_job._fields_ = [("scene", C.c_int32), ("view", C.c_int32), ("sensor", tof_sensor), ("emitter", tof_emitter),
+                    ("gate", tof_gate), ("bins", tof_bins), ("transient", C.c_int32), ("params", tof_params),
+                    ("seed", C.c_uint64), ("frame", C.c_uint32), ("out_dev", C.c_void_p)]
 
 
 def _declare(L):
@@ -80,6 +88,7 @@ def _declare(L):
     L.tof_render_pt.argtypes = [_vp, C.c_int32, C.POINTER(tof_sensor), C.POINTER(tof_emitter), C.POINTER(tof_gate),
                                 C.POINTER(tof_bins), C.POINTER(tof_params), C.c_uint64, C.c_uint32, C.c_int32, _vp, _vp]
     L.tof_reservoirs_reset.argtypes = [_vp, C.c_int32]
+    L.tof_render_batch.argtypes = [_vp, C.POINTER(tof_job), C.c_uint32, _vp]
     L.tof_view_stats.argtypes = [_vp, C.c_int32, C.POINTER(C.c_double)]
     L.tof_view_profile.argtypes = [_vp, C.c_int32, C.c_int]
     L.tof_view_stage_ms.argtypes = [_vp, C.c_int32, C.POINTER(C.c_float)]
@@ -253,3 +262,22 @@ def tof_view_stage_ms(ctx, view: int):
     a = (C.c_float * 10)()
     _check(ctx, lib().tof_view_stage_ms(ctx, view, a), "tof_view_stage_ms")
     return dict(zip(STAGES, [float(x) for x in a]))
+
+
+def job(scene, view, sensor_d, emitter_d, params_p, seed, frame, out_ptr, gate=None, bins=None) -> tof_job:
+    j = tof_job()
+    j.scene, j.view = int(scene), int(view)
+    j.sensor, j.emitter, j.params = sensor(sensor_d), emitter(emitter_d), params(params_p)
+    if bins is not None:
+        j.bins = tof_bins(float(bins[0]), float(bins[1]), int(bins[2]))
+        j.transient = 1
+    else:
+        j.gate = tof_gate(float(gate[0]), float(gate[1]))
+        j.transient = 0
+    j.seed, j.frame, j.out_dev = int(seed), int(frame), int(out_ptr)
+    return j
+
+
+def tof_render_batch(ctx, jobs, stream: int = 0):
+    arr = (tof_job * len(jobs))(*jobs)
+    _check(ctx, lib().tof_render_batch(ctx, arr, len(jobs), C.c_void_p(stream)), "tof_render_batch")
