@@ -319,6 +319,100 @@ def run_batched(args, steps=6, warmup=2):
             "speedup": res["per_launch"] / res["batched"], "frames_timed": steps}
 
 
+def run_served(args, seconds=1.5, rate=240.0, seed=4):
+    """Served form: 8 dynamic streams (6 gated like the dynamic workload at 256..1024 px, 2 transient
+    confocal 256x256 x 512 bins), Poisson arrivals at `rate` requests/s for `seconds`, continuous
+    batching by tof_server_step; against the same requests rendered one launch each."""
+    import torch
+    from paper_2605_11536_gb300 import scenes, tof
+    rng = np.random.default_rng(seed)
+    gated_res = [256, 362, 512, 512, 724, 1024]
+    nfr = 32
+    scs = [scenes.heightfield_spheres(W=r, H=r, frames=nfr, seed=20 + k) for k, r in enumerate(gated_res)]
+    for k in range(2):
+        c = scenes.confocal_nlos(W=256, H=256, frames=nfr, B=512, seed=30 + k)
+        c.bins = (1.35, 0.002, 512)
+        scs.append(c)
+    # arrivals: 70 % gated requests spread over the gated streams, 30 % over the transient ones
+    t, arrivals = 0.0, []
+    while t < seconds:
+        t += rng.exponential(1.0 / rate)
+        st = int(rng.integers(0, 6)) if rng.uniform() < 0.7 else 6 + int(rng.integers(0, 2))
+        arrivals.append((t, st))
+    ctx = tof.tof_create(torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    result = {}
+    try:
+        sids = [tof.tof_scene_upload(ctx, s.verts, s.tris, s.tri_object, s.materials, s.object_material) for s in scs]
+        for k, s in enumerate(scs):
+            tof.tof_bvh_build(ctx, sids[k], s.xforms[0].reshape(-1), stream=sptr)
+        shape = [(s.sensors[0]["W"], s.sensors[0]["H"], s.bins[2] if s.bins else 0) for s in scs]
+        out = [torch.zeros(W * H * max(B, 1), device="cuda") for W, H, B in shape]
+        torch.cuda.synchronize()
+
+        def job_for(k, f):
+            s = scs[k]
+            return tof.job(sids[k], 0, s.sensors[f % nfr], s.emitters[f % nfr], s.params, 50 + k, f, out[k].data_ptr(),
+                           gate=None if s.bins else s.gates[0], bins=s.bins)
+
+        # served
+        srv = tof.tof_server_create(ctx, 120 << 30)
+        streams = [tof.tof_server_open_stream(srv, sids[k], *shape[k]) for k in range(len(scs))]
+        nframe = [0] * len(scs)
+        tickets = []
+        t0 = time.perf_counter()
+        i = 0
+        while True:
+            now = time.perf_counter() - t0
+            while i < len(arrivals) and arrivals[i][0] <= now:
+                k = arrivals[i][1]
+                f = nframe[k]
+                nframe[k] += 1
+                tickets.append((k, tof.tof_server_submit(srv, streams[k], job_for(k, f), scs[k].xforms[f % nfr].reshape(-1))))
+                i += 1
+            tof.tof_server_step(srv, sptr)
+            st = tof.tof_server_stats(srv)
+            if i == len(arrivals) and st["completed"] == len(arrivals):
+                break
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        lat = [tof.tof_server_poll(srv, tk)[1] for _, tk in tickets]
+        lat512 = [tof.tof_server_poll(srv, tk)[1] for k, tk in tickets if shape[k][:2] == (512, 512) and shape[k][2] == 0]
+        st = tof.tof_server_stats(srv)
+        tof.tof_server_destroy(srv)
+        # one launch per request, the same requests in arrival order on one stream
+        views = [tof.tof_view_create(ctx, sids[k], *shape[k]) for k in range(len(scs))]
+        nframe = [0] * len(scs)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _, k in arrivals:
+            f = nframe[k]
+            nframe[k] += 1
+            s = scs[k]
+            tof.tof_bvh_build(ctx, sids[k], s.xforms[f % nfr].reshape(-1), refit_only=1, stream=sptr)
+            if s.bins:
+                tof.tof_render_transient(ctx, sids[k], views[k], s.sensors[f % nfr], s.emitters[f % nfr], s.bins, s.params,
+                                         50 + k, f, out[k].data_ptr(), sptr)
+            else:
+                tof.tof_render_gated(ctx, sids[k], views[k], s.sensors[f % nfr], s.emitters[f % nfr], s.gates[0], s.params,
+                                     50 + k, f, out[k].data_ptr(), sptr)
+        stream.synchronize()
+        per_launch_s = time.perf_counter() - t1
+        result = {"streams": len(scs), "requests": len(arrivals), "arrival_rate": rate, "arrival_seconds": seconds,
+                  "served_frames_per_s": len(arrivals) / wall, "served_wall_s": wall,
+                  "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                  "latency_512_gated_ms": {"p50": float(np.percentile(lat512, 50)), "p99": float(np.percentile(lat512, 99))}
+                  if lat512 else None,
+                  "batches": st["batches"], "resident_gb": st["resident_bytes"] / 2 ** 30,
+                  "per_launch_frames_per_s": len(arrivals) / per_launch_s, "per_launch_s": per_launch_s,
+                  "mix": "6 gated streams (256, 362, 512, 512, 724, 1024 px) + 2 transient 256x256x512, "
+                         "70/30 gated/transient requests"}
+    finally:
+        tof.tof_destroy(ctx)
+    return result
+
+
 def cpu_baseline(args, crop=None, frames=3):
     """The oracle as it stands on the host cores (all of them, OpenMP): the first `frames` frames of
     the workload at full resolution (or on a crop of it, with the margin the spatial reuse needs),
@@ -377,6 +471,7 @@ def main():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -453,6 +548,11 @@ def main():
             line["batched"] = run_batched(args)
         except Exception as e:
             line["batched"] = {"error": str(e)[:300]}
+    if not args.no_serve:
+        try:
+            line["served"] = run_served(args)
+        except Exception as e:
+            line["served"] = {"error": str(e)[:300]}
     if not args.no_cpu:
         try:
             line["cpu_baseline"] = cpu_baseline(args)

@@ -196,6 +196,30 @@ typedef struct {
  * Scratch for every view is allocated before the graph is captured (first use of a view). */
 tof_status tof_render_batch(tof_ctx* ctx, const tof_job* jobs, uint32_t n, void* stream);
 
+/* Served form (configs[4]): a request scheduler over several dynamic streams.
+ *   A stream is a scene plus a fixed sensor resolution (and bin count for transient streams); its
+ *   view -- reservoirs, G-buffers, confidences -- is created on first admission and stays resident,
+ *   so frames of a stream reuse their predecessors temporally.
+ *   tof_server_submit queues one frame request: the job (view field ignored) and the frame's
+ *   object transforms (nobj * 12 floats, copied).  tof_server_step retires batches whose GPU work
+ *   has finished, admits pending requests in arrival order -- at most one frame in flight per stream,
+ *   and a stream's first admission only if its view fits the server's HBM budget -- applies each
+ *   admitted stream's transforms (tof_bvh_build, refit), and launches all admitted frames as one
+ *   batch (tof_render_batch) on `stream`.  Requests arriving while a batch runs join the next step
+ *   (continuous batching).  Times are host wall-clock: submit -> observed completion. */
+typedef struct tof_server tof_server;
+tof_status tof_server_create(tof_ctx* ctx, uint64_t hbm_budget_bytes, tof_server** out);
+tof_status tof_server_destroy(tof_server* srv);
+tof_status tof_server_open_stream(tof_server* srv, tof_scene scene, int32_t W, int32_t H, int32_t B, int32_t* stream_id);
+tof_status tof_server_submit(tof_server* srv, int32_t stream_id, const tof_job* job, const float* object_xforms,
+                             uint64_t* ticket);
+tof_status tof_server_step(tof_server* srv, void* stream);
+/* state: 0 queued, 1 on the GPU, 2 done (latency_ms = submit -> completion), -1 unknown ticket */
+tof_status tof_server_poll(tof_server* srv, uint64_t ticket, int32_t* state, double* latency_ms);
+/* out[0] submitted, out[1] completed, out[2] launched batches, out[3] admissions deferred by the
+ * budget, out[4] device bytes of resident stream views, out[5] queued, out[6] in flight */
+tof_status tof_server_stats(tof_server* srv, double out[7]);
+
 /* Plain gated (bins == NULL) or transient path tracing without reuse, spp paths per pixel each
  * with its own jitter (the comparison method of Sec. 6).  Output layout as above. */
 tof_status tof_render_pt(tof_ctx* ctx, tof_scene scene, const tof_sensor* sensor, const tof_emitter* emitter,

@@ -732,6 +732,12 @@ tof_status tof_render_transient(tof_ctx* c, tof_scene scene, tof_view view, cons
     return render(c, scene, view, sensor, emitter, bins->t0, bins->width, bins->B, params, seed, frame, out_hist_dev, stream);
 }
 
+// number of objects of a scene (used by the server to copy a request's transforms); -1 if invalid
+__attribute__((visibility("hidden"))) int tof_internal_scene_objects(tof_ctx* c, tof_scene id) {
+    if (!c || id < 0 || id >= (int)c->scenes.size() || !c->scenes[id].alive) return -1;
+    return c->scenes[id].nobj;
+}
+
 tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* stream) {
     if (!c) return TOF_EINVAL;
     if (!jobs || n == 0) return fail(c, TOF_EINVAL, "empty batch");

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// number of objects of a scene (server -> context); hidden from the library's exports
+extern "C" __attribute__((visibility("hidden"))) int tof_internal_scene_objects(struct tof_ctx* c, int32_t scene);
+
 namespace tof {
 
 constexpr int kMaxDepth = 5;        // surface vertices per path

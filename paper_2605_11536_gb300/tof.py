@@ -57,7 +57,8 @@ class tof_job(C.Structure):
 EXPORTS = ["tof_create", "tof_destroy", "tof_last_error", "tof_device_bytes", "tof_scene_upload", "tof_scene_destroy",
            "tof_bvh_build", "tof_view_create", "tof_view_destroy", "tof_render_gated", "tof_render_transient",
            "tof_render_pt", "tof_reservoirs_reset", "tof_view_stats", "tof_view_profile", "tof_view_stage_ms",
-           "tof_render_gated_noalloc", "tof_render_batch"]
+           "tof_render_gated_noalloc", "tof_render_batch", "tof_server_create", "tof_server_destroy",
+           "tof_server_open_stream", "tof_server_submit", "tof_server_step", "tof_server_poll", "tof_server_stats"]
 
 _vp, _fp, _u32p = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)
 
@@ -89,6 +90,13 @@ def _declare(L):
                                 C.POINTER(tof_bins), C.POINTER(tof_params), C.c_uint64, C.c_uint32, C.c_int32, _vp, _vp]
     L.tof_reservoirs_reset.argtypes = [_vp, C.c_int32]
     L.tof_render_batch.argtypes = [_vp, C.POINTER(tof_job), C.c_uint32, _vp]
+    L.tof_server_create.argtypes = [_vp, C.c_uint64, C.POINTER(C.c_void_p)]
+    L.tof_server_destroy.argtypes = [_vp]
+    L.tof_server_open_stream.argtypes = [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
+    L.tof_server_submit.argtypes = [_vp, C.c_int32, C.POINTER(tof_job), _fp, C.POINTER(C.c_uint64)]
+    L.tof_server_step.argtypes = [_vp, _vp]
+    L.tof_server_poll.argtypes = [_vp, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+    L.tof_server_stats.argtypes = [_vp, C.POINTER(C.c_double)]
     L.tof_view_stats.argtypes = [_vp, C.c_int32, C.POINTER(C.c_double)]
     L.tof_view_profile.argtypes = [_vp, C.c_int32, C.c_int]
     L.tof_view_stage_ms.argtypes = [_vp, C.c_int32, C.POINTER(C.c_float)]
@@ -281,3 +289,44 @@ def job(scene, view, sensor_d, emitter_d, params_p, seed, frame, out_ptr, gate=N
 def tof_render_batch(ctx, jobs, stream: int = 0):
     arr = (tof_job * len(jobs))(*jobs)
     _check(ctx, lib().tof_render_batch(ctx, arr, len(jobs), C.c_void_p(stream)), "tof_render_batch")
+
+
+def tof_server_create(ctx, hbm_budget_bytes: int = 0):
+    s = C.c_void_p()
+    _check(ctx, lib().tof_server_create(ctx, int(hbm_budget_bytes), C.byref(s)), "tof_server_create")
+    return s
+
+
+def tof_server_destroy(srv):
+    _check(None, lib().tof_server_destroy(srv), "tof_server_destroy")
+
+
+def tof_server_open_stream(srv, scene: int, W: int, H: int, B: int = 0) -> int:
+    out = C.c_int32()
+    _check(None, lib().tof_server_open_stream(srv, scene, W, H, B, C.byref(out)), "tof_server_open_stream")
+    return out.value
+
+
+def tof_server_submit(srv, stream_id: int, job_s: tof_job, object_xforms) -> int:
+    x = np.ascontiguousarray(object_xforms, dtype=np.float32)
+    t = C.c_uint64()
+    _check(None, lib().tof_server_submit(srv, stream_id, C.byref(job_s), x.ctypes.data_as(_fp), C.byref(t)),
+           "tof_server_submit")
+    return t.value
+
+
+def tof_server_step(srv, stream: int = 0):
+    _check(None, lib().tof_server_step(srv, C.c_void_p(stream)), "tof_server_step")
+
+
+def tof_server_poll(srv, ticket: int):
+    st, lat = C.c_int32(), C.c_double()
+    _check(None, lib().tof_server_poll(srv, int(ticket), C.byref(st), C.byref(lat)), "tof_server_poll")
+    return st.value, lat.value
+
+
+def tof_server_stats(srv):
+    a = (C.c_double * 7)()
+    _check(None, lib().tof_server_stats(srv, a), "tof_server_stats")
+    return dict(submitted=a[0], completed=a[1], batches=a[2], deferred=a[3], resident_bytes=a[4], queued=a[5],
+                inflight=a[6])
