@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(128) reuse_setup_kernel(const __grid_constant_
 // --------------------------------------------------------------------------------------------
 // forward shifts: slot s's sample into the unit's domain
 // --------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 4) shift_fwd_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+__global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
     ShiftStats st = {0, 0, 0, 0, 0};
     const uint32_t ntask = min(w.counters[1], (uint32_t)w.cap_units * (uint32_t)(w.slots - 1));
     const int S = w.slots;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(128, 4) shift_fwd_kernel(const __grid_constant
 // --------------------------------------------------------------------------------------------
 // inverse shifts: candidate s's offset path (in the unit's domain) into domain j
 // --------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 4) shift_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+__global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
     const uint32_t cap = (uint32_t)w.cap_units * (uint32_t)w.slots * (uint32_t)(w.slots - 1);
     const uint32_t ntask = min(w.counters[2], cap);
     const int S = w.slots;
