@@ -126,7 +126,9 @@ tof_status tof_scene_destroy(tof_ctx* ctx, tof_scene scene);
 
 /* Place the objects (row-major 3x4 object-to-world matrices, nobj*12 floats) and build the GPU
  * LBVH (Morton codes, radix sort, hierarchy, bounds).  refit_only = 1 keeps the hierarchy and
- * refits bounds after rigid motion.  Call once per frame before rendering it: the library keeps
+ * refits bounds after rigid motion: cheaper to build, but the hierarchy's quality decays as objects
+ * move away from where it was built (a full build of 66k triangles takes about 0.2 ms on GB300 and
+ * pays for itself within a few frames of motion).  Call once per frame before rendering it: the library keeps
  * the geometry of the previous call resident for temporal reuse (an exact inverse shift into the
  * previous frame needs the previous scene).  Transforms identical to the current ones are a
  * no-op (the scene is static between the two frames). */
@@ -204,7 +206,7 @@ tof_status tof_render_batch(tof_ctx* ctx, const tof_job* jobs, uint32_t n, void*
  *   object transforms (nobj * 12 floats, copied).  tof_server_step retires batches whose GPU work
  *   has finished, admits pending requests in arrival order -- at most one frame in flight per stream,
  *   and a stream's first admission only if its view fits the server's HBM budget -- applies each
- *   admitted stream's transforms (tof_bvh_build, refit), and launches all admitted frames as one
+ *   admitted stream's transforms (tof_bvh_build, full build), and launches all admitted frames as one
  *   batch (tof_render_batch) on `stream`.  Requests arriving while a batch runs join the next step
  *   (continuous batching).  Times are host wall-clock: submit -> observed completion. */
 typedef struct tof_server tof_server;

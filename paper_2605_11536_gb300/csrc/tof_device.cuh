@@ -809,17 +809,12 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
         if (find_r(cls, pos, k, P.d_min) != r) return false;
     }
 
-    // (6) visibility of the two reconnection segments
-    if (!visible(gi, yv[r - 1].p, yv[r - 1].n, pp.p, &pp.n, eps)) return false;
-    if (ns > 0) { if (!visible(gi, pp.p, pp.n, sv[0].p, &sv[0].n, eps)) return false; }
-    else if (!light_visible(Di, gi, pp, eps)) return false;
-
-    // (7) target function in Di
+    // (6) target function in Di without the suffix radiance, the gate and the Jacobian: cheap
+    // rejections, taken before any ray is traced (the result is the same in either order)
     float3 wprev = dir_to(yv[r - 1].p, r - 1 == 1 ? Di.x0 : yv[r - 2].p);
     float f = fpre;
     f *= bsdf_f(load_mat(gi, yv[r - 1].mat), yv[r - 1].n, wprev, dir_to(yv[r - 1].p, pp.p));
     f *= Gterm(yv[r - 1], pp);
-    float Lsuf_i = x.Lsuf;
     Mat mp = load_mat(gi, pp.mat);
     if (ns == 0) {
         float3 wl; float seg;
@@ -830,9 +825,24 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
         f *= Gterm(pp, sv[0]);
         float3 wnext = ns > 1 ? dir_to(sv[0].p, sv[1].p) : dir_to(sv[0].p, lpos_i);
         f *= bsdf_f(load_mat(gi, sv[0].mat), sv[0].n, dir_to(sv[0].p, pp.p), wnext);
+    }
+    if (!(f > 0.f) || !isfinite(f)) return false;
+    float Lnew = plen + len3(yv[r - 1].p - pp.p) + len3(pp.p - p2y) + slen;
+    float tau = Lnew - Di.o;
+    if (!(tau >= Di.L0 && tau < Di.L0 + Di.dL)) return false;
+    float jac = (x.pdf_pre / pdfy) * jn;
+    if (!(jac > 0.f) || !isfinite(jac)) return false;
+
+    // (7) visibility of the two reconnection segments
+    if (!visible(gi, yv[r - 1].p, yv[r - 1].n, pp.p, &pp.n, eps)) return false;
+    if (ns > 0) { if (!visible(gi, pp.p, pp.n, sv[0].p, &sv[0].n, eps)) return false; }
+    else if (!light_visible(Di, gi, pp, eps)) return false;
+
+    // (8) suffix radiance: cached, or re-evaluated when the scene or light differs (Sec. 5)
+    float Lsuf_i = x.Lsuf;
+    if (ns > 0) {
         bool cache_ok = geom_static && light_same(Dj.light, Di.light);
         if (!cache_ok) {
-            // Sec. 5: re-evaluate the reconnection information when the scene or light differs
             float Ls = 1.0f;
             for (int q = 1; q < ns; ++q) {
                 Mat mq = load_mat(gi, sv[q].mat);
@@ -853,14 +863,7 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
         }
         f *= Lsuf_i;
     }
-    float Lnew = plen + len3(yv[r - 1].p - pp.p) + len3(pp.p - p2y) + slen;
-    float tau = Lnew - Di.o;
-    if (!(tau >= Di.L0 && tau < Di.L0 + Di.dL)) return false;
     if (!(f > 0.f) || !isfinite(f)) return false;
-
-    // (8) Jacobian
-    float jac = (x.pdf_pre / pdfy) * jn;
-    if (!(jac > 0.f) || !isfinite(jac)) return false;
 
     y = x;
     y.tau = tau;

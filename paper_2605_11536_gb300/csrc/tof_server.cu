@@ -158,7 +158,7 @@ tof_status tof_server_step(tof_server* s, void* stream) {
             st.bytes = tof_device_bytes(s->ctx) - before;
             s->resident += st.bytes;
         }
-        tof_status rc = tof_bvh_build(s->ctx, st.scene, r.xf.data(), 1, stream);
+        tof_status rc = tof_bvh_build(s->ctx, st.scene, r.xf.data(), 0, stream);   // full rebuild: see tof.h
         if (rc != TOF_OK) return rc;
         r.job.view = st.view;
         r.state = 1;
