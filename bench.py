@@ -524,7 +524,7 @@ def main():
     units = {"initial": r["npix"], "spatial_fwd_shift": pf["spatial_fwd_calls"], "spatial_inv_shift": pf["spatial_inv_calls"],
              "spatial_merge": r["npix"]}
     kernels = {"gbuffer": "gbuffer_kernel", "initial": "initial_kernel", "temporal": "temporal pass (4 kernels)",
-               "spatial_setup": "reuse_setup_kernel", "spatial_fwd_shift": "shift_fwd_kernel",
+               "spatial_setup": "reuse_slots_kernel + reuse_units_kernel", "spatial_fwd_shift": "shift_fwd_kernel",
                "spatial_inv_shift": "shift_inv_kernel", "spatial_merge": "reuse_merge_kernel"}
     dom = max(kernels, key=lambda k: st.get(k, 0.0))
     dom_ms = st[dom]
@@ -555,8 +555,8 @@ def main():
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 12 * 4 * r["nobj"],
                     "d2h_bytes_per_step": 4 * r["npix"]},
             # per frame: LBVH (xform, bounds, morton, 4 x 3 radix-sort, karras, refit = 17), gbuffer,
-            # initial, 4 temporal-pass and 4 spatial-pass kernels
-            "gpu_launches": 27 * K,
+            # initial, 5 temporal-pass and 5 spatial-pass kernels
+            "gpu_launches": 29 * K,
             "roofline": roof,
             "clocks": r["clocks"],
             "quality": r["quality"],

@@ -710,6 +710,8 @@ static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float
 // ============================================================================================
 struct ShiftStats { uint32_t newton_calls, newton_iters, newton_ok, shift_calls, shift_ok; };
 
+// kOut = false: only the target value and the Jacobian are wanted (the MIS terms), not the record
+template <bool kOut>
 static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& Di, const ParamsDev& P, bool geom_static, Rec& y,
                           float& phat_out, float& jac_out, ShiftStats* st) {
     const int r = rec_r(x);
@@ -865,13 +867,15 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
     }
     if (!(f > 0.f) || !isfinite(f)) return false;
 
-    y = x;
-    y.tau = tau;
-    y.xprev = yv[r - 1].p;
-    y.pdf_pre = pdfy;
-    y.p_b1 = nb1; y.p_b2 = nb2;
-    y.Lsuf = Lsuf_i;
-    y.phat = f;
+    if (kOut) {
+        y = x;
+        y.tau = tau;
+        y.xprev = yv[r - 1].p;
+        y.pdf_pre = pdfy;
+        y.p_b1 = nb1; y.p_b2 = nb2;
+        y.Lsuf = Lsuf_i;
+        y.phat = f;
+    }
     phat_out = f;
     jac_out = jac;
     if (st) st->shift_ok++;

@@ -6,9 +6,10 @@
 // samples, k forward shifts into the pixel's domain and, for every surviving candidate, one
 // inverse shift into each other reused domain.  Run as one thread per pixel, the shifts of the
 // few pixels that hold samples serialise while the rest of the warp idles, so the pass is split:
-//   reuse_setup_kernel   per pixel: slots (neighbours or the back-projected previous pixel),
-//                        capped confidences, merge units (pixel, bin), forward-shift tasks and
-//                        the canonical sample's inverse-shift tasks
+//   reuse_slots_kernel   per pixel: slots (neighbours or the back-projected previous pixel) and
+//                        capped confidences
+//   reuse_units_kernel   per (pixel, 32-bin word): merge units (pixel, bin), forward-shift tasks
+//                        and the canonical sample's inverse-shift tasks
 //   shift_fwd_kernel     persistent over forward tasks: shift slot s's sample into the unit's
 //                        domain; emit the inverse-shift tasks of the shifted candidate
 //   shift_inv_kernel     persistent over inverse tasks: shift candidate s's offset path into
@@ -71,6 +72,25 @@ __device__ __forceinline__ uint32_t reserve(uint32_t* counter, uint32_t n) {
     return base + incl - n;
 }
 
+// the same for whichever lanes are converged here (any subset of the warp): one atomic per group.
+// Every lane of the mask runs the same straight-line sequence of shuffles, so all of them meet.
+__device__ __forceinline__ uint32_t reserve_coalesced(uint32_t* counter, uint32_t n) {
+    const uint32_t mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    uint32_t prefix = 0, total = 0;
+    for (int k = 0; k < 32; ++k) {
+        if (!((mask >> k) & 1u)) continue;   // uniform over the group
+        uint32_t v = __shfl_sync(mask, n, k);
+        total += v;
+        if (k < lane) prefix += v;
+    }
+    uint32_t base = 0;
+    if (lane == leader && total) base = atomicAdd(counter, total);
+    base = __shfl_sync(mask, base, leader);
+    return base + prefix;
+}
+
 __device__ __forceinline__ void store_rec(float4* P, size_t stride, size_t idx, const Rec& r) {
     ResDev R;
     R.planes = P; R.stride = stride;
@@ -78,105 +98,125 @@ __device__ __forceinline__ void store_rec(float4* P, size_t stride, size_t idx, 
 }
 
 // --------------------------------------------------------------------------------------------
-// per pixel: slots, confidence, units and tasks
+// per pixel: slots (the pixel, its reused pixels) and capped confidences
 // --------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) reuse_setup_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w,
+__global__ void __launch_bounds__(128) reuse_slots_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w,
                                                           int p0, int p1) {
     const FrameDev& C = a.cur;
     const int pix = p0 + blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = pix < p1;
+    if (pix >= p1) return;
     const ParamsDev& P = a.P;
-    const int Bn = C.B > 0 ? C.B : 1;
-    const int words = a.dst.words;
     int n = 1;
     int sp[kMaxSlots];
     float sM[kMaxSlots];
-    if (active) {
-        sp[0] = pix;
-        sM[0] = a.src.M[pix];
-        bool gb_valid = __float_as_uint(C.gb[pix].x) != kNoHit;
-        if (gb_valid) {
-            if (a.temporal) {
-                int q = -1;
-                if (C.mode == 1) q = pix;
-                else {
-                    float4 gb = C.gb[pix];
-                    Surf sp0 = surf_at(a.prev.g, __float_as_int(gb.x), gb.y, gb.z);
-                    int qx, qy;
-                    if (project(a.prev, sp0.p, qx, qy)) q = qy * C.W + qx;
-                }
-                if (q >= 0) { sp[1] = q; sM[1] = fminf(a.prv.M[q], P.m_cap); n = 2; }
-            } else {
-                for (int s = 1; s <= P.n_spatial; ++s) {
-                    int q = pick_nb(P.seed, (uint32_t)pix, C.frame, a.pass, s, C.W, C.H, P.radius);
-                    if (q < 0) continue;
-                    sp[n] = q; sM[n] = fminf(a.src.M[q], P.m_cap); ++n;
-                }
+    sp[0] = pix;
+    sM[0] = a.src.M[pix];
+    bool gb_valid = __float_as_uint(C.gb[pix].x) != kNoHit;
+    if (gb_valid) {
+        if (a.temporal) {
+            int q = -1;
+            if (C.mode == 1) q = pix;
+            else {
+                float4 gb = C.gb[pix];
+                Surf sp0 = surf_at(a.prev.g, __float_as_int(gb.x), gb.y, gb.z);
+                int qx, qy;
+                if (project(a.prev, sp0.p, qx, qy)) q = qy * C.W + qx;
+            }
+            if (q >= 0) { sp[1] = q; sM[1] = fminf(a.prv.M[q], P.m_cap); n = 2; }
+        } else {
+            for (int s = 1; s <= P.n_spatial; ++s) {
+                int q = pick_nb(P.seed, (uint32_t)pix, C.frame, a.pass, s, C.W, C.H, P.radius);
+                if (q < 0) continue;
+                sp[n] = q; sM[n] = fminf(a.src.M[q], P.m_cap); ++n;
             }
         }
-        float Msum = 0.f;
-        for (int s = 0; s < n; ++s) Msum += sM[s];
-        a.dst.M[pix] = Msum;
-        const int S = w.slots;
-        w.nslot[pix] = (uint8_t)n;
-        for (int s = 0; s < n; ++s) { w.slot_pix[(size_t)pix * S + s] = sp[s]; w.slot_M[(size_t)pix * S + s] = sM[s]; }
     }
-    // units: one per bin that any slot occupies (pixels without reuse candidates copy through)
-    uint32_t* docc = active ? a.dst.occ + (size_t)pix * words : nullptr;
-    const uint32_t* socc = active ? a.src.occ + (size_t)pix * words : nullptr;
+    float Msum = 0.f;
+    for (int s = 0; s < n; ++s) Msum += sM[s];
+    a.dst.M[pix] = Msum;
+    const int S = w.slots;
+    w.nslot[pix] = (uint8_t)n;
+    for (int s = 0; s < n; ++s) { w.slot_pix[(size_t)pix * S + s] = sp[s]; w.slot_M[(size_t)pix * S + s] = sM[s]; }
+}
+
+// --------------------------------------------------------------------------------------------
+// per (pixel, 32-bin occupancy word): merge units and their tasks. One thread per word keeps the
+// transient passes parallel over bins (a pixel may occupy hundreds of bins); gated views have one
+// word per pixel.
+// --------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) reuse_units_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w,
+                                                          int p0, int p1) {
+    const FrameDev& C = a.cur;
+    const int Bn = C.B > 0 ? C.B : 1;
+    const int words = a.dst.words;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < (long long)(p1 - p0) * words;
+    const int pix = active ? p0 + (int)(t / words) : 0;
+    const int wd = active ? (int)(t % words) : 0;
+    const int S = w.slots;
+    int n = 0;
+    int sp[kMaxSlots];
+    uint32_t m = 0u;
     float outv = 0.f;
-    for (int wd = 0; wd < words; ++wd) {
-        uint32_t m = 0u;
-        if (active) {
-            if (n == 1) {
-                m = socc[wd];
-                docc[wd] = m;
-                while (m) {
-                    int bit = __ffs(m) - 1;
-                    m &= m - 1;
-                    size_t idx = (size_t)pix * Bn + (wd << 5) + bit;
-                    for (int k = 0; k < 6; ++k) a.dst.planes[k * a.dst.stride + idx] = a.src.planes[k * a.src.stride + idx];
-                    if (C.B == 0) { float4 p0v = a.src.planes[idx]; outv = p0v.y * p0v.x; }
-                }
-                m = 0u;
-            } else {
-                docc[wd] = 0u;
-                for (int s = 0; s < n; ++s) {
-                    const ResDev* R = slot_res(a, s);
-                    m |= R->occ[(size_t)sp[s] * R->words + wd];
-                }
+    if (active) {
+        n = w.nslot[pix];
+        for (int s = 0; s < n; ++s) sp[s] = w.slot_pix[(size_t)pix * S + s];
+        uint32_t* docc = a.dst.occ + (size_t)pix * words;
+        if (n == 1) {
+            // no reuse candidates: the reservoirs copy through
+            uint32_t c = a.src.occ[(size_t)pix * words + wd];
+            docc[wd] = c;
+            while (c) {
+                int bit = __ffs(c) - 1;
+                c &= c - 1;
+                size_t idx = (size_t)pix * Bn + (wd << 5) + bit;
+                for (int k = 0; k < 6; ++k) a.dst.planes[k * a.dst.stride + idx] = a.src.planes[k * a.src.stride + idx];
+                if (C.B == 0) { float4 p0v = a.src.planes[idx]; outv = p0v.y * p0v.x; }
             }
-        }
-        // one unit per set bit; reserve units, forward tasks and canonical inverse tasks
-        uint32_t nu = __popc(m);
-        uint32_t ubase = reserve(&w.counters[0], nu);
-        uint32_t k = 0;
-        while (m) {
-            int bit = __ffs(m) - 1;
-            m &= m - 1;
-            int b = (wd << 5) + bit;
-            uint32_t u = ubase + k++;
-            if (u >= (uint32_t)w.cap_units) { atomicOr(&w.counters[3], 1u); continue; }
-            w.units[u] = make_int2(pix, b);
-            uint32_t nf = 0;
-            for (int s = 1; s < n; ++s) {
+        } else {
+            docc[wd] = 0u;
+            for (int s = 0; s < n; ++s) {
                 const ResDev* R = slot_res(a, s);
-                if (occ_get(*R, sp[s], b)) ++nf;
-            }
-            bool canon = occ_get(a.src, pix, b);
-            uint32_t fb = nf ? atomicAdd(&w.counters[1], nf) : 0u;
-            uint32_t i = 0;
-            for (int s = 1; s < n; ++s) {
-                const ResDev* R = slot_res(a, s);
-                if (occ_get(*R, sp[s], b)) w.fwd[fb + i++] = (u << 4) | (uint32_t)s;
-            }
-            if (canon && n > 1) {
-                uint32_t ib = atomicAdd(&w.counters[2], (uint32_t)(n - 1));
-                for (int j = 1; j < n; ++j) w.inv[ib + j - 1] = (u << 8) | (uint32_t)j;
+                m |= R->occ[(size_t)sp[s] * R->words + wd];
             }
         }
     }
-    // gated: pixels that form a unit get their value from the merge (which runs after this kernel)
+    // one unit per set bit. Reserve the units, then count and reserve the forward tasks and the
+    // canonical inverse tasks of the units inside the capacity, then write them: three warp-wide
+    // atomics instead of two per unit.
+    const uint32_t nu = __popc(m);
+    const uint32_t ubase = reserve(&w.counters[0], nu);
+    const uint32_t nvalid = ubase >= (uint32_t)w.cap_units ? 0u : min(nu, (uint32_t)w.cap_units - ubase);
+    if (nvalid < nu) atomicOr(&w.counters[3], 1u);
+    uint32_t nf_tot = 0, ni_tot = 0;
+    {
+        uint32_t mm = m;
+        for (uint32_t k = 0; k < nvalid; ++k) {
+            int b = (wd << 5) + __ffs(mm) - 1;
+            mm &= mm - 1;
+            for (int s = 1; s < n; ++s) {
+                const ResDev* R = slot_res(a, s);
+                if (occ_get(*R, sp[s], b)) ++nf_tot;
+            }
+            if (n > 1 && occ_get(a.src, pix, b)) ni_tot += (uint32_t)(n - 1);
+        }
+    }
+    uint32_t fb = reserve(&w.counters[1], nf_tot);
+    uint32_t ib = reserve(&w.counters[2], ni_tot);
+    for (uint32_t k = 0; k < nvalid; ++k) {
+        int b = (wd << 5) + __ffs(m) - 1;
+        m &= m - 1;
+        uint32_t u = ubase + k;
+        w.units[u] = make_int2(pix, b);
+        for (int s = 1; s < n; ++s) {
+            const ResDev* R = slot_res(a, s);
+            if (occ_get(*R, sp[s], b)) w.fwd[fb++] = (u << 4) | (uint32_t)s;
+        }
+        if (n > 1 && occ_get(a.src, pix, b)) {
+            for (int j = 1; j < n; ++j) w.inv[ib++] = (u << 8) | (uint32_t)j;
+        }
+    }
+    // gated (one word per pixel): pixels that form a unit get their value from the merge
     if (active && a.out) a.out[pix] = n == 1 ? outv : 0.f;
 }
 
@@ -204,20 +244,19 @@ __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant
         Rec y;
         float py = 0.f, J = 1.f;
         bool geom_static = (a.temporal && s == 1) ? a.geom_static != 0 : true;
-        bool ok = shift_rec(x, Ds, D0, a.P, geom_static, y, py, J, &st);
+        bool ok = shift_rec<true>(x, Ds, D0, a.P, geom_static, y, py, J, &st);
         size_t ui = (size_t)u * S + s;
         w.py[ui] = ok ? py : 0.f;
         w.jac[ui] = ok ? J : 1.f;
         if (ok) {
             store_rec(w.yrec, (size_t)w.cap_units * (S - 1), (size_t)u * (S - 1) + (s - 1), y);
-            int n = w.nslot[pix];
-            if (n > 2) {
-                uint32_t ib = atomicAdd(&w.counters[2], (uint32_t)(n - 2));
-                uint32_t i = 0;
-                for (int j = 1; j < n; ++j)
-                    if (j != s) w.inv[ib + i++] = (u << 8) | ((uint32_t)s << 4) | (uint32_t)j;
-            }
         }
+        // the shifted candidate's inverse shifts into the other reused domains
+        const int n = w.nslot[pix];
+        const uint32_t ne = (ok && n > 2) ? (uint32_t)(n - 2) : 0u;
+        uint32_t ib = reserve_coalesced(&w.counters[2], ne);
+        for (int j = 1; j < n && ne; ++j)
+            if (j != s) w.inv[ib++] = (u << 8) | ((uint32_t)s << 4) | (uint32_t)j;
     }
     // warp-level flush of the shift statistics
     if (a.stats) {
@@ -263,7 +302,7 @@ __global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant
         Rec tmp;
         float pj = 0.f, Jj = 1.f;
         float term = 0.f;
-        if (shift_rec(y, D0, Dj, a.P, geom_static, tmp, pj, Jj, nullptr)) term = w.slot_M[(size_t)pix * S + j] * pj * Jj;
+        if (shift_rec<false>(y, D0, Dj, a.P, geom_static, tmp, pj, Jj, nullptr)) term = w.slot_M[(size_t)pix * S + j] * pj * Jj;
         w.terms[((size_t)u * S + s) * S + j] = term;
     }
     if (a.stats) {
@@ -348,7 +387,9 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
     int np = p1 - p0;
     if (np <= 0) return cudaSuccess;
     if (ev) cudaEventRecord(ev[0], s);
-    reuse_setup_kernel<<<(np + 127) / 128, 128, 0, s>>>(a, w, p0, p1);
+    reuse_slots_kernel<<<(np + 127) / 128, 128, 0, s>>>(a, w, p0, p1);
+    const long long nw = (long long)np * a.dst.words;
+    reuse_units_kernel<<<(unsigned)((nw + 127) / 128), 128, 0, s>>>(a, w, p0, p1);
     if (ev) cudaEventRecord(ev[1], s);
     shift_fwd_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
     if (ev) cudaEventRecord(ev[2], s);
