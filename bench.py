@@ -152,7 +152,7 @@ def workload(W=512, H=512, frames=32, seed=1):
 
 def run_ours(args, rank, world):
     import torch
-    from paper_2605_11536_gb300 import tof
+    from paper_2605_11536_gb300 import scenes, tof
     dev = torch.device("cuda", torch.cuda.current_device())
     sc = workload(seed=1 + rank)
     p = sc.params
@@ -227,6 +227,38 @@ def run_ours(args, rank, world):
             if i >= args.warmup + args.steps - nq:
                 kept[f] = host_img.numpy().astype(np.float64).reshape(H, W).copy()
 
+    # the same frames with pairwise MIS (TOF_FLAG_PAIRWISE_MIS: 2k shifts per merge instead of
+    # k + k^2), timed like the headline loop; reported beside it, not as the headline
+    pairwise = {}
+    kept_pw = {}
+    if not args.no_pairwise:
+        p_pw = type(p)(**vars(p))
+        p_pw.flags = p.flags | scenes.FLAG_PAIRWISE_MIS
+        vid3 = tof.tof_view_create(ctx, sid, W, H, 0)
+        tof.tof_view_profile(ctx, vid3, 1)
+        pw_ms, pw_st = [], {k: [] for k in tof.STAGES}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for i in range(args.warmup + args.steps):
+                f = i
+                flush.zero_()
+                e0.record(stream)
+                tof.tof_bvh_build(ctx, sid, xf32[f % nf], refit_only=0, stream=sptr)
+                tof.tof_render_gated(ctx, sid, vid3, sc.sensors[f % nf], sc.emitters[f % nf], sc.gates[f % nf], p_pw,
+                                     sc.seed, f, out.data_ptr(), sptr)
+                e1.record(stream)
+                if i >= args.warmup:
+                    e1.synchronize()
+                    pw_ms.append(e0.elapsed_time(e1))
+                    for k, v in tof.tof_view_stage_ms(ctx, vid3).items():
+                        pw_st[k].append(v)
+                if i >= args.warmup + args.steps - nq:
+                    stream.synchronize()
+                    kept_pw[f] = out.cpu().numpy().astype(np.float64).reshape(H, W)
+        torch.cuda.synchronize()
+        pairwise = {"value": 1e3 / float(np.mean(pw_ms)), "unit": "frames/s", "ms_per_step": float(np.mean(pw_ms)),
+                    "stage_ms": {k: float(np.mean(v)) for k, v in pw_st.items()}}
+
     # quality: relMSE of the last frames against high-spp plain path-traced references, and plain
     # path tracing at equal time on the same frames; relMSE is averaged over the frames because a
     # single frame's value is dominated by a few hundred firefly pixels and varies several-fold
@@ -235,7 +267,7 @@ def run_ours(args, rank, world):
         ms_frame = float(np.median(step_ms))
         ref = torch.zeros(H * W, device=dev)
         pt_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        e_restir, e_pt, pt_ms_all, spp = [], [], [], 1
+        e_restir, e_pt, e_pw, pt_ms_all, spp = [], [], [], [], 1
         with torch.cuda.stream(stream):
             for f, img in sorted(kept.items()):
                 fq = f % nf
@@ -260,6 +292,8 @@ def run_ours(args, rank, world):
                         break
                     spp = max(spp + 1, int(spp * ms_frame / max(pt_ms, 1e-3)))
                 pt_ms_all.append(pt_ms)
+                if f in kept_pw:
+                    e_pw.append(rel_mse(kept_pw[f], refimg))
                 e_restir.append(rel_mse(img, refimg))
                 e_pt.append(rel_mse(ref.cpu().numpy().astype(np.float64).reshape(H, W), refimg))
         er, ep, pm = float(np.mean(e_restir)), float(np.mean(e_pt)), float(np.mean(pt_ms_all))
@@ -268,8 +302,14 @@ def run_ours(args, rank, world):
                    "relmse_restir_per_frame": e_restir, "relmse_pt_per_frame": e_pt,
                    "pt_spp": spp, "pt_ms": pm, "restir_ms": ms_frame,
                    "restir_vs_pt_inv_mse_time": (1.0 / (er * ms_frame)) / (1.0 / (ep * pm)) if er > 0 and ep > 0 else None}
+        if e_pw and pairwise:
+            ew = float(np.mean(e_pw))
+            pairwise["relmse"] = ew
+            pairwise["relmse_per_frame"] = e_pw
+            pairwise["vs_pt_inv_mse_time"] = (1.0 / (ew * pairwise["ms_per_step"])) / (1.0 / (ep * pm)) if ew > 0 and ep > 0 else None
     tof.tof_destroy(ctx)
     return dict(step_ms=step_ms, dev_s=dev_s, wall=wall, stages=stage_acc, e2e_ms=e2e_ms, clocks=clocks.summary(),
+                pairwise=pairwise,
                 quality=quality, stats=shift_stats, per_frame=per_frame, npix=W * H, W=W, H=H,
                 nobj=len(sc.object_material))
 
@@ -494,6 +534,7 @@ def main():
     ap.add_argument("--ref-spp", type=int, default=4096)
     ap.add_argument("--quality-frames", type=int, default=4, help="frames whose relMSE is averaged")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-pairwise", action="store_true", help="skip the pairwise-MIS line")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -560,6 +601,7 @@ def main():
             "roofline": roof,
             "clocks": r["clocks"],
             "quality": r["quality"],
+            "pairwise_mis": r["pairwise"],
             "newton": {"calls": r["stats"]["newton_calls"], "mean_iters": r["stats"]["newton_iters"] / max(1, r["stats"]["newton_calls"]),
                        "newton_sr": r["stats"]["newton_ok"] / max(1, r["stats"]["newton_calls"]),
                        "shift_sr": r["stats"]["shift_ok"] / max(1, r["stats"]["shift_calls"])},

@@ -87,6 +87,13 @@ typedef struct { float t0, width; int32_t B; } tof_bins;
 /* flags */
 #define TOF_FLAG_DIRECT 1u       /* include length-1 (direct) paths; the paper reports indirect only */
 #define TOF_FLAG_NAIVE_SHIFT 2u  /* hybrid shift without the path-length correction (comparison) */
+/* pairwise MIS instead of the generalized balance heuristic: the canonical sample pairs with each
+ * of the k reused ones; pair i is a two-technique balance heuristic between the canonical domain
+ * (confidence M_c/k) and domain i (confidence M_i), weighted by (M_i + M_c/k)/sum M.  The weights
+ * still sum to one (unbiased), equal the balance heuristic when k = 1 or when every domain's
+ * target agrees, and need 2k shifts per merge instead of k + k^2.  Not in the paper (which states
+ * the balance heuristic only); an optimisation from the ReSTIR literature. */
+#define TOF_FLAG_PAIRWISE_MIS 4u
 
 /* reuse / sampling parameters (Sec. 6: path depth, candidates, neighbours, radius, M-cap;
  * Newton tolerance 1 % of the gate width with at most 5 iterations) */

@@ -421,7 +421,7 @@ typedef struct {
     double newton_tol_frac, jac_max, d_min, ray_eps;
     uint32_t flags;
 } oparams;
-enum { F_DIRECT = 1, F_NAIVE = 2 };
+enum { F_DIRECT = 1, F_NAIVE = 2, F_PAIRWISE = 4 };
 
 /* Sec. 5 "Light Source": a point light (direct NEE) or a collimated laser whose spot acts as a
  * secondary emitter I(w) = P f_s(spot; to laser, w) |cos| (a light ray is traced first). */
@@ -1143,7 +1143,35 @@ static double merge(const oslot* sl, int n, const oparams* P, uint64_t seed, uin
         if (s == 0) { y[0] = *sl[0].x; py[0] = sl[0].x->phat; J[0] = 1.0; ok[0] = py[0] > 0; continue; }
         ok[s] = shift_rec(sl[s].x, sl[s].D, sl[0].D, P, seed, sl[s].geom_static, &y[s], &py[s], &J[s], st);
     }
-    for (int s = 0; s < n; ++s) {
+    if ((P->flags & F_PAIRWISE) && n > 1) {
+        /* pairwise MIS: pair i = {canonical with confidence M_0/k, domain i with confidence M_i},
+         * a two-technique balance heuristic at the same y, weighted by
+         * alpha_i = (M_i + M_0/k) / sum_t M_t; the weights over all techniques sum to one. */
+        const int k = n - 1;
+        const double Mck = sl[0].M / k;
+        for (int s = 0; s < n; ++s) {
+            if (!ok[s]) continue;
+            double m = 0.0;
+            if (s == 0) {
+                for (int i = 1; i < n; ++i) {
+                    double alpha = (sl[i].M + Mck) / Msum;
+                    double ti = 0.0;
+                    orec tmp; double pj, Jj;
+                    if (shift_rec(&y[0], sl[0].D, sl[i].D, P, seed, sl[i].geom_static, &tmp, &pj, &Jj, NULL))
+                        ti = sl[i].M * pj * Jj;
+                    double pc = Mck * py[0];
+                    m += alpha * (pc / (pc + ti));
+                }
+            } else {
+                double alpha = (sl[s].M + Mck) / Msum;
+                double pi = sl[s].M * sl[s].x->phat / J[s];
+                double pc = Mck * py[s];
+                m = alpha * (pi / (pi + pc));
+            }
+            w[s] = m * py[s] * sl[s].x->W * J[s];
+            if (!(w[s] > 0) || !isfinite(w[s])) w[s] = 0.0;
+        }
+    } else for (int s = 0; s < n; ++s) {
         if (!ok[s]) continue;
         double num = s == 0 ? sl[0].M * py[0] : sl[s].M * sl[s].x->phat / J[s];
         double den = sl[0].M * py[s];

@@ -16,6 +16,7 @@ constexpr int kMaxSlots = 1 + kMaxNb;
 constexpr int kStack = 64;          // BVH traversal stack
 constexpr int kMaxBinsPerPixel = 32;  // distinct transient bins a pixel's initial candidates may hit
 constexpr uint32_t kNoHit = 0xFFFFFFFFu;
+constexpr uint32_t kFlagPairwiseMis = 4u;  // TOF_FLAG_PAIRWISE_MIS
 
 // material record: (type, albedo, alpha, unused)
 // triangle record (original order): 3 float4 = (v0.xyz, material id bits), (e1.xyz, 0), (e2.xyz, 0)

@@ -253,7 +253,9 @@ __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant
         }
         // the shifted candidate's inverse shifts into the other reused domains
         const int n = w.nslot[pix];
-        const uint32_t ne = (ok && n > 2) ? (uint32_t)(n - 2) : 0u;
+        // (pairwise MIS needs none: it pairs the canonical domain with each reused one)
+        const bool pairwise = (a.P.flags & kFlagPairwiseMis) != 0u;
+        const uint32_t ne = (ok && n > 2 && !pairwise) ? (uint32_t)(n - 2) : 0u;
         uint32_t ib = reserve_coalesced(&w.counters[2], ne);
         for (int j = 1; j < n && ne; ++j)
             if (j != s) w.inv[ib++] = (u << 8) | ((uint32_t)s << 4) | (uint32_t)j;
@@ -343,12 +345,41 @@ __global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant_
             if (s == 0) { py[0] = p0.y; J[0] = 1.f; ok[0] = py[0] > 0.f; }
             else { py[s] = w.py[(size_t)u * S + s]; J[s] = w.jac[(size_t)u * S + s]; ok[s] = py[s] > 0.f; }
         }
-        for (int s = 0; s < n; ++s) {
+        // MIS weights with explicitly rounded operations (no contraction into FMAs), so that
+        // pairwise MIS with one reused domain reproduces the balance heuristic bit for bit
+        if ((a.P.flags & kFlagPairwiseMis) && n > 1) {
+            // pairwise MIS: pair i = {canonical with confidence M_0/k, domain i with M_i}, a
+            // two-technique balance heuristic at the same y weighted by (M_i + M_0/k) / sum M
+            const int k = n - 1;
+            float Msum = 0.f;
+            for (int s = 0; s < n; ++s) Msum = __fadd_rn(Msum, M[s]);
+            const float Mck = __fdiv_rn(M[0], (float)k);
+            for (int s = 0; s < n; ++s) {
+                if (!ok[s]) continue;
+                float m = 0.f;
+                if (s == 0) {
+                    const float pc = __fmul_rn(Mck, py[0]);
+                    for (int i = 1; i < n; ++i) {
+                        float alpha = __fdiv_rn(__fadd_rn(M[i], Mck), Msum);
+                        float ti = w.terms[((size_t)u * S + 0) * S + i];
+                        m = __fadd_rn(m, __fmul_rn(alpha, __fdiv_rn(pc, __fadd_rn(pc, ti))));
+                    }
+                } else {
+                    float alpha = __fdiv_rn(__fadd_rn(M[s], Mck), Msum);
+                    float pi = __fdiv_rn(__fmul_rn(M[s], ph[s]), J[s]);
+                    float pc = __fmul_rn(Mck, py[s]);
+                    m = __fmul_rn(alpha, __fdiv_rn(pi, __fadd_rn(pc, pi)));
+                }
+                wv[s] = m * py[s] * Wx[s] * J[s];
+                if (!(wv[s] > 0.f) || !isfinite(wv[s])) wv[s] = 0.f;
+            }
+        } else for (int s = 0; s < n; ++s) {
             if (!ok[s]) continue;
-            float num = s == 0 ? M[0] * py[0] : M[s] * ph[s] / J[s];
-            float den = M[0] * py[s];
-            for (int j = 1; j < n; ++j) den += (j == s) ? M[s] * ph[s] / J[s] : w.terms[((size_t)u * S + s) * S + j];
-            float m = den > 0.f ? num / den : 0.f;
+            float num = s == 0 ? __fmul_rn(M[0], py[0]) : __fdiv_rn(__fmul_rn(M[s], ph[s]), J[s]);
+            float den = __fmul_rn(M[0], py[s]);
+            for (int j = 1; j < n; ++j)
+                den = __fadd_rn(den, (j == s) ? __fdiv_rn(__fmul_rn(M[s], ph[s]), J[s]) : w.terms[((size_t)u * S + s) * S + j]);
+            float m = den > 0.f ? __fdiv_rn(num, den) : 0.f;
             wv[s] = m * py[s] * Wx[s] * J[s];
             if (!(wv[s] > 0.f) || !isfinite(wv[s])) wv[s] = 0.f;
         }

@@ -34,7 +34,7 @@ EMIT_POINT, EMIT_LASER, EMIT_CONFOCAL = 0, 1, 2
 # flags (same bit values on both sides of the library boundary)
 FLAG_DIRECT = 1          # include length-1 (direct) candidates
 FLAG_NAIVE_SHIFT = 2     # hybrid shift without the path-length Newton correction
-FLAG_PAIRWISE_MIS = 4    # reserved
+FLAG_PAIRWISE_MIS = 4    # pairwise MIS instead of the generalized balance heuristic (2k shifts)
 
 
 @dataclass

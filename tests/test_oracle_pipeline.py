@@ -145,3 +145,41 @@ def test_newton_statistics_in_paper_range(oracle_lib):
     assert st["newton_calls"] > 500
     assert 1.0 <= st["newton_iters"] / st["newton_calls"] <= 3.0
     assert st["newton_ok"] / st["newton_calls"] > 0.8
+
+
+def test_pairwise_mis_equals_balance_heuristic_for_one_reused_domain(oracle_lib):
+    """With one reused domain (k = 1) pairwise MIS is the two-technique balance heuristic: a
+    spatial pass with one neighbour and a temporal pass give the same images bit for bit."""
+    O = oracle_lib
+    for nf, temporal in [(1, 0), (2, 1)]:
+        sc = scenes.box_icosphere(W=24, H=24, frames=nf)
+        sc.gates = [(5.0, 0.25)] * nf
+        sc.params.n_spatial, sc.params.radius, sc.params.temporal = 1, 4, temporal
+        geoms = [O.Geom(sc, f) for f in range(nf)]
+        out = []
+        for flags in (0, scenes.FLAG_PAIRWISE_MIS):
+            sc.params.flags = flags
+            v = O.View(24, 24, 0)
+            for f in range(nf):
+                img, ok = O.render_frame(v, geoms[f], sc, f, seed=3, nthreads=8)
+            out.append(img)
+        assert np.array_equal(out[0], out[1])
+        assert out[0].sum() > 0
+
+
+def test_pairwise_mis_unbiased(oracle_lib):
+    """Pairwise MIS weights sum to one over the techniques at every y, so the estimator stays
+    unbiased with k = 3 reused domains (and differs from the balance heuristic per seed)."""
+    O = oracle_lib
+    sc = _box(1)
+    sc.params.n_spatial = 3
+    sc.params.flags = scenes.FLAG_PAIRWISE_MIS
+    gz, rel, z = _unbiased(O, sc, 1)
+    assert abs(gz) < 3.5, (gz, rel)
+    assert abs(rel) < 0.03, (gz, rel)
+    assert np.max(np.abs(z)) < 4.5, z
+    g = O.Geom(sc, 0)
+    a = O.render_frame(O.View(32, 32, 0), g, sc, 0, seed=5, nthreads=8)[0]
+    sc.params.flags = 0
+    b = O.render_frame(O.View(32, 32, 0), g, sc, 0, seed=5, nthreads=8)[0]
+    assert not np.array_equal(a, b)
