@@ -164,7 +164,7 @@ tof_status tof_render_gated(tof_ctx* ctx, tof_scene scene, tof_view view, const 
  * of tof_render_gated.
  *   - Limits: the view has W*H <= 16384 pixels (e.g. 128 x 128), is a gated view (B = 0), and
  *     params->n_spatial <= 5; larger requests fail with TOF_EINVAL and a message naming the limit.
- *   - The static array (about 14.5 MiB) belongs to the library's device image: every GPU that
+ *   - The static array (about 15.6 MiB) belongs to the library's device image: every GPU that
  *     loads libtof.so holds it until the process exits.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress with
  *     that device current); make that first call before any stream capture.

@@ -18,8 +18,9 @@
 namespace tof {
 cudaError_t launch_gbuffer(const GbufArgs& a, cudaStream_t s);
 cudaError_t launch_initial(const InitArgs& a, int* err, cudaStream_t s);
-cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, cudaEvent_t* ev, cudaStream_t s);
-cudaError_t reuse_persist_blocks(int* out);
+cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, int vis_blocks,
+                              cudaEvent_t* ev, cudaStream_t s);
+cudaError_t reuse_persist_blocks(int* out, int* vis_out);
 cudaError_t launch_splat(const SplatArgs& a, cudaStream_t s);
 cudaError_t launch_pt(const PtArgs& a, cudaStream_t s);
 cudaError_t launch_laser(const GeomDev& g, float3 o, float3 d, float power, LightDev* out, cudaStream_t s);
@@ -114,6 +115,7 @@ struct tof_ctx {
     int* d_err = nullptr;
     float* d_scratch = nullptr;  // laser spot of plain PT renders
     int persist_blocks = 0;      // resident blocks of the persistent reuse kernels
+    int vis_blocks = 0;          // resident blocks of the visibility kernel
     // batched rendering: stream pool, fork / join events, and the instantiated graph
     std::vector<cudaStream_t> pool;
     std::vector<cudaEvent_t> join;
@@ -255,8 +257,10 @@ constexpr size_t kNA_yrec = kNA_inv + al256(sizeof(uint32_t) * kNA_U * kNA_S * (
 constexpr size_t kNA_py = kNA_yrec + al256(sizeof(float4) * 6 * kNA_U * (kNA_S - 1));
 constexpr size_t kNA_jac = kNA_py + al256(sizeof(float) * kNA_U * kNA_S);
 constexpr size_t kNA_terms = kNA_jac + al256(sizeof(float) * kNA_U * kNA_S);
-constexpr size_t kNA_counters = kNA_terms + al256(sizeof(float) * kNA_U * kNA_S * kNA_S);
-constexpr size_t kNoAllocBytes = kNA_counters + 256;   // about 14.5 MiB
+constexpr size_t kNA_rays = kNA_terms + al256(sizeof(float) * kNA_U * kNA_S * kNA_S);
+constexpr size_t kNoAllocRays = 65536;   // queued visibility segments; the rest are traced in place
+constexpr size_t kNA_counters = kNA_rays + al256(sizeof(float4) * 2 * kNoAllocRays);
+constexpr size_t kNoAllocBytes = kNA_counters + 256;   // about 15.6 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -292,6 +296,8 @@ static tof_status noalloc_wave(tof_ctx* c, WaveDev* w) {
     w->py = (float*)(b + kNA_py);
     w->jac = (float*)(b + kNA_jac);
     w->terms = (float*)(b + kNA_terms);
+    w->rays = (float4*)(b + kNA_rays);
+    w->ray_cap = (uint32_t)kNoAllocRays;
     w->counters = (uint32_t*)(b + kNA_counters);
     return TOF_OK;
 }
@@ -517,8 +523,15 @@ static tof_status ensure_wave(tof_ctx* c, ViewH& V, int S, int cap) {
     TRY(dalloc(c, &w.py, sizeof(float) * U * S, "shifted targets"));
     TRY(dalloc(c, &w.jac, sizeof(float) * U * S, "shift Jacobians"));
     TRY(dalloc(c, &w.terms, sizeof(float) * U * S * S, "MIS terms"));
-    TRY(dalloc(c, &w.counters, sizeof(uint32_t) * 4, "task counters"));
-    void* ps[12] = {w.slot_pix, w.slot_M, w.nslot, w.units, w.fwd, w.inv, w.yrec, w.py, w.jac, w.terms, w.counters, nullptr};
+    // queued visibility segments: two per inverse shift would need up to 2 U S (S - 1); a pass
+    // shifts far fewer, and segments beyond the queue are traced in place
+    size_t rcap = 2 * U * S * (S - 1);
+    size_t rmax = npix * 16 > ((size_t)1 << 22) ? npix * 16 : ((size_t)1 << 22);
+    if (rcap > rmax) rcap = rmax;
+    TRY(dalloc(c, &w.rays, sizeof(float4) * 2 * rcap, "visibility queue"));
+    w.ray_cap = (uint32_t)rcap;
+    TRY(dalloc(c, &w.counters, sizeof(uint32_t) * kWaveCounters, "task counters"));
+    void* ps[12] = {w.slot_pix, w.slot_M, w.nslot, w.units, w.fwd, w.inv, w.yrec, w.py, w.jac, w.terms, w.rays, w.counters};
     for (int k = 0; k < 12; ++k) V.wave_ptrs[k] = ps[k];
     V.wave_slots = S; V.wave_cap = cap;
     return TOF_OK;
@@ -534,7 +547,7 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
     size_t cap = npix * Bn < kMaxUnits ? npix * Bn : kMaxUnits;
     if (cap < npix && V.B == 0) cap = npix;
     if (!fixed) TRY(ensure_wave(c, V, S, (int)cap));
-    if (!c->persist_blocks) CK(reuse_persist_blocks(&c->persist_blocks));
+    if (!c->persist_blocks) CK(reuse_persist_blocks(&c->persist_blocks, &c->vis_blocks));
     WaveDev w = fixed ? *fixed : V.wave;
     w.slots = S;
     if (!fixed) w.cap_units = V.wave_cap;
@@ -552,7 +565,7 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
             ev = &V.kev[V.kev_used];
             V.kev_used += 5;
         }
-        CK(launch_reuse_wave(ra, w, (int)p0, (int)p1, c->persist_blocks, ev, s));
+        CK(launch_reuse_wave(ra, w, (int)p0, (int)p1, c->persist_blocks, c->vis_blocks, ev, s));
     }
     return TOF_OK;
 }
@@ -766,7 +779,7 @@ tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* s
         int S = 1 + J.params.n_spatial > 2 ? 1 + J.params.n_spatial : 2;
         TRY(ensure_wave(c, V, S, (int)cap));
     }
-    if (!c->persist_blocks) CK(reuse_persist_blocks(&c->persist_blocks));
+    if (!c->persist_blocks) CK(reuse_persist_blocks(&c->persist_blocks, &c->vis_blocks));
     const uint32_t P = n < 16 ? n : 16;
     while (c->pool.size() < P) {
         cudaStream_t q;

@@ -286,6 +286,56 @@ static __device__ bool visible(const GeomDev& g, float3 a, float3 an, float3 b, 
     return !traverse<true>(g, ao, d, dist, tri, b1, b2, t);
 }
 
+// Deferred visibility: a shift kernel hands its visibility segments to a queue instead of tracing
+// them in place, and a separate kernel (vis_kernel) traces the queue with every lane of a warp on
+// a ray.  A queued ray carries the index of the float result it guards (a shifted target or an MIS
+// term); an occluded ray zeroes that result.  The traced segment is exactly the one visible()
+// traces, so deferring it changes no result.  A full queue falls back to tracing in place.
+struct VisQ {
+    float4* rays;        // 2 float4 per ray: (origin, tmax), (direction, target index bits)
+    uint32_t* counter;   // rays reserved so far (may exceed cap)
+    uint32_t cap;
+    uint32_t target;     // index of the guarded result
+};
+
+// one atomic for whichever lanes are converged here (any subset of the warp); every lane of the
+// mask runs the same straight-line sequence of shuffles, so all of them meet
+static __device__ __forceinline__ uint32_t reserve_coalesced(uint32_t* counter, uint32_t n) {
+    const uint32_t mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    uint32_t prefix = 0, total = 0;
+    for (int k = 0; k < 32; ++k) {
+        if (!((mask >> k) & 1u)) continue;   // uniform over the group
+        uint32_t v = __shfl_sync(mask, n, k);
+        total += v;
+        if (k < lane) prefix += v;
+    }
+    uint32_t base = 0;
+    if (lane == leader && total) base = atomicAdd(counter, total);
+    base = __shfl_sync(mask, base, leader);
+    return base + prefix;
+}
+
+// visible(), or the same segment queued for vis_kernel (returns true: not known to be occluded)
+static __device__ bool visible_q(const VisQ* q, const GeomDev& g, float3 a, float3 an, float3 b, const float3* bn, float eps) {
+    if (!q) return visible(g, a, an, b, bn, eps);
+    float3 ao = offset_point(a, an, b - a, eps);
+    float3 bo = bn ? offset_point(b, *bn, a - b, eps) : b;
+    float3 d = bo - ao;
+    float dist = len3(d);
+    if (!(dist > 0.f)) return true;
+    d = d * (1.0f / dist);
+    uint32_t i = reserve_coalesced(q->counter, 1u);
+    if (i >= q->cap) {
+        int tri; float b1, b2, t;
+        return !traverse<true>(g, ao, d, dist, tri, b1, b2, t);
+    }
+    q->rays[2 * (size_t)i] = make_float4(ao.x, ao.y, ao.z, dist);
+    q->rays[2 * (size_t)i + 1] = make_float4(d.x, d.y, d.z, __uint_as_float(q->target));
+    return true;
+}
+
 // ============================================================================================
 // sensor rays and back-projection
 // ============================================================================================
@@ -432,9 +482,10 @@ static __device__ float light_term(const Domain& D, const Surf& x, float3& wl, f
     seg = dist + (L.kind == 2 ? L.emit_len : 0.f);
     return I * fabsf(dot3(x.n, wl)) / (dist * dist);
 }
-static __device__ __forceinline__ bool light_visible(const Domain& D, const GeomDev& g, const Surf& x, float eps) {
-    if (D.light.kind == 2) return visible(g, x.p, x.n, D.light.pos, &D.spot_n, eps);
-    return visible(g, x.p, x.n, D.light.pos, nullptr, eps);
+static __device__ __forceinline__ bool light_visible(const Domain& D, const GeomDev& g, const Surf& x, float eps,
+                                                     const VisQ* q = nullptr) {
+    if (D.light.kind == 2) return visible_q(q, g, x.p, x.n, D.light.pos, &D.spot_n, eps);
+    return visible_q(q, g, x.p, x.n, D.light.pos, nullptr, eps);
 }
 
 static __device__ __forceinline__ float Gterm(const Surf& a, const Surf& b) {
@@ -710,10 +761,12 @@ static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float
 // ============================================================================================
 struct ShiftStats { uint32_t newton_calls, newton_iters, newton_ok, shift_calls, shift_ok; };
 
-// kOut = false: only the target value and the Jacobian are wanted (the MIS terms), not the record
+// kOut = false: only the target value and the Jacobian are wanted (the MIS terms), not the record.
+// vq: the visibility segments of a shift that passes every other test are queued there (vis_kernel
+// zeroes the guarded result when one is occluded); null: they are traced in place.
 template <bool kOut>
 static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& Di, const ParamsDev& P, bool geom_static, Rec& y,
-                          float& phat_out, float& jac_out, ShiftStats* st) {
+                          float& phat_out, float& jac_out, ShiftStats* st, const VisQ* vq = nullptr) {
     const int r = rec_r(x);
     if (r < 2 || !Di.valid || !Dj.valid) return false;
     const GeomDev& gi = Di.F->g;
@@ -835,16 +888,14 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
     float jac = (x.pdf_pre / pdfy) * jn;
     if (!(jac > 0.f) || !isfinite(jac)) return false;
 
-    // (7) visibility of the two reconnection segments
-    if (!visible(gi, yv[r - 1].p, yv[r - 1].n, pp.p, &pp.n, eps)) return false;
-    if (ns > 0) { if (!visible(gi, pp.p, pp.n, sv[0].p, &sv[0].n, eps)) return false; }
-    else if (!light_visible(Di, gi, pp, eps)) return false;
-
-    // (8) suffix radiance: cached, or re-evaluated when the scene or light differs (Sec. 5)
+    // (7) suffix radiance: cached, or re-evaluated when the scene or light differs (Sec. 5); the
+    // re-evaluated suffix's segments must be unoccluded too (tested in (8))
     float Lsuf_i = x.Lsuf;
+    bool suffix_eval = false;
     if (ns > 0) {
         bool cache_ok = geom_static && light_same(Dj.light, Di.light);
         if (!cache_ok) {
+            suffix_eval = true;
             float Ls = 1.0f;
             for (int q = 1; q < ns; ++q) {
                 Mat mq = load_mat(gi, sv[q].mat);
@@ -856,16 +907,25 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
                     float3 wn = q + 1 < ns ? dir_to(sv[q].p, sv[q + 1].p) : dir_to(sv[q].p, lpos_i);
                     Ls *= gg * bsdf_f(mq, sv[q].n, dir_to(sv[q].p, sv[q - 1].p), wn);
                 }
-                if (!visible(gi, sv[q - 1].p, sv[q - 1].n, sv[q].p, &sv[q].n, eps)) return false;
             }
             float3 wl; float seg;
             Ls *= light_term(Di, sv[ns - 1], wl, seg);
-            if (!light_visible(Di, gi, sv[ns - 1], eps)) return false;
             Lsuf_i = Ls;
         }
         f *= Lsuf_i;
     }
     if (!(f > 0.f) || !isfinite(f)) return false;
+
+    // (8) visibility of the two reconnection segments and of a re-evaluated suffix, last: every
+    // other test has passed, so only shifts that visibility alone decides queue segments
+    if (!visible_q(vq, gi, yv[r - 1].p, yv[r - 1].n, pp.p, &pp.n, eps)) return false;
+    if (ns > 0) { if (!visible_q(vq, gi, pp.p, pp.n, sv[0].p, &sv[0].n, eps)) return false; }
+    else if (!light_visible(Di, gi, pp, eps, vq)) return false;
+    if (suffix_eval) {
+        for (int q = 1; q < ns; ++q)
+            if (!visible_q(vq, gi, sv[q - 1].p, sv[q - 1].n, sv[q].p, &sv[q].n, eps)) return false;
+        if (!light_visible(Di, gi, sv[ns - 1], eps, vq)) return false;
+    }
 
     if (kOut) {
         y = x;

@@ -126,8 +126,12 @@ struct WaveDev {
     float* py;              // cap_units * S
     float* jac;             // cap_units * S
     float* terms;           // cap_units * S * S
-    uint32_t* counters;     // units, forward tasks, inverse tasks, overflow
+    float4* rays;           // 2 * ray_cap: queued visibility segments of the shifts (VisQ)
+    uint32_t ray_cap;
+    uint32_t* counters;     // units, forward tasks, inverse tasks, overflow, forward rays, inverse rays,
+                            // forward rays fetched, inverse rays fetched
 };
+constexpr int kWaveCounters = 8;
 
 struct SplatArgs {
     ResDev src;

@@ -11,9 +11,12 @@
 //   reuse_units_kernel   per (pixel, 32-bin word): merge units (pixel, bin), forward-shift tasks
 //                        and the canonical sample's inverse-shift tasks
 //   shift_fwd_kernel     persistent over forward tasks: shift slot s's sample into the unit's
-//                        domain; emit the inverse-shift tasks of the shifted candidate
+//                        domain, queueing its visibility segments
+//   vis_kernel           traces the queued segments, zeroing the results of occluded shifts
+//   emit_inv_kernel      per surviving shifted candidate: its inverse-shift tasks
 //   shift_inv_kernel     persistent over inverse tasks: shift candidate s's offset path into
 //                        domain j -> the term M_j p_hat_j(S_j^-1(y_s)) |dS_j^-1/dy_s|
+//                        (visibility queued again, then vis_kernel)
 //   reuse_merge_kernel   persistent over units: MIS weights, streaming selection, output
 // Task lists are compacted with atomics, read by the next kernel in stream order; no kernel
 // waits on another's progress.
@@ -70,25 +73,6 @@ __device__ __forceinline__ uint32_t reserve(uint32_t* counter, uint32_t n) {
     if (lane == 31) base = total ? atomicAdd(counter, total) : 0u;
     base = __shfl_sync(mask, base, 31);
     return base + incl - n;
-}
-
-// the same for whichever lanes are converged here (any subset of the warp): one atomic per group.
-// Every lane of the mask runs the same straight-line sequence of shuffles, so all of them meet.
-__device__ __forceinline__ uint32_t reserve_coalesced(uint32_t* counter, uint32_t n) {
-    const uint32_t mask = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    uint32_t prefix = 0, total = 0;
-    for (int k = 0; k < 32; ++k) {
-        if (!((mask >> k) & 1u)) continue;   // uniform over the group
-        uint32_t v = __shfl_sync(mask, n, k);
-        total += v;
-        if (k < lane) prefix += v;
-    }
-    uint32_t base = 0;
-    if (lane == leader && total) base = atomicAdd(counter, total);
-    base = __shfl_sync(mask, base, leader);
-    return base + prefix;
 }
 
 __device__ __forceinline__ void store_rec(float4* P, size_t stride, size_t idx, const Rec& r) {
@@ -244,21 +228,16 @@ __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant
         Rec y;
         float py = 0.f, J = 1.f;
         bool geom_static = (a.temporal && s == 1) ? a.geom_static != 0 : true;
-        bool ok = shift_rec<true>(x, Ds, D0, a.P, geom_static, y, py, J, &st);
         size_t ui = (size_t)u * S + s;
+        VisQ vq;
+        vq.rays = w.rays; vq.counter = &w.counters[4]; vq.cap = w.ray_cap; vq.target = (uint32_t)ui;
+        bool ok = shift_rec<true>(x, Ds, D0, a.P, geom_static, y, py, J, &st, &vq);
+        // visibility is settled by vis_kernel, which zeroes py of an occluded shift
         w.py[ui] = ok ? py : 0.f;
         w.jac[ui] = ok ? J : 1.f;
         if (ok) {
             store_rec(w.yrec, (size_t)w.cap_units * (S - 1), (size_t)u * (S - 1) + (s - 1), y);
         }
-        // the shifted candidate's inverse shifts into the other reused domains
-        const int n = w.nslot[pix];
-        // (pairwise MIS needs none: it pairs the canonical domain with each reused one)
-        const bool pairwise = (a.P.flags & kFlagPairwiseMis) != 0u;
-        const uint32_t ne = (ok && n > 2 && !pairwise) ? (uint32_t)(n - 2) : 0u;
-        uint32_t ib = reserve_coalesced(&w.counters[2], ne);
-        for (int j = 1; j < n && ne; ++j)
-            if (j != s) w.inv[ib++] = (u << 8) | ((uint32_t)s << 4) | (uint32_t)j;
     }
     // warp-level flush of the shift statistics
     if (a.stats) {
@@ -270,6 +249,134 @@ __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant
             for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
             if ((threadIdx.x & 31) == 0 && x) atomicAdd(&a.stats->v[i], x);
         }
+    }
+}
+
+// --------------------------------------------------------------------------------------------
+// visibility segments queued by a shift kernel; an occluded segment zeroes the result it guards.
+// Persistent, with dynamic fetch: a lane whose segment is settled takes the next queued one
+// between rounds of at most kVisSteps node visits, so lanes do not idle while the warp's longest
+// traversal (grazing segments over a heightfield visit many nodes) runs to its end.  Each
+// segment's node visits are those of traverse<true> in the same order, so the answer is the same.
+// stat >= 0: the stats counter that counted the guarded shifts as successes (one decrement per
+// shift, however many of its segments are occluded).
+// --------------------------------------------------------------------------------------------
+constexpr int kVisSteps = 8;
+
+__global__ void __launch_bounds__(128) vis_kernel(const GeomDev g, const float4* __restrict__ rays, const uint32_t* counter,
+                                                  uint32_t cap, uint32_t* fetch, float* target, StatsDev* stats, int stat) {
+    const uint32_t n = min(*counter, cap);
+    const int lane = threadIdx.x & 31;
+    unsigned long long lost = 0;
+    bool has = false, done = false;
+    float3 o = f3(0.f, 0.f, 0.f), d = o, id = o, ood = o;
+    float tmax = 0.f;
+    uint32_t tgt = 0;
+    int node = 0, sp = 0, budget = 0;
+    int stack[kStack];
+    while (true) {
+        // refill: every lane of the warp takes part (uniform control flow around the ballot)
+        const bool need = !has && !done;
+        const uint32_t want = __ballot_sync(0xFFFFFFFFu, need);
+        if (want) {
+            const int leader = __ffs(want) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(fetch, (uint32_t)__popc(want));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            if (need) {
+                const uint32_t i = base + (uint32_t)__popc(want & ((1u << lane) - 1u));
+                if (i < n) {
+                    float4 a = rays[2 * (size_t)i], b = rays[2 * (size_t)i + 1];
+                    o = f3(a.x, a.y, a.z); d = f3(b.x, b.y, b.z); tmax = a.w; tgt = __float_as_uint(b.w);
+                    id = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+                    ood = f3(o.x * id.x, o.y * id.y, o.z * id.z);
+                    node = 0; sp = 0; budget = g.nt + 64;
+                    has = true;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (__all_sync(0xFFFFFFFFu, done)) break;
+        bool hit = false;
+        for (int step = 0; step < kVisSteps && has; ++step) {
+            if (g.nt <= 0) { has = false; break; }
+            if (g.nt == 1) {
+                float t, u, w; int orig;
+                hit = tri_test(g.leaf, 0, o, d, tmax, t, u, w, orig) && t < tmax;
+                has = false;
+                break;
+            }
+            if (--budget < 0) { has = false; break; }
+            const float4* N = g.nodes + 4 * node;
+            float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
+            float a0 = n0.x * id.x - ood.x, a1 = n0.y * id.x - ood.x;
+            float b0 = n0.z * id.y - ood.y, bb1 = n0.w * id.y - ood.y;
+            float c0 = n2.x * id.z - ood.z, c1 = n2.y * id.z - ood.z;
+            float lo0 = fmaxf(fmaxf(fminf(a0, a1), fminf(b0, bb1)), fmaxf(fminf(c0, c1), 0.f));
+            float hi0 = fminf(fminf(fmaxf(a0, a1), fmaxf(b0, bb1)), fminf(fmaxf(c0, c1), tmax));
+            float d0 = n1.x * id.x - ood.x, d1 = n1.y * id.x - ood.x;
+            float e0 = n1.z * id.y - ood.y, e1 = n1.w * id.y - ood.y;
+            float f0 = n2.z * id.z - ood.z, f1 = n2.w * id.z - ood.z;
+            float lo1 = fmaxf(fmaxf(fminf(d0, d1), fminf(e0, e1)), fmaxf(fminf(f0, f1), 0.f));
+            float hi1 = fminf(fminf(fmaxf(d0, d1), fmaxf(e0, e1)), fminf(fmaxf(f0, f1), tmax));
+            bool h0 = lo0 <= hi0, h1 = lo1 <= hi1;
+            int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
+            if (h0 && ch0 < 0) {
+                float t, u, w; int orig;
+                if (tri_test(g.leaf, ~ch0, o, d, tmax, t, u, w, orig) && t < tmax) { hit = true; has = false; break; }
+                h0 = false;
+            }
+            if (h1 && ch1 < 0) {
+                float t, u, w; int orig;
+                if (tri_test(g.leaf, ~ch1, o, d, tmax, t, u, w, orig) && t < tmax) { hit = true; has = false; break; }
+                h1 = false;
+            }
+            if (h0 && h1) {
+                int nearc = lo0 <= lo1 ? ch0 : ch1, farc = lo0 <= lo1 ? ch1 : ch0;
+                if (sp < kStack) stack[sp++] = farc;
+                node = nearc;
+            } else if (h0) {
+                node = ch0;
+            } else if (h1) {
+                node = ch1;
+            } else {
+                if (sp == 0) { has = false; break; }
+                node = stack[--sp];
+            }
+        }
+        if (hit) {
+            float old = atomicExch(&target[tgt], 0.f);
+            if (old != 0.f) ++lost;
+        }
+    }
+    if (stats && stat >= 0) {
+        unsigned long long x = lost;
+        for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o2);
+        if (lane == 0 && x) atomicAdd(&stats->v[stat], 0ull - x);
+    }
+}
+
+// --------------------------------------------------------------------------------------------
+// after the forward shifts' visibility: each surviving shifted candidate's inverse shifts into
+// the other reused domains (pairwise MIS needs none: it pairs the canonical domain with each
+// reused one)
+// --------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) emit_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+    const uint32_t ntask = min(w.counters[1], (uint32_t)w.cap_units * (uint32_t)(w.slots - 1));
+    const int S = w.slots;
+    const bool pairwise = (a.P.flags & kFlagPairwiseMis) != 0u;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
+        uint32_t task = w.fwd[t];
+        uint32_t u = task >> 4;
+        int s = (int)(task & 15u);
+        int pix = w.units[u].x;
+        const int n = w.nslot[pix];
+        const bool ok = w.py[(size_t)u * S + s] > 0.f;
+        const uint32_t ne = (ok && n > 2 && !pairwise) ? (uint32_t)(n - 2) : 0u;
+        uint32_t ib = reserve_coalesced(&w.counters[2], ne);
+        for (int j = 1; j < n && ne; ++j)
+            if (j != s) w.inv[ib++] = (u << 8) | ((uint32_t)s << 4) | (uint32_t)j;
     }
 }
 
@@ -304,8 +411,11 @@ __global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant
         Rec tmp;
         float pj = 0.f, Jj = 1.f;
         float term = 0.f;
-        if (shift_rec<false>(y, D0, Dj, a.P, geom_static, tmp, pj, Jj, nullptr)) term = w.slot_M[(size_t)pix * S + j] * pj * Jj;
-        w.terms[((size_t)u * S + s) * S + j] = term;
+        const size_t ti = ((size_t)u * S + s) * S + j;
+        VisQ vq;
+        vq.rays = w.rays; vq.counter = &w.counters[5]; vq.cap = w.ray_cap; vq.target = (uint32_t)ti;
+        if (shift_rec<false>(y, D0, Dj, a.P, geom_static, tmp, pj, Jj, nullptr, &vq)) term = w.slot_M[(size_t)pix * S + j] * pj * Jj;
+        w.terms[ti] = term;
     }
     if (a.stats) {
         unsigned long long x = ninv;
@@ -410,10 +520,11 @@ __global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant_
     }
 }
 
-// ev (optional): 5 events recorded around the four kernels for per-kernel timing
-cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, cudaEvent_t* ev,
-                              cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(w.counters, 0, 4 * sizeof(uint32_t), s);
+// ev (optional): 5 events recorded around the stages (setup | forward shifts + their visibility +
+// inverse-task emission | inverse shifts + their visibility | merge) for per-stage timing
+cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, int vis_blocks,
+                              cudaEvent_t* ev, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(w.counters, 0, kWaveCounters * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     int np = p1 - p0;
     if (np <= 0) return cudaSuccess;
@@ -423,26 +534,35 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
     reuse_units_kernel<<<(unsigned)((nw + 127) / 128), 128, 0, s>>>(a, w, p0, p1);
     if (ev) cudaEventRecord(ev[1], s);
     shift_fwd_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    // forward shifts land in the current frame; counter 4 of the stats counted them as successes
+    vis_kernel<<<vis_blocks, 128, 0, s>>>(a.cur.g, w.rays, &w.counters[4], w.ray_cap, &w.counters[6], w.py, a.stats, 4);
+    emit_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
     if (ev) cudaEventRecord(ev[2], s);
     shift_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    // inverse shifts land in the reused domain: the previous frame for the temporal pass (its one
+    // reused slot), the current frame for spatial passes
+    vis_kernel<<<vis_blocks, 128, 0, s>>>(a.temporal ? a.prev.g : a.cur.g, w.rays, &w.counters[5], w.ray_cap, &w.counters[7],
+                                          w.terms, nullptr, -1);
     if (ev) cudaEventRecord(ev[3], s);
     reuse_merge_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
     if (ev) cudaEventRecord(ev[4], s);
     return cudaGetLastError();
 }
 
-cudaError_t reuse_persist_blocks(int* out) {
-    int dev = 0, sms = 0, b1 = 0, b2 = 0, b3 = 0;
+cudaError_t reuse_persist_blocks(int* out, int* vis_out) {
+    int dev = 0, sms = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, shift_fwd_kernel, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, shift_inv_kernel, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, reuse_merge_kernel, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, vis_kernel, 128, 0);
     int b = b1;
     if (b2 < b) b = b2;
     if (b3 < b) b = b3;
     *out = sms * (b > 0 ? b : 1);
+    *vis_out = sms * (b4 > 0 ? b4 : 1);
     return cudaGetLastError();
 }
 
