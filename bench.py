@@ -265,45 +265,10 @@ def run_ours(args, rank, world):
     quality = {}
     if kept:
         ms_frame = float(np.median(step_ms))
-        ref = torch.zeros(H * W, device=dev)
-        pt_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        e_restir, e_pt, e_pw, pt_ms_all, spp = [], [], [], [], 1
-        with torch.cuda.stream(stream):
-            for f, img in sorted(kept.items()):
-                fq = f % nf
-                tof.tof_bvh_build(ctx, sid, xf32[fq], refit_only=0, stream=sptr)
-                acc = torch.zeros(H * W, device=dev, dtype=torch.float64)
-                chunk = 64
-                for c0 in range(0, args.ref_spp, chunk):
-                    tof.tof_render_pt(ctx, sid, sc.sensors[fq], sc.emitters[fq], sc.gates[fq], None, p, 9000 + c0, fq, chunk,
-                                      ref.data_ptr(), sptr)
-                    acc += ref.double()
-                stream.synchronize()
-                refimg = (acc / (args.ref_spp // chunk)).cpu().numpy().reshape(H, W)
-                # plain PT at (approximately) equal time: grow spp until one render takes a frame's time
-                for _ in range(8):
-                    pt_ev[0].record(stream)
-                    tof.tof_render_pt(ctx, sid, sc.sensors[fq], sc.emitters[fq], sc.gates[fq], None, p, 77 + f, fq, spp,
-                                      ref.data_ptr(), sptr)
-                    pt_ev[1].record(stream)
-                    stream.synchronize()
-                    pt_ms = pt_ev[0].elapsed_time(pt_ev[1])
-                    if pt_ms >= ms_frame or spp >= 4096:
-                        break
-                    spp = max(spp + 1, int(spp * ms_frame / max(pt_ms, 1e-3)))
-                pt_ms_all.append(pt_ms)
-                if f in kept_pw:
-                    e_pw.append(rel_mse(kept_pw[f], refimg))
-                e_restir.append(rel_mse(img, refimg))
-                e_pt.append(rel_mse(ref.cpu().numpy().astype(np.float64).reshape(H, W), refimg))
-        er, ep, pm = float(np.mean(e_restir)), float(np.mean(e_pt)), float(np.mean(pt_ms_all))
-        quality = {"frames": sorted(int(f % nf) for f in kept), "ref_spp": int(args.ref_spp),
-                   "relmse_restir": er, "relmse_pt_equal_time": ep,
-                   "relmse_restir_per_frame": e_restir, "relmse_pt_per_frame": e_pt,
-                   "pt_spp": spp, "pt_ms": pm, "restir_ms": ms_frame,
-                   "restir_vs_pt_inv_mse_time": (1.0 / (er * ms_frame)) / (1.0 / (ep * pm)) if er > 0 and ep > 0 else None}
+        quality, e_pw = _quality(args, ctx, sid, sc, p, kept, ms_frame, stream, extra=kept_pw)
         if e_pw and pairwise:
             ew = float(np.mean(e_pw))
+            ep, pm = quality["relmse_pt_equal_time"], quality["pt_ms"]
             pairwise["relmse"] = ew
             pairwise["relmse_per_frame"] = e_pw
             pairwise["vs_pt_inv_mse_time"] = (1.0 / (ew * pairwise["ms_per_step"])) / (1.0 / (ep * pm)) if ew > 0 and ep > 0 else None
@@ -312,6 +277,104 @@ def run_ours(args, rank, world):
                 pairwise=pairwise,
                 quality=quality, stats=shift_stats, per_frame=per_frame, npix=W * H, W=W, H=H,
                 nobj=len(sc.object_material))
+
+
+def _quality(args, ctx, sid, sc, p, kept, ms_frame, stream, extra=None):
+    """relMSE of the kept frames {frame: image} against args.ref_spp-spp plain path-traced references,
+    and of plain path tracing at (about) the frame time `ms_frame` on the same frames; the frames'
+    geometry is rebuilt here.  extra: more {frame: image} scored against the same references."""
+    import torch
+    from paper_2605_11536_gb300 import tof
+    sptr = stream.cuda_stream
+    nf = sc.n_frames
+    W, H = sc.sensors[0]["W"], sc.sensors[0]["H"]
+    ref = torch.zeros(H * W, device="cuda")
+    pt_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    e_restir, e_pt, e_extra, pt_ms_all, spp = [], [], [], [], 1
+    with torch.cuda.stream(stream):
+        for f, img in sorted(kept.items()):
+            fq = f % nf
+            tof.tof_bvh_build(ctx, sid, np.ascontiguousarray(sc.xforms[fq].reshape(-1), dtype=np.float32), refit_only=0,
+                              stream=sptr)
+            acc = torch.zeros(H * W, device="cuda", dtype=torch.float64)
+            chunk = 64
+            for c0 in range(0, args.ref_spp, chunk):
+                tof.tof_render_pt(ctx, sid, sc.sensors[fq], sc.emitters[fq], sc.gates[fq], None, p, 9000 + c0, fq, chunk,
+                                  ref.data_ptr(), sptr)
+                acc += ref.double()
+            stream.synchronize()
+            refimg = (acc / (args.ref_spp // chunk)).cpu().numpy().reshape(H, W)
+            # plain PT at (approximately) equal time: grow spp until one render takes a frame's time
+            for _ in range(8):
+                pt_ev[0].record(stream)
+                tof.tof_render_pt(ctx, sid, sc.sensors[fq], sc.emitters[fq], sc.gates[fq], None, p, 77 + f, fq, spp,
+                                  ref.data_ptr(), sptr)
+                pt_ev[1].record(stream)
+                stream.synchronize()
+                pt_ms = pt_ev[0].elapsed_time(pt_ev[1])
+                if pt_ms >= ms_frame or spp >= 4096:
+                    break
+                spp = max(spp + 1, int(spp * ms_frame / max(pt_ms, 1e-3)))
+            pt_ms_all.append(pt_ms)
+            if extra and f in extra:
+                e_extra.append(rel_mse(extra[f], refimg))
+            e_restir.append(rel_mse(img, refimg))
+            e_pt.append(rel_mse(ref.cpu().numpy().astype(np.float64).reshape(H, W), refimg))
+    er, ep, pm = float(np.mean(e_restir)), float(np.mean(e_pt)), float(np.mean(pt_ms_all))
+    q = {"frames": sorted(int(f % nf) for f in kept), "ref_spp": int(args.ref_spp),
+         "relmse_restir": er, "relmse_pt_equal_time": ep,
+         "relmse_restir_per_frame": e_restir, "relmse_pt_per_frame": e_pt,
+         "pt_spp": spp, "pt_ms": pm, "restir_ms": ms_frame,
+         "restir_vs_pt_inv_mse_time": (1.0 / (er * ms_frame)) / (1.0 / (ep * pm)) if er > 0 and ep > 0 else None}
+    return q, e_extra
+
+
+def run_quality_rough(args, frames=24):
+    """The dynamic workload with every GGX lobe at least as rough as the reconnection threshold
+    (alpha >= 0.2; mirrors and Lambert unchanged): the same frames, timing and references as the
+    headline's quality, on a material mix where the glossy-to-light paths that no shift can reach
+    (and that make most of the headline's relative error) are absent."""
+    import torch
+    from paper_2605_11536_gb300 import scenes, tof
+    sc = workload(seed=1)
+    mats = np.array(sc.materials, dtype=np.float64)
+    ggx = mats[:, 0] == scenes.GGX
+    mats[ggx, 2] = np.maximum(mats[ggx, 2], 0.2)
+    sc.materials = mats
+    p = sc.params
+    W, H = sc.sensors[0]["W"], sc.sensors[0]["H"]
+    nf = sc.n_frames
+    nq = min(args.quality_frames, frames)
+    ctx = tof.tof_create(torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    try:
+        sid = tof.tof_scene_upload(ctx, sc.verts, sc.tris, sc.tri_object, sc.materials, sc.object_material)
+        vid = tof.tof_view_create(ctx, sid, W, H, 0)
+        out = torch.zeros(H * W, device="cuda")
+        flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+        kept, ms = {}, []
+        with torch.cuda.stream(stream):
+            for f in range(frames):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tof.tof_bvh_build(ctx, sid, np.ascontiguousarray(sc.xforms[f % nf].reshape(-1), dtype=np.float32),
+                                  refit_only=0, stream=sptr)
+                tof.tof_render_gated(ctx, sid, vid, sc.sensors[f % nf], sc.emitters[f % nf], sc.gates[f % nf], p, sc.seed, f,
+                                     out.data_ptr(), sptr)
+                e1.record(stream)
+                stream.synchronize()
+                if f >= 8:
+                    ms.append(e0.elapsed_time(e1))
+                if f >= frames - nq:
+                    kept[f] = out.cpu().numpy().astype(np.float64).reshape(H, W)
+        q, _ = _quality(args, ctx, sid, sc, p, kept, float(np.median(ms)), stream)
+    finally:
+        tof.tof_destroy(ctx)
+    q["materials"] = "GGX alpha clamped to >= 0.2 (%d of %d objects' lobes changed)" % (
+        int(np.count_nonzero(ggx & (np.array(workload(seed=1).materials)[:, 2] < 0.2))), len(mats))
+    return q
 
 
 def batch_workload(n=64, seed=3):
@@ -327,7 +390,8 @@ def batch_workload(n=64, seed=3):
 
 def run_batched(args, steps=6, warmup=2):
     """Batched form: all instances in one tof_render_batch graph launch, against one
-    tof_render_gated launch per instance on one stream (same jobs, same frames)."""
+    tof_render_gated launch per instance on one stream (same jobs, same frames); batched again after
+    tof_autotune has chosen each instance class's pixel tile, task packet and reservoir layout."""
     import torch
     from paper_2605_11536_gb300 import tof
     scs, inst = batch_workload()
@@ -337,7 +401,8 @@ def run_batched(args, steps=6, warmup=2):
     try:
         sids = [tof.tof_scene_upload(ctx, s.verts, s.tris, s.tri_object, s.materials, s.object_material) for s in scs]
         res = {}
-        for mode in ("per_launch", "batched"):
+        tuned = {}
+        for mode in ("per_launch", "batched", "batched_tuned"):
             views, bufs, params = [], [], []
             for it in inst:
                 views.append(tof.tof_view_create(ctx, sids[it["scene"]], it["W"], it["H"], 0))
@@ -346,6 +411,22 @@ def run_batched(args, steps=6, warmup=2):
                 p = type(sc.params)(**vars(sc.params))
                 p.depth = it["depth"]
                 params.append(p)
+            if mode == "batched_tuned":
+                for k, s in enumerate(scs):
+                    tof.tof_bvh_build(ctx, sids[k], s.xforms[0].reshape(-1), refit_only=0, stream=sptr)
+                jobs0 = []
+                for i, it in enumerate(inst):
+                    sc = scs[it["scene"]]
+                    jobs0.append(tof.job(sids[it["scene"]], views[i], dict(sc.sensors[0], W=it["W"], H=it["H"]),
+                                         sc.emitters[0], params[i], it["seed"], 0, bufs[i].data_ptr(),
+                                         gate=(sc.gates[0][0], it["dL"])))
+                t_tune = time.perf_counter()
+                chosen = tof.tof_autotune(ctx, jobs0, frames=2, stream=sptr)
+                t_tune = time.perf_counter() - t_tune
+                for it, t in zip(inst, chosen):
+                    key = "%dx%d/p%d/%s" % (t["tile_w"], t["tile_h"], t["packet"], "aos" if t["layout"] else "soa")
+                    tuned[key] = tuned.get(key, 0) + 1
+                tuned = {"tunings": tuned, "tune_seconds": t_tune}
             times = []
             for f in range(warmup + steps):
                 for k, s in enumerate(scs):
@@ -358,13 +439,13 @@ def run_batched(args, steps=6, warmup=2):
                     sc = scs[it["scene"]]
                     sens = dict(sc.sensors[f % sc.n_frames], W=it["W"], H=it["H"])
                     gate = (sc.gates[0][0], it["dL"])
-                    if mode == "batched":
+                    if mode != "per_launch":
                         jobs.append(tof.job(sids[it["scene"]], views[i], sens, sc.emitters[0], params[i], it["seed"], f,
                                             bufs[i].data_ptr(), gate=gate))
                     else:
                         tof.tof_render_gated(ctx, sids[it["scene"]], views[i], sens, sc.emitters[0], gate, params[i],
                                              it["seed"], f, bufs[i].data_ptr(), sptr)
-                if mode == "batched":
+                if mode != "per_launch":
                     tof.tof_render_batch(ctx, jobs, sptr)
                 e1.record(stream)
                 stream.synchronize()
@@ -377,36 +458,24 @@ def run_batched(args, steps=6, warmup=2):
         tof.tof_destroy(ctx)
     npx = sum(it["W"] * it["H"] for it in inst)
     return {"instances": len(inst), "pixels": npx, "scene_tris": [int(s.nt) for s in scs],
-            "batched_ms": res["batched"], "per_launch_ms": res["per_launch"],
+            "batched_ms": res["batched"], "batched_tuned_ms": res["batched_tuned"], "per_launch_ms": res["per_launch"],
             "batched_instances_per_s": len(inst) / (res["batched"] / 1e3),
+            "batched_tuned_instances_per_s": len(inst) / (res["batched_tuned"] / 1e3),
             "per_launch_instances_per_s": len(inst) / (res["per_launch"] / 1e3),
-            "speedup": res["per_launch"] / res["batched"], "frames_timed": steps}
+            "speedup": res["per_launch"] / res["batched"], "speedup_tuned": res["per_launch"] / res["batched_tuned"],
+            "autotune": tuned, "frames_timed": steps}
 
 
-def run_served(args, seconds=1.5, rate=240.0, seed=4):
-    """Served form: 8 dynamic streams (6 gated like the dynamic workload at 256..1024 px, 2 transient
-    confocal 256x256 x 512 bins), Poisson arrivals at `rate` requests/s for `seconds`, continuous
-    batching by tof_server_step; against the same requests rendered one launch each."""
+def _serve_scenario(scs, arrivals, nfr):
+    """Serve `arrivals` [(t, stream)] over the scenes `scs` with tof_server_* (continuous batching),
+    then the same requests one launch per request: back to back on one stream (throughput), and as a
+    FIFO that renders each request when it has arrived and the previous one is done (latency under the
+    same arrival process)."""
     import torch
-    from paper_2605_11536_gb300 import scenes, tof
-    rng = np.random.default_rng(seed)
-    gated_res = [256, 362, 512, 512, 724, 1024]
-    nfr = 32
-    scs = [scenes.heightfield_spheres(W=r, H=r, frames=nfr, seed=20 + k) for k, r in enumerate(gated_res)]
-    for k in range(2):
-        c = scenes.confocal_nlos(W=256, H=256, frames=nfr, B=512, seed=30 + k)
-        c.bins = (1.35, 0.002, 512)
-        scs.append(c)
-    # arrivals: 70 % gated requests spread over the gated streams, 30 % over the transient ones
-    t, arrivals = 0.0, []
-    while t < seconds:
-        t += rng.exponential(1.0 / rate)
-        st = int(rng.integers(0, 6)) if rng.uniform() < 0.7 else 6 + int(rng.integers(0, 2))
-        arrivals.append((t, st))
+    from paper_2605_11536_gb300 import tof
     ctx = tof.tof_create(torch.cuda.current_device())
     stream = torch.cuda.Stream()
     sptr = stream.cuda_stream
-    result = {}
     try:
         sids = [tof.tof_scene_upload(ctx, s.verts, s.tris, s.tri_object, s.materials, s.object_material) for s in scs]
         for k, s in enumerate(scs):
@@ -420,7 +489,6 @@ def run_served(args, seconds=1.5, rate=240.0, seed=4):
             return tof.job(sids[k], 0, s.sensors[f % nfr], s.emitters[f % nfr], s.params, 50 + k, f, out[k].data_ptr(),
                            gate=None if s.bins else s.gates[0], bins=s.bins)
 
-        # served
         srv = tof.tof_server_create(ctx, 120 << 30)
         streams = [tof.tof_server_open_stream(srv, sids[k], *shape[k]) for k in range(len(scs))]
         nframe = [0] * len(scs)
@@ -445,14 +513,10 @@ def run_served(args, seconds=1.5, rate=240.0, seed=4):
         lat512 = [tof.tof_server_poll(srv, tk)[1] for k, tk in tickets if shape[k][:2] == (512, 512) and shape[k][2] == 0]
         st = tof.tof_server_stats(srv)
         tof.tof_server_destroy(srv)
-        # one launch per request, the same requests in arrival order on one stream
+
         views = [tof.tof_view_create(ctx, sids[k], *shape[k]) for k in range(len(scs))]
-        nframe = [0] * len(scs)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        for _, k in arrivals:
-            f = nframe[k]
-            nframe[k] += 1
+
+        def render_one(k, f):
             s = scs[k]
             tof.tof_bvh_build(ctx, sids[k], s.xforms[f % nfr].reshape(-1), refit_only=0, stream=sptr)
             if s.bins:
@@ -461,20 +525,84 @@ def run_served(args, seconds=1.5, rate=240.0, seed=4):
             else:
                 tof.tof_render_gated(ctx, sids[k], views[k], s.sensors[f % nfr], s.emitters[f % nfr], s.gates[0], s.params,
                                      50 + k, f, out[k].data_ptr(), sptr)
+
+        # one launch per request, back to back (the per-launch throughput)
+        nframe = [0] * len(scs)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _, k in arrivals:
+            render_one(k, nframe[k])
+            nframe[k] += 1
         stream.synchronize()
         per_launch_s = time.perf_counter() - t1
-        result = {"streams": len(scs), "requests": len(arrivals), "arrival_rate": rate, "arrival_seconds": seconds,
-                  "served_frames_per_s": len(arrivals) / wall, "served_wall_s": wall,
-                  "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-                  "latency_512_gated_ms": {"p50": float(np.percentile(lat512, 50)), "p99": float(np.percentile(lat512, 99))}
-                  if lat512 else None,
-                  "batches": st["batches"], "resident_gb": st["resident_bytes"] / 2 ** 30,
-                  "per_launch_frames_per_s": len(arrivals) / per_launch_s, "per_launch_s": per_launch_s,
-                  "mix": "6 gated streams (256, 362, 512, 512, 724, 1024 px) + 2 transient 256x256x512, "
-                         "70/30 gated/transient requests"}
+        # one launch per request as a FIFO under the same arrivals (latency)
+        for v in views:
+            tof.tof_reservoirs_reset(ctx, v)
+        nframe = [0] * len(scs)
+        fifo_lat = []
+        t2 = time.perf_counter()
+        for ta, k in arrivals:
+            while time.perf_counter() - t2 < ta:
+                time.sleep(0.0002)
+            render_one(k, nframe[k])
+            nframe[k] += 1
+            stream.synchronize()
+            fifo_lat.append((time.perf_counter() - t2 - ta) * 1e3)
+        fifo_wall = time.perf_counter() - t2
     finally:
         tof.tof_destroy(ctx)
-    return result
+    pct = lambda x, q: float(np.percentile(x, q)) if x else None
+    return {"streams": len(scs), "requests": len(arrivals), "served_frames_per_s": len(arrivals) / wall, "served_wall_s": wall,
+            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+            "latency_512_gated_ms": {"p50": pct(lat512, 50), "p99": pct(lat512, 99)} if lat512 else None,
+            "batches": st["batches"], "resident_gb": st["resident_bytes"] / 2 ** 30,
+            "per_launch_frames_per_s": len(arrivals) / per_launch_s, "per_launch_s": per_launch_s,
+            "fifo_per_launch": {"frames_per_s": len(arrivals) / fifo_wall,
+                                "latency_ms": {"p50": pct(fifo_lat, 50), "p99": pct(fifo_lat, 99)}}}
+
+
+def _poisson(rng, rate, seconds, pick):
+    t, arrivals = 0.0, []
+    while t < seconds:
+        t += rng.exponential(1.0 / rate)
+        arrivals.append((t, pick()))
+    return arrivals
+
+
+def run_served(args, seconds=1.5, rate=240.0, seed=4):
+    """Served form: 8 dynamic streams (6 gated like the dynamic workload at 256..1024 px, 2 transient
+    confocal 256x256 x 512 bins), Poisson arrivals at `rate` requests/s for `seconds`, continuous
+    batching by tof_server_step; against the same requests rendered one launch each."""
+    from paper_2605_11536_gb300 import scenes
+    rng = np.random.default_rng(seed)
+    gated_res = [256, 362, 512, 512, 724, 1024]
+    nfr = 32
+    scs = [scenes.heightfield_spheres(W=r, H=r, frames=nfr, seed=20 + k) for k, r in enumerate(gated_res)]
+    for k in range(2):
+        c = scenes.confocal_nlos(W=256, H=256, frames=nfr, B=512, seed=30 + k)
+        c.bins = (1.35, 0.002, 512)
+        scs.append(c)
+    # 70 % gated requests spread over the gated streams, 30 % over the transient ones
+    arrivals = _poisson(rng, rate, seconds, lambda: int(rng.integers(0, 6)) if rng.uniform() < 0.7 else 6 + int(rng.integers(0, 2)))
+    r = _serve_scenario(scs, arrivals, nfr)
+    r.update({"arrival_rate": rate, "arrival_seconds": seconds,
+              "mix": "6 gated streams (256, 362, 512, 512, 724, 1024 px) + 2 transient 256x256x512, 70/30 gated/transient "
+                     "requests"})
+    return r
+
+
+def run_served_gated(args, seconds=1.5, rate=120.0, seed=5):
+    """Served 512x512 gated frames: 8 dynamic streams like the dynamic workload (seeds 40..47), Poisson
+    arrivals at `rate` requests/s, which one GB300 sustains; latency and throughput served against
+    one launch per request."""
+    from paper_2605_11536_gb300 import scenes
+    rng = np.random.default_rng(seed)
+    nfr = 32
+    scs = [scenes.heightfield_spheres(W=512, H=512, frames=nfr, seed=40 + k) for k in range(8)]
+    arrivals = _poisson(rng, rate, seconds, lambda: int(rng.integers(0, 8)))
+    r = _serve_scenario(scs, arrivals, nfr)
+    r.update({"arrival_rate": rate, "arrival_seconds": seconds, "mix": "8 gated 512x512 streams"})
+    return r
 
 
 def cpu_baseline(args, crop=None, frames=3):
@@ -538,6 +666,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-transient", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -596,8 +725,9 @@ def main():
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 12 * 4 * r["nobj"],
                     "d2h_bytes_per_step": 4 * r["npix"]},
             # per frame: LBVH (xform, bounds, morton, 4 x 3 radix-sort, karras, refit = 17), gbuffer,
-            # initial, 5 temporal-pass and 5 spatial-pass kernels
-            "gpu_launches": 29 * K,
+            # initial, 8 temporal-pass and 8 spatial-pass kernels (slots, units, forward shifts,
+            # visibility, inverse-task emission, inverse shifts, visibility, merge)
+            "gpu_launches": 35 * K,
             "roofline": roof,
             "clocks": r["clocks"],
             "quality": r["quality"],
@@ -608,6 +738,16 @@ def main():
             "shifts_per_frame": {"spatial_forward": pf["spatial_fwd_calls"], "spatial_inverse": pf["spatial_inv_calls"],
                                  "all_forward": pf["shift_calls"], "all_inverse": pf["inv_calls"]},
             "wall_s": r["wall"]}
+    if not args.no_quality:
+        try:
+            line["quality_rough_variant"] = run_quality_rough(args)
+        except Exception as e:
+            line["quality_rough_variant"] = {"error": str(e)[:300]}
+    if not args.no_transient:
+        try:
+            line["transient"] = run_transient(args)
+        except Exception as e:
+            line["transient"] = {"error": str(e)[:300]}
     if not args.no_batch:
         try:
             line["batched"] = run_batched(args)
@@ -618,6 +758,10 @@ def main():
             line["served"] = run_served(args)
         except Exception as e:
             line["served"] = {"error": str(e)[:300]}
+        try:
+            line["served_gated_512"] = run_served_gated(args)
+        except Exception as e:
+            line["served_gated_512"] = {"error": str(e)[:300]}
     if not args.no_cpu:
         try:
             line["cpu_baseline"] = cpu_baseline(args)

@@ -205,6 +205,42 @@ typedef struct {
  * Scratch for every view is allocated before the graph is captured (first use of a view). */
 tof_status tof_render_batch(tof_ctx* ctx, const tof_job* jobs, uint32_t n, void* stream);
 
+/* Launch shapes and reservoir layout of a view (the batched form's per-instance-class tuning).
+ * None of them changes a result: every pixel's random numbers are keyed by the pixel, and the
+ * merges read their inputs by index, so a frame renders to the same bits under every tuning.
+ *   tile_w x tile_h: pixel tile of the per-pixel kernels (G-buffer, initial candidates), one thread
+ *     per pixel; tile_w a power of two in [4, 32], tile_w * tile_h = 64 or 128.
+ *   packet: blocks of 128 threads per SM that pull shift and visibility tasks in the persistent
+ *     reuse kernels (the width of the task packets in flight per SM), 1..8; 0 = as many as fit.
+ *     Fewer leave room for other instances of a batch to run beside this one.
+ *   layout: TOF_LAYOUT_SOA (six 16-byte planes, the default) or TOF_LAYOUT_AOS (each reservoir's
+ *     96 bytes contiguous). */
+#define TOF_LAYOUT_SOA 0
+#define TOF_LAYOUT_AOS 1
+typedef struct {
+    int32_t tile_w, tile_h;
+    int32_t packet;
+    int32_t layout;
+} tof_tuning;
+
+/* Set / read a view's tuning.  Changing the layout forgets the view's history (the next frame
+ * renders without temporal reuse); the other fields take effect at the next frame.  TOF_EINVAL for
+ * out-of-range fields. */
+tof_status tof_view_set_tuning(tof_ctx* ctx, tof_view view, const tof_tuning* t);
+tof_status tof_view_get_tuning(tof_ctx* ctx, tof_view view, tof_tuning* out);
+
+/* Autotuner for batched rendering.  Groups the jobs into instance classes (gated or transient with
+ * its bin count, and the pixel count: below 128^2, 256^2, 512^2, or above) and chooses each class's
+ * tuning by coordinate descent -- tiles 8x8, 32x4, 8x16 against the default 16x8, then packets 8,
+ * 4, 2, then the AoS layout, each kept only if it makes the whole batch faster -- with classes of
+ * more pixels first.  Every candidate is timed on the whole batch (tof_render_batch, `frames`
+ * consecutive frames, the first untimed), rendered on scratch views of the jobs' scenes and sizes
+ * that the call creates and destroys, so the jobs' own views keep their history (unless their
+ * layout changes) and the scratch views take as much device memory again while it runs.  The
+ * scenes must have been built.  The chosen tunings are set on the jobs' views and, if out is not
+ * NULL, written to out[i].  Synchronises `stream`; not for use during stream capture. */
+tof_status tof_autotune(tof_ctx* ctx, const tof_job* jobs, uint32_t n, int32_t frames, void* stream, tof_tuning* out);
+
 /* Served form (configs[4]): a request scheduler over several dynamic streams.
  *   A stream is a scene plus a fixed sensor resolution (and bin count for transient streams); its
  *   view -- reservoirs, G-buffers, confidences -- is created on first admission and stays resident,

@@ -8,6 +8,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -16,8 +18,8 @@
 #include "tof_internal.h"
 
 namespace tof {
-cudaError_t launch_gbuffer(const GbufArgs& a, cudaStream_t s);
-cudaError_t launch_initial(const InitArgs& a, int* err, cudaStream_t s);
+cudaError_t launch_gbuffer(const GbufArgs& a, int tile_h, cudaStream_t s);
+cudaError_t launch_initial(const InitArgs& a, int tile_h, int* err, cudaStream_t s);
 cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, int vis_blocks,
                               cudaEvent_t* ev, cudaStream_t s);
 cudaError_t reuse_persist_blocks(int* out, int* vis_out);
@@ -67,11 +69,14 @@ struct ResH {
     float4* planes = nullptr;
     float* M = nullptr;
     uint32_t* occ = nullptr;
-    size_t stride = 0;
+    size_t entries = 0;
+    int layout = TOF_LAYOUT_SOA;
     int words = 1;
     ResDev dev() const {
         ResDev r;
-        r.planes = planes; r.stride = stride; r.M = M; r.occ = occ; r.words = words;
+        r.planes = planes; r.M = M; r.occ = occ; r.words = words;
+        r.stride = layout == TOF_LAYOUT_AOS ? 1 : entries;
+        r.estride = layout == TOF_LAYOUT_AOS ? 6 : 1;
         return r;
     }
 };
@@ -99,6 +104,7 @@ struct ViewH {
     std::vector<cudaEvent_t> kev;   // 5 events per timed spatial launch group
     size_t kev_used = 0;
     void* wave_ptrs[12] = {nullptr};
+    tof_tuning tune = {16, 8, 0, TOF_LAYOUT_SOA};   // launch shapes and reservoir layout (autotuner)
 };
 
 }  // namespace
@@ -114,8 +120,9 @@ struct tof_ctx {
     uint32_t version_counter = 0;
     int* d_err = nullptr;
     float* d_scratch = nullptr;  // laser spot of plain PT renders
-    int persist_blocks = 0;      // resident blocks of the persistent reuse kernels
-    int vis_blocks = 0;          // resident blocks of the visibility kernel
+    int persist_blocks = 0;      // resident blocks of the persistent reuse kernels (all SMs)
+    int vis_blocks = 0;          // resident blocks of the visibility kernel (all SMs)
+    int sms = 0;                 // streaming multiprocessors
     // batched rendering: stream pool, fork / join events, and the instantiated graph
     std::vector<cudaStream_t> pool;
     std::vector<cudaEvent_t> join;
@@ -452,9 +459,9 @@ tof_status tof_view_create(tof_ctx* c, tof_scene scene, int32_t W, int32_t H, in
     }
     for (int k = 0; k < 3; ++k) {
         ResH& R = V.res[k];
-        R.stride = npix * Bn;
+        R.entries = npix * Bn;
         R.words = words;
-        TRY(dalloc(c, &R.planes, sizeof(float4) * 6 * R.stride, "reservoirs"));
+        TRY(dalloc(c, &R.planes, sizeof(float4) * 6 * R.entries, "reservoirs"));
         TRY(dalloc(c, &R.M, sizeof(float) * npix, "confidence"));
         TRY(dalloc(c, &R.occ, sizeof(uint32_t) * npix * words, "occupancy"));
         CK(cudaMemset(R.occ, 0, sizeof(uint32_t) * npix * words));
@@ -504,6 +511,14 @@ tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[8]) {
 
 static bool g_no_marks = false;   // set while a batch is being captured (no profiling events)
 
+// resident-block counts of the persistent reuse kernels, once per context
+static tof_status persist_init(tof_ctx* c) {
+    if (c->persist_blocks) return TOF_OK;
+    CK(reuse_persist_blocks(&c->persist_blocks, &c->vis_blocks));
+    CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
+    return TOF_OK;
+}
+
 // (re)allocate the view's wavefront scratch for S slots per pixel and cap merge units
 static tof_status ensure_wave(tof_ctx* c, ViewH& V, int S, int cap) {
     if (V.wave_slots >= S && V.wave_cap >= cap) return TOF_OK;
@@ -547,7 +562,7 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
     size_t cap = npix * Bn < kMaxUnits ? npix * Bn : kMaxUnits;
     if (cap < npix && V.B == 0) cap = npix;
     if (!fixed) TRY(ensure_wave(c, V, S, (int)cap));
-    if (!c->persist_blocks) CK(reuse_persist_blocks(&c->persist_blocks, &c->vis_blocks));
+    TRY(persist_init(c));
     WaveDev w = fixed ? *fixed : V.wave;
     w.slots = S;
     if (!fixed) w.cap_units = V.wave_cap;
@@ -565,7 +580,12 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
             ev = &V.kev[V.kev_used];
             V.kev_used += 5;
         }
-        CK(launch_reuse_wave(ra, w, (int)p0, (int)p1, c->persist_blocks, c->vis_blocks, ev, s));
+        int pb = c->persist_blocks, vb = c->vis_blocks;
+        if (V.tune.packet > 0) {
+            pb = std::min(pb, c->sms * V.tune.packet);
+            vb = std::min(vb, c->sms * V.tune.packet);
+        }
+        CK(launch_reuse_wave(ra, w, (int)p0, (int)p1, pb, vb, ev, s));
     }
     return TOF_OK;
 }
@@ -605,8 +625,8 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     mark(V, 0, s);
     if (emitter->type == TOF_EMIT_LASER) CK(launch_laser(F.g, v3f(emitter->pos), v3f(emitter->dir), emitter->power, V.laser[fc], s));
     GbufArgs ga;
-    ga.F = F; ga.gb = V.gb[fc]; ga.P = P;
-    CK(launch_gbuffer(ga, s));
+    ga.F = F; ga.gb = V.gb[fc]; ga.P = P; ga.tile_w = V.tune.tile_w;
+    CK(launch_gbuffer(ga, V.tune.tile_h, s));
     mark(V, 1, s);
     V.ran[0] = true;
 
@@ -624,7 +644,8 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     InitArgs ia;
     ia.F = F; ia.dst = V.res[out_of(stage)].dev(); ia.P = P;
     ia.out = (stage == stages - 1 && B == 0) ? out : nullptr;
-    CK(launch_initial(ia, c->d_err, s));
+    ia.tile_w = V.tune.tile_w;
+    CK(launch_initial(ia, V.tune.tile_h, c->d_err, s));
     mark(V, 2, s);
     V.ran[1] = true;
     int src = out_of(stage);
@@ -779,7 +800,7 @@ tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* s
         int S = 1 + J.params.n_spatial > 2 ? 1 + J.params.n_spatial : 2;
         TRY(ensure_wave(c, V, S, (int)cap));
     }
-    if (!c->persist_blocks) CK(reuse_persist_blocks(&c->persist_blocks, &c->vis_blocks));
+    TRY(persist_init(c));
     const uint32_t P = n < 16 ? n : 16;
     while (c->pool.size() < P) {
         cudaStream_t q;
@@ -791,6 +812,25 @@ tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* s
     }
     if (!c->fork) CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     if (!c->capture) CK(cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+    // stream of each job: longest estimated work first onto the least loaded stream, so that no
+    // branch of the graph carries several of the largest instances (the critical path)
+    std::vector<double> cost(n), load(P, 0.0);
+    std::vector<uint32_t> order(n), branch(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        const tof_job& J = jobs[i];
+        const ViewH& V = c->views[J.view];
+        const double passes = 1.0 + (J.params.temporal ? 1.0 : 0.0) + J.params.n_spatial_iters * (1.0 + J.params.n_spatial);
+        cost[i] = (double)V.W * V.H * J.params.depth * (J.params.n_cand + passes) * (J.transient ? 8.0 : 1.0);
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+    for (uint32_t i : order) {
+        uint32_t best = 0;
+        for (uint32_t p = 1; p < P; ++p)
+            if (load[p] < load[best]) best = p;
+        branch[i] = best;
+        load[best] += cost[i];
+    }
     // capture: fork onto the pool, one branch per stream, join
     c->in_batch = true;
     g_no_marks = true;
@@ -800,9 +840,10 @@ tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* s
     if (e == cudaSuccess) {
         cudaEventRecord(c->fork, c->capture);
         for (uint32_t p = 0; p < P; ++p) cudaStreamWaitEvent(c->pool[p], c->fork, 0);
-        for (uint32_t i = 0; i < n && st == TOF_OK; ++i) {
+        for (uint32_t k = 0; k < n && st == TOF_OK; ++k) {
+            const uint32_t i = order[k];
             const tof_job& J = jobs[i];
-            cudaStream_t q = c->pool[i % P];
+            cudaStream_t q = c->pool[branch[i]];
             if (J.transient)
                 st = render(c, J.scene, J.view, &J.sensor, &J.emitter, J.bins.t0, J.bins.width, J.bins.B, &J.params, J.seed,
                             J.frame, J.out_dev, q);
@@ -848,6 +889,162 @@ tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* s
     cudaGraphDestroy(graph);
     CK(cudaGraphLaunch(c->batch_exec, (cudaStream_t)stream));
     for (uint32_t i = 0; i < n; ++i) c->views[jobs[i].view].last_stream = (cudaStream_t)stream;
+    return TOF_OK;
+}
+
+static tof_status check_tuning(tof_ctx* c, const tof_tuning* t) {
+    if (!t) return fail(c, TOF_EINVAL, "tuning is NULL");
+    const int tw = t->tile_w, th = t->tile_h;
+    if (tw < 4 || tw > 32 || (tw & (tw - 1)) || th < 1 || (tw * th != 64 && tw * th != 128))
+        return fail(c, TOF_EINVAL, "tile %d x %d: tile_w must be a power of two in [4, 32] and tile_w * tile_h 64 or 128",
+                    tw, th);
+    if (t->packet < 0 || t->packet > 8) return fail(c, TOF_EINVAL, "packet %d outside [0, 8]", t->packet);
+    if (t->layout != TOF_LAYOUT_SOA && t->layout != TOF_LAYOUT_AOS) return fail(c, TOF_EINVAL, "unknown layout %d", t->layout);
+    return TOF_OK;
+}
+
+tof_status tof_view_set_tuning(tof_ctx* c, tof_view id, const tof_tuning* t) {
+    if (!c) return TOF_EINVAL;
+    if (id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return fail(c, TOF_EINVAL, "bad view handle");
+    TRY(check_tuning(c, t));
+    ViewH& V = c->views[id];
+    if (t->layout != V.tune.layout) {
+        // the stored reservoirs are in the old layout: forget them
+        V.has_prev = false;
+        V.prev_final = -1;
+        for (int k = 0; k < 3; ++k) V.res[k].layout = t->layout;
+    }
+    V.tune = *t;
+    return TOF_OK;
+}
+
+tof_status tof_view_get_tuning(tof_ctx* c, tof_view id, tof_tuning* out) {
+    if (!c) return TOF_EINVAL;
+    if (!out || id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return fail(c, TOF_EINVAL, "bad view handle");
+    *out = c->views[id].tune;
+    return TOF_OK;
+}
+
+// instance class of a job for the autotuner: transient bins (0 = gated) and a pixel-count bucket
+static std::pair<int, int> tune_class(const ViewH& V) {
+    const long long np = (long long)V.W * V.H;
+    int bucket = np < 128 * 128 ? 0 : np < 256 * 256 ? 1 : np < 512 * 512 ? 2 : 3;
+    return std::make_pair(V.B, bucket);
+}
+
+tof_status tof_autotune(tof_ctx* c, const tof_job* jobs, uint32_t n, int32_t frames, void* stream, tof_tuning* out) {
+    if (!c) return TOF_EINVAL;
+    if (!jobs || n == 0) return fail(c, TOF_EINVAL, "no jobs");
+    if (frames < 2 || frames > 64) return fail(c, TOF_EINVAL, "frames %d outside [2, 64]", frames);
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::map<std::pair<int, int>, std::vector<uint32_t>> classes;
+    for (uint32_t i = 0; i < n; ++i) {
+        const tof_job& J = jobs[i];
+        if (J.view < 0 || J.view >= (int)c->views.size() || !c->views[J.view].alive)
+            return fail(c, TOF_EINVAL, "job %u: bad view handle", i);
+        if (J.scene < 0 || J.scene >= (int)c->scenes.size() || !c->scenes[J.scene].alive || !c->scenes[J.scene].built)
+            return fail(c, TOF_EINVAL, "job %u: bad or unbuilt scene", i);
+        if (c->views[J.view].scene != J.scene) return fail(c, TOF_EINVAL, "job %u: view and scene differ", i);
+        classes[tune_class(c->views[J.view])].push_back(i);
+    }
+    // the jobs on scratch views (same scene, size and bins) with scratch outputs: the candidates are
+    // timed on the whole batch, where instances of different classes run beside each other
+    std::vector<tof_job> sj(jobs, jobs + n);
+    std::vector<tof_view> sv;
+    std::vector<float*> so;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    tof_status st = TOF_OK;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(s);
+        for (float* p : so) dfree(c, p);
+        for (tof_view v : sv) tof_view_destroy(c, v);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    for (uint32_t i = 0; i < n && st == TOF_OK; ++i) {
+        const ViewH& V = c->views[jobs[i].view];
+        tof_view v = -1;
+        st = tof_view_create(c, jobs[i].scene, V.W, V.H, V.B, &v);
+        if (st != TOF_OK) break;
+        sv.push_back(v);
+        float* o = nullptr;
+        st = dalloc(c, &o, sizeof(float) * (size_t)V.W * V.H * (V.B > 0 ? V.B : 1), "autotune output");
+        if (st != TOF_OK) break;
+        so.push_back(o);
+        sj[i].view = v;
+        sj[i].out_dev = o;
+    }
+    if (st == TOF_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = fail(c, TOF_ECUDA, "cudaEventCreate failed");
+    if (st != TOF_OK) { cleanup(); return st; }
+    std::map<std::pair<int, int>, tof_tuning> cur;
+    for (auto& kv : classes) cur[kv.first] = tof_tuning{16, 8, 0, TOF_LAYOUT_SOA};
+    // `frames` consecutive batches under the current tunings, the first untimed
+    auto time_batch = [&](float* ms) -> tof_status {
+        for (auto& kv : classes)
+            for (uint32_t i : kv.second) {
+                TRY(tof_view_set_tuning(c, sj[i].view, &cur[kv.first]));
+                TRY(tof_reservoirs_reset(c, sj[i].view));
+            }
+        for (int f = 0; f < frames; ++f) {
+            for (uint32_t i = 0; i < n; ++i) sj[i].frame = jobs[i].frame + (uint32_t)f;
+            if (f == 1) CK(cudaEventRecord(e0, s));
+            TRY(tof_render_batch(c, sj.data(), n, stream));
+        }
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(ms, e0, e1));
+        return TOF_OK;
+    };
+    float best_ms = 0.f;
+    st = time_batch(&best_ms);
+    // classes with the most pixels first; per class tiles, then packets, then the layout
+    std::vector<std::pair<long long, std::pair<int, int>>> by_size;
+    for (auto& kv : classes) {
+        long long px = 0;
+        for (uint32_t i : kv.second) px += (long long)c->views[jobs[i].view].W * c->views[jobs[i].view].H;
+        by_size.push_back(std::make_pair(px, kv.first));
+    }
+    std::sort(by_size.begin(), by_size.end(), [](const std::pair<long long, std::pair<int, int>>& a,
+                                                 const std::pair<long long, std::pair<int, int>>& b) { return a.first > b.first; });
+    const int tiles[3][2] = {{8, 8}, {32, 4}, {8, 16}};
+    const int packets[3] = {8, 4, 2};
+    for (auto& cl : by_size) {
+        const std::pair<int, int> key = cl.second;
+        auto trial = [&](const tof_tuning& t) -> tof_status {
+            const tof_tuning keep = cur[key];
+            cur[key] = t;
+            float ms = 0.f;
+            TRY(time_batch(&ms));
+            if (ms < best_ms) best_ms = ms;
+            else cur[key] = keep;
+            return TOF_OK;
+        };
+        for (int k = 0; k < 3 && st == TOF_OK; ++k) {
+            tof_tuning t = cur[key];
+            t.tile_w = tiles[k][0]; t.tile_h = tiles[k][1];
+            st = trial(t);
+        }
+        for (int k = 0; k < 3 && st == TOF_OK; ++k) {
+            tof_tuning t = cur[key];
+            t.packet = packets[k];
+            st = trial(t);
+        }
+        if (st == TOF_OK) {
+            tof_tuning t = cur[key];
+            t.layout = TOF_LAYOUT_AOS;
+            st = trial(t);
+        }
+        if (st != TOF_OK) break;
+    }
+    cleanup();
+    if (st != TOF_OK) return st;
+    for (auto& kv : classes)
+        for (uint32_t i : kv.second) {
+            TRY(tof_view_set_tuning(c, jobs[i].view, &cur[kv.first]));
+            if (out) out[i] = cur[kv.first];
+        }
     return TOF_OK;
 }
 

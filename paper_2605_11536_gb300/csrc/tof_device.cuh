@@ -500,6 +500,7 @@ static __device__ __forceinline__ float Gterm(const Surf& a, const Surf& b) {
 // reservoir records: decoded form and the 6-plane float4 encoding
 //   P0 (W, phat, tau, Lsuf)   P1 (key_px, key_frame, meta, pdf_pre)   P2 (xprev.xyz, p_tri)
 //   P3 (p_b1, p_b2, s0_tri, s0_b1)   P4 (s0_b2, s1_tri, s1_b1, s1_b2)   P5 (s2_tri, s2_b1, s2_b2, 0)
+//   (six planes, or six consecutive words per entry: see ResDev)
 //   meta: tree [0,8) | k [8,11) | r [11,14) | ns [14,16) | class of x_1..x_4, 2 bits each [16,24)
 // (Sec. 5: the reservoir stores the vertex after the reconnection vertex; the reconnection
 //  radiance Lsuf is attached to it)
@@ -520,37 +521,37 @@ static __device__ __forceinline__ int rec_r(const Rec& r) { return (int)((r.meta
 static __device__ __forceinline__ int rec_ns(const Rec& r) { return (int)((r.meta >> 14) & 3u); }
 static __device__ __forceinline__ int rec_cls(const Rec& r, int j) { return (int)((r.meta >> (16 + 2 * (j - 1))) & 3u); }
 
+// word k of entry idx (SoA or AoS, see ResDev)
+static __device__ __forceinline__ float4* res_at(const ResDev& R, int k, size_t idx) {
+    return R.planes + (size_t)k * R.stride + idx * R.estride;
+}
 static __device__ __forceinline__ void rec_store(const ResDev& R, size_t idx, const Rec& r) {
-    float4* P = R.planes;
-    const size_t s = R.stride;
-    P[idx] = make_float4(r.W, r.phat, r.tau, r.Lsuf);
-    P[s + idx] = make_float4(__uint_as_float(r.key_px), __uint_as_float(r.key_frame), __uint_as_float(r.meta), r.pdf_pre);
+    *res_at(R, 0, idx) = make_float4(r.W, r.phat, r.tau, r.Lsuf);
+    *res_at(R, 1, idx) = make_float4(__uint_as_float(r.key_px), __uint_as_float(r.key_frame), __uint_as_float(r.meta), r.pdf_pre);
     if (rec_r(r) >= 2) {
-        P[2 * s + idx] = make_float4(r.xprev.x, r.xprev.y, r.xprev.z, __int_as_float(r.p_tri));
-        P[3 * s + idx] = make_float4(r.p_b1, r.p_b2, __int_as_float(r.s_tri[0]), r.s_b1[0]);
+        *res_at(R, 2, idx) = make_float4(r.xprev.x, r.xprev.y, r.xprev.z, __int_as_float(r.p_tri));
+        *res_at(R, 3, idx) = make_float4(r.p_b1, r.p_b2, __int_as_float(r.s_tri[0]), r.s_b1[0]);
         int ns = rec_ns(r);
-        if (ns >= 2) P[4 * s + idx] = make_float4(r.s_b2[0], __int_as_float(r.s_tri[1]), r.s_b1[1], r.s_b2[1]);
-        else if (ns == 1) P[4 * s + idx] = make_float4(r.s_b2[0], 0.f, 0.f, 0.f);
-        if (ns >= 3) P[5 * s + idx] = make_float4(__int_as_float(r.s_tri[2]), r.s_b1[2], r.s_b2[2], 0.f);
+        if (ns >= 2) *res_at(R, 4, idx) = make_float4(r.s_b2[0], __int_as_float(r.s_tri[1]), r.s_b1[1], r.s_b2[1]);
+        else if (ns == 1) *res_at(R, 4, idx) = make_float4(r.s_b2[0], 0.f, 0.f, 0.f);
+        if (ns >= 3) *res_at(R, 5, idx) = make_float4(__int_as_float(r.s_tri[2]), r.s_b1[2], r.s_b2[2], 0.f);
     }
 }
 static __device__ __forceinline__ void rec_load(const ResDev& R, size_t idx, Rec& r) {
-    const float4* P = R.planes;
-    const size_t s = R.stride;
-    float4 a = P[idx], b = P[s + idx];
+    float4 a = *res_at(R, 0, idx), b = *res_at(R, 1, idx);
     r.W = a.x; r.phat = a.y; r.tau = a.z; r.Lsuf = a.w;
     r.key_px = __float_as_uint(b.x); r.key_frame = __float_as_uint(b.y); r.meta = __float_as_uint(b.z); r.pdf_pre = b.w;
     if (rec_r(r) >= 2) {
-        float4 c = P[2 * s + idx], d = P[3 * s + idx];
+        float4 c = *res_at(R, 2, idx), d = *res_at(R, 3, idx);
         r.xprev = f3(c.x, c.y, c.z); r.p_tri = __float_as_int(c.w);
         r.p_b1 = d.x; r.p_b2 = d.y; r.s_tri[0] = __float_as_int(d.z); r.s_b1[0] = d.w;
         int ns = rec_ns(r);
         if (ns >= 1) {
-            float4 e = P[4 * s + idx];
+            float4 e = *res_at(R, 4, idx);
             r.s_b2[0] = e.x; r.s_tri[1] = __float_as_int(e.y); r.s_b1[1] = e.z; r.s_b2[1] = e.w;
         }
         if (ns >= 3) {
-            float4 f = P[5 * s + idx];
+            float4 f = *res_at(R, 5, idx);
             r.s_tri[2] = __float_as_int(f.x); r.s_b1[2] = f.y; r.s_b2[2] = f.z;
         }
     }

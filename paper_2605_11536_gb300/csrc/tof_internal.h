@@ -61,11 +61,14 @@ struct FrameDev {
     const float4* gb;        // (tri bits, b1, b2, t) per pixel
 };
 
-// reservoir buffer: 6 planes of float4 with `stride` entries each, per-pixel confidence M and
-// one occupancy bit per (pixel, bin)
+// reservoir buffer: 6 float4 words per entry, per-pixel confidence M and one occupancy bit per
+// (pixel, bin).  Word k of entry i sits at planes[k * stride + i * estride]: structure of arrays
+// (stride = entries, estride = 1; each word a plane read with 16-byte vectors) or array of
+// structures (stride = 1, estride = 6; an entry's 96 bytes contiguous)
 struct ResDev {
-    float4* planes;          // plane k at planes + k * stride
-    size_t stride;           // W*H*max(B,1)
+    float4* planes;
+    size_t stride;           // SoA: W*H*max(B,1); AoS: 1
+    size_t estride;          // SoA: 1; AoS: 6
     float* M;                // W*H
     uint32_t* occ;           // W*H*words, words = ceil(max(B,1)/32)
     int words;
@@ -90,6 +93,7 @@ struct GbufArgs {
     FrameDev F;
     float4* gb;
     ParamsDev P;
+    int tile_w;              // pixel tile width (a power of two); tile height = threads / tile_w
 };
 
 struct InitArgs {
@@ -97,6 +101,7 @@ struct InitArgs {
     ResDev dst;
     ParamsDev P;
     float* out;              // gated image if this is the last stage (else null)
+    int tile_w;
 };
 
 struct ReuseArgs {

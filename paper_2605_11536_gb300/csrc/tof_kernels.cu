@@ -66,16 +66,21 @@ __device__ __forceinline__ void stats_flush(StatsDev* S, const ShiftStats& s) {
 }
 
 __device__ __forceinline__ void store_tail(const ResDev& R, size_t idx, const Rec& r) {
-    float4* Pl = R.planes;
-    const size_t s = R.stride;
-    Pl[s + idx] = make_float4(__uint_as_float(r.key_px), __uint_as_float(r.key_frame), __uint_as_float(r.meta), r.pdf_pre);
+    *res_at(R, 1, idx) = make_float4(__uint_as_float(r.key_px), __uint_as_float(r.key_frame), __uint_as_float(r.meta), r.pdf_pre);
     if (rec_r(r) >= 2) {
-        Pl[2 * s + idx] = make_float4(r.xprev.x, r.xprev.y, r.xprev.z, __int_as_float(r.p_tri));
-        Pl[3 * s + idx] = make_float4(r.p_b1, r.p_b2, __int_as_float(r.s_tri[0]), r.s_b1[0]);
+        *res_at(R, 2, idx) = make_float4(r.xprev.x, r.xprev.y, r.xprev.z, __int_as_float(r.p_tri));
+        *res_at(R, 3, idx) = make_float4(r.p_b1, r.p_b2, __int_as_float(r.s_tri[0]), r.s_b1[0]);
         int ns = rec_ns(r);
-        if (ns >= 1) Pl[4 * s + idx] = make_float4(r.s_b2[0], __int_as_float(r.s_tri[1]), r.s_b1[1], r.s_b2[1]);
-        if (ns >= 3) Pl[5 * s + idx] = make_float4(__int_as_float(r.s_tri[2]), r.s_b1[2], r.s_b2[2], 0.f);
+        if (ns >= 1) *res_at(R, 4, idx) = make_float4(r.s_b2[0], __int_as_float(r.s_tri[1]), r.s_b1[1], r.s_b2[1]);
+        if (ns >= 3) *res_at(R, 5, idx) = make_float4(__int_as_float(r.s_tri[2]), r.s_b1[2], r.s_b2[2], 0.f);
     }
+}
+
+// pixel of this thread in a tile_w x (blockDim.x / tile_w) tile (tile_w a power of two)
+__device__ __forceinline__ void tile_pixel(int tile_w, int& ix, int& iy) {
+    const int sh = __ffs(tile_w) - 1;
+    ix = blockIdx.x * tile_w + (int)(threadIdx.x & (unsigned)(tile_w - 1));
+    iy = blockIdx.y * (int)(blockDim.x >> sh) + (int)(threadIdx.x >> sh);
 }
 
 // --------------------------------------------------------------------------------------------
@@ -83,7 +88,8 @@ __device__ __forceinline__ void store_tail(const ResDev& R, size_t idx, const Re
 // --------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) gbuffer_kernel(const __grid_constant__ GbufArgs a) {
     const FrameDev& F = a.F;
-    int ix = blockIdx.x * 16 + (threadIdx.x & 15), iy = blockIdx.y * 8 + (threadIdx.x >> 4);
+    int ix, iy;
+    tile_pixel(a.tile_w, ix, iy);
     if (ix >= F.W || iy >= F.H) return;
     int pix = iy * F.W + ix;
     uint4 u = philox((uint32_t)pix, F.frame, 0u, P_JITTER, a.P.seed);
@@ -143,7 +149,8 @@ struct InitSink {
 
 __global__ void __launch_bounds__(128) initial_kernel(const __grid_constant__ InitArgs a, int* err) {
     const FrameDev& F = a.F;
-    int ix = blockIdx.x * 16 + (threadIdx.x & 15), iy = blockIdx.y * 8 + (threadIdx.x >> 4);
+    int ix, iy;
+    tile_pixel(a.tile_w, ix, iy);
     if (ix >= F.W || iy >= F.H) return;
     const int pix = iy * F.W + ix;
     const ParamsDev& P = a.P;
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(128) initial_kernel(const __grid_constant__ In
         if (!(sink.phat[e] > 0.f)) continue;
         float W = sink.S[e] / sink.phat[e];
         size_t idx = (size_t)pix * Bn + sink.bin[e];
-        a.dst.planes[idx] = make_float4(W, sink.phat[e], sink.tau[e], sink.Lsuf[e]);
+        *res_at(a.dst, 0, idx) = make_float4(W, sink.phat[e], sink.tau[e], sink.Lsuf[e]);
         occ[sink.bin[e] >> 5] |= 1u << (sink.bin[e] & 31);
         outv = sink.phat[e] * W;
     }
@@ -190,13 +197,12 @@ __global__ void __launch_bounds__(256) splat_kernel(const __grid_constant__ Spla
     const int pix = warp, B = a.B;
     const uint32_t* occ = a.src.occ + (size_t)pix * a.src.words;
     float* row = a.out + (size_t)pix * B;
-    const float4* P0 = a.src.planes + (size_t)pix * B;
     for (int w = 0; w < a.src.words; ++w) {
         uint32_t m = occ[w];
         int b = (w << 5) + lane;
         if (b >= B) break;
         float v = 0.f;
-        if ((m >> lane) & 1u) { float4 p = P0[b]; v = p.y * p.x; }
+        if ((m >> lane) & 1u) { float4 p = *res_at(a.src, 0, (size_t)pix * B + b); v = p.y * p.x; }
         row[b] = v;
     }
 }
@@ -270,13 +276,15 @@ __global__ void laser_kernel(GeomDev g, float3 o, float3 dir, float power, Light
 // host-side launchers
 // --------------------------------------------------------------------------------------------
 static inline dim3 pix_grid(int W, int H) { return dim3((W + 15) / 16, (H + 7) / 8); }
+static inline dim3 tile_grid(int W, int H, int tw, int th) { return dim3((W + tw - 1) / tw, (H + th - 1) / th); }
 
-cudaError_t launch_gbuffer(const GbufArgs& a, cudaStream_t s) {
-    gbuffer_kernel<<<pix_grid(a.F.W, a.F.H), 128, 0, s>>>(a);
+// tile_w x tile_h pixel tiles, tile_w a power of two in [4, 32], tile_w * tile_h = 64 or 128
+cudaError_t launch_gbuffer(const GbufArgs& a, int tile_h, cudaStream_t s) {
+    gbuffer_kernel<<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_initial(const InitArgs& a, int* err, cudaStream_t s) {
-    initial_kernel<<<pix_grid(a.F.W, a.F.H), 128, 0, s>>>(a, err);
+cudaError_t launch_initial(const InitArgs& a, int tile_h, int* err, cudaStream_t s) {
+    initial_kernel<<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, err);
     return cudaGetLastError();
 }
 cudaError_t launch_splat(const SplatArgs& a, cudaStream_t s) {

@@ -77,7 +77,7 @@ __device__ __forceinline__ uint32_t reserve(uint32_t* counter, uint32_t n) {
 
 __device__ __forceinline__ void store_rec(float4* P, size_t stride, size_t idx, const Rec& r) {
     ResDev R;
-    R.planes = P; R.stride = stride;
+    R.planes = P; R.stride = stride; R.estride = 1;
     rec_store(R, idx, r);
 }
 
@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(128) reuse_units_kernel(const __grid_constant_
                 int bit = __ffs(c) - 1;
                 c &= c - 1;
                 size_t idx = (size_t)pix * Bn + (wd << 5) + bit;
-                for (int k = 0; k < 6; ++k) a.dst.planes[k * a.dst.stride + idx] = a.src.planes[k * a.src.stride + idx];
-                if (C.B == 0) { float4 p0v = a.src.planes[idx]; outv = p0v.y * p0v.x; }
+                for (int k = 0; k < 6; ++k) *res_at(a.dst, k, idx) = *res_at(a.src, k, idx);
+                if (C.B == 0) { float4 p0v = *res_at(a.src, 0, idx); outv = p0v.y * p0v.x; }
             }
         } else {
             docc[wd] = 0u;
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant
             rec_load(a.src, (size_t)pix * Bn + b, y);
         } else {
             ResDev R;
-            R.planes = w.yrec; R.stride = (size_t)w.cap_units * (S - 1);
+            R.planes = w.yrec; R.stride = (size_t)w.cap_units * (S - 1); R.estride = 1;
             rec_load(R, (size_t)u * (S - 1) + (s - 1), y);
         }
         int q = w.slot_pix[(size_t)pix * S + j];
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant_
             if (!occ_get(*R, q, b)) continue;
             const FrameDev* Fs = slot_frame(a, s);
             int Bs = Fs->B > 0 ? Fs->B : 1;
-            float4 p0 = R->planes[(size_t)q * Bs + b];
+            float4 p0 = *res_at(*R, 0, (size_t)q * Bs + b);
             ph[s] = p0.y; Wx[s] = p0.x;
             if (s == 0) { py[0] = p0.y; J[0] = 1.f; ok[0] = py[0] > 0.f; }
             else { py[s] = w.py[(size_t)u * S + s]; J[s] = w.jac[(size_t)u * S + s]; ok[s] = py[s] > 0.f; }
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant_
             if (sel == 0) rec_load(a.src, (size_t)pix * Bn + b, y);
             else {
                 ResDev R;
-                R.planes = w.yrec; R.stride = (size_t)w.cap_units * (S - 1);
+                R.planes = w.yrec; R.stride = (size_t)w.cap_units * (S - 1); R.estride = 1;
                 rec_load(R, (size_t)u * (S - 1) + (sel - 1), y);
             }
             y.W = Ssum / py[sel];

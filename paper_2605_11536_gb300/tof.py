@@ -54,11 +54,19 @@ class tof_job(C.Structure):
     pass
 
 
+class tof_tuning(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("packet", C.c_int32), ("layout", C.c_int32)]
+
+
+LAYOUT_SOA, LAYOUT_AOS = 0, 1
+
+
 EXPORTS = ["tof_create", "tof_destroy", "tof_last_error", "tof_device_bytes", "tof_scene_upload", "tof_scene_destroy",
            "tof_bvh_build", "tof_view_create", "tof_view_destroy", "tof_render_gated", "tof_render_transient",
            "tof_render_pt", "tof_reservoirs_reset", "tof_view_stats", "tof_view_profile", "tof_view_stage_ms",
            "tof_render_gated_noalloc", "tof_render_batch", "tof_server_create", "tof_server_destroy",
-           "tof_server_open_stream", "tof_server_submit", "tof_server_step", "tof_server_poll", "tof_server_stats"]
+           "tof_server_open_stream", "tof_server_submit", "tof_server_step", "tof_server_poll", "tof_server_stats",
+           "tof_view_set_tuning", "tof_view_get_tuning", "tof_autotune"]
 
 _vp, _fp, _u32p = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)
 
@@ -90,6 +98,9 @@ def _declare(L):
                                 C.POINTER(tof_bins), C.POINTER(tof_params), C.c_uint64, C.c_uint32, C.c_int32, _vp, _vp]
     L.tof_reservoirs_reset.argtypes = [_vp, C.c_int32]
     L.tof_render_batch.argtypes = [_vp, C.POINTER(tof_job), C.c_uint32, _vp]
+    L.tof_view_set_tuning.argtypes = [_vp, C.c_int32, C.POINTER(tof_tuning)]
+    L.tof_view_get_tuning.argtypes = [_vp, C.c_int32, C.POINTER(tof_tuning)]
+    L.tof_autotune.argtypes = [_vp, C.POINTER(tof_job), C.c_uint32, C.c_int32, _vp, C.POINTER(tof_tuning)]
     L.tof_server_create.argtypes = [_vp, C.c_uint64, C.POINTER(C.c_void_p)]
     L.tof_server_destroy.argtypes = [_vp]
     L.tof_server_open_stream.argtypes = [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
@@ -289,6 +300,25 @@ def job(scene, view, sensor_d, emitter_d, params_p, seed, frame, out_ptr, gate=N
 def tof_render_batch(ctx, jobs, stream: int = 0):
     arr = (tof_job * len(jobs))(*jobs)
     _check(ctx, lib().tof_render_batch(ctx, arr, len(jobs), C.c_void_p(stream)), "tof_render_batch")
+
+
+def tof_view_set_tuning(ctx, view: int, tile_w: int = 16, tile_h: int = 8, packet: int = 0, layout: int = LAYOUT_SOA):
+    t = tof_tuning(int(tile_w), int(tile_h), int(packet), int(layout))
+    _check(ctx, lib().tof_view_set_tuning(ctx, view, C.byref(t)), "tof_view_set_tuning")
+
+
+def tof_view_get_tuning(ctx, view: int) -> dict:
+    t = tof_tuning()
+    _check(ctx, lib().tof_view_get_tuning(ctx, view, C.byref(t)), "tof_view_get_tuning")
+    return dict(tile_w=t.tile_w, tile_h=t.tile_h, packet=t.packet, layout=t.layout)
+
+
+def tof_autotune(ctx, jobs, frames: int = 3, stream: int = 0):
+    """Tune every job's view (tof_autotune); returns each job's chosen tuning as a dict."""
+    arr = (tof_job * len(jobs))(*jobs)
+    out = (tof_tuning * len(jobs))()
+    _check(ctx, lib().tof_autotune(ctx, arr, len(jobs), int(frames), C.c_void_p(stream), out), "tof_autotune")
+    return [dict(tile_w=t.tile_w, tile_h=t.tile_h, packet=t.packet, layout=t.layout) for t in out]
 
 
 def tof_server_create(ctx, hbm_budget_bytes: int = 0):

@@ -17,7 +17,7 @@ def _declared():
 def test_header_and_binding_agree():
     from paper_2605_11536_gb300 import tof
     assert sorted(_declared()) == sorted(tof.EXPORTS)
-    assert len(tof.EXPORTS) == 25
+    assert len(tof.EXPORTS) == 28
 
 
 def test_library_builds_and_exports_every_symbol():
@@ -51,8 +51,9 @@ def test_struct_sizes_match_header():
     import subprocess
     import tempfile
     from paper_2605_11536_gb300 import tof
-    src = '#include <stdio.h>\n#include "tof.h"\nint main(){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(tof_material),' \
-          ' sizeof(tof_sensor), sizeof(tof_emitter), sizeof(tof_gate), sizeof(tof_bins), sizeof(tof_params), sizeof(tof_job));}\n'
+    src = '#include <stdio.h>\n#include "tof.h"\nint main(){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(tof_material),' \
+          ' sizeof(tof_sensor), sizeof(tof_emitter), sizeof(tof_gate), sizeof(tof_bins), sizeof(tof_params), sizeof(tof_job),' \
+          ' sizeof(tof_tuning));}\n'
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "p.c")
         open(c, "w").write(src)
@@ -60,4 +61,4 @@ def test_struct_sizes_match_header():
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         sizes = [int(x) for x in subprocess.check_output([exe]).split()]
     assert sizes == [C.sizeof(t) for t in (tof.tof_material, tof.tof_sensor, tof.tof_emitter, tof.tof_gate,
-                                             tof.tof_bins, tof.tof_params, tof.tof_job)]
+                                             tof.tof_bins, tof.tof_params, tof.tof_job, tof.tof_tuning)]

@@ -31,7 +31,10 @@ def _sensor(sc, f, W, H):
     return dict(sc.sensors[f], W=W, H=H)
 
 
-def _run(batched):
+def _run(batched, tune=None, chosen=None):
+    """Render the spec's jobs over two frames, batched or one launch per job.  tune: None (default
+    tuning), a dict of tof_view_set_tuning fields for every view, or "auto" (tof_autotune on the
+    first frame's jobs, chosen tunings appended to `chosen`)."""
     import torch
     from paper_2605_11536_gb300 import tof
     spec = _jobs_spec()
@@ -50,6 +53,8 @@ def _run(batched):
             p = scenes.Params(**vars(sc.params))
             p.depth, p.n_spatial, p.radius, p.temporal = depth, nsp, rad, temporal
             params.append(p)
+            if isinstance(tune, dict):
+                tof.tof_view_set_tuning(ctx, views[-1], **tune)
         for f in range(2):
             done = set()
             for sc, *_ in spec:
@@ -68,6 +73,13 @@ def _run(batched):
                 else:
                     tof.tof_render_gated(ctx, sids[id(sc)], views[i], s, sc.emitters[f], gate, params[i], 100 + i, f,
                                          bufs[i].data_ptr())
+            if tune == "auto" and f == 0:
+                auto_jobs = [tof.job(sids[id(sc)], views[i], _sensor(sc, 0, W, H), sc.emitters[0], params[i], 100 + i, 0,
+                                     bufs[i].data_ptr(), gate=None if tr else gate, bins=sc.bins if tr else None)
+                             for i, (sc, W, H, gate, _d, _n, _r, _t, tr) in enumerate(spec)]
+                got = tof.tof_autotune(ctx, auto_jobs, frames=2)
+                if chosen is not None:
+                    chosen.extend(got)
             if batched:
                 tof.tof_render_batch(ctx, jobs)
             torch.cuda.synchronize()
@@ -98,3 +110,31 @@ def test_batched_instance_matches_oracle():
     for f in range(2):
         frac, relmse, _ = compare(bat[f][1].reshape(H, W), o[f])
         assert frac >= 0.995 and relmse <= 1e-4, (f, frac, relmse)
+
+
+@pytest.mark.parametrize("tune", [dict(tile_w=8, tile_h=8, packet=0, layout=0),
+                                  dict(tile_w=32, tile_h=4, packet=2, layout=1),
+                                  dict(tile_w=8, tile_h=16, packet=4, layout=0),
+                                  dict(tile_w=4, tile_h=16, packet=1, layout=1)])
+def test_tunings_render_identical_frames(tune):
+    """Pixel tiles, task packets and the reservoir layout change launch shapes and addresses only:
+    every job renders to the same bits (one launch per job, two frames with temporal state)."""
+    ref = _run(False)
+    got = _run(False, tune=tune)
+    for f in range(2):
+        for i, (a, b) in enumerate(zip(ref[f], got[f])):
+            assert np.count_nonzero(a) > 0, (f, i)
+            assert np.array_equal(a, b), (tune, f, i, float(np.abs(a - b).max()))
+
+
+def test_autotune_chooses_valid_tunings_and_keeps_results():
+    chosen = []
+    ref = _run(True)
+    got = _run(True, tune="auto", chosen=chosen)
+    assert len(chosen) == len(_jobs_spec())
+    for t in chosen:
+        assert t["tile_w"] * t["tile_h"] in (64, 128) and 0 <= t["packet"] <= 8 and t["layout"] in (0, 1), t
+    for f in range(2):
+        for i, (a, b) in enumerate(zip(ref[f], got[f])):
+            frac, relmse, _ = compare(b, a)
+            assert frac >= 0.999 and relmse <= 1e-6, (f, i, frac, relmse)
