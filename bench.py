@@ -37,17 +37,21 @@ if ROOT not in sys.path:
 
 METRIC = "frames/s at rel-MSE 1e-2, batched/served vs per-launch; p50/p99 frame latency"
 HBM_FALLBACK = 6800.0
-# Algorithmic bytes per unit of work of each kernel (the data it must move; the scene's BVH and
-# triangles, 7 MB, stay L2-resident and are not counted).  Reservoir = 6 x 16 B = 96 B.
+# Algorithmic bytes of each kernel per unit of its work (the data it must move; the scene's BVH and
+# triangles, 7 MB, stay L2-resident and are not counted).  Reservoir = 6 x 16 B = 96 B; a queued
+# visibility segment = 32 B.
 BYTES = {
     # per pixel: G-buffer read 16, reservoir write 96, confidence 4, occupancy 4, image 4
     "initial": 16 + 96 + 4 + 4 + 4,
     # per forward shift task: task 4 + unit 8 + slot pixel / confidence 8 + source reservoir 96 +
-    # two G-buffer entries 32 + shifted record write 96 + target / Jacobian 8 + inverse tasks 12
-    "spatial_fwd_shift": 4 + 8 + 8 + 96 + 32 + 96 + 8 + 12,
+    # two G-buffer entries 32 + shifted record write 96 + target / Jacobian 8; plus 32 B per segment queued
+    "spatial_fwd_shift": 4 + 8 + 8 + 96 + 32 + 96 + 8,
     # per inverse shift task: task 4 + unit 8 + candidate record 96 + slot pixel / confidence 8 +
-    # two G-buffer entries 32 + MIS term write 4
+    # two G-buffer entries 32 + MIS term write 4; plus 32 B per segment queued
     "spatial_inv_shift": 4 + 8 + 96 + 8 + 32 + 4,
+    # per segment: the queued segment 32 read + the guarded result 4
+    "spatial_fwd_vis": 36,
+    "spatial_inv_vis": 36,
     # per pixel of the merge: slot table 48, six source P0 96, targets / Jacobians 48, MIS terms 144,
     # record write 96, occupancy 4, image 4
     "spatial_merge": 48 + 96 + 48 + 144 + 96 + 4 + 4,
@@ -291,6 +295,7 @@ def _quality(args, ctx, sid, sc, p, kept, ms_frame, stream, extra=None):
     ref = torch.zeros(H * W, device="cuda")
     pt_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     e_restir, e_pt, e_extra, pt_ms_all, spp = [], [], [], [], 1
+    mean_ratio = []
     with torch.cuda.stream(stream):
         for f, img in sorted(kept.items()):
             fq = f % nf
@@ -319,28 +324,25 @@ def _quality(args, ctx, sid, sc, p, kept, ms_frame, stream, extra=None):
             if extra and f in extra:
                 e_extra.append(rel_mse(extra[f], refimg))
             e_restir.append(rel_mse(img, refimg))
+            mean_ratio.append(float(img.mean() / refimg.mean()) if refimg.mean() > 0 else None)
             e_pt.append(rel_mse(ref.cpu().numpy().astype(np.float64).reshape(H, W), refimg))
     er, ep, pm = float(np.mean(e_restir)), float(np.mean(e_pt)), float(np.mean(pt_ms_all))
     q = {"frames": sorted(int(f % nf) for f in kept), "ref_spp": int(args.ref_spp),
          "relmse_restir": er, "relmse_pt_equal_time": ep,
          "relmse_restir_per_frame": e_restir, "relmse_pt_per_frame": e_pt,
+         "mean_vs_reference_per_frame": mean_ratio,
          "pt_spp": spp, "pt_ms": pm, "restir_ms": ms_frame,
          "restir_vs_pt_inv_mse_time": (1.0 / (er * ms_frame)) / (1.0 / (ep * pm)) if er > 0 and ep > 0 else None}
     return q, e_extra
 
 
-def run_quality_rough(args, frames=24):
-    """The dynamic workload with every GGX lobe at least as rough as the reconnection threshold
-    (alpha >= 0.2; mirrors and Lambert unchanged): the same frames, timing and references as the
-    headline's quality, on a material mix where the glossy-to-light paths that no shift can reach
-    (and that make most of the headline's relative error) are absent."""
+def run_quality_variant(args, mutate, frames=24):
+    """The dynamic workload after `mutate(scene)`: frames 0..frames-1 rendered in sequence (timed
+    after 8 with CUDA events, L2 flushed), the last frames scored like the headline's quality."""
     import torch
-    from paper_2605_11536_gb300 import scenes, tof
+    from paper_2605_11536_gb300 import tof
     sc = workload(seed=1)
-    mats = np.array(sc.materials, dtype=np.float64)
-    ggx = mats[:, 0] == scenes.GGX
-    mats[ggx, 2] = np.maximum(mats[ggx, 2], 0.2)
-    sc.materials = mats
+    note = mutate(sc)
     p = sc.params
     W, H = sc.sensors[0]["W"], sc.sensors[0]["H"]
     nf = sc.n_frames
@@ -351,9 +353,10 @@ def run_quality_rough(args, frames=24):
     try:
         sid = tof.tof_scene_upload(ctx, sc.verts, sc.tris, sc.tri_object, sc.materials, sc.object_material)
         vid = tof.tof_view_create(ctx, sid, W, H, 0)
+        tof.tof_view_profile(ctx, vid, 1)
         out = torch.zeros(H * W, device="cuda")
         flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
-        kept, ms = {}, []
+        kept, ms, init_ms = {}, [], []
         with torch.cuda.stream(stream):
             for f in range(frames):
                 flush.zero_()
@@ -367,14 +370,42 @@ def run_quality_rough(args, frames=24):
                 stream.synchronize()
                 if f >= 8:
                     ms.append(e0.elapsed_time(e1))
+                    init_ms.append(tof.tof_view_stage_ms(ctx, vid)["initial"])
                 if f >= frames - nq:
                     kept[f] = out.cpu().numpy().astype(np.float64).reshape(H, W)
         q, _ = _quality(args, ctx, sid, sc, p, kept, float(np.median(ms)), stream)
     finally:
         tof.tof_destroy(ctx)
-    q["materials"] = "GGX alpha clamped to >= 0.2 (%d of %d objects' lobes changed)" % (
-        int(np.count_nonzero(ggx & (np.array(workload(seed=1).materials)[:, 2] < 0.2))), len(mats))
+    q["variant"] = note
+    q["initial_ms"] = float(np.mean(init_ms))
     return q
+
+
+def _all_rough(sc):
+    """Every surface rough enough to reconnect at: GGX alpha >= 0.2, the mirrors turned into GGX
+    with alpha 0.2, Lambert unchanged -- no path through a glossy or mirror vertex into the light
+    that no shift can reach."""
+    from paper_2605_11536_gb300 import scenes
+    mats = np.array(sc.materials, dtype=np.float64)
+    orig = mats.copy()
+    mats[mats[:, 0] == scenes.MIRROR, 2] = 0.2
+    mats[mats[:, 0] == scenes.MIRROR, 0] = scenes.GGX
+    ggx = mats[:, 0] == scenes.GGX
+    mats[ggx, 2] = np.maximum(mats[ggx, 2], 0.2)
+    sc.materials = mats
+    return "every surface rough: %d mirrors -> GGX alpha 0.2, %d GGX lobes clamped to alpha 0.2, of %d objects" % (
+        int(np.count_nonzero(orig[:, 0] == scenes.MIRROR)),
+        int(np.count_nonzero((orig[:, 0] == scenes.GGX) & (orig[:, 2] < 0.2))), len(mats))
+
+
+def _shrink(K, fine):
+    def mutate(sc):
+        sc.params = type(sc.params)(**vars(sc.params))
+        sc.params.shrink_k, sc.params.shrink_fine = K, fine
+        return "shrink mapping (Sec. 4.4): gate widened K = %g times for initial sampling, %d of %d trees kept in " \
+               "the gate (R = %.2f)%s" % (K, fine, sc.params.n_cand, 1 - fine / sc.params.n_cand,
+                                            "; biased (darker) by design" if fine == 0 else "; unbiased")
+    return mutate
 
 
 def batch_workload(n=64, seed=3):
@@ -691,25 +722,37 @@ def main():
     value = agg["value"]
     st = {k: float(np.mean(v)) for k, v in r["stages"].items()}
     pf = r["per_frame"]
-    units = {"initial": r["npix"], "spatial_fwd_shift": pf["spatial_fwd_calls"], "spatial_inv_shift": pf["spatial_inv_calls"],
-             "spatial_merge": r["npix"]}
-    kernels = {"gbuffer": "gbuffer_kernel", "initial": "initial_kernel", "temporal": "temporal pass (4 kernels)",
+    # algorithmic bytes of each kernel per frame: bytes per unit x units (+ the segments it queues)
+    algo = {"initial": BYTES["initial"] * r["npix"],
+            "spatial_fwd_shift": BYTES["spatial_fwd_shift"] * pf["spatial_fwd_calls"] + 32 * pf["spatial_fwd_rays"],
+            "spatial_inv_shift": BYTES["spatial_inv_shift"] * pf["spatial_inv_calls"] + 32 * pf["spatial_inv_rays"],
+            "spatial_fwd_vis": BYTES["spatial_fwd_vis"] * pf["spatial_fwd_rays"],
+            "spatial_inv_vis": BYTES["spatial_inv_vis"] * pf["spatial_inv_rays"],
+            "spatial_merge": BYTES["spatial_merge"] * r["npix"]}
+    units = {"initial": "%d px" % r["npix"],
+             "spatial_fwd_shift": "%.0f tasks + %.0f segments" % (pf["spatial_fwd_calls"], pf["spatial_fwd_rays"]),
+             "spatial_inv_shift": "%.0f tasks + %.0f segments" % (pf["spatial_inv_calls"], pf["spatial_inv_rays"]),
+             "spatial_fwd_vis": "%.0f segments" % pf["spatial_fwd_rays"], "spatial_inv_vis": "%.0f segments" % pf["spatial_inv_rays"],
+             "spatial_merge": "%d px" % r["npix"]}
+    kernels = {"gbuffer": "gbuffer_kernel", "initial": "initial_kernel", "temporal": "temporal pass (8 kernels)",
                "spatial_setup": "reuse_slots_kernel + reuse_units_kernel", "spatial_fwd_shift": "shift_fwd_kernel",
-               "spatial_inv_shift": "shift_inv_kernel", "spatial_merge": "reuse_merge_kernel"}
+               "spatial_fwd_vis": "vis_kernel (forward segments) + emit_inv_kernel", "spatial_inv_shift": "shift_inv_kernel",
+               "spatial_inv_vis": "vis_kernel (inverse segments)", "spatial_merge": "reuse_merge_kernel"}
+
+    def roofline(k):
+        ms = st[k]
+        a = algo[k] / (ms / 1e3) / 1e9
+        return {"bound": "hbm", "kernel": kernels[k], "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                "traffic": None, "ms": ms,
+                "note": "achieved = algorithmic bytes (%s, %.1f MB per launch) / mean launch time (CUDA events, %.3f ms); "
+                        "peak = %s HBM copy bandwidth" % (units[k], algo[k] / 1e6, ms, hbm_kind)}
+
     dom = max(kernels, key=lambda k: st.get(k, 0.0))
-    dom_ms = st[dom]
-    if dom in BYTES:
-        algo = BYTES[dom] * units[dom]
-        achieved = algo / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": kernels[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
-                "note": "achieved = %d algorithmic B x %.0f %s per launch / mean launch time (CUDA events, %.3f ms); "
-                        "peak = %s HBM copy bandwidth; the shift kernels are bound by BVH traversal latency "
-                        "and issue, not by DRAM" % (BYTES[dom], units[dom], "tasks" if "shift" in dom else "px", dom_ms,
-                                                    hbm_kind)}
-    else:
-        roof = {"bound": "hbm", "kernel": kernels[dom], "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
-                "traffic": None}
+    roof = roofline(dom) if dom in algo else {"bound": "hbm", "kernel": kernels[dom], "achieved": None, "peak": hbm,
+                                               "unit": "GB/s", "frac": None, "traffic": None}
+    roof["note"] = roof.get("note", "") + "; the shift, visibility and initial kernels are bound by BVH traversal " \
+                                          "latency and instruction issue, not by DRAM"
+    per_kernel = {kernels[k]: roofline(k) for k in algo if st.get(k, 0.0) > 0}
     e2e_fps = len(r["e2e_ms"]) / (sum(r["e2e_ms"]) / 1e3)
     steps_sorted = sorted(r["step_ms"])
     p50 = float(np.percentile(steps_sorted, 50))
@@ -729,6 +772,7 @@ def main():
             # visibility, inverse-task emission, inverse shifts, visibility, merge)
             "gpu_launches": 35 * K,
             "roofline": roof,
+            "kernel_rooflines": per_kernel,
             "clocks": r["clocks"],
             "quality": r["quality"],
             "pairwise_mis": r["pairwise"],
@@ -736,13 +780,17 @@ def main():
                        "newton_sr": r["stats"]["newton_ok"] / max(1, r["stats"]["newton_calls"]),
                        "shift_sr": r["stats"]["shift_ok"] / max(1, r["stats"]["shift_calls"])},
             "shifts_per_frame": {"spatial_forward": pf["spatial_fwd_calls"], "spatial_inverse": pf["spatial_inv_calls"],
-                                 "all_forward": pf["shift_calls"], "all_inverse": pf["inv_calls"]},
+                                 "all_forward": pf["shift_calls"], "all_inverse": pf["inv_calls"],
+                                 "spatial_forward_segments": pf["spatial_fwd_rays"],
+                                 "spatial_inverse_segments": pf["spatial_inv_rays"]},
             "wall_s": r["wall"]}
     if not args.no_quality:
-        try:
-            line["quality_rough_variant"] = run_quality_rough(args)
-        except Exception as e:
-            line["quality_rough_variant"] = {"error": str(e)[:300]}
+        for key, mut in (("quality_shrink_K10_R1", _shrink(10.0, 0)), ("quality_shrink_K10_R05", _shrink(10.0, 2)),
+                         ("quality_all_rough_variant", _all_rough)):
+            try:
+                line[key] = run_quality_variant(args, mut)
+            except Exception as e:
+                line[key] = {"error": str(e)[:300]}
     if not args.no_transient:
         try:
             line["transient"] = run_transient(args)
@@ -758,10 +806,12 @@ def main():
             line["served"] = run_served(args)
         except Exception as e:
             line["served"] = {"error": str(e)[:300]}
-        try:
-            line["served_gated_512"] = run_served_gated(args)
-        except Exception as e:
-            line["served_gated_512"] = {"error": str(e)[:300]}
+        line["served_gated_512"] = {}
+        for rate in (120.0, 200.0):
+            try:
+                line["served_gated_512"]["%d_per_s" % rate] = run_served_gated(args, rate=rate)
+            except Exception as e:
+                line["served_gated_512"]["%d_per_s" % rate] = {"error": str(e)[:300]}
     if not args.no_cpu:
         try:
             line["cpu_baseline"] = cpu_baseline(args)

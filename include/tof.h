@@ -111,6 +111,15 @@ typedef struct {
     float d_min;              /* minimum reconnection segment length */
     float ray_eps;            /* ray origin offset along the normal */
     uint32_t flags;
+    /* Sec. 4.4 path-length shrink mapping for initial sampling (gated rendering only): the trees
+     * from shrink_fine on draw their candidates in the gate widened shrink_k times about its
+     * centre c, and their RIS winner is moved into the gate by the path-length Newton solve with
+     * tau' = c + (tau - c) / shrink_k (Jacobian scaled by 1 / shrink_k).  Trees below shrink_fine
+     * keep drawing in the gate itself; their winner and the shrunk one are combined with the
+     * generalized balance heuristic (unbiased).  shrink_fine = 0 widens every tree (the paper's
+     * R = 1: lower variance, darker where shrinking fails).  shrink_k <= 1 turns it off. */
+    float shrink_k;
+    int32_t shrink_fine;      /* 0 .. n_cand - 1 */
 } tof_params;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
@@ -278,18 +287,21 @@ tof_status tof_reservoirs_reset(tof_ctx* ctx, tof_view view);
  * out[0] Newton solves, out[1] Newton iterations, out[2] Newton successes, out[3] forward shift
  * attempts, out[4] successful forward shifts (these five over forward shifts of every reuse
  * pass), out[5] inverse (MIS) shift attempts of every pass, out[6] forward and out[7] inverse
- * shift attempts of the spatial passes alone.  Synchronises the view's last stream. */
-tof_status tof_view_stats(tof_ctx* ctx, tof_view view, double out[8]);
+ * shift attempts of the spatial passes alone, out[8] and out[9] visibility segments traced for
+ * the spatial passes' forward and inverse shifts.  Synchronises the view's last stream. */
+tof_status tof_view_stats(tof_ctx* ctx, tof_view view, double out[10]);
 
 /* Per-stage timing of a view's frames with CUDA events recorded on the render stream
  * (enable = 1 turns it on; off by default).  tof_view_stage_ms synchronises that stream and
  * returns the device durations (ms) of the last rendered frame: out[0] G-buffer (and laser spot),
  * out[1] initial candidates, out[2] temporal reuse, out[3] spatial reuse (all passes), out[4]
  * transient splat, out[5] the whole frame, and the spatial passes' kernels summed over passes:
- * out[6] setup (slots, units, tasks), out[7] forward shifts, out[8] inverse (MIS) shifts,
- * out[9] merge.  A stage that did not run reports 0. */
+ * out[6] setup (slots, units, tasks), out[7] forward shifts (shift_fwd_kernel), out[8] inverse
+ * (MIS) shifts (shift_inv_kernel), out[9] merge, out[10] the forward shifts' visibility and the
+ * inverse-task emission, out[11] the inverse shifts' visibility.  A stage that did not run
+ * reports 0. */
 tof_status tof_view_profile(tof_ctx* ctx, tof_view view, int enable);
-tof_status tof_view_stage_ms(tof_ctx* ctx, tof_view view, float out[10]);
+tof_status tof_view_stage_ms(tof_ctx* ctx, tof_view view, float out[12]);
 
 #ifdef __cplusplus
 }

@@ -53,7 +53,8 @@ class OParams(C.Structure):
     _fields_ = [("depth", C.c_int), ("n_cand", C.c_int), ("n_spatial", C.c_int), ("radius", C.c_int),
                 ("n_spatial_iters", C.c_int), ("temporal", C.c_int), ("m_cap", C.c_double),
                 ("newton_max_iter", C.c_int), ("newton_tol_frac", C.c_double), ("jac_max", C.c_double),
-                ("d_min", C.c_double), ("ray_eps", C.c_double), ("flags", C.c_uint32)]
+                ("d_min", C.c_double), ("ray_eps", C.c_double), ("flags", C.c_uint32), ("shrink_k", C.c_double),
+                ("shrink_fine", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -95,6 +96,8 @@ def _declare(L):
     L.or_view_reservoir.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, C.POINTER(C.c_int)]
     L.or_shift_roundtrip.restype = C.c_int
     L.or_shift_roundtrip.argtypes = [C.c_void_p, C.POINTER(OParams), C.c_uint64, C.c_int, C.c_int, _dp]
+    L.or_shrink_roundtrip.restype = C.c_int
+    L.or_shrink_roundtrip.argtypes = [C.c_void_p, C.POINTER(OParams), C.c_uint64, C.c_int, C.c_double, _dp]
 
 
 def _d(a):
@@ -286,4 +289,14 @@ def shift_roundtrip(view: View, params, seed, src, dst):
     out = np.zeros(6)
     pp = params_struct(params)
     rc = lib().or_shift_roundtrip(view.ptr, C.byref(pp), seed, src, dst, out.ctypes.data_as(_dp))
+    return rc, out
+
+
+def shrink_roundtrip(view: View, params, seed, pix, K):
+    """Expand pixel `pix`'s stored gated sample K times about the gate centre and shrink it back
+    (Sec. 4.4).  Returns (rc, out): out = (J_expand, J_shrink, bary error, tau, tau expanded,
+    tau shrunk back, p_hat, p_hat expanded)."""
+    out = np.zeros(8)
+    pp = params_struct(params)
+    rc = lib().or_shrink_roundtrip(view.ptr, C.byref(pp), seed, pix, float(K), out.ctypes.data_as(_dp))
     return rc, out

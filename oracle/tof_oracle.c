@@ -420,6 +420,8 @@ typedef struct {
     int newton_max_iter;
     double newton_tol_frac, jac_max, d_min, ray_eps;
     uint32_t flags;
+    double shrink_k;     /* Sec. 4.4 shrink mapping: gate widened K times for initial sampling (<= 1: off) */
+    int shrink_fine;     /* trees kept in the gate itself (canonical samples); 0 = all trees widened */
 } oparams;
 enum { F_DIRECT = 1, F_NAIVE = 2, F_PAIRWISE = 4 };
 
@@ -723,9 +725,18 @@ static void stat_add(double* a, double v) {
  * p = x_r) followed by the path-length-aware perturbation of p, from domain Dj (the record's
  * own) to domain Di.  Returns 1 on success with the offset path record, its target p_hat in Di
  * and the Jacobian |dS/dx|.
+ *
+ * gm (optional) replaces the translation of the path length by the scaling of Sec. 4.4 (the
+ * path-length shrink mapping): the offset path's gated length is tau' = c + s (tau - c), accepted
+ * in [lo, hi), instead of keeping its position inside Di's gate.  s = 1/K shrinks a sample drawn
+ * in a gate K times wider about its centre c into the gate; s = K expands it back.  Newton is the
+ * same with delta = tau' - tau; only the constraint row of dF/dxi scales by s, so the Jacobian
+ * gains the factor s.
  * ==========================================================================================*/
-static int shift_rec(const orec* x, const odomain* Dj, const odomain* Di, const oparams* P, uint64_t seed,
-                     int geom_static, orec* y, double* phat_out, double* jac_out, ostats* st) {
+typedef struct { double scale, centre, lo, hi; } ogatemap;
+
+static int shift_rec_g(const orec* x, const odomain* Dj, const odomain* Di, const oparams* P, uint64_t seed,
+                       int geom_static, orec* y, double* phat_out, double* jac_out, ostats* st, const ogatemap* gm) {
     if (!x->valid || x->r < 2 || !Di->valid || !Dj->valid) return 0;
     const ogeom* gi = Di->g;
     const ogeom* gj = Dj->g;
@@ -789,15 +800,17 @@ static int shift_rec(const orec* x, const odomain* Dj, const odomain* Di, const 
     N.p1x = x->xprev; N.p2x = p2x; N.fx = fx;
     N.p1y = yv[r - 1].p; N.p2y = p2y; N.fy = tri_frame(gi, x->p_tri);
     double Lx_seg = vlen(vsub(x->xprev, pbase.p)) + vlen(vsub(p2x, pbase.p));
-    double ell = x->tau - Dj->L0 + Di->L0 + Di->o - plen - slen;   /* target for L_y(xi') */
+    /* target gated length tau' of the offset path, and the matching target for L_y(xi') */
+    double tau_t = gm ? gm->centre + gm->scale * (x->tau - gm->centre) : x->tau - Dj->L0 + Di->L0;
+    double ell = tau_t + Di->o - plen - slen;
     double delta = ell - Lx_seg;
     double xp[2], jnewton = 1.0;
     int iters = 0;
     if (P->flags & F_NAIVE) {
         xp[0] = xi[0]; xp[1] = xi[1];
     } else {
-        double tol_stop = 1e-6 * fabs(x->tau + Di->o + Di->L0 - Dj->L0);
-        double tol_succ = P->newton_tol_frac * Di->dL;
+        double tol_stop = 1e-6 * fabs(gm ? tau_t + Di->o : x->tau + Di->o + Di->L0 - Dj->L0);
+        double tol_succ = P->newton_tol_frac * (gm ? gm->hi - gm->lo : Di->dL);
         int ok = newton_solve(&N, xi, delta, P->newton_max_iter, tol_stop, tol_succ, xp, &jnewton, &iters);
         if (st) { stat_add(&st->newton_calls, 1); stat_add(&st->newton_iters, iters); if (ok) stat_add(&st->newton_ok, 1); }
         if (!ok) return 0;
@@ -867,12 +880,14 @@ static int shift_rec(const orec* x, const odomain* Dj, const odomain* Di, const 
     }
     double Lnew = plen + vlen(vsub(yv[r - 1].p, pp.p)) + vlen(vsub(pp.p, p2y)) + slen;
     double tau = Lnew - Di->o;
-    if (!(tau >= Di->L0 && tau < Di->L0 + Di->dL)) return 0;
+    if (gm) { if (!(tau >= gm->lo && tau < gm->hi)) return 0; }
+    else if (!(tau >= Di->L0 && tau < Di->L0 + Di->dL)) return 0;
     if (!(f > 0) || !isfinite(f)) return 0;
 
     /* (8) Jacobian: replay pdf ratios (area measure) times the Newton determinant; the frame
-     * factor sqrt(det J'^T J') / sqrt(det J^T J) is 1 for the orthonormal in-plane frames */
-    double jac = (x->pdf_pre / pdf_pre_y) * jnewton;
+     * factor sqrt(det J'^T J') / sqrt(det J^T J) is 1 for the orthonormal in-plane frames; a
+     * scaling gate map contributes its factor s */
+    double jac = (x->pdf_pre / pdf_pre_y) * jnewton * (gm ? gm->scale : 1.0);
     if (!(jac > 0) || !isfinite(jac)) return 0;
 
     *y = *x;
@@ -886,6 +901,11 @@ static int shift_rec(const orec* x, const odomain* Dj, const odomain* Di, const 
     *jac_out = jac;
     if (st) stat_add(&st->shift_ok, 1);
     return 1;
+}
+
+static int shift_rec(const orec* x, const odomain* Dj, const odomain* Di, const oparams* P, uint64_t seed,
+                     int geom_static, orec* y, double* phat_out, double* jac_out, ostats* st) {
+    return shift_rec_g(x, Dj, Di, P, seed, geom_static, y, phat_out, jac_out, st, NULL);
 }
 
 /* ============================================================================================
@@ -1123,6 +1143,71 @@ static void init_sink(void* vctx, int k, double c, double tau, const opathbuf* p
 }
 
 /* ============================================================================================
+ * initial sampling with the path-length shrink mapping (Sec. 4.4), gated rendering.
+ * Trees t >= N_A = shrink_fine draw their candidates in the gate widened K times about its
+ * centre c = L0 + dL/2 (target f 1[tau in the wide gate], w = (1/N_B) f/p, N_B = n_cand - N_A)
+ * and keep their RIS winner x_B with W_B; the winner alone is shrunk into the gate,
+ * y_B = T(x_B) with tau' = c + (tau - c)/K and |dT/dx| = det(dxi'/dxi)/K.  Trees t < N_A keep
+ * their candidates in the gate itself (canonical winner y_A with W_A).  The two are combined as a
+ * GRIS merge with the generalized balance heuristic and confidences N_A, N_B:
+ *   m_A(y_A) = N_A p(y_A) / (N_A p(y_A) + N_B p_wide(T^-1(y_A)) |dT^-1/dy|),
+ *   m_B(y_B) = N_B p_wide(x_B)/|dT/dx| / (N_A p(y_B) + N_B p_wide(x_B)/|dT/dx|),
+ *   w = m p(y) W |J| (|J| = 1 for A), selection with one uniform each, W = (w_A + w_B) / p(y).
+ * With N_A = 0 (R = 1, the paper's practical setting) m_B = 1 and W = W_B |dT/dx|: biased where
+ * the shrink fails or the shrunk samples do not cover the gate (the paper's darkening); with
+ * N_A > 0 the canonical samples cover the whole gate and the estimate is unbiased.
+ * ==========================================================================================*/
+static void initial_shrink(const ogeom* g, const odomain* D, const oparams* P, uint64_t seed, uint32_t px, uint32_t frame,
+                           double L0, double dL, orec* out) {
+    const int NA = P->shrink_fine, NB = P->n_cand - P->shrink_fine;
+    const double K = P->shrink_k, c = L0 + 0.5 * dL, half = 0.5 * K * dL;
+    orec xa = EMPTY_REC, xb = EMPTY_REC;
+    double Sa = 0.0, Sb = 0.0;
+    oinit_ctx Ca = {g, D, P, seed, px, frame, 0, 0, L0, dL, &xa, &Sa, NA > 0 ? 1.0 / NA : 0.0};
+    oinit_ctx Cb = {g, D, P, seed, px, frame, 0, 0, L0, dL, &xb, &Sb, 1.0 / NB};
+    for (int t = 0; t < P->n_cand; ++t) {
+        if (t < NA) { Ca.tree = t; trace_tree(g, D, P, seed, px, frame, t, 1, L0, L0 + dL, init_sink, &Ca); }
+        else { Cb.tree = t; trace_tree(g, D, P, seed, px, frame, t, 1, c - half, c + half, init_sink, &Cb); }
+    }
+    const double Wa = (xa.valid && xa.phat > 0) ? Sa / xa.phat : 0.0;
+    const double Wb = (xb.valid && xb.phat > 0) ? Sb / xb.phat : 0.0;
+    const ogatemap to_gate = {1.0 / K, c, L0, L0 + dL}, to_wide = {K, c, c - half, c + half};
+    orec yb = EMPTY_REC;
+    double pyb = 0.0, Jb = 0.0;
+    int okb = Wb > 0 && shift_rec_g(&xb, D, D, P, seed, 1, &yb, &pyb, &Jb, NULL, &to_gate);
+    double w[2] = {0.0, 0.0};
+    if (NA == 0) {
+        if (okb) w[1] = pyb * Wb * Jb;
+    } else {
+        if (Wa > 0) {
+            orec tmp;
+            double pe = 0.0, Je = 0.0;
+            double pb_at_a = shift_rec_g(&xa, D, D, P, seed, 1, &tmp, &pe, &Je, NULL, &to_wide) ? pe * Je : 0.0;
+            double ma = NA * xa.phat / (NA * xa.phat + NB * pb_at_a);
+            w[0] = ma * xa.phat * Wa;
+        }
+        if (okb) {
+            double nb = NB * xb.phat / Jb;
+            double mb = nb / (NA * pyb + nb);
+            w[1] = mb * pyb * Wb * Jb;
+        }
+    }
+    double S = 0.0;
+    int sel = -1;
+    for (int s = 0; s < 2; ++s) {
+        if (!(w[s] > 0) || !isfinite(w[s])) continue;
+        uint32_t u[4];
+        rng4(seed, px, frame, (0xFFu << 8) | (uint32_t)s, P_MERGE, u);
+        S += w[s];
+        if (u01(u[0]) * S < w[s]) sel = s;
+    }
+    *out = EMPTY_REC;
+    if (sel == 0) { *out = xa; out->valid = 1; out->W = S / xa.phat; }
+    else if (sel == 1) { *out = yb; out->valid = 1; out->W = S / pyb; }
+    out->M = P->n_cand;
+}
+
+/* ============================================================================================
  * GRIS merge (Sec. 3.2: w_i = m_i(y_i) p_hat(y_i) W_i |dS_i/dx_i|, generalized balance
  * heuristic m_i(y_i) = M_i p_hat_{<-i}(y_i) / sum_j M_j p_hat_{<-j}(y_i), with the denominator
  * evaluated at the same y_i for every j, and p_hat_{<-i}(y_i) = p_hat_i(x_i) / |dS_i/dx_i|).
@@ -1289,6 +1374,7 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
 
     /* initial candidates */
     orec* R0 = (orec*)calloc((size_t)W * H * Bn, sizeof(orec));
+    const int shrink = B == 0 && P->shrink_k > 1.0;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 4)
 #endif
@@ -1297,6 +1383,10 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
         for (int b = 0; b < Bn; ++b) { rr[b] = EMPTY_REC; rr[b].M = P->n_cand; }
         if (!F->ok[pix] || !F->gb[pix].valid) continue;
         odomain D = make_domain(F, pix, P, L0, dL);
+        if (shrink) {
+            initial_shrink(g, &D, P, seed, (uint32_t)pix, frame, L0, dL, rr);
+            continue;
+        }
         double* S = (double*)calloc((size_t)Bn, sizeof(double));
         oinit_ctx C = {g, &D, P, seed, (uint32_t)pix, frame, 0, B, L0, dL, rr, S, 1.0 / P->n_cand};
         for (int t = 0; t < P->n_cand; ++t) {
@@ -1560,5 +1650,26 @@ int or_shift_roundtrip(const oview* v, const oparams* P, uint64_t seed, int src,
     if (!shift_rec(&y, &Dd, &Ds, P, seed, 1, &z, &pz, &Jz, NULL)) return -1;
     out[0] = J; out[1] = Jz; out[2] = fabs(z.p_b1 - x->p_b1) + fabs(z.p_b2 - x->p_b2);
     out[3] = py; out[4] = pz; out[5] = x->phat;
+    return 1;
+}
+
+/* exercise the shrink mapping of Sec. 4.4 on a stored gated reservoir: expand the record of pixel
+ * `pix` (current frame) from its gate into the gate widened K times about the same centre, then
+ * shrink the result back.  Returns 1 if both succeed; out = (J_expand, J_shrink, round-trip
+ * barycentric error, tau, tau after expanding, tau after shrinking back, p_hat, p_hat expanded). */
+int or_shrink_roundtrip(const oview* v, const oparams* P, uint64_t seed, int pix, double K, double out[8]) {
+    const oframe* F = &v->fr[v->cur];
+    const orec* x = &F->res[(size_t)pix * v->Bn];
+    odomain D = make_domain(F, pix, P, F->L0, F->dL);
+    const double c = F->L0 + 0.5 * F->dL, half = 0.5 * K * F->dL;
+    const ogatemap to_wide = {K, c, c - half, c + half}, to_gate = {1.0 / K, c, F->L0, F->L0 + F->dL};
+    orec y, z;
+    double py, Jy, pz, Jz;
+    for (int i = 0; i < 8; ++i) out[i] = 0;
+    if (!x->valid) return 0;
+    if (!shift_rec_g(x, &D, &D, P, seed, 1, &y, &py, &Jy, NULL, &to_wide)) return 0;
+    if (!shift_rec_g(&y, &D, &D, P, seed, 1, &z, &pz, &Jz, NULL, &to_gate)) return -1;
+    out[0] = Jy; out[1] = Jz; out[2] = fabs(z.p_b1 - x->p_b1) + fabs(z.p_b2 - x->p_b2);
+    out[3] = x->tau; out[4] = y.tau; out[5] = z.tau; out[6] = x->phat; out[7] = py;
     return 1;
 }

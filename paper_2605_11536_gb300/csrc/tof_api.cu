@@ -20,6 +20,7 @@
 namespace tof {
 cudaError_t launch_gbuffer(const GbufArgs& a, int tile_h, cudaStream_t s);
 cudaError_t launch_initial(const InitArgs& a, int tile_h, int* err, cudaStream_t s);
+cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s);
 cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, int vis_blocks,
                               cudaEvent_t* ev, cudaStream_t s);
 cudaError_t reuse_persist_blocks(int* out, int* vis_out);
@@ -101,7 +102,7 @@ struct ViewH {
     // wavefront scratch of the reuse passes (sized on first use)
     WaveDev wave;
     int wave_slots = 0, wave_cap = 0;
-    std::vector<cudaEvent_t> kev;   // 5 events per timed spatial launch group
+    std::vector<cudaEvent_t> kev;   // kReuseEvents events per timed spatial launch group
     size_t kev_used = 0;
     void* wave_ptrs[12] = {nullptr};
     tof_tuning tune = {16, 8, 0, TOF_LAYOUT_SOA};   // launch shapes and reservoir layout (autotuner)
@@ -192,6 +193,7 @@ static ParamsDev to_dev(const tof_params* p, uint64_t seed) {
     d.n_spatial_iters = p->n_spatial_iters; d.temporal = p->temporal; d.m_cap = p->m_cap;
     d.newton_max_iter = p->newton_max_iter; d.newton_tol_frac = p->newton_tol_frac; d.jac_max = p->jac_max;
     d.d_min = p->d_min; d.ray_eps = p->ray_eps; d.flags = p->flags; d.seed = seed;
+    d.shrink_k = p->shrink_k; d.shrink_fine = p->shrink_fine;
     return d;
 }
 
@@ -206,6 +208,13 @@ static tof_status check_params(tof_ctx* c, const tof_params* p, int transient) {
     if (p->newton_max_iter < 0 || p->newton_max_iter > 16) return fail(c, TOF_EINVAL, "newton_max_iter outside [0, 16]");
     if (!(p->m_cap > 0) || !(p->jac_max >= 1) || !(p->newton_tol_frac > 0) || !(p->ray_eps > 0) || !(p->d_min >= 0))
         return fail(c, TOF_EINVAL, "m_cap, jac_max, newton_tol_frac, ray_eps must be positive, d_min >= 0");
+    if (!std::isfinite(p->shrink_k) || p->shrink_k > 1000.f)
+        return fail(c, TOF_EINVAL, "shrink_k must be finite and at most 1000");
+    if (p->shrink_k > 1.f) {
+        if (transient) return fail(c, TOF_EINVAL, "the shrink mapping applies to gated rendering only");
+        if (p->shrink_fine < 0 || p->shrink_fine >= p->n_cand)
+            return fail(c, TOF_EINVAL, "shrink_fine %d outside [0, n_cand - 1]", p->shrink_fine);
+    }
     if (transient) {
         int kmin = (p->flags & TOF_FLAG_DIRECT) ? 1 : 2;
         int lengths = p->depth - kmin + 1;
@@ -498,18 +507,19 @@ tof_status tof_reservoirs_reset(tof_ctx* c, tof_view id) {
     return TOF_OK;
 }
 
-tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[8]) {
+tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[10]) {
     if (!c || !out || id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return c ? fail(c, TOF_EINVAL, "bad view") : TOF_EINVAL;
     cudaSetDevice(c->device);
     ViewH& V = c->views[id];
     StatsDev h;
     CK(cudaStreamSynchronize(V.last_stream));
     CK(cudaMemcpy(&h, V.stats, sizeof(h), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < 8; ++i) out[i] = (double)h.v[i];
+    for (int i = 0; i < 10; ++i) out[i] = (double)h.v[i];
     return TOF_OK;
 }
 
 static bool g_no_marks = false;   // set while a batch is being captured (no profiling events)
+constexpr int kReuseEvents = 7;   // events around the kernels of one reuse launch group
 
 // resident-block counts of the persistent reuse kernels, once per context
 static tof_status persist_init(tof_ctx* c) {
@@ -572,13 +582,13 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
         size_t p1 = p0 + chunk < npix ? p0 + chunk : npix;
         cudaEvent_t* ev = nullptr;
         if (V.profile && !ra.temporal && !fixed && !g_no_marks) {
-            while (V.kev.size() < V.kev_used + 5) {
+            while (V.kev.size() < V.kev_used + kReuseEvents) {
                 cudaEvent_t e;
                 CK(cudaEventCreate(&e));
                 V.kev.push_back(e);
             }
             ev = &V.kev[V.kev_used];
-            V.kev_used += 5;
+            V.kev_used += kReuseEvents;
         }
         int pb = c->persist_blocks, vb = c->vis_blocks;
         if (V.tune.packet > 0) {
@@ -645,7 +655,8 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     ia.F = F; ia.dst = V.res[out_of(stage)].dev(); ia.P = P;
     ia.out = (stage == stages - 1 && B == 0) ? out : nullptr;
     ia.tile_w = V.tune.tile_w;
-    CK(launch_initial(ia, V.tune.tile_h, c->d_err, s));
+    if (B == 0 && params->shrink_k > 1.f) CK(launch_initial_shrink(ia, V.tune.tile_h, s));
+    else CK(launch_initial(ia, V.tune.tile_h, c->d_err, s));
     mark(V, 2, s);
     V.ran[1] = true;
     int src = out_of(stage);
@@ -709,7 +720,7 @@ tof_status tof_view_profile(tof_ctx* c, tof_view id, int enable) {
     return TOF_OK;
 }
 
-tof_status tof_view_stage_ms(tof_ctx* c, tof_view id, float out[10]) {
+tof_status tof_view_stage_ms(tof_ctx* c, tof_view id, float out[12]) {
     if (!c || !out || id < 0 || id >= (int)c->views.size() || !c->views[id].alive) return c ? fail(c, TOF_EINVAL, "bad view") : TOF_EINVAL;
     ViewH& V = c->views[id];
     if (!V.profile || !V.ev[0]) return fail(c, TOF_ESTATE, "profiling is off for view %d", id);
@@ -720,12 +731,15 @@ tof_status tof_view_stage_ms(tof_ctx* c, tof_view id, float out[10]) {
         if (V.ran[k]) CK(cudaEventElapsedTime(&out[k], V.ev[k], V.ev[k + 1]));
     }
     CK(cudaEventElapsedTime(&out[5], V.ev[0], V.ev[6]));
-    for (int k = 6; k < 10; ++k) out[k] = 0.f;
-    for (size_t g = 0; g + 5 <= V.kev_used; g += 5)
-        for (int k = 0; k < 4; ++k) {
+    for (int k = 6; k < 12; ++k) out[k] = 0.f;
+    // per launch group: setup, forward shifts, forward visibility + emission, inverse shifts,
+    // inverse visibility, merge
+    const int slot[kReuseEvents - 1] = {6, 7, 10, 8, 11, 9};
+    for (size_t g = 0; g + kReuseEvents <= V.kev_used; g += kReuseEvents)
+        for (int k = 0; k < kReuseEvents - 1; ++k) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, V.kev[g + k], V.kev[g + k + 1]));
-            out[6 + k] += ms;
+            out[slot[k]] += ms;
         }
     return TOF_OK;
 }

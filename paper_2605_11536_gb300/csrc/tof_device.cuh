@@ -762,12 +762,20 @@ static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float
 // ============================================================================================
 struct ShiftStats { uint32_t newton_calls, newton_iters, newton_ok, shift_calls, shift_ok; };
 
+// Sec. 4.4 path-length shrink mapping: instead of keeping the sample's position inside the target
+// gate, the offset path's gated length becomes tau' = centre + scale (tau - centre), accepted in
+// [lo, hi).  scale = 1/K shrinks a sample drawn in a gate K times wider into the gate, scale = K
+// expands it back; the constraint row of dF/dxi scales by `scale`, and so does the Jacobian.
+struct GateMap { float scale, centre, lo, hi; };
+
 // kOut = false: only the target value and the Jacobian are wanted (the MIS terms), not the record.
 // vq: the visibility segments of a shift that passes every other test are queued there (vis_kernel
 // zeroes the guarded result when one is occluded); null: they are traced in place.
+// gm: the gate map of the shrink mapping (null: translation between gates)
 template <bool kOut>
 static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& Di, const ParamsDev& P, bool geom_static, Rec& y,
-                          float& phat_out, float& jac_out, ShiftStats* st, const VisQ* vq = nullptr) {
+                          float& phat_out, float& jac_out, ShiftStats* st, const VisQ* vq = nullptr,
+                          const GateMap* gm = nullptr) {
     const int r = rec_r(x);
     if (r < 2 || !Di.valid || !Dj.valid) return false;
     const GeomDev& gi = Di.F->g;
@@ -828,7 +836,14 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
     // (4) Newton solve of L(y') = L(x) + delta (eq. path_length_constraint), delta keeping the
     // sample at the same position inside the target gate
     float Lx_seg = len3(x.xprev - pbase.p) + len3(p2x - pbase.p);
-    float ell = x.tau - Dj.L0 + Di.L0 + Di.o - plen - slen;
+    float tau_t = 0.f;   // target gated length under a gate map
+    float ell;
+    if (gm) {
+        tau_t = gm->centre + gm->scale * (x.tau - gm->centre);
+        ell = tau_t + Di.o - plen - slen;
+    } else {
+        ell = x.tau - Dj.L0 + Di.L0 + Di.o - plen - slen;
+    }
     float delta = ell - Lx_seg;
     float xp[2];
     float jn = 1.0f;
@@ -836,8 +851,8 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
         xp[0] = xi[0]; xp[1] = xi[1];
     } else {
         int iters = 0;
-        float tol_stop = 1e-6f * fabsf(x.tau + Di.o + Di.L0 - Dj.L0);
-        float tol_succ = P.newton_tol_frac * Di.dL;
+        float tol_stop = gm ? 1e-6f * fabsf(tau_t + Di.o) : 1e-6f * fabsf(x.tau + Di.o + Di.L0 - Dj.L0);
+        float tol_succ = P.newton_tol_frac * (gm ? gm->hi - gm->lo : Di.dL);
         bool ok = newton_solve(N, xi, delta, P.newton_max_iter, tol_stop, tol_succ, xp, jn, iters);
         if (st) { st->newton_calls++; st->newton_iters += iters; if (ok) st->newton_ok++; }
         if (!ok) return false;
@@ -885,8 +900,11 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
     if (!(f > 0.f) || !isfinite(f)) return false;
     float Lnew = plen + len3(yv[r - 1].p - pp.p) + len3(pp.p - p2y) + slen;
     float tau = Lnew - Di.o;
-    if (!(tau >= Di.L0 && tau < Di.L0 + Di.dL)) return false;
+    if (gm) {
+        if (!(tau >= gm->lo && tau < gm->hi)) return false;
+    } else if (!(tau >= Di.L0 && tau < Di.L0 + Di.dL)) return false;
     float jac = (x.pdf_pre / pdfy) * jn;
+    if (gm) jac *= gm->scale;
     if (!(jac > 0.f) || !isfinite(jac)) return false;
 
     // (7) suffix radiance: cached, or re-evaluated when the scene or light differs (Sec. 5); the

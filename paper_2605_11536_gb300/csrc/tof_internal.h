@@ -80,13 +80,16 @@ struct ParamsDev {
     int newton_max_iter;
     float newton_tol_frac, jac_max, d_min, ray_eps;
     uint32_t flags;
+    float shrink_k;          // Sec. 4.4 shrink mapping (<= 1: off)
+    int shrink_fine;         // trees kept in the gate itself
     uint64_t seed;
 };
 
 // shift statistics (device, accumulated): newton calls, iterations, successes, forward shift
-// calls, forward successes, inverse shift calls, spatial forward calls, spatial inverse calls
+// calls, forward successes, inverse shift calls, spatial forward calls, spatial inverse calls,
+// visibility segments traced by vis_kernel for the spatial forward / inverse shifts
 struct StatsDev {
-    unsigned long long v[8];
+    unsigned long long v[10];
 };
 
 struct GbufArgs {

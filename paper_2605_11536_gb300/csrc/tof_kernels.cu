@@ -188,6 +188,109 @@ __global__ void __launch_bounds__(128) initial_kernel(const __grid_constant__ In
 }
 
 // --------------------------------------------------------------------------------------------
+// initial candidates with the path-length shrink mapping (Sec. 4.4), gated views.  Trees from
+// N_A = shrink_fine on draw in the gate widened K times about its centre c and keep their RIS
+// winner x_B (W_B); the winner alone is shrunk into the gate, y_B = T(x_B), tau' = c + (tau - c)/K,
+// |dT/dx| = det(dxi'/dxi)/K.  Trees below N_A draw in the gate itself (winner y_A, W_A).  The two
+// are combined by the generalized balance heuristic with confidences N_A and N_B = n_cand - N_A:
+//   m_A = N_A p(y_A) / (N_A p(y_A) + N_B p_wide(T^-1(y_A)) |dT^-1/dy|)
+//   m_B = N_B p_wide(x_B)/|dT/dx| / (N_A p(y_B) + N_B p_wide(x_B)/|dT/dx|)
+// With N_A = 0 (every tree widened) W = W_B |dT/dx|.
+// --------------------------------------------------------------------------------------------
+struct ShrinkSink {
+    const Domain* D;
+    const ParamsDev* P;
+    uint32_t px, frame;
+    int tree;
+    float invN, S;
+    bool has;
+    Rec rec;
+    __device__ void operator()(int k, float c, float tauv, const TreeVerts& T) {
+        float wv = invN * c;
+        if (!(wv > 0.f)) return;
+        uint4 u = philox(px, frame, ((uint32_t)tree << 8) | (uint32_t)k, P_RIS, P->seed);
+        S += wv;
+        if (u01(u.x) * S < wv) {
+            build_rec(*D, T, k, tree, px, frame, tauv, *P, rec);
+            has = true;
+        }
+    }
+};
+
+__global__ void __launch_bounds__(128) initial_shrink_kernel(const __grid_constant__ InitArgs a) {
+    const FrameDev& F = a.F;
+    int ix, iy;
+    tile_pixel(a.tile_w, ix, iy);
+    if (ix >= F.W || iy >= F.H) return;
+    const int pix = iy * F.W + ix;
+    const ParamsDev& P = a.P;
+    a.dst.occ[pix] = 0u;
+    a.dst.M[pix] = (float)P.n_cand;
+    float4 gb = F.gb[pix];
+    uint32_t tri = __float_as_uint(gb.x);
+    Domain D = make_domain_hit(&F, tri != kNoHit, (int)tri, gb.y, gb.z, gb.w, F.L0, F.dL);
+    if (!D.valid) {
+        if (a.out) a.out[pix] = 0.f;
+        return;
+    }
+    const int NA = P.shrink_fine, NB = P.n_cand - P.shrink_fine;
+    const float K = P.shrink_k, c = F.L0 + 0.5f * F.dL, half = 0.5f * K * F.dL;
+    ShrinkSink sa, sb;
+    sa.D = sb.D = &D; sa.P = sb.P = &P; sa.px = sb.px = (uint32_t)pix; sa.frame = sb.frame = F.frame;
+    sa.invN = NA > 0 ? 1.0f / (float)NA : 0.f; sb.invN = 1.0f / (float)NB;
+    sa.S = sb.S = 0.f; sa.has = sb.has = false;
+    TreeVerts T;
+    for (int t = 0; t < P.n_cand; ++t) {
+        if (t < NA) { sa.tree = t; trace_tree(D, P, (uint32_t)pix, F.frame, t, F.L0, F.L0 + F.dL, T, sa); }
+        else { sb.tree = t; trace_tree(D, P, (uint32_t)pix, F.frame, t, c - half, c + half, T, sb); }
+    }
+    const float Wa = (sa.has && sa.rec.phat > 0.f) ? sa.S / sa.rec.phat : 0.f;
+    const float Wb = (sb.has && sb.rec.phat > 0.f) ? sb.S / sb.rec.phat : 0.f;
+    GateMap to_gate, to_wide;
+    to_gate.scale = 1.0f / K; to_gate.centre = c; to_gate.lo = F.L0; to_gate.hi = F.L0 + F.dL;
+    to_wide.scale = K; to_wide.centre = c; to_wide.lo = c - half; to_wide.hi = c + half;
+    Rec yb;
+    float pyb = 0.f, Jb = 0.f;
+    const bool okb = Wb > 0.f && shift_rec<true>(sb.rec, D, D, P, true, yb, pyb, Jb, nullptr, nullptr, &to_gate);
+    float w[2] = {0.f, 0.f};
+    if (NA == 0) {
+        if (okb) w[1] = pyb * Wb * Jb;
+    } else {
+        if (Wa > 0.f) {
+            Rec tmp;
+            float pe = 0.f, Je = 0.f;
+            float pba = shift_rec<false>(sa.rec, D, D, P, true, tmp, pe, Je, nullptr, nullptr, &to_wide) ? pe * Je : 0.f;
+            float ma = NA * sa.rec.phat / (NA * sa.rec.phat + NB * pba);
+            w[0] = ma * sa.rec.phat * Wa;
+        }
+        if (okb) {
+            float nb = NB * sb.rec.phat / Jb;
+            float mb = nb / (NA * pyb + nb);
+            w[1] = mb * pyb * Wb * Jb;
+        }
+    }
+    float S = 0.f;
+    int sel = -1;
+    for (int q = 0; q < 2; ++q) {
+        if (!(w[q] > 0.f) || !isfinite(w[q])) continue;
+        uint4 u = philox((uint32_t)pix, F.frame, (0xFFu << 8) | (uint32_t)q, P_MERGE, P.seed);
+        S += w[q];
+        if (u01(u.x) * S < w[q]) sel = q;
+    }
+    float outv = 0.f;
+    if (sel >= 0) {
+        Rec& r = sel == 0 ? sa.rec : yb;
+        const float ph = sel == 0 ? sa.rec.phat : pyb;
+        r.W = S / ph;
+        r.phat = ph;
+        rec_store(a.dst, (size_t)pix, r);
+        a.dst.occ[pix] = 1u;
+        outv = ph * r.W;
+    }
+    if (a.out) a.out[pix] = outv;
+}
+
+// --------------------------------------------------------------------------------------------
 // transient splat (stage (4)): H[px, b] = f(y_b) W_b for occupied bins, 0 elsewhere; one warp
 // per pixel so that the histogram row is written with coalesced stores
 // --------------------------------------------------------------------------------------------
@@ -285,6 +388,10 @@ cudaError_t launch_gbuffer(const GbufArgs& a, int tile_h, cudaStream_t s) {
 }
 cudaError_t launch_initial(const InitArgs& a, int tile_h, int* err, cudaStream_t s) {
     initial_kernel<<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, err);
+    return cudaGetLastError();
+}
+cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s) {
+    initial_shrink_kernel<<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_splat(const SplatArgs& a, cudaStream_t s) {

@@ -259,13 +259,15 @@ __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant
 // traversal (grazing segments over a heightfield visit many nodes) runs to its end.  Each
 // segment's node visits are those of traverse<true> in the same order, so the answer is the same.
 // stat >= 0: the stats counter that counted the guarded shifts as successes (one decrement per
-// shift, however many of its segments are occluded).
+// shift, however many of its segments are occluded); ray_stat >= 0: the counter of segments.
 // --------------------------------------------------------------------------------------------
 constexpr int kVisSteps = 8;
 
 __global__ void __launch_bounds__(128) vis_kernel(const GeomDev g, const float4* __restrict__ rays, const uint32_t* counter,
-                                                  uint32_t cap, uint32_t* fetch, float* target, StatsDev* stats, int stat) {
+                                                  uint32_t cap, uint32_t* fetch, float* target, StatsDev* stats, int stat,
+                                                  int ray_stat) {
     const uint32_t n = min(*counter, cap);
+    if (stats && ray_stat >= 0 && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(&stats->v[ray_stat], (unsigned long long)n);
     const int lane = threadIdx.x & 31;
     unsigned long long lost = 0;
     bool has = false, done = false;
@@ -520,8 +522,8 @@ __global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant_
     }
 }
 
-// ev (optional): 5 events recorded around the stages (setup | forward shifts + their visibility +
-// inverse-task emission | inverse shifts + their visibility | merge) for per-stage timing
+// ev (optional): 7 events recorded around the stages (setup | forward shifts | their visibility and
+// the inverse-task emission | inverse shifts | their visibility | merge) for per-stage timing
 cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, int vis_blocks,
                               cudaEvent_t* ev, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(w.counters, 0, kWaveCounters * sizeof(uint32_t), s);
@@ -534,18 +536,21 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
     reuse_units_kernel<<<(unsigned)((nw + 127) / 128), 128, 0, s>>>(a, w, p0, p1);
     if (ev) cudaEventRecord(ev[1], s);
     shift_fwd_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
-    // forward shifts land in the current frame; counter 4 of the stats counted them as successes
-    vis_kernel<<<vis_blocks, 128, 0, s>>>(a.cur.g, w.rays, &w.counters[4], w.ray_cap, &w.counters[6], w.py, a.stats, 4);
-    emit_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
     if (ev) cudaEventRecord(ev[2], s);
+    // forward shifts land in the current frame; counter 4 of the stats counted them as successes
+    vis_kernel<<<vis_blocks, 128, 0, s>>>(a.cur.g, w.rays, &w.counters[4], w.ray_cap, &w.counters[6], w.py, a.stats, 4,
+                                          a.temporal ? -1 : 8);
+    emit_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    if (ev) cudaEventRecord(ev[3], s);
     shift_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    if (ev) cudaEventRecord(ev[4], s);
     // inverse shifts land in the reused domain: the previous frame for the temporal pass (its one
     // reused slot), the current frame for spatial passes
     vis_kernel<<<vis_blocks, 128, 0, s>>>(a.temporal ? a.prev.g : a.cur.g, w.rays, &w.counters[5], w.ray_cap, &w.counters[7],
-                                          w.terms, nullptr, -1);
-    if (ev) cudaEventRecord(ev[3], s);
+                                          w.terms, a.stats, -1, a.temporal ? -1 : 9);
+    if (ev) cudaEventRecord(ev[5], s);
     reuse_merge_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
-    if (ev) cudaEventRecord(ev[4], s);
+    if (ev) cudaEventRecord(ev[6], s);
     return cudaGetLastError();
 }
 

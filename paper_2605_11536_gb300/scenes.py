@@ -52,6 +52,8 @@ class Params:
     d_min: float = 0.01            # minimum reconnection segment length (m)
     ray_eps: float = 1e-4          # ray origin offset along the normal (m)
     flags: int = 0
+    shrink_k: float = 1.0          # Sec. 4.4 shrink mapping: initial gate widened K times (<= 1: off)
+    shrink_fine: int = 0           # trees kept in the gate itself (0: every tree widened, R = 1)
 
 
 @dataclass

@@ -47,7 +47,8 @@ class tof_params(C.Structure):
     _fields_ = [("depth", C.c_int32), ("n_cand", C.c_int32), ("n_spatial", C.c_int32), ("radius", C.c_int32),
                 ("n_spatial_iters", C.c_int32), ("temporal", C.c_int32), ("m_cap", C.c_float),
                 ("newton_max_iter", C.c_int32), ("newton_tol_frac", C.c_float), ("jac_max", C.c_float),
-                ("d_min", C.c_float), ("ray_eps", C.c_float), ("flags", C.c_uint32)]
+                ("d_min", C.c_float), ("ray_eps", C.c_float), ("flags", C.c_uint32), ("shrink_k", C.c_float),
+                ("shrink_fine", C.c_int32)]
 
 
 class tof_job(C.Structure):
@@ -263,10 +264,10 @@ def tof_reservoirs_reset(ctx, view: int):
 
 
 def tof_view_stats(ctx, view: int):
-    a = (C.c_double * 8)()
+    a = (C.c_double * 10)()
     _check(ctx, lib().tof_view_stats(ctx, view, a), "tof_view_stats")
     return dict(newton_calls=a[0], newton_iters=a[1], newton_ok=a[2], shift_calls=a[3], shift_ok=a[4], inv_calls=a[5],
-                spatial_fwd_calls=a[6], spatial_inv_calls=a[7])
+                spatial_fwd_calls=a[6], spatial_inv_calls=a[7], spatial_fwd_rays=a[8], spatial_inv_rays=a[9])
 
 
 def tof_view_profile(ctx, view: int, enable: int = 1):
@@ -274,11 +275,11 @@ def tof_view_profile(ctx, view: int, enable: int = 1):
 
 
 STAGES = ("gbuffer", "initial", "temporal", "spatial", "splat", "frame", "spatial_setup", "spatial_fwd_shift",
-          "spatial_inv_shift", "spatial_merge")
+          "spatial_inv_shift", "spatial_merge", "spatial_fwd_vis", "spatial_inv_vis")
 
 
 def tof_view_stage_ms(ctx, view: int):
-    a = (C.c_float * 10)()
+    a = (C.c_float * 12)()
     _check(ctx, lib().tof_view_stage_ms(ctx, view, a), "tof_view_stage_ms")
     return dict(zip(STAGES, [float(x) for x in a]))
 

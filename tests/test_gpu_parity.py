@@ -183,3 +183,18 @@ def test_pairwise_mis_matches_balance_bitwise_for_one_neighbour():
     for f in range(2):
         assert np.array_equal(np.asarray(a[f]), np.asarray(b[f]))
     assert np.asarray(a[1]).sum() > 0
+
+
+@pytest.mark.parametrize("K,fine,nsp", [(10.0, 0, 1), (4.0, 2, 2), (20.0, 1, 0)])
+def test_shrink_mapping_initial_sampling(K, fine, nsp):
+    """Sec. 4.4 shrink mapping: wide-gate candidates whose RIS winner is shrunk into the 5 cm gate
+    (every tree widened, or combined with canonical gate samples by the balance heuristic), then
+    spatial reuse; same images as the oracle over two frames with temporal reuse."""
+    sc = scenes.box_icosphere(W=64, H=48, frames=2)
+    sc.gates = [(5.0, 0.05)] * 2
+    sc.params.n_spatial, sc.params.radius, sc.params.temporal = nsp, 6, 1
+    sc.params.shrink_k, sc.params.shrink_fine = K, fine
+    o, ok, st, _ = oracle_render(sc, [0, 1])
+    g = gpu_render(sc, [0, 1])
+    for f in range(2):
+        _check(g[f], o[f], min_nonzero=50)
