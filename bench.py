@@ -408,6 +408,58 @@ def _shrink(K, fine):
     return mutate
 
 
+def run_gate_sweep(args, widths=(0.01, 0.03, 0.1, 0.3, 1.0), frames=6, warm=3):
+    """Sec. 6 "Effect of Time Gate Width" / "Gauge Direction Comparison" on the dynamic workload: for
+    gate widths from 1 cm to 1 m, the reuse success rate (successful forward shifts / attempts over
+    the temporal and spatial passes), the Newton iterations and the frame time of the path-length
+    shift with the average-gradient gauge, the two fixed-axis gauges, and naive reuse (no
+    path-length correction)."""
+    import torch
+    from paper_2605_11536_gb300 import scenes, tof
+    sc = workload(seed=1)
+    W, H = sc.sensors[0]["W"], sc.sensors[0]["H"]
+    methods = [("average_gradient", 0), ("axis_t", scenes.FLAG_GAUGE_AXIS_T), ("axis_b", scenes.FLAG_GAUGE_AXIS_B),
+               ("naive", scenes.FLAG_NAIVE_SHIFT)]
+    ctx = tof.tof_create(torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    res = {}
+    try:
+        sid = tof.tof_scene_upload(ctx, sc.verts, sc.tris, sc.tri_object, sc.materials, sc.object_material)
+        out = torch.zeros(H * W, device="cuda")
+        for dL in widths:
+            row = {}
+            for name, flag in methods:
+                p = type(sc.params)(**vars(sc.params))
+                p.flags = flag
+                vid = tof.tof_view_create(ctx, sid, W, H, 0)
+                ms = []
+                with torch.cuda.stream(stream):
+                    for f in range(frames):
+                        if f == warm:
+                            s0 = tof.tof_view_stats(ctx, vid)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        tof.tof_bvh_build(ctx, sid, np.ascontiguousarray(sc.xforms[f].reshape(-1), dtype=np.float32), 0,
+                                          sptr)
+                        tof.tof_render_gated(ctx, sid, vid, sc.sensors[f], sc.emitters[f], (sc.gates[f][0], dL), p, sc.seed,
+                                             f, out.data_ptr(), sptr)
+                        e1.record(stream)
+                        stream.synchronize()
+                        if f >= warm:
+                            ms.append(e0.elapsed_time(e1))
+                s1 = tof.tof_view_stats(ctx, vid)
+                tof.tof_view_destroy(ctx, vid)
+                d = {k: s1[k] - s0[k] for k in s1}
+                row[name] = {"reuse_success": d["shift_ok"] / max(1.0, d["shift_calls"]),
+                             "newton_iters": d["newton_iters"] / max(1.0, d["newton_calls"]),
+                             "ms_per_frame": float(np.mean(ms))}
+            res["%g" % dL] = row
+    finally:
+        tof.tof_destroy(ctx)
+    return res
+
+
 def batch_workload(n=64, seed=3):
     """64 instances over 4 scenes built like the dynamic workload (10k..200k triangles), resolutions
     log-uniform in [64, 1024], gate widths U[0.01, 0.1] m, depths U{2..5}."""
@@ -698,6 +750,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-transient", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -791,6 +844,11 @@ def main():
                 line[key] = run_quality_variant(args, mut)
             except Exception as e:
                 line[key] = {"error": str(e)[:300]}
+    if not args.no_sweep:
+        try:
+            line["gate_width_sweep"] = run_gate_sweep(args)
+        except Exception as e:
+            line["gate_width_sweep"] = {"error": str(e)[:300]}
     if not args.no_transient:
         try:
             line["transient"] = run_transient(args)

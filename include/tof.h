@@ -94,6 +94,14 @@ typedef struct { float t0, width; int32_t B; } tof_bins;
  * target agrees, and need 2k shifts per merge instead of k + k^2.  Not in the paper (which states
  * the balance heuristic only); an optimisation from the ReSTIR literature. */
 #define TOF_FLAG_PAIRWISE_MIS 4u
+/* comparison gauges of the Newton system (Sec. 4.3 "Selecting a Good Gauge Condition"; the default
+ * is the paper's average-gradient gauge): a fixed axis G(xi) = a^T xi of the reconnection
+ * triangle's in-plane frame (the vertex moves along t, or along b), reversible; or the gradient at
+ * the start point alone, which is not reversible (biased under MIS: the paper's counterexample).
+ * At most one of the three. */
+#define TOF_FLAG_GAUGE_AXIS_T 8u
+#define TOF_FLAG_GAUGE_AXIS_B 16u
+#define TOF_FLAG_GAUGE_START 32u
 
 /* reuse / sampling parameters (Sec. 6: path depth, candidates, neighbours, radius, M-cap;
  * Newton tolerance 1 % of the gate width with at most 5 iterations) */

@@ -91,6 +91,9 @@ def _declare(L):
     L.or_newton.restype = C.c_int
     L.or_newton.argtypes = [_dp] * 10 + [_dp, C.c_double, C.c_int, C.c_double, C.c_double, _dp, _dp,
                                          C.POINTER(C.c_int), _dp]
+    L.or_newton_g.restype = C.c_int
+    L.or_newton_g.argtypes = [_dp] * 10 + [_dp, C.c_double, C.c_int, C.c_double, C.c_double, _dp, _dp,
+                                           C.POINTER(C.c_int), _dp, C.c_int]
     L.or_stream_select.restype = C.c_int
     L.or_stream_select.argtypes = [_dp, _dp, C.c_int, _dp]
     L.or_view_reservoir.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, C.POINTER(C.c_int)]
@@ -264,7 +267,10 @@ def length_derivs(p1, p2, o, t, b, xi):
     return L.value, g, h
 
 
-def newton(base, offset, xi, delta, max_iter=5, tol_stop=1e-12, tol_succ=1e-9):
+GAUGES = {"average": 0, "axis_t": 1, "axis_b": 2, "start": 3}
+
+
+def newton(base, offset, xi, delta, max_iter=5, tol_stop=1e-12, tol_succ=1e-9, gauge="average"):
     """base / offset: dict(p1, p2, o, t, b) of the two paths.  Returns (ok, xi', |det|, iters, F)."""
     arrs = [_d(base[k]) for k in ("p1", "p2", "o", "t", "b")] + [_d(offset[k]) for k in ("p1", "p2", "o", "t", "b")]
     xa, xp_ = _d(xi)
@@ -272,8 +278,8 @@ def newton(base, offset, xi, delta, max_iter=5, tol_stop=1e-12, tol_succ=1e-9):
     F = np.zeros(2)
     det = C.c_double()
     it = C.c_int()
-    ok = lib().or_newton(*[a[1] for a in arrs], xp_, float(delta), int(max_iter), float(tol_stop), float(tol_succ),
-                         out.ctypes.data_as(_dp), C.byref(det), C.byref(it), F.ctypes.data_as(_dp))
+    ok = lib().or_newton_g(*[a[1] for a in arrs], xp_, float(delta), int(max_iter), float(tol_stop), float(tol_succ),
+                           out.ctypes.data_as(_dp), C.byref(det), C.byref(it), F.ctypes.data_as(_dp), GAUGES[gauge])
     return bool(ok), out, det.value, it.value, F
 
 

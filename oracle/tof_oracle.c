@@ -423,7 +423,15 @@ typedef struct {
     double shrink_k;     /* Sec. 4.4 shrink mapping: gate widened K times for initial sampling (<= 1: off) */
     int shrink_fine;     /* trees kept in the gate itself (canonical samples); 0 = all trees widened */
 } oparams;
-enum { F_DIRECT = 1, F_NAIVE = 2, F_PAIRWISE = 4 };
+enum { F_DIRECT = 1, F_NAIVE = 2, F_PAIRWISE = 4, F_GAUGE_AXIS_T = 8, F_GAUGE_AXIS_B = 16, F_GAUGE_START = 32 };
+/* gauge of the Newton system (Sec. 4.3 "Selecting a Good Gauge Condition") */
+enum { G_AVERAGE = 0, G_AXIS_T = 1, G_AXIS_B = 2, G_START = 3 };
+static int gauge_of(uint32_t flags) {
+    if (flags & F_GAUGE_AXIS_T) return G_AXIS_T;
+    if (flags & F_GAUGE_AXIS_B) return G_AXIS_B;
+    if (flags & F_GAUGE_START) return G_START;
+    return G_AVERAGE;
+}
 
 /* Sec. 5 "Light Source": a point light (direct NEE) or a collimated laser whose spot acts as a
  * secondary emitter I(w) = P f_s(spot; to laser, w) |cos| (a light ray is traced first). */
@@ -558,6 +566,7 @@ void or_length_derivs(const double* p1d, const double* p2d, const double* od, co
 typedef struct {
     v3 p1x, p2x; oframe2 fx;   /* base path: neighbours and frame of the reconnection vertex */
     v3 p1y, p2y; oframe2 fy;   /* offset path: neighbours and frame (same triangle, its frame) */
+    int gauge;                 /* G_AVERAGE (the paper's choice) or a comparison gauge */
 } onewton;
 
 static void derivs(v3 p1, v3 p2, const oframe2* f, const double xi[2], double* L, double g[2], double h[3]) {
@@ -570,7 +579,10 @@ static void derivs(v3 p1, v3 p2, const oframe2* f, const double xi[2], double* L
  * m = (grad L_x(xi) + grad L_y(xi')) / 2, R the 90-degree rotation (x, y) -> (-y, x).
  * Each gradient is taken on its own path (base path x for xi, offset path y for xi'), which
  * is what makes the gauge symmetric under swapping the two paths (the reversibility argument
- * of the average-gradient gauge). */
+ * of the average-gradient gauge).  The comparison gauges of the same section replace the second
+ * row: a fixed axis G(xi) = a^T xi (G_AXIS_T keeps the b coordinate, moving along t; G_AXIS_B
+ * keeps the t coordinate) or the gradient at the start point alone, m = grad L_x(xi) (G_START,
+ * not reversible: the paper's counterexample). */
 static void eval_F(const onewton* N, const double xi[2], double delta, const double xp[2],
                    double gx[2], double hx[3], double Lx, double F[2], double gy[2], double hy[3], double m[2]) {
     double Ly;
@@ -579,7 +591,10 @@ static void eval_F(const onewton* N, const double xi[2], double delta, const dou
     m[1] = 0.5 * (gx[1] + gy[1]);
     double Rm[2] = {-m[1], m[0]};
     F[0] = Ly - Lx - delta;
-    F[1] = Rm[0] * (xp[0] - xi[0]) + Rm[1] * (xp[1] - xi[1]);
+    if (N->gauge == G_AXIS_T) F[1] = xp[1] - xi[1];
+    else if (N->gauge == G_AXIS_B) F[1] = xp[0] - xi[0];
+    else if (N->gauge == G_START) F[1] = -gx[1] * (xp[0] - xi[0]) + gx[0] * (xp[1] - xi[1]);
+    else F[1] = Rm[0] * (xp[0] - xi[0]) + Rm[1] * (xp[1] - xi[1]);
 }
 
 /* rows of dF/dxi' (A) and dF/dxi (Bm), by differentiating F directly:
@@ -587,7 +602,7 @@ static void eval_F(const onewton* N, const double xi[2], double delta, const dou
  *   dF1/dxi  = -grad L_x(xi),  dF2/dxi  = -(R m + 0.5 H_x(xi) R (xi' - xi))
  * (the printed dF/dxi' second row carries +0.5; the derivative of the stated F, using
  *  R^T = -R, carries -0.5 -- the sign used here, pinned by finite differences in the tests) */
-static void jac_F(const double xi[2], const double xp[2], const double gx[2], const double hx[3],
+static void jac_F(int gauge, const double xi[2], const double xp[2], const double gx[2], const double hx[3],
                   const double gy[2], const double hy[3], const double m[2], double A[4], double Bm[4]) {
     double Rm[2] = {-m[1], m[0]};
     double dd[2] = {xp[0] - xi[0], xp[1] - xi[1]};
@@ -595,8 +610,16 @@ static void jac_F(const double xi[2], const double xp[2], const double gx[2], co
     double HyRd[2] = {hy[0] * Rd[0] + hy[1] * Rd[1], hy[1] * Rd[0] + hy[2] * Rd[1]};
     double HxRd[2] = {hx[0] * Rd[0] + hx[1] * Rd[1], hx[1] * Rd[0] + hx[2] * Rd[1]};
     A[0] = gy[0]; A[1] = gy[1];
-    A[2] = Rm[0] - 0.5 * HyRd[0]; A[3] = Rm[1] - 0.5 * HyRd[1];
     Bm[0] = -gx[0]; Bm[1] = -gx[1];
+    if (gauge == G_AXIS_T) { A[2] = 0.0; A[3] = 1.0; Bm[2] = 0.0; Bm[3] = -1.0; return; }
+    if (gauge == G_AXIS_B) { A[2] = 1.0; A[3] = 0.0; Bm[2] = -1.0; Bm[3] = 0.0; return; }
+    if (gauge == G_START) {
+        /* F2 = (R g_x)^T d: dF2/dxi' = R g_x, dF2/dxi = -(R g_x + H_x R d) */
+        A[2] = -gx[1]; A[3] = gx[0];
+        Bm[2] = -(-gx[1] + HxRd[0]); Bm[3] = -(gx[0] + HxRd[1]);
+        return;
+    }
+    A[2] = Rm[0] - 0.5 * HyRd[0]; A[3] = Rm[1] - 0.5 * HyRd[1];
     Bm[2] = -(Rm[0] + 0.5 * HxRd[0]); Bm[3] = -(Rm[1] + 0.5 * HxRd[1]);
 }
 
@@ -616,7 +639,7 @@ static int newton_solve(const onewton* N, const double xi[2], double delta, int 
         double nF = fmax(fabs(F[0]), fabs(F[1]));
         if (nF <= tol_stop) break;
         double A[4], Bm[4];
-        jac_F(xi, xp, gx, hx, gy, hy, m, A, Bm);
+        jac_F(N->gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
         double det = A[0] * A[3] - A[1] * A[2];
         if (!(fabs(det) > 1e-300)) break;
         double step[2] = {-(A[3] * F[0] - A[1] * F[1]) / det, -(-A[2] * F[0] + A[0] * F[1]) / det};
@@ -642,19 +665,20 @@ static int newton_solve(const onewton* N, const double xi[2], double delta, int 
     *iters = it;
     if (!(fmax(fabs(F[0]), fabs(F[1])) <= tol_succ)) return 0;
     double A[4], Bm[4];
-    jac_F(xi, xp, gx, hx, gy, hy, m, A, Bm);
+    jac_F(N->gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
     double dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
     if (!(fabs(dA) > 0)) return 0;
     *jdet = fabs(dB / dA);
     return isfinite(*jdet);
 }
 
-/* exported for the pins: solve on explicit geometry (both frames given) */
-int or_newton(const double* p1x, const double* p2x, const double* fxo, const double* fxt, const double* fxb,
-              const double* p1y, const double* p2y, const double* fyo, const double* fyt, const double* fyb,
-              const double xi[2], double delta, int max_iter, double tol_stop, double tol_succ,
-              double xp[2], double* jdet, int* iters, double F_out[2]) {
+/* exported for the pins: solve on explicit geometry (both frames given) with a gauge */
+int or_newton_g(const double* p1x, const double* p2x, const double* fxo, const double* fxt, const double* fxb,
+                const double* p1y, const double* p2y, const double* fyo, const double* fyt, const double* fyb,
+                const double xi[2], double delta, int max_iter, double tol_stop, double tol_succ,
+                double xp[2], double* jdet, int* iters, double F_out[2], int gauge) {
     onewton N;
+    N.gauge = gauge;
     N.p1x = vload(p1x); N.p2x = vload(p2x); N.fx.o = vload(fxo); N.fx.t = vload(fxt); N.fx.b = vload(fxb);
     N.p1y = vload(p1y); N.p2y = vload(p2y); N.fy.o = vload(fyo); N.fy.t = vload(fyt); N.fy.b = vload(fyb);
     *jdet = 0; *iters = 0;
@@ -663,6 +687,13 @@ int or_newton(const double* p1x, const double* p2x, const double* fxo, const dou
     derivs(N.p1x, N.p2x, &N.fx, xi, &Lx, gx, hx);
     eval_F(&N, xi, delta, xp, gx, hx, Lx, F_out, gy, hy, m);
     return ok;
+}
+int or_newton(const double* p1x, const double* p2x, const double* fxo, const double* fxt, const double* fxb,
+              const double* p1y, const double* p2y, const double* fyo, const double* fyt, const double* fyb,
+              const double xi[2], double delta, int max_iter, double tol_stop, double tol_succ,
+              double xp[2], double* jdet, int* iters, double F_out[2]) {
+    return or_newton_g(p1x, p2x, fxo, fxt, fxb, p1y, p2y, fyo, fyt, fyb, xi, delta, max_iter, tol_stop, tol_succ, xp, jdet,
+                       iters, F_out, G_AVERAGE);
 }
 
 /* barycentrics (b1, b2) of in-plane coordinates xi on triangle tri */
@@ -797,7 +828,7 @@ static int shift_rec_g(const orec* x, const odomain* Dj, const odomain* Di, cons
     /* (4) Newton solve for xi' (eq. path_length_constraint: L(y') = L(x) + delta, with delta
      * chosen so the sample keeps its position inside the gate of the target domain) */
     onewton N;
-    N.p1x = x->xprev; N.p2x = p2x; N.fx = fx;
+    N.p1x = x->xprev; N.p2x = p2x; N.fx = fx; N.gauge = gauge_of(P->flags);
     N.p1y = yv[r - 1].p; N.p2y = p2y; N.fy = tri_frame(gi, x->p_tri);
     double Lx_seg = vlen(vsub(x->xprev, pbase.p)) + vlen(vsub(p2x, pbase.p));
     /* target gated length tau' of the offset path, and the matching target for L_y(xi') */

@@ -204,7 +204,10 @@ static tof_status check_params(tof_ctx* c, const tof_params* p, int transient) {
     if (p->n_spatial < 0 || p->n_spatial > kMaxNb) return fail(c, TOF_EINVAL, "n_spatial %d outside [0, %d]", p->n_spatial, kMaxNb);
     if (p->radius < 1 || p->radius > 255) return fail(c, TOF_EINVAL, "radius %d outside [1, 255]", p->radius);
     if (p->n_spatial_iters < 0 || p->n_spatial_iters > 4) return fail(c, TOF_EINVAL, "n_spatial_iters outside [0, 4]");
-    if (p->flags & ~(TOF_FLAG_DIRECT | TOF_FLAG_NAIVE_SHIFT | TOF_FLAG_PAIRWISE_MIS)) return fail(c, TOF_EINVAL, "unknown flag bits 0x%x", p->flags);
+    const uint32_t gauges = p->flags & (TOF_FLAG_GAUGE_AXIS_T | TOF_FLAG_GAUGE_AXIS_B | TOF_FLAG_GAUGE_START);
+    if (p->flags & ~(TOF_FLAG_DIRECT | TOF_FLAG_NAIVE_SHIFT | TOF_FLAG_PAIRWISE_MIS | gauges))
+        return fail(c, TOF_EINVAL, "unknown flag bits 0x%x", p->flags);
+    if (gauges & (gauges - 1)) return fail(c, TOF_EINVAL, "at most one gauge flag");
     if (p->newton_max_iter < 0 || p->newton_max_iter > 16) return fail(c, TOF_EINVAL, "newton_max_iter outside [0, 16]");
     if (!(p->m_cap > 0) || !(p->jac_max >= 1) || !(p->newton_tol_frac > 0) || !(p->ray_eps > 0) || !(p->d_min >= 0))
         return fail(c, TOF_EINVAL, "m_cap, jac_max, newton_tol_frac, ray_eps must be positive, d_min >= 0");

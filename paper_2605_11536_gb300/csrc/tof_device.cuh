@@ -681,7 +681,13 @@ static __device__ __forceinline__ void length_derivs(float3 p1, float3 p2, const
     h[2] = (1.0f - d1b * d1b) / l1 + (1.0f - d2b * d2b) / l2;
 }
 
-struct NewtonGeo { float3 p1x, p2x; Frame2 fx; float3 p1y, p2y; Frame2 fy; };
+// gauge of the Newton system: the paper's average gradient, or a comparison gauge of Sec. 4.3
+// (fixed axis: the vertex moves along t or along b; gradient at the start point only)
+enum { G_AVERAGE = 0, G_AXIS_T = 1, G_AXIS_B = 2, G_START = 3 };
+static __device__ __forceinline__ int gauge_of(uint32_t flags) {
+    return (flags & 8u) ? G_AXIS_T : (flags & 16u) ? G_AXIS_B : (flags & 32u) ? G_START : G_AVERAGE;
+}
+struct NewtonGeo { float3 p1x, p2x; Frame2 fx; float3 p1y, p2y; Frame2 fy; int gauge; };
 
 // F(xi, xi') = [L_y(xi') - L_x(xi) - delta ; (R m)^T (xi' - xi)], m = (grad L_x(xi) + grad L_y(xi'))/2,
 // R = 90-degree rotation; each gradient on its own path (Sec. 4.3, average-gradient gauge)
@@ -692,18 +698,34 @@ static __device__ __forceinline__ void newton_F(const NewtonGeo& N, const float 
     m[0] = 0.5f * (gx[0] + gy[0]);
     m[1] = 0.5f * (gx[1] + gy[1]);
     F[0] = Ly - Lx - delta;
-    F[1] = -m[1] * (xp[0] - xi[0]) + m[0] * (xp[1] - xi[1]);
+    if (N.gauge == G_AVERAGE) F[1] = -m[1] * (xp[0] - xi[0]) + m[0] * (xp[1] - xi[1]);
+    else if (N.gauge == G_AXIS_T) F[1] = xp[1] - xi[1];
+    else if (N.gauge == G_AXIS_B) F[1] = xp[0] - xi[0];
+    else F[1] = -gx[1] * (xp[0] - xi[0]) + gx[0] * (xp[1] - xi[1]);
 }
 // dF/dxi' rows: (grad L_y(xi'), R m - 0.5 H_y R (xi' - xi)); dF/dxi rows: (-grad L_x(xi), -(R m + 0.5 H_x R (xi' - xi)))
-static __device__ __forceinline__ void newton_J(const float xi[2], const float xp[2], const float gx[2], const float hx[3],
+// comparison gauges: fixed axis rows (0, 1) / (1, 0); start gradient dF2/dxi' = R g_x,
+// dF2/dxi = -(R g_x + H_x R (xi' - xi))
+static __device__ __forceinline__ void newton_J(int gauge, const float xi[2], const float xp[2], const float gx[2], const float hx[3],
                                          const float gy[2], const float hy[3], const float m[2], float A[4], float Bm[4]) {
     float Rm0 = -m[1], Rm1 = m[0];
     float dd0 = xp[0] - xi[0], dd1 = xp[1] - xi[1];
     float Rd0 = -dd1, Rd1 = dd0;
     float HyRd0 = hy[0] * Rd0 + hy[1] * Rd1, HyRd1 = hy[1] * Rd0 + hy[2] * Rd1;
     float HxRd0 = hx[0] * Rd0 + hx[1] * Rd1, HxRd1 = hx[1] * Rd0 + hx[2] * Rd1;
-    A[0] = gy[0]; A[1] = gy[1]; A[2] = Rm0 - 0.5f * HyRd0; A[3] = Rm1 - 0.5f * HyRd1;
-    Bm[0] = -gx[0]; Bm[1] = -gx[1]; Bm[2] = -(Rm0 + 0.5f * HxRd0); Bm[3] = -(Rm1 + 0.5f * HxRd1);
+    A[0] = gy[0]; A[1] = gy[1];
+    Bm[0] = -gx[0]; Bm[1] = -gx[1];
+    if (gauge == G_AVERAGE) {
+        A[2] = Rm0 - 0.5f * HyRd0; A[3] = Rm1 - 0.5f * HyRd1;
+        Bm[2] = -(Rm0 + 0.5f * HxRd0); Bm[3] = -(Rm1 + 0.5f * HxRd1);
+    } else if (gauge == G_AXIS_T) {
+        A[2] = 0.f; A[3] = 1.f; Bm[2] = 0.f; Bm[3] = -1.f;
+    } else if (gauge == G_AXIS_B) {
+        A[2] = 1.f; A[3] = 0.f; Bm[2] = -1.f; Bm[3] = 0.f;
+    } else {
+        A[2] = -gx[1]; A[3] = gx[0];
+        Bm[2] = -(-gx[1] + HxRd0); Bm[3] = -(gx[0] + HxRd1);
+    }
 }
 
 // Newton iteration with backtracking (Sec. 4.3); returns success, xi', |det(dxi'/dxi)| and the
@@ -720,7 +742,7 @@ static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float
         float nF = fmaxf(fabsf(F[0]), fabsf(F[1]));
         if (nF <= tol_stop) break;
         float A[4], Bm[4];
-        newton_J(xi, xp, gx, hx, gy, hy, m, A, Bm);
+        newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
         float det = A[0] * A[3] - A[1] * A[2];
         if (!(fabsf(det) > 1e-30f)) break;
         float s0 = -(A[3] * F[0] - A[1] * F[1]) / det, s1 = -(-A[2] * F[0] + A[0] * F[1]) / det;
@@ -746,7 +768,7 @@ static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float
     iters = it;
     if (!(fmaxf(fabsf(F[0]), fabsf(F[1])) <= tol_succ)) return false;
     float A[4], Bm[4];
-    newton_J(xi, xp, gx, hx, gy, hy, m, A, Bm);
+    newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
     float dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
     if (!(fabsf(dA) > 0.f)) return false;
     jdet = fabsf(dB / dA);
@@ -830,7 +852,7 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
         xi[0] = dot3(dd, N.fx.t);
         xi[1] = dot3(dd, N.fx.b);
     }
-    N.p1x = x.xprev; N.p2x = p2x;
+    N.p1x = x.xprev; N.p2x = p2x; N.gauge = gauge_of(P.flags);
     N.p1y = yv[r - 1].p; N.p2y = p2y; N.fy = tri_frame(gi, x.p_tri);
 
     // (4) Newton solve of L(y') = L(x) + delta (eq. path_length_constraint), delta keeping the

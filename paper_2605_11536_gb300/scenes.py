@@ -35,6 +35,9 @@ EMIT_POINT, EMIT_LASER, EMIT_CONFOCAL = 0, 1, 2
 FLAG_DIRECT = 1          # include length-1 (direct) candidates
 FLAG_NAIVE_SHIFT = 2     # hybrid shift without the path-length Newton correction
 FLAG_PAIRWISE_MIS = 4    # pairwise MIS instead of the generalized balance heuristic (2k shifts)
+FLAG_GAUGE_AXIS_T = 8    # comparison gauge: fixed axis, the reconnection vertex moves along t
+FLAG_GAUGE_AXIS_B = 16   # comparison gauge: fixed axis, the reconnection vertex moves along b
+FLAG_GAUGE_START = 32    # comparison gauge: gradient at the start point only (not reversible)
 
 
 @dataclass

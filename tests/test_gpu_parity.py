@@ -198,3 +198,18 @@ def test_shrink_mapping_initial_sampling(K, fine, nsp):
     g = gpu_render(sc, [0, 1])
     for f in range(2):
         _check(g[f], o[f], min_nonzero=50)
+
+
+@pytest.mark.parametrize("flag", [scenes.FLAG_GAUGE_AXIS_T, scenes.FLAG_GAUGE_AXIS_B, scenes.FLAG_GAUGE_START,
+                                  scenes.FLAG_NAIVE_SHIFT])
+def test_comparison_gauges_and_naive_reuse(flag):
+    """Sec. 4.3 comparison gauges (fixed axes, start-point gradient) and naive reuse (no
+    path-length correction): same images as the oracle with spatial and temporal reuse."""
+    sc = scenes.box_icosphere(W=48, H=40, frames=2)
+    sc.gates = [(5.0, 0.25)] * 2
+    sc.params.n_spatial, sc.params.radius, sc.params.temporal = 3, 6, 1
+    sc.params.flags = flag
+    o, ok, st, _ = oracle_render(sc, [0, 1])
+    g = gpu_render(sc, [0, 1])
+    for f in range(2):
+        _check(g[f], o[f])

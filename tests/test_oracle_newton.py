@@ -130,3 +130,46 @@ def test_printed_sign_of_gauge_row_disagrees_with_fd(oracle_lib):
     fd = abs(np.linalg.det(Jfd))
     assert det_derived == pytest.approx(fd, rel=2e-5)
     assert abs(det_printed - fd) > 1e-3 * fd
+
+
+@pytest.mark.parametrize("gauge", ["axis_t", "axis_b", "start"])
+def test_comparison_gauges_jacobian_fd(oracle_lib, gauge):
+    """The comparison gauges of Sec. 4.3 (fixed axis G(xi) = a^T xi, start-point gradient): the
+    implicit-function determinant of each matches central differences of its solved map."""
+    O = oracle_lib
+    base, off, xi = _setup(9)
+    delta = 0.03
+    kw = dict(max_iter=30, tol_stop=1e-14, tol_succ=1e-10, gauge=gauge)
+    ok, xp, det, it, F = O.newton(base, off, xi, delta, **kw)
+    assert ok and abs(F[0]) < 1e-10 and abs(F[1]) < 1e-10
+    h = 1e-5
+    Jfd = np.zeros((2, 2))
+    for i in range(2):
+        e = np.zeros(2)
+        e[i] = h
+        Jfd[:, i] = (O.newton(base, off, xi + e, delta, **kw)[1] - O.newton(base, off, xi - e, delta, **kw)[1]) / (2 * h)
+    assert abs(np.linalg.det(Jfd)) == pytest.approx(det, rel=2e-5)
+    if gauge == "axis_t":
+        assert xp[1] == pytest.approx(xi[1], abs=1e-12)
+    if gauge == "axis_b":
+        assert xp[0] == pytest.approx(xi[0], abs=1e-12)
+
+
+def test_axis_gauges_reversible_start_gradient_is_not(oracle_lib):
+    """Sec. 4.3: a fixed axis and the average gradient are reversible (solving back with -delta
+    returns xi, the determinants multiply to 1); moving along the start point's gradient alone is
+    not, unless the gradients at both ends are parallel."""
+    O = oracle_lib
+    base, _, xi = _setup(10)
+    delta = 0.15
+    kw = dict(max_iter=40, tol_stop=1e-15, tol_succ=1e-10)
+    for gauge in ("average", "axis_t", "axis_b", "start"):
+        ok, xp, det, *_ = O.newton(base, base, xi, delta, gauge=gauge, **kw)
+        assert ok, gauge
+        ok2, xb, det2, *_ = O.newton(base, base, xp, -delta, gauge=gauge, **kw)
+        assert ok2, gauge
+        err = float(np.abs(xb - xi).max())
+        if gauge == "start":
+            assert err > 1e-4, err
+        else:
+            assert err < 1e-9 and det * det2 == pytest.approx(1.0, rel=1e-8), (gauge, err)
