@@ -398,14 +398,25 @@ def _all_rough(sc):
         int(np.count_nonzero((orig[:, 0] == scenes.GGX) & (orig[:, 2] < 0.2))), len(mats))
 
 
-def _shrink(K, fine):
+def _shrink(K, fine, walk=False):
     def mutate(sc):
+        from paper_2605_11536_gb300 import scenes
         sc.params = type(sc.params)(**vars(sc.params))
         sc.params.shrink_k, sc.params.shrink_fine = K, fine
+        if walk:
+            sc.params.flags |= scenes.FLAG_TRIANGLE_WALK
         return "shrink mapping (Sec. 4.4): gate widened K = %g times for initial sampling, %d of %d trees kept in " \
-               "the gate (R = %.2f)%s" % (K, fine, sc.params.n_cand, 1 - fine / sc.params.n_cand,
-                                            "; biased (darker) by design" if fine == 0 else "; unbiased")
+               "the gate (R = %.2f)%s%s" % (K, fine, sc.params.n_cand, 1 - fine / sc.params.n_cand,
+                                              "; biased (darker) by design" if fine == 0 else "; unbiased",
+                                              "; cross-triangle walk" if walk else "")
     return mutate
+
+
+def _walk(sc):
+    from paper_2605_11536_gb300 import scenes
+    sc.params = type(sc.params)(**vars(sc.params))
+    sc.params.flags |= scenes.FLAG_TRIANGLE_WALK
+    return "the headline configuration with the cross-triangle walk of the reconnection vertex"
 
 
 def run_gate_sweep(args, widths=(0.01, 0.03, 0.1, 0.3, 1.0), frames=6, warm=3):
@@ -838,7 +849,11 @@ def main():
                                  "spatial_inverse_segments": pf["spatial_inv_rays"]},
             "wall_s": r["wall"]}
     if not args.no_quality:
-        for key, mut in (("quality_shrink_K10_R1", _shrink(10.0, 0)), ("quality_shrink_K10_R05", _shrink(10.0, 2)),
+        for key, mut in (("quality_walk", _walk), ("quality_shrink_K10_R1", _shrink(10.0, 0)),
+                         ("quality_shrink_K10_R1_walk", _shrink(10.0, 0, walk=True)),
+                         ("quality_shrink_K3_R1_walk", _shrink(3.0, 0, walk=True)),
+                         ("quality_shrink_K10_R05", _shrink(10.0, 2)), ("quality_shrink_K10_R05_walk", _shrink(10.0, 2, walk=True)),
+                         ("quality_shrink_K3_R05_walk", _shrink(3.0, 2, walk=True)),
                          ("quality_all_rough_variant", _all_rough)):
             try:
                 line[key] = run_quality_variant(args, mut)

@@ -102,6 +102,12 @@ typedef struct { float t0, width; int32_t B; } tof_bins;
 #define TOF_FLAG_GAUGE_AXIS_T 8u
 #define TOF_FLAG_GAUGE_AXIS_B 16u
 #define TOF_FLAG_GAUGE_START 32u
+/* cross-triangle walk of the reconnection vertex: when Newton moves the vertex off its triangle,
+ * it continues on the neighbour across the edge it crossed (the neighbour unfolded into the
+ * triangle's plane about the shared edge), instead of failing the shift.  Neighbours share an edge
+ * (two vertex indices) within one object.  Shifts stay reversible; on planar surfaces the result
+ * no longer depends on the tessellation. */
+#define TOF_FLAG_TRIANGLE_WALK 64u
 
 /* reuse / sampling parameters (Sec. 6: path depth, candidates, neighbours, radius, M-cap;
  * Newton tolerance 1 % of the gate width with at most 5 iterations) */

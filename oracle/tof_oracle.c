@@ -200,6 +200,8 @@ typedef struct {
     int nnodes;
     onode* nodes;
     int* prim;
+    int* adj;       /* nt*3: across the edge opposite vertex i of t, 4 * neighbour + the neighbour's
+                       vertex opposite that edge, or -1 (boundary, non-manifold or another object) */
 } ogeom;
 
 static const double* tri_v(const ogeom* g, int t) { return g->tv + 9 * (size_t)t; }
@@ -244,6 +246,39 @@ static int bvh_build_rec(ogeom* g, double* cent, int start, int count) {
     return id;
 }
 
+/* edge adjacency from the index buffer: an edge (its two vertex indices) shared by exactly two
+ * triangles of one object links them */
+typedef struct { uint32_t a, b; int tri, opp; } oedge;
+static int cmp_edge(const void* x, const void* y) {
+    const oedge* e = (const oedge*)x;
+    const oedge* f = (const oedge*)y;
+    if (e->a != f->a) return e->a < f->a ? -1 : 1;
+    if (e->b != f->b) return e->b < f->b ? -1 : 1;
+    return e->tri - f->tri;
+}
+static void build_adjacency(ogeom* g, const uint32_t* tris, const uint32_t* tri_obj, int nt) {
+    g->adj = (int*)malloc(sizeof(int) * 3 * (size_t)(nt > 0 ? nt : 1));
+    oedge* E = (oedge*)malloc(sizeof(oedge) * 3 * (size_t)(nt > 0 ? nt : 1));
+    for (int t = 0; t < nt; ++t)
+        for (int i = 0; i < 3; ++i) {
+            uint32_t u = tris[3 * t + (i + 1) % 3], w = tris[3 * t + (i + 2) % 3];
+            oedge* e = &E[3 * t + i];
+            e->a = u < w ? u : w; e->b = u < w ? w : u; e->tri = t; e->opp = i;
+            g->adj[3 * t + i] = -1;
+        }
+    qsort(E, 3 * (size_t)nt, sizeof(oedge), cmp_edge);
+    for (int k = 0; k < 3 * nt;) {
+        int m = k + 1;
+        while (m < 3 * nt && E[m].a == E[k].a && E[m].b == E[k].b) ++m;
+        if (m - k == 2 && tri_obj[E[k].tri] == tri_obj[E[k + 1].tri] && E[k].tri != E[k + 1].tri) {
+            g->adj[3 * E[k].tri + E[k].opp] = 4 * E[k + 1].tri + E[k + 1].opp;
+            g->adj[3 * E[k + 1].tri + E[k + 1].opp] = 4 * E[k].tri + E[k].opp;
+        }
+        k = m;
+    }
+    free(E);
+}
+
 /* verts: object-local vertices; xforms: nobj row-major 3x4 object-to-world matrices */
 ogeom* or_geom_create(const double* verts, int nv, const uint32_t* tris, int nt, const uint32_t* tri_obj,
                       const uint32_t* obj_mat, int nobj, const double* mats, int nmat, const double* xforms) {
@@ -276,12 +311,13 @@ ogeom* or_geom_create(const double* verts, int nv, const uint32_t* tris, int nt,
     g->nnodes = 0;
     if (nt > 0) bvh_build_rec(g, cent, 0, nt);
     free(cent);
+    build_adjacency(g, tris, tri_obj, nt);
     return g;
 }
 
 void or_geom_destroy(ogeom* g) {
     if (!g) return;
-    free(g->tv); free(g->tmat); free(g->mats); free(g->xf); free(g->nodes); free(g->prim); free(g);
+    free(g->tv); free(g->tmat); free(g->mats); free(g->xf); free(g->nodes); free(g->prim); free(g->adj); free(g);
 }
 
 /* Moller-Trumbore ray/triangle test (Moller, Trumbore 1997); t in (tmin, tmax).  The barycentric
@@ -423,7 +459,8 @@ typedef struct {
     double shrink_k;     /* Sec. 4.4 shrink mapping: gate widened K times for initial sampling (<= 1: off) */
     int shrink_fine;     /* trees kept in the gate itself (canonical samples); 0 = all trees widened */
 } oparams;
-enum { F_DIRECT = 1, F_NAIVE = 2, F_PAIRWISE = 4, F_GAUGE_AXIS_T = 8, F_GAUGE_AXIS_B = 16, F_GAUGE_START = 32 };
+enum { F_DIRECT = 1, F_NAIVE = 2, F_PAIRWISE = 4, F_GAUGE_AXIS_T = 8, F_GAUGE_AXIS_B = 16, F_GAUGE_START = 32,
+       F_WALK = 64 };
 /* gauge of the Newton system (Sec. 4.3 "Selecting a Good Gauge Condition") */
 enum { G_AVERAGE = 0, G_AXIS_T = 1, G_AXIS_B = 2, G_START = 3 };
 static int gauge_of(uint32_t flags) {
@@ -711,6 +748,147 @@ static void point_to_xi(const oframe2* f, v3 p, double xi[2]) {
 }
 
 /* ============================================================================================
+ * cross-triangle walk of the reconnection vertex (reading R25; the paper parameterises p on the
+ * surface, Sec. 4.2, without saying what happens at a triangle's edge).  The Newton unknown xi'
+ * lives in a 2-D chart: the plane of p's triangle, into which each neighbour entered is unfolded
+ * about the shared edge (an isometry, so lengths, gradients and |det| carry over).  A candidate
+ * that leaves the current triangle crosses its exit edge into the neighbour; the walk fails at a
+ * boundary or after MAX_CROSS crossings.  Two developments of one triangle strip differ by a rigid
+ * motion, under which the average-gradient gauge is invariant, so the walk keeps the shift
+ * reversible.
+ * ==========================================================================================*/
+#define MAX_CROSS 8
+typedef struct { int tri; oframe2 f; double q[3][2]; } owalk;   /* f: chart -> 3-D on tri; q: its corners */
+
+static void walk_init(const ogeom* g, int tri, owalk* W) {
+    W->tri = tri;
+    W->f = tri_frame(g, tri);
+    const double* v = tri_v(g, tri);
+    for (int j = 0; j < 3; ++j) {
+        v3 d = vsub(vload(v + 3 * j), W->f.o);
+        W->q[j][0] = vdot(d, W->f.t);
+        W->q[j][1] = vdot(d, W->f.b);
+    }
+}
+static void walk_bary(const owalk* W, const double c[2], double lam[3]) {
+    double a0 = W->q[1][0] - W->q[0][0], a1 = W->q[1][1] - W->q[0][1];
+    double b0 = W->q[2][0] - W->q[0][0], b1 = W->q[2][1] - W->q[0][1];
+    double d0 = c[0] - W->q[0][0], d1 = c[1] - W->q[0][1];
+    double det = a0 * b1 - a1 * b0;
+    lam[1] = (d0 * b1 - d1 * b0) / det;
+    lam[2] = (a0 * d1 - a1 * d0) / det;
+    lam[0] = 1.0 - lam[1] - lam[2];
+}
+/* move W along the chart segment from -> to (from inside W) until the triangle holding `to` */
+static int walk_locate(const ogeom* g, owalk* W, const double from_in[2], const double to[2]) {
+    double from[2] = {from_in[0], from_in[1]};
+    for (int k = 0; k <= MAX_CROSS; ++k) {
+        double lt[3], lf[3];
+        walk_bary(W, to, lt);
+        if (lt[0] >= -BARY_EPS && lt[1] >= -BARY_EPS && lt[2] >= -BARY_EPS) return 1;
+        if (k == MAX_CROSS) break;
+        walk_bary(W, from, lf);
+        int ex = -1;
+        double sbest = 1e300;
+        for (int i = 0; i < 3; ++i) {
+            if (!(lt[i] < -BARY_EPS)) continue;
+            double den = lf[i] - lt[i];
+            double sx = den > 0 ? lf[i] / den : 0.0;
+            if (sx < 0) sx = 0;
+            if (sx < sbest) { sbest = sx; ex = i; }
+        }
+        if (ex < 0) return 0;
+        int n = g->adj[3 * W->tri + ex];
+        if (n < 0) return 0;
+        int nb = n >> 2, opp = n & 3;
+        int ia = (ex + 1) % 3, ib = (ex + 2) % 3;
+        const double* v = tri_v(g, W->tri);
+        v3 A = vload(v + 3 * ia), B = vload(v + 3 * ib), C = vload(tri_v(g, nb) + 3 * opp);
+        double a[2] = {W->q[ia][0], W->q[ia][1]}, b[2] = {W->q[ib][0], W->q[ib][1]};
+        /* 3-D: edge direction U and in-plane normal N toward the neighbour's third corner;
+         * chart: edge direction u and normal n away from the current triangle's third corner */
+        v3 U = vnorm(vsub(B, A));
+        v3 CA = vsub(C, A);
+        v3 Nv = vnorm(vsub(CA, vmul(U, vdot(CA, U))));
+        double ul = hypot(b[0] - a[0], b[1] - a[1]);
+        double u[2] = {(b[0] - a[0]) / ul, (b[1] - a[1]) / ul};
+        double nn[2] = {-u[1], u[0]};
+        if ((W->q[ex][0] - a[0]) * nn[0] + (W->q[ex][1] - a[1]) * nn[1] > 0) { nn[0] = -nn[0]; nn[1] = -nn[1]; }
+        /* p(c) = A + ((c - a).u) U + ((c - a).n) N = o + c0 t + c1 b */
+        owalk Nw;
+        Nw.tri = nb;
+        Nw.f.t = vadd(vmul(U, u[0]), vmul(Nv, nn[0]));
+        Nw.f.b = vadd(vmul(U, u[1]), vmul(Nv, nn[1]));
+        Nw.f.o = vsub(A, vadd(vmul(U, a[0] * u[0] + a[1] * u[1]), vmul(Nv, a[0] * nn[0] + a[1] * nn[1])));
+        const double* vn = tri_v(g, nb);
+        for (int j = 0; j < 3; ++j) {
+            v3 d = vsub(vload(vn + 3 * j), Nw.f.o);
+            Nw.q[j][0] = vdot(d, Nw.f.t);
+            Nw.q[j][1] = vdot(d, Nw.f.b);
+        }
+        from[0] += sbest * (to[0] - from[0]);
+        from[1] += sbest * (to[1] - from[1]);
+        *W = Nw;
+    }
+    return 0;
+}
+
+/* newton_solve with the offset vertex walking across triangles (W: its triangle and chart) */
+static int newton_solve_walk(const ogeom* gi, const onewton* N0, owalk* W, const double xi[2], double delta, int max_iter,
+                             double tol_stop, double tol_succ, double xp[2], double* jdet, int* iters) {
+    onewton N = *N0;
+    N.fy = W->f;
+    double Lx, gx[2], hx[3];
+    derivs(N.p1x, N.p2x, &N.fx, xi, &Lx, gx, hx);
+    xp[0] = xi[0]; xp[1] = xi[1];
+    double F[2], gy[2], hy[3], m[2];
+    eval_F(&N, xi, delta, xp, gx, hx, Lx, F, gy, hy, m);
+    int it = 0;
+    while (it < max_iter) {
+        double nF = fmax(fabs(F[0]), fabs(F[1]));
+        if (nF <= tol_stop) break;
+        double A[4], Bm[4];
+        jac_F(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
+        double det = A[0] * A[3] - A[1] * A[2];
+        if (!(fabs(det) > 1e-300)) break;
+        double step[2] = {-(A[3] * F[0] - A[1] * F[1]) / det, -(-A[2] * F[0] + A[0] * F[1]) / det};
+        double lam = 1.0;
+        int accepted = 0;
+        for (int ls = 0; ls < 5; ++ls) {
+            double cand[2] = {xp[0] + lam * step[0], xp[1] + lam * step[1]};
+            owalk Wc = *W;
+            if (walk_locate(gi, &Wc, xp, cand)) {
+                onewton Nc = N;
+                Nc.fy = Wc.f;
+                double Fc[2], gyc[2], hyc[3], mc[2];
+                eval_F(&Nc, xi, delta, cand, gx, hx, Lx, Fc, gyc, hyc, mc);
+                if (fmax(fabs(Fc[0]), fabs(Fc[1])) < nF) {
+                    xp[0] = cand[0]; xp[1] = cand[1];
+                    F[0] = Fc[0]; F[1] = Fc[1];
+                    gy[0] = gyc[0]; gy[1] = gyc[1]; hy[0] = hyc[0]; hy[1] = hyc[1]; hy[2] = hyc[2];
+                    m[0] = mc[0]; m[1] = mc[1];
+                    *W = Wc;
+                    N.fy = Wc.f;
+                    accepted = 1;
+                    break;
+                }
+            }
+            lam *= 0.5;
+        }
+        if (!accepted) break;
+        ++it;
+    }
+    *iters = it;
+    if (!(fmax(fabs(F[0]), fabs(F[1])) <= tol_succ)) return 0;
+    double A[4], Bm[4];
+    jac_F(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
+    double dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
+    if (!(fabs(dA) > 0)) return 0;
+    *jdet = fabs(dB / dA);
+    return isfinite(*jdet);
+}
+
+/* ============================================================================================
  * path evaluation helpers
  * ==========================================================================================*/
 /* geometry term between two surface points (no visibility) */
@@ -837,20 +1015,31 @@ static int shift_rec_g(const orec* x, const odomain* Dj, const odomain* Di, cons
     double delta = ell - Lx_seg;
     double xp[2], jnewton = 1.0;
     int iters = 0;
+    const int walk = (P->flags & F_WALK) && !(P->flags & F_NAIVE);
+    owalk W;
+    if (walk) walk_init(gi, x->p_tri, &W);
     if (P->flags & F_NAIVE) {
         xp[0] = xi[0]; xp[1] = xi[1];
     } else {
         double tol_stop = 1e-6 * fabs(gm ? tau_t + Di->o : x->tau + Di->o + Di->L0 - Dj->L0);
         double tol_succ = P->newton_tol_frac * (gm ? gm->hi - gm->lo : Di->dL);
-        int ok = newton_solve(&N, xi, delta, P->newton_max_iter, tol_stop, tol_succ, xp, &jnewton, &iters);
+        int ok = walk ? newton_solve_walk(gi, &N, &W, xi, delta, P->newton_max_iter, tol_stop, tol_succ, xp, &jnewton, &iters)
+                      : newton_solve(&N, xi, delta, P->newton_max_iter, tol_stop, tol_succ, xp, &jnewton, &iters);
         if (st) { stat_add(&st->newton_calls, 1); stat_add(&st->newton_iters, iters); if (ok) stat_add(&st->newton_ok, 1); }
         if (!ok) return 0;
         if (!(jnewton >= 1.0 / P->jac_max && jnewton <= P->jac_max)) return 0;
     }
     double nb1, nb2;
-    xi_to_bary(gi, x->p_tri, &N.fy, xp, &nb1, &nb2);
+    int ptri = x->p_tri;
+    if (walk) {
+        double lam[3];
+        walk_bary(&W, xp, lam);
+        ptri = W.tri; nb1 = lam[1]; nb2 = lam[2];
+    } else {
+        xi_to_bary(gi, x->p_tri, &N.fy, xp, &nb1, &nb2);
+    }
     if (!(nb1 >= -BARY_EPS && nb2 >= -BARY_EPS && nb1 + nb2 <= 1.0 + BARY_EPS)) return 0;
-    osurf pp = surf_at(gi, x->p_tri, nb1, nb2);
+    osurf pp = surf_at(gi, ptri, nb1, nb2);
 
     /* (5) the offset path must reconnect at the same index (bijectivity of the hybrid shift) */
     {
@@ -925,7 +1114,7 @@ static int shift_rec_g(const orec* x, const odomain* Dj, const odomain* Di, cons
     y->tau = tau;
     y->xprev = yv[r - 1].p;
     y->pdf_pre = pdf_pre_y;
-    y->p_b1 = nb1; y->p_b2 = nb2;
+    y->p_tri = ptri; y->p_b1 = nb1; y->p_b2 = nb2;
     y->Lsuf = Lsuf_i;
     y->phat = f;
     *phat_out = f;

@@ -57,6 +57,7 @@ struct SceneH {
     uint32_t* prim = nullptr;   // points into vals after a build
     int *child = nullptr, *parent_int = nullptr, *parent_leaf = nullptr;
     uint32_t* counter = nullptr;
+    int* adj = nullptr;          // edge adjacency (original triangle order)
     float4* tri[2] = {nullptr, nullptr};
     float4* leaf[2] = {nullptr, nullptr};
     float4* nodes[2] = {nullptr, nullptr};
@@ -205,7 +206,7 @@ static tof_status check_params(tof_ctx* c, const tof_params* p, int transient) {
     if (p->radius < 1 || p->radius > 255) return fail(c, TOF_EINVAL, "radius %d outside [1, 255]", p->radius);
     if (p->n_spatial_iters < 0 || p->n_spatial_iters > 4) return fail(c, TOF_EINVAL, "n_spatial_iters outside [0, 4]");
     const uint32_t gauges = p->flags & (TOF_FLAG_GAUGE_AXIS_T | TOF_FLAG_GAUGE_AXIS_B | TOF_FLAG_GAUGE_START);
-    if (p->flags & ~(TOF_FLAG_DIRECT | TOF_FLAG_NAIVE_SHIFT | TOF_FLAG_PAIRWISE_MIS | gauges))
+    if (p->flags & ~(TOF_FLAG_DIRECT | TOF_FLAG_NAIVE_SHIFT | TOF_FLAG_PAIRWISE_MIS | TOF_FLAG_TRIANGLE_WALK | gauges))
         return fail(c, TOF_EINVAL, "unknown flag bits 0x%x", p->flags);
     if (gauges & (gauges - 1)) return fail(c, TOF_EINVAL, "at most one gauge flag");
     if (p->newton_max_iter < 0 || p->newton_max_iter > 16) return fail(c, TOF_EINVAL, "newton_max_iter outside [0, 16]");
@@ -241,6 +242,7 @@ static FrameDev make_frame(const SceneH& S, int slot, const tof_sensor* s, const
     FrameDev F;
     memset(&F, 0, sizeof(F));
     F.g.tri = S.tri[slot]; F.g.leaf = S.leaf[slot]; F.g.nodes = S.nodes[slot]; F.g.mats = S.mats; F.g.nt = S.nt;
+    F.g.adj = S.adj;
     F.g.version = S.version[slot];
     F.mode = s->mode; F.W = s->W; F.H = s->H;
     F.pos = v3f(s->pos); F.fwd = v3f(s->fwd); F.up = v3f(s->up); F.fov_y = s->fov_y;
@@ -412,6 +414,31 @@ tof_status tof_scene_upload(tof_ctx* c, const float* verts, uint32_t nv, const u
     CK(cudaMemcpy(S.triobj, tri_object, sizeof(uint32_t) * nt, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(S.objmat, object_material, sizeof(uint32_t) * nobj, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(S.mats, mh.data(), sizeof(float4) * nmat, cudaMemcpyHostToDevice));
+    {
+        // edge adjacency: an edge (two vertex indices) shared by exactly two triangles of one object
+        struct Edge { uint32_t a, b, t, opp; };
+        std::vector<Edge> E((size_t)nt * 3);
+        for (uint32_t t = 0; t < nt; ++t)
+            for (uint32_t i = 0; i < 3; ++i) {
+                uint32_t u = tris[3 * t + (i + 1) % 3], w = tris[3 * t + (i + 2) % 3];
+                E[3 * t + i] = Edge{u < w ? u : w, u < w ? w : u, t, i};
+            }
+        std::sort(E.begin(), E.end(), [](const Edge& x, const Edge& y) {
+            return x.a != y.a ? x.a < y.a : x.b != y.b ? x.b < y.b : x.t < y.t;
+        });
+        std::vector<int> adj((size_t)nt * 3, -1);
+        for (size_t k = 0; k < E.size();) {
+            size_t m = k + 1;
+            while (m < E.size() && E[m].a == E[k].a && E[m].b == E[k].b) ++m;
+            if (m - k == 2 && tri_object[E[k].t] == tri_object[E[k + 1].t] && E[k].t != E[k + 1].t) {
+                adj[3 * (size_t)E[k].t + E[k].opp] = (int)(4 * E[k + 1].t + E[k + 1].opp);
+                adj[3 * (size_t)E[k + 1].t + E[k + 1].opp] = (int)(4 * E[k].t + E[k].opp);
+            }
+            k = m;
+        }
+        TRY(dalloc(c, &S.adj, sizeof(int) * 3 * (size_t)nt, "adjacency"));
+        CK(cudaMemcpy(S.adj, adj.data(), sizeof(int) * 3 * (size_t)nt, cudaMemcpyHostToDevice));
+    }
     S.alive = true;
     c->scenes.push_back(S);
     *out = (tof_scene)(c->scenes.size() - 1);
@@ -424,7 +451,8 @@ tof_status tof_scene_destroy(tof_ctx* c, tof_scene id) {
     cudaDeviceSynchronize();
     SceneH& S = c->scenes[id];
     void* ps[] = {S.vloc, S.tris, S.triobj, S.objmat, S.mats, S.xf, S.cent, S.keys, S.vals, S.keys2, S.vals2, S.hist, S.bb,
-                  S.child, S.parent_int, S.parent_leaf, S.counter, S.tri[0], S.tri[1], S.leaf[0], S.leaf[1], S.nodes[0], S.nodes[1]};
+                  S.child, S.parent_int, S.parent_leaf, S.counter, S.tri[0], S.tri[1], S.leaf[0], S.leaf[1], S.nodes[0], S.nodes[1],
+                  S.adj};
     for (void* p : ps) dfree(c, p);
     S = SceneH();
     return TOF_OK;
@@ -552,9 +580,10 @@ static tof_status ensure_wave(tof_ctx* c, ViewH& V, int S, int cap) {
     TRY(dalloc(c, &w.jac, sizeof(float) * U * S, "shift Jacobians"));
     TRY(dalloc(c, &w.terms, sizeof(float) * U * S * S, "MIS terms"));
     // queued visibility segments: two per inverse shift would need up to 2 U S (S - 1); a pass
-    // shifts far fewer, and segments beyond the queue are traced in place
+    // shifts far fewer (a 512 x 512 spatial pass with 5 neighbours queues 3-6 M), and segments
+    // beyond the queue are traced in place
     size_t rcap = 2 * U * S * (S - 1);
-    size_t rmax = npix * 16 > ((size_t)1 << 22) ? npix * 16 : ((size_t)1 << 22);
+    size_t rmax = npix * 24 + ((size_t)1 << 20);
     if (rcap > rmax) rcap = rmax;
     TRY(dalloc(c, &w.rays, sizeof(float4) * 2 * rcap, "visibility queue"));
     w.ray_cap = (uint32_t)rcap;

@@ -691,10 +691,10 @@ struct NewtonGeo { float3 p1x, p2x; Frame2 fx; float3 p1y, p2y; Frame2 fy; int g
 
 // F(xi, xi') = [L_y(xi') - L_x(xi) - delta ; (R m)^T (xi' - xi)], m = (grad L_x(xi) + grad L_y(xi'))/2,
 // R = 90-degree rotation; each gradient on its own path (Sec. 4.3, average-gradient gauge)
-static __device__ __forceinline__ void newton_F(const NewtonGeo& N, const float xi[2], float Lx, const float gx[2], float delta,
-                                         const float xp[2], float F[2], float gy[2], float hy[3], float m[2]) {
+static __device__ __forceinline__ void newton_F_f(const NewtonGeo& N, const Frame2& fy, const float xi[2], float Lx, const float gx[2],
+                                           float delta, const float xp[2], float F[2], float gy[2], float hy[3], float m[2]) {
     float Ly;
-    length_derivs(N.p1y, N.p2y, N.fy, xp[0], xp[1], Ly, gy, hy);
+    length_derivs(N.p1y, N.p2y, fy, xp[0], xp[1], Ly, gy, hy);
     m[0] = 0.5f * (gx[0] + gy[0]);
     m[1] = 0.5f * (gx[1] + gy[1]);
     F[0] = Ly - Lx - delta;
@@ -702,6 +702,10 @@ static __device__ __forceinline__ void newton_F(const NewtonGeo& N, const float 
     else if (N.gauge == G_AXIS_T) F[1] = xp[1] - xi[1];
     else if (N.gauge == G_AXIS_B) F[1] = xp[0] - xi[0];
     else F[1] = -gx[1] * (xp[0] - xi[0]) + gx[0] * (xp[1] - xi[1]);
+}
+static __device__ __forceinline__ void newton_F(const NewtonGeo& N, const float xi[2], float Lx, const float gx[2], float delta,
+                                         const float xp[2], float F[2], float gy[2], float hy[3], float m[2]) {
+    newton_F_f(N, N.fy, xi, Lx, gx, delta, xp, F, gy, hy, m);
 }
 // dF/dxi' rows: (grad L_y(xi'), R m - 0.5 H_y R (xi' - xi)); dF/dxi rows: (-grad L_x(xi), -(R m + 0.5 H_x R (xi' - xi)))
 // comparison gauges: fixed axis rows (0, 1) / (1, 0); start gradient dF2/dxi' = R g_x,
@@ -776,6 +780,144 @@ static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float
 }
 
 // ============================================================================================
+// cross-triangle walk of the reconnection vertex (TOF_FLAG_TRIANGLE_WALK; the paper
+// parameterises p on the surface, Sec. 4.2, without saying what happens at a triangle's edge).
+// The Newton unknown xi' lives in a 2-D chart: the plane of p's triangle, into which each
+// neighbour entered is unfolded about the shared edge (an isometry: lengths, gradients and |det|
+// carry over).  A candidate that leaves the current triangle crosses its exit edge into the
+// neighbour; the walk fails at a boundary or after kMaxCross crossings.  Two developments of a
+// triangle strip differ by a rigid motion, under which the average-gradient gauge is invariant,
+// so the shift stays reversible.
+// ============================================================================================
+constexpr int kMaxCross = 8;
+struct Walk { int tri; Frame2 f; };   // f: chart -> 3-D on tri (corners found from the triangle record)
+
+static __device__ __forceinline__ float3 tri_corner(const GeomDev& g, int tri, int j) {
+    float3 v0 = xyz(__ldg(&g.tri[3 * tri]));
+    if (j == 0) return v0;
+    return v0 + xyz(__ldg(&g.tri[3 * tri + j]));
+}
+static __device__ __forceinline__ void walk_init(const GeomDev& g, int tri, Walk& W) {
+    W.tri = tri;
+    W.f = tri_frame(g, tri);
+}
+// corner j of W's triangle in the chart
+static __device__ __forceinline__ void walk_corner(const GeomDev& g, const Walk& W, int j, float& q0, float& q1) {
+    float3 d = tri_corner(g, W.tri, j) - W.f.o;
+    q0 = dot3(d, W.f.t);
+    q1 = dot3(d, W.f.b);
+}
+static __device__ void walk_bary(const GeomDev& g, const Walk& W, float c0, float c1, float lam[3]) {
+    float q00, q01, q10, q11, q20, q21;
+    walk_corner(g, W, 0, q00, q01);
+    walk_corner(g, W, 1, q10, q11);
+    walk_corner(g, W, 2, q20, q21);
+    float a0 = q10 - q00, a1 = q11 - q01;
+    float b0 = q20 - q00, b1 = q21 - q01;
+    float d0 = c0 - q00, d1 = c1 - q01;
+    float det = a0 * b1 - a1 * b0;
+    lam[1] = (d0 * b1 - d1 * b0) / det;
+    lam[2] = (a0 * d1 - a1 * d0) / det;
+    lam[0] = 1.0f - lam[1] - lam[2];
+}
+// move W along the chart segment from -> to (from inside W) to the triangle holding `to`
+static __device__ bool walk_locate(const GeomDev& g, Walk& W, const float from_in[2], const float to[2]) {
+    float from[2] = {from_in[0], from_in[1]};
+    for (int k = 0; k <= kMaxCross; ++k) {
+        float lt[3], lf[3];
+        walk_bary(g, W, to[0], to[1], lt);
+        if (lt[0] >= -kBaryEps && lt[1] >= -kBaryEps && lt[2] >= -kBaryEps) return true;
+        if (k == kMaxCross || !g.adj) break;
+        walk_bary(g, W, from[0], from[1], lf);
+        int ex = -1;
+        float sbest = 3.0e38f;
+        for (int i = 0; i < 3; ++i) {
+            if (!(lt[i] < -kBaryEps)) continue;
+            float den = lf[i] - lt[i];
+            float sx = den > 0.f ? lf[i] / den : 0.f;
+            if (sx < 0.f) sx = 0.f;
+            if (sx < sbest) { sbest = sx; ex = i; }
+        }
+        if (ex < 0) return false;
+        int n = __ldg(&g.adj[3 * W.tri + ex]);
+        if (n < 0) return false;
+        const int nb = n >> 2, opp = n & 3;
+        const int ia = ex == 2 ? 0 : ex + 1, ib = ex == 0 ? 2 : ex - 1;
+        float3 A = tri_corner(g, W.tri, ia), B = tri_corner(g, W.tri, ib), C = tri_corner(g, nb, opp);
+        float a0, a1, b0, b1, e0, e1;
+        walk_corner(g, W, ia, a0, a1);
+        walk_corner(g, W, ib, b0, b1);
+        walk_corner(g, W, ex, e0, e1);
+        // 3-D: edge direction U and in-plane normal toward the neighbour's third corner; chart: edge
+        // direction u and normal away from the current triangle's third corner
+        float3 U = norm3(B - A);
+        float3 CA = C - A;
+        float3 Nv = norm3(CA - U * dot3(CA, U));
+        float ul = sqrtf((b0 - a0) * (b0 - a0) + (b1 - a1) * (b1 - a1));
+        float u0 = (b0 - a0) / ul, u1 = (b1 - a1) / ul;
+        float n0 = -u1, n1 = u0;
+        if ((e0 - a0) * n0 + (e1 - a1) * n1 > 0.f) { n0 = -n0; n1 = -n1; }
+        W.tri = nb;
+        W.f.t = U * u0 + Nv * n0;
+        W.f.b = U * u1 + Nv * n1;
+        W.f.o = A - (U * (a0 * u0 + a1 * u1) + Nv * (a0 * n0 + a1 * n1));
+        from[0] += sbest * (to[0] - from[0]);
+        from[1] += sbest * (to[1] - from[1]);
+    }
+    return false;
+}
+
+// newton_solve with the offset vertex walking across triangles (W: its triangle and chart)
+static __device__ bool newton_solve_walk(const GeomDev& gi, const NewtonGeo& N, Walk& W, const float xi[2], float delta,
+                                         int max_iter, float tol_stop, float tol_succ, float xp[2], float& jdet, int& iters) {
+    float Lx, gx[2], hx[3];
+    length_derivs(N.p1x, N.p2x, N.fx, xi[0], xi[1], Lx, gx, hx);
+    xp[0] = xi[0]; xp[1] = xi[1];
+    float F[2], gy[2], hy[3], m[2];
+    newton_F_f(N, W.f, xi, Lx, gx, delta, xp, F, gy, hy, m);
+    int it = 0;
+    while (it < max_iter) {
+        float nF = fmaxf(fabsf(F[0]), fabsf(F[1]));
+        if (nF <= tol_stop) break;
+        float A[4], Bm[4];
+        newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
+        float det = A[0] * A[3] - A[1] * A[2];
+        if (!(fabsf(det) > 1e-30f)) break;
+        float s0 = -(A[3] * F[0] - A[1] * F[1]) / det, s1 = -(-A[2] * F[0] + A[0] * F[1]) / det;
+        float lam = 1.0f;
+        bool accepted = false;
+        for (int ls = 0; ls < 5; ++ls) {
+            float c[2] = {xp[0] + lam * s0, xp[1] + lam * s1};
+            Walk Wc = W;
+            if (walk_locate(gi, Wc, xp, c)) {
+                float Fc[2], gyc[2], hyc[3], mc[2];
+                newton_F_f(N, Wc.f, xi, Lx, gx, delta, c, Fc, gyc, hyc, mc);
+                if (fmaxf(fabsf(Fc[0]), fabsf(Fc[1])) < nF) {
+                    xp[0] = c[0]; xp[1] = c[1];
+                    F[0] = Fc[0]; F[1] = Fc[1];
+                    gy[0] = gyc[0]; gy[1] = gyc[1]; hy[0] = hyc[0]; hy[1] = hyc[1]; hy[2] = hyc[2];
+                    m[0] = mc[0]; m[1] = mc[1];
+                    W = Wc;
+                    accepted = true;
+                    break;
+                }
+            }
+            lam *= 0.5f;
+        }
+        if (!accepted) break;
+        ++it;
+    }
+    iters = it;
+    if (!(fmaxf(fabsf(F[0]), fabsf(F[1])) <= tol_succ)) return false;
+    float A[4], Bm[4];
+    newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
+    float dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
+    if (!(fabsf(dA) > 0.f)) return false;
+    jdet = fabsf(dB / dA);
+    return isfinite(jdet);
+}
+
+// ============================================================================================
 // the shift map (Sec. 4.1-4.3): hybrid shift of the record x from domain Dj to domain Di --
 // random replay of x_2..x_{r-1} from y_1, reconnection at p = x_r, path-length-aware
 // perturbation of p on its triangle -- returning the offset record, its target in Di and the
@@ -793,8 +935,10 @@ struct GateMap { float scale, centre, lo, hi; };
 // kOut = false: only the target value and the Jacobian are wanted (the MIS terms), not the record.
 // vq: the visibility segments of a shift that passes every other test are queued there (vis_kernel
 // zeroes the guarded result when one is occluded); null: they are traced in place.
-// gm: the gate map of the shrink mapping (null: translation between gates)
-template <bool kOut>
+// gm: the gate map of the shrink mapping (null: translation between gates).  kWalk: the
+// reconnection vertex may walk across triangle edges (TOF_FLAG_TRIANGLE_WALK), compiled apart so
+// that the default shift keeps its code size and registers.
+template <bool kOut, bool kWalk = false>
 static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& Di, const ParamsDev& P, bool geom_static, Rec& y,
                           float& phat_out, float& jac_out, ShiftStats* st, const VisQ* vq = nullptr,
                           const GateMap* gm = nullptr) {
@@ -869,19 +1013,28 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
     float delta = ell - Lx_seg;
     float xp[2];
     float jn = 1.0f;
+    const bool walk = kWalk && !(P.flags & 2u);
+    Walk W;
+    if (walk) walk_init(gi, x.p_tri, W);
     if (P.flags & 2u) {
         xp[0] = xi[0]; xp[1] = xi[1];
     } else {
         int iters = 0;
         float tol_stop = gm ? 1e-6f * fabsf(tau_t + Di.o) : 1e-6f * fabsf(x.tau + Di.o + Di.L0 - Dj.L0);
         float tol_succ = P.newton_tol_frac * (gm ? gm->hi - gm->lo : Di.dL);
-        bool ok = newton_solve(N, xi, delta, P.newton_max_iter, tol_stop, tol_succ, xp, jn, iters);
+        bool ok = walk ? newton_solve_walk(gi, N, W, xi, delta, P.newton_max_iter, tol_stop, tol_succ, xp, jn, iters)
+                       : newton_solve(N, xi, delta, P.newton_max_iter, tol_stop, tol_succ, xp, jn, iters);
         if (st) { st->newton_calls++; st->newton_iters += iters; if (ok) st->newton_ok++; }
         if (!ok) return false;
         if (!(jn >= 1.0f / P.jac_max && jn <= P.jac_max)) return false;
     }
     float nb1, nb2;
-    {
+    int ptri = x.p_tri;
+    if (walk) {
+        float lam[3];
+        walk_bary(gi, W, xp[0], xp[1], lam);
+        ptri = W.tri; nb1 = lam[1]; nb2 = lam[2];
+    } else {
         float4 a = __ldg(&gi.tri[3 * x.p_tri]), e1v = __ldg(&gi.tri[3 * x.p_tri + 1]), e2v = __ldg(&gi.tri[3 * x.p_tri + 2]);
         (void)a;
         float3 e1 = xyz(e1v), e2 = xyz(e2v);
@@ -890,7 +1043,7 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
         nb1 = (xp[0] - nb2 * e2t) / e1t;
     }
     if (!(nb1 >= -kBaryEps && nb2 >= -kBaryEps && nb1 + nb2 <= 1.0f + kBaryEps)) return false;
-    Surf pp = surf_at(gi, x.p_tri, nb1, nb2);
+    Surf pp = surf_at(gi, ptri, nb1, nb2);
 
     // (5) the offset path must reconnect at the same index
     {
@@ -973,7 +1126,7 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
         y.tau = tau;
         y.xprev = yv[r - 1].p;
         y.pdf_pre = pdfy;
-        y.p_b1 = nb1; y.p_b2 = nb2;
+        y.p_tri = ptri; y.p_b1 = nb1; y.p_b2 = nb2;
         y.Lsuf = Lsuf_i;
         y.phat = f;
     }

@@ -17,6 +17,7 @@ constexpr int kStack = 64;          // BVH traversal stack
 constexpr int kMaxBinsPerPixel = 32;  // distinct transient bins a pixel's initial candidates may hit
 constexpr uint32_t kNoHit = 0xFFFFFFFFu;
 constexpr uint32_t kFlagPairwiseMis = 4u;  // TOF_FLAG_PAIRWISE_MIS
+constexpr uint32_t kFlagTriangleWalk = 64u;  // TOF_FLAG_TRIANGLE_WALK
 
 // material record: (type, albedo, alpha, unused)
 // triangle record (original order): 3 float4 = (v0.xyz, material id bits), (e1.xyz, 0), (e2.xyz, 0)
@@ -24,11 +25,14 @@ constexpr uint32_t kFlagPairwiseMis = 4u;  // TOF_FLAG_PAIRWISE_MIS
 // internal node: 4 float4 = (c0 lo.x, hi.x, lo.y, hi.y), (c1 lo.x, hi.x, lo.y, hi.y),
 //                           (c0 lo.z, hi.z, c1 lo.z, hi.z), (child0 bits, child1 bits, 0, 0)
 //                child >= 0: internal node, child < 0: leaf ~child.
+// adjacency (original order), nt * 3: across the edge opposite vertex i of triangle t,
+// 4 * neighbour + the neighbour's vertex opposite that edge, or -1
 struct GeomDev {
     const float4* tri;
     const float4* leaf;
     const float4* nodes;
     const float4* mats;
+    const int* adj;
     int nt;
     uint32_t version;
 };

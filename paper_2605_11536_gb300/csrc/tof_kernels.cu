@@ -217,6 +217,7 @@ struct ShrinkSink {
     }
 };
 
+template <bool kWalk>
 __global__ void __launch_bounds__(128) initial_shrink_kernel(const __grid_constant__ InitArgs a) {
     const FrameDev& F = a.F;
     int ix, iy;
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(128) initial_shrink_kernel(const __grid_consta
     to_wide.scale = K; to_wide.centre = c; to_wide.lo = c - half; to_wide.hi = c + half;
     Rec yb;
     float pyb = 0.f, Jb = 0.f;
-    const bool okb = Wb > 0.f && shift_rec<true>(sb.rec, D, D, P, true, yb, pyb, Jb, nullptr, nullptr, &to_gate);
+    const bool okb = Wb > 0.f && shift_rec<true, kWalk>(sb.rec, D, D, P, true, yb, pyb, Jb, nullptr, nullptr, &to_gate);
     float w[2] = {0.f, 0.f};
     if (NA == 0) {
         if (okb) w[1] = pyb * Wb * Jb;
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(128) initial_shrink_kernel(const __grid_consta
         if (Wa > 0.f) {
             Rec tmp;
             float pe = 0.f, Je = 0.f;
-            float pba = shift_rec<false>(sa.rec, D, D, P, true, tmp, pe, Je, nullptr, nullptr, &to_wide) ? pe * Je : 0.f;
+            float pba = shift_rec<false, kWalk>(sa.rec, D, D, P, true, tmp, pe, Je, nullptr, nullptr, &to_wide) ? pe * Je : 0.f;
             float ma = NA * sa.rec.phat / (NA * sa.rec.phat + NB * pba);
             w[0] = ma * sa.rec.phat * Wa;
         }
@@ -391,7 +392,10 @@ cudaError_t launch_initial(const InitArgs& a, int tile_h, int* err, cudaStream_t
     return cudaGetLastError();
 }
 cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s) {
-    initial_shrink_kernel<<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a);
+    if (a.P.flags & kFlagTriangleWalk)
+        initial_shrink_kernel<true><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a);
+    else
+        initial_shrink_kernel<false><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_splat(const SplatArgs& a, cudaStream_t s) {

@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(128) reuse_units_kernel(const __grid_constant_
 // --------------------------------------------------------------------------------------------
 // forward shifts: slot s's sample into the unit's domain
 // --------------------------------------------------------------------------------------------
+template <bool kWalk>
 __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
     ShiftStats st = {0, 0, 0, 0, 0};
     const uint32_t ntask = min(w.counters[1], (uint32_t)w.cap_units * (uint32_t)(w.slots - 1));
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant
         size_t ui = (size_t)u * S + s;
         VisQ vq;
         vq.rays = w.rays; vq.counter = &w.counters[4]; vq.cap = w.ray_cap; vq.target = (uint32_t)ui;
-        bool ok = shift_rec<true>(x, Ds, D0, a.P, geom_static, y, py, J, &st, &vq);
+        bool ok = shift_rec<true, kWalk>(x, Ds, D0, a.P, geom_static, y, py, J, &st, &vq);
         // visibility is settled by vis_kernel, which zeroes py of an occluded shift
         w.py[ui] = ok ? py : 0.f;
         w.jac[ui] = ok ? J : 1.f;
@@ -385,6 +386,7 @@ __global__ void __launch_bounds__(128) emit_inv_kernel(const __grid_constant__ R
 // --------------------------------------------------------------------------------------------
 // inverse shifts: candidate s's offset path (in the unit's domain) into domain j
 // --------------------------------------------------------------------------------------------
+template <bool kWalk>
 __global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
     const uint32_t cap = (uint32_t)w.cap_units * (uint32_t)w.slots * (uint32_t)(w.slots - 1);
     const uint32_t ntask = min(w.counters[2], cap);
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant
         const size_t ti = ((size_t)u * S + s) * S + j;
         VisQ vq;
         vq.rays = w.rays; vq.counter = &w.counters[5]; vq.cap = w.ray_cap; vq.target = (uint32_t)ti;
-        if (shift_rec<false>(y, D0, Dj, a.P, geom_static, tmp, pj, Jj, nullptr, &vq)) term = w.slot_M[(size_t)pix * S + j] * pj * Jj;
+        if (shift_rec<false, kWalk>(y, D0, Dj, a.P, geom_static, tmp, pj, Jj, nullptr, &vq)) term = w.slot_M[(size_t)pix * S + j] * pj * Jj;
         w.terms[ti] = term;
     }
     if (a.stats) {
@@ -535,14 +537,17 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
     const long long nw = (long long)np * a.dst.words;
     reuse_units_kernel<<<(unsigned)((nw + 127) / 128), 128, 0, s>>>(a, w, p0, p1);
     if (ev) cudaEventRecord(ev[1], s);
-    shift_fwd_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    const bool walk = (a.P.flags & kFlagTriangleWalk) != 0u;
+    if (walk) shift_fwd_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w);
+    else shift_fwd_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w);
     if (ev) cudaEventRecord(ev[2], s);
     // forward shifts land in the current frame; counter 4 of the stats counted them as successes
     vis_kernel<<<vis_blocks, 128, 0, s>>>(a.cur.g, w.rays, &w.counters[4], w.ray_cap, &w.counters[6], w.py, a.stats, 4,
                                           a.temporal ? -1 : 8);
     emit_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
     if (ev) cudaEventRecord(ev[3], s);
-    shift_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    if (walk) shift_inv_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w);
+    else shift_inv_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w);
     if (ev) cudaEventRecord(ev[4], s);
     // inverse shifts land in the reused domain: the previous frame for the temporal pass (its one
     // reused slot), the current frame for spatial passes
@@ -559,8 +564,8 @@ cudaError_t reuse_persist_blocks(int* out, int* vis_out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, shift_fwd_kernel, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, shift_inv_kernel, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, shift_fwd_kernel<false>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, shift_inv_kernel<false>, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, reuse_merge_kernel, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, vis_kernel, 128, 0);
     int b = b1;

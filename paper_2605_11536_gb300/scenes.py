@@ -38,6 +38,7 @@ FLAG_PAIRWISE_MIS = 4    # pairwise MIS instead of the generalized balance heuri
 FLAG_GAUGE_AXIS_T = 8    # comparison gauge: fixed axis, the reconnection vertex moves along t
 FLAG_GAUGE_AXIS_B = 16   # comparison gauge: fixed axis, the reconnection vertex moves along b
 FLAG_GAUGE_START = 32    # comparison gauge: gradient at the start point only (not reversible)
+FLAG_TRIANGLE_WALK = 64  # the reconnection vertex may walk across triangle edges during Newton
 
 
 @dataclass

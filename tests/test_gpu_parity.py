@@ -213,3 +213,28 @@ def test_comparison_gauges_and_naive_reuse(flag):
     g = gpu_render(sc, [0, 1])
     for f in range(2):
         _check(g[f], o[f])
+
+
+@pytest.mark.parametrize("case", ["box_fine_spatial", "heightfield_temporal", "shrink_fine"])
+def test_triangle_walk(case):
+    """TOF_FLAG_TRIANGLE_WALK: the reconnection vertex walks across triangle edges during Newton
+    (finely tessellated box walls, the heightfield with moving spheres and temporal reuse, the
+    shrink mapping's long moves); same images as the oracle."""
+    from tests.test_oracle_walk import _subdivide
+    if case == "heightfield_temporal":
+        sc = scenes.heightfield_spheres(W=96, H=80, frames=3)
+        sc.params.radius = 8
+        sc.gates = [(8.0, 0.3)] * 3
+        frames = [0, 1, 2]
+    else:
+        sc = _subdivide(scenes.box_icosphere(W=48, H=40, frames=1), 0, 2)
+        sc.gates = [(5.0, 0.25 if case == "box_fine_spatial" else 0.05)]
+        sc.params.n_spatial, sc.params.radius = 3, 8
+        if case == "shrink_fine":
+            sc.params.shrink_k, sc.params.shrink_fine = 10.0, 0
+        frames = [0]
+    sc.params.flags = scenes.FLAG_TRIANGLE_WALK
+    o, ok, st, _ = oracle_render(sc, frames)
+    g = gpu_render(sc, frames)
+    for f in range(len(frames)):
+        _check(g[f], o[f], min_nonzero=50)
