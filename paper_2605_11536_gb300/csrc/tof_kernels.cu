@@ -147,7 +147,9 @@ struct InitSink {
     }
 };
 
-__global__ void __launch_bounds__(128) initial_kernel(const __grid_constant__ InitArgs a, int* err) {
+// 6 resident blocks per SM (80 registers): 1.08 against 1.11 ms at 5 blocks (96 registers) on the
+// 512 x 512 dynamic workload; 8 blocks (64 registers, more spills) were slower
+__global__ void __launch_bounds__(128, 6) initial_kernel(const __grid_constant__ InitArgs a, int* err) {
     const FrameDev& F = a.F;
     int ix, iy;
     tile_pixel(a.tile_w, ix, iy);
