@@ -699,6 +699,66 @@ def run_served_gated(args, seconds=1.5, rate=120.0, seed=5):
     return r
 
 
+def run_transient(args, frames=None):
+    """Transient histogram workload shaped like the paper's NLOS setting: a confocal scan of a relay
+    wall (256 x 256 by default), 1024 bins of 1 mm (a 256 MiB float32 histogram per frame at 256^2),
+    depth 4, 8 path trees, temporal + 3 spatial neighbours, the device translating 5 mm per frame
+    (16 frames by default).  Every frame of the sequence is timed with CUDA events (L2 flushed
+    between frames); reuse fills more bins per pixel as the sequence goes on, so later frames cost
+    more.  The splat kernel is the HBM-bound pass: its roofline counts the histogram written, the
+    occupancy words read and one 16-byte reservoir word per nonzero bin read."""
+    import torch
+    from paper_2605_11536_gb300 import scenes, tof
+    W = H = args.transient_px
+    B = 1024
+    frames = frames or args.transient_frames
+    sc = scenes.confocal_nlos(W=W, H=H, frames=frames, B=B, seed=2)
+    ctx = tof.tof_create(torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    try:
+        sid = tof.tof_scene_upload(ctx, sc.verts, sc.tris, sc.tri_object, sc.materials, sc.object_material)
+        vid = tof.tof_view_create(ctx, sid, W, H, B)
+        tof.tof_view_profile(ctx, vid, 1)
+        out = torch.zeros(W * H * B, device="cuda")
+        flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+        ms, stages = [], []
+        with torch.cuda.stream(stream):
+            for f in range(frames):
+                tof.tof_bvh_build(ctx, sid, sc.xforms[f].reshape(-1), refit_only=0, stream=sptr)
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tof.tof_render_transient(ctx, sid, vid, sc.sensors[f], sc.emitters[f], sc.bins, sc.params, sc.seed, f,
+                                         out.data_ptr(), sptr)
+                e1.record(stream)
+                stream.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                stages.append(tof.tof_view_stage_ms(ctx, vid))
+        nnz = int(torch.count_nonzero(out).item())
+        st = tof.tof_view_stats(ctx, vid)
+    finally:
+        tof.tof_destroy(ctx)
+    hbm, hbm_kind = _peaks()
+    npix = W * H
+    words = (B + 31) // 32
+    splat_ms = float(np.mean([x["splat"] for x in stages]))
+    splat_bytes = 4 * B * npix + 4 * words * npix + 16 * nnz
+    achieved = splat_bytes / (splat_ms / 1e3) / 1e9
+    return {"workload": "confocal transient %dx%d x 1024 bins of 1 mm, ~100k tris, depth 4, 8 trees, temporal + 3 "
+                        "spatial within 10 px, %d frames" % (W, H, frames),
+            "value": frames / (sum(ms) / 1e3), "unit": "frames/s", "ms_per_frame": ms,
+            "stage_ms_mean": {k: float(np.mean([x[k] for x in stages])) for k in stages[0]},
+            "nonzero_bins_last_frame_per_px": nnz / npix,
+            "shifts_per_frame": {"forward": st["shift_calls"] / frames, "inverse": st["inv_calls"] / frames},
+            "splat_roofline": {"bound": "hbm", "kernel": "splat_kernel", "achieved": achieved, "peak": hbm,
+                               "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                               "note": "algorithmic bytes per launch = histogram 4 B x %d bins x %d px written + "
+                                       "occupancy %d B/px + 16 B per nonzero bin (%d on the last frame) read = %.1f MB; "
+                                       "time = mean CUDA-event splat stage over %d frames (%.4f ms); peak = %s HBM"
+                                       % (B, npix, 4 * words, nnz, splat_bytes / 1e6, frames, splat_ms, hbm_kind)}}
+
+
 def cpu_baseline(args, crop=None, frames=3):
     """The oracle as it stands on the host cores (all of them, OpenMP): the first `frames` frames of
     the workload at full resolution (or on a crop of it, with the margin the spatial reuse needs),
@@ -762,6 +822,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-transient", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--transient-px", type=int, default=256, help="sensor side of the transient line (a smaller one "
+                    "keeps an ncu capture of its kernels within a few GB)")
+    ap.add_argument("--transient-frames", type=int, default=16)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -890,6 +953,9 @@ def main():
             line["cpu_baseline"] = cpu_baseline(args)
         except Exception as e:  # the oracle is optional for the GPU number itself
             line["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+    for k, v in line.items():   # a failed section stays in the line as {"error": ...}; say so on stderr too
+        if isinstance(v, dict) and "error" in v:
+            print("bench section %s failed: %s" % (k, v["error"]), file=sys.stderr)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
