@@ -58,6 +58,13 @@ BYTES = {
 }
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
+# kernel as it is now, on the dynamic gated workload; None for kernels whose launches vary too much
+# from frame to frame for one capture to stand for the mean launch (task counts grow over the
+# first frames).  Must be retaken whenever the kernel changes.
+NCU_TRAFFIC = {"initial_kernel": 30.859264e6 + 34.762496e6, "reuse_merge_kernel": 85.374208e6 + 9.837824e6}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -870,7 +877,7 @@ def main():
         ms = st[k]
         a = algo[k] / (ms / 1e3) / 1e9
         return {"bound": "hbm", "kernel": kernels[k], "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-                "traffic": None, "ms": ms,
+                "traffic": NCU_TRAFFIC.get(kernels[k]), "ms": ms,
                 "note": "achieved = algorithmic bytes (%s, %.1f MB per launch) / mean launch time (CUDA events, %.3f ms); "
                         "peak = %s HBM copy bandwidth" % (units[k], algo[k] / 1e6, ms, hbm_kind)}
 
