@@ -108,6 +108,10 @@ typedef struct { float t0, width; int32_t B; } tof_bins;
  * (two vertex indices) within one object.  Shifts stay reversible; on planar surfaces the result
  * no longer depends on the tessellation. */
 #define TOF_FLAG_TRIANGLE_WALK 64u
+/* transient rendering: bin reuse (Sec. 4.5, the histogram's extra reuse axis) -- one pass after
+ * temporal reuse in which the reservoir of bin b also reuses the same pixel's bins b - 1 and
+ * b + 1, shifted into bin b's gate by one bin width; bins outside the histogram are no domains. */
+#define TOF_FLAG_BIN_REUSE 128u
 
 /* reuse / sampling parameters (Sec. 6: path depth, candidates, neighbours, radius, M-cap;
  * Newton tolerance 1 % of the gate width with at most 5 iterations) */

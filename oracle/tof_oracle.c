@@ -460,7 +460,7 @@ typedef struct {
     int shrink_fine;     /* trees kept in the gate itself (canonical samples); 0 = all trees widened */
 } oparams;
 enum { F_DIRECT = 1, F_NAIVE = 2, F_PAIRWISE = 4, F_GAUGE_AXIS_T = 8, F_GAUGE_AXIS_B = 16, F_GAUGE_START = 32,
-       F_WALK = 64 };
+       F_WALK = 64, F_BIN_REUSE = 128 };
 /* gauge of the Newton system (Sec. 4.3 "Selecting a Good Gauge Condition") */
 enum { G_AVERAGE = 0, G_AXIS_T = 1, G_AXIS_B = 2, G_START = 3 };
 static int gauge_of(uint32_t flags) {
@@ -1669,6 +1669,54 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
         }
         free(Mc);
         Mc = Mt;
+    }
+
+    /* bin reuse (Sec. 4.5: the histogram's extra reuse axis), transient views with F_BIN_REUSE: one
+     * pass after temporal reuse in which the reservoir of bin b reuses the same pixel's bins b - 1
+     * and b + 1, shifted into bin b's gate by the gate translation (delta = -+ w).  Bins outside
+     * [0, B) are not domains (no candidate was ever drawn for them): they take no part in the MIS.
+     * The stored per-pixel confidence counts both neighbours for every bin -- any structural
+     * confidence keeps the balance heuristic a partition of unity. */
+    if (B > 0 && (P->flags & F_BIN_REUSE)) {
+        orec* Rb = (orec*)calloc((size_t)W * H * Bn, sizeof(orec));
+        double* Mb = (double*)malloc(sizeof(double) * (size_t)W * H);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+        for (int pix = 0; pix < W * H; ++pix) {
+            orec* dst = &Rb[(size_t)pix * Bn];
+            memcpy(dst, &R1[(size_t)pix * Bn], sizeof(orec) * Bn);
+            const double Mn = fmin(Mc[pix], P->m_cap);
+            Mb[pix] = Mc[pix] + 2.0 * Mn;
+            if (!ok1[pix] || !F->gb[pix].valid) continue;
+            for (int b = 0; b < Bn; ++b) {
+                const orec* xc = &R1[(size_t)pix * Bn + b];
+                int any = xc->valid;
+                if (b >= 1) any |= R1[(size_t)pix * Bn + b - 1].valid;
+                if (b + 1 < Bn) any |= R1[(size_t)pix * Bn + b + 1].valid;
+                if (!any) continue;
+                /* slots 0 (bin b), 1 (bin b - 1), 2 (bin b + 1); an absent bin is an empty slot with
+                 * confidence 0, so it adds nothing to any MIS weight */
+                odomain Dc = make_domain(F, pix, P, GATE_L0(b), dL);
+                odomain Dn[2];
+                oslot sl[3];
+                sl[0].D = &Dc; sl[0].x = xc; sl[0].M = Mc[pix]; sl[0].geom_static = 1;
+                for (int k = 0; k < 2; ++k) {
+                    int bb = k == 0 ? b - 1 : b + 1;
+                    int present = bb >= 0 && bb < Bn;
+                    Dn[k] = make_domain(F, pix, P, GATE_L0(bb), dL);
+                    sl[1 + k].D = &Dn[k];
+                    sl[1 + k].x = present ? &R1[(size_t)pix * Bn + bb] : &EMPTY_REC;
+                    sl[1 + k].M = present ? Mn : 0.0;
+                    sl[1 + k].geom_static = 1;
+                }
+                merge(sl, 3, P, seed, (uint32_t)pix, frame, 8, b, &dst[b], &v->st);
+            }
+        }
+        if (R1 != R0) free(R1);
+        R1 = Rb;
+        free(Mc);
+        Mc = Mb;
     }
 
     /* spatial reuse (stage (3)) */

@@ -206,9 +206,10 @@ static tof_status check_params(tof_ctx* c, const tof_params* p, int transient) {
     if (p->radius < 1 || p->radius > 255) return fail(c, TOF_EINVAL, "radius %d outside [1, 255]", p->radius);
     if (p->n_spatial_iters < 0 || p->n_spatial_iters > 4) return fail(c, TOF_EINVAL, "n_spatial_iters outside [0, 4]");
     const uint32_t gauges = p->flags & (TOF_FLAG_GAUGE_AXIS_T | TOF_FLAG_GAUGE_AXIS_B | TOF_FLAG_GAUGE_START);
-    if (p->flags & ~(TOF_FLAG_DIRECT | TOF_FLAG_NAIVE_SHIFT | TOF_FLAG_PAIRWISE_MIS | TOF_FLAG_TRIANGLE_WALK | gauges))
+    if (p->flags & ~(TOF_FLAG_DIRECT | TOF_FLAG_NAIVE_SHIFT | TOF_FLAG_PAIRWISE_MIS | TOF_FLAG_TRIANGLE_WALK | TOF_FLAG_BIN_REUSE | gauges))
         return fail(c, TOF_EINVAL, "unknown flag bits 0x%x", p->flags);
     if (gauges & (gauges - 1)) return fail(c, TOF_EINVAL, "at most one gauge flag");
+    if ((p->flags & TOF_FLAG_BIN_REUSE) && !transient) return fail(c, TOF_EINVAL, "bin reuse applies to transient rendering");
     if (p->newton_max_iter < 0 || p->newton_max_iter > 16) return fail(c, TOF_EINVAL, "newton_max_iter outside [0, 16]");
     if (!(p->m_cap > 0) || !(p->jac_max >= 1) || !(p->newton_tol_frac > 0) || !(p->ray_eps > 0) || !(p->d_min >= 0))
         return fail(c, TOF_EINVAL, "m_cap, jac_max, newton_tol_frac, ray_eps must be positive, d_min >= 0");
@@ -597,7 +598,7 @@ static tof_status ensure_wave(tof_ctx* c, ViewH& V, int S, int cap) {
 // one reuse pass as a wavefront; transient passes run in pixel chunks so that a chunk's merge
 // units (at most B per pixel) never exceed the scratch capacity
 static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const WaveDev* fixed, cudaStream_t s) {
-    const int S = ra.temporal ? 2 : 1 + ra.P.n_spatial;
+    const int S = ra.binpass ? 3 : ra.temporal ? 2 : 1 + ra.P.n_spatial;
     const size_t npix = (size_t)V.W * V.H;
     const size_t Bn = V.B > 0 ? (size_t)V.B : 1;
     const size_t kMaxUnits = (size_t)1 << 22;
@@ -675,7 +676,8 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     // temporal reuse needs the previous frame's geometry still resident
     bool temporal = params->temporal && V.has_prev && V.prev_final >= 0 &&
                     S.version[V.geom_slot[1 - fc]] == V.geom_version[1 - fc];
-    int stages = 1 + (temporal ? 1 : 0) + (params->n_spatial > 0 ? params->n_spatial_iters : 0);
+    const bool binpass = B > 0 && (params->flags & TOF_FLAG_BIN_REUSE);
+    int stages = 1 + (temporal ? 1 : 0) + (binpass ? 1 : 0) + (params->n_spatial > 0 ? params->n_spatial_iters : 0);
     int bufs[2], nb = 0;
     for (int k = 0; k < 3 && nb < 2; ++k)
         if (k != V.prev_final) bufs[nb++] = k;
@@ -710,6 +712,20 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
         V.ran[2] = true;
     }
     mark(V, 3, s);
+    if (binpass) {
+        // bin reuse: the same pixel's neighbouring bins (timed with the spatial stage)
+        ra.prev = F;
+        ra.src = V.res[src].dev();
+        ra.prv = ra.src;
+        ra.dst = V.res[out_of(stage)].dev();
+        ra.temporal = 0; ra.binpass = 1; ra.pass = 8; ra.geom_static = 1;
+        ra.out = nullptr;
+        TRY(reuse_pass(c, V, ra, fixed_wave, s));
+        ra.binpass = 0;
+        src = out_of(stage);
+        ++stage;
+        V.ran[3] = true;
+    }
     if (params->n_spatial > 0) {
         for (int it = 0; it < params->n_spatial_iters; ++it) {
             ra.prev = F;
@@ -844,6 +860,7 @@ tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* s
         size_t cap = npix * Bn < ((size_t)1 << 22) ? npix * Bn : ((size_t)1 << 22);
         if (cap < npix && V.B == 0) cap = npix;
         int S = 1 + J.params.n_spatial > 2 ? 1 + J.params.n_spatial : 2;
+        if (J.transient && (J.params.flags & TOF_FLAG_BIN_REUSE) && S < 3) S = 3;
         TRY(ensure_wave(c, V, S, (int)cap));
     }
     TRY(persist_init(c));

@@ -118,7 +118,8 @@ struct ReuseArgs {
     ResDev dst;
     ParamsDev P;
     int temporal;            // 1: temporal pass, 0: spatial pass
-    int pass;                // 0 temporal, 1.. spatial
+    int binpass;             // 1: bin pass (slots 1, 2 = the same pixel's bins b - 1, b + 1)
+    int pass;                // 0 temporal, 1.. spatial, 8 bin pass
     int geom_static;         // previous and current geometry identical
     float* out;              // gated image if last stage
     StatsDev* stats;

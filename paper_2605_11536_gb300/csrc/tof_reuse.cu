@@ -33,6 +33,21 @@ __device__ __forceinline__ const ResDev* slot_res(const ReuseArgs& a, int s) {
     return (a.temporal && s == 1) ? &a.prv : &a.src;
 }
 
+// bin of slot s for the unit of bin b: the bin pass reuses the same pixel's bins b - 1 (slot 1)
+// and b + 1 (slot 2); bins outside [0, B) are not domains (no candidate was drawn for them)
+__device__ __forceinline__ int slot_bin(const ReuseArgs& a, int s, int b) {
+    return a.binpass ? (s == 1 ? b - 1 : s == 2 ? b + 1 : b) : b;
+}
+__device__ __forceinline__ bool slot_present(const ReuseArgs& a, int s, int b) {
+    if (!a.binpass) return true;
+    const int sb = slot_bin(a, s, b);
+    return sb >= 0 && sb < a.cur.B;
+}
+__device__ __forceinline__ bool slot_occ(const ReuseArgs& a, int s, int q, int b) {
+    if (!slot_present(a, s, b)) return false;
+    return occ_get(*slot_res(a, s), q, slot_bin(a, s, b));
+}
+
 __device__ __forceinline__ Domain pix_domain(const FrameDev* F, int pix, int b) {
     float4 gb = __ldg(&F->gb[pix]);
     uint32_t tri = __float_as_uint(gb.x);
@@ -97,7 +112,12 @@ __global__ void __launch_bounds__(128) reuse_slots_kernel(const __grid_constant_
     sM[0] = a.src.M[pix];
     bool gb_valid = __float_as_uint(C.gb[pix].x) != kNoHit;
     if (gb_valid) {
-        if (a.temporal) {
+        if (a.binpass) {
+            // the same pixel's neighbouring bins: confidence capped like any reused domain
+            sp[1] = sp[2] = pix;
+            sM[1] = sM[2] = fminf(sM[0], P.m_cap);
+            n = 3;
+        } else if (a.temporal) {
             int q = -1;
             if (C.mode == 1) q = pix;
             else {
@@ -157,6 +177,15 @@ __global__ void __launch_bounds__(128) reuse_units_kernel(const __grid_constant_
                 for (int k = 0; k < 6; ++k) *res_at(a.dst, k, idx) = *res_at(a.src, k, idx);
                 if (C.B == 0) { float4 p0v = *res_at(a.src, 0, idx); outv = p0v.y * p0v.x; }
             }
+        } else if (a.binpass) {
+            // units: bins whose own, lower or upper neighbour's reservoir holds a sample
+            docc[wd] = 0u;
+            const uint32_t* o = a.src.occ + (size_t)pix * words;
+            const uint32_t c = o[wd];
+            const uint32_t lo = wd > 0 ? o[wd - 1] : 0u, hi = wd + 1 < words ? o[wd + 1] : 0u;
+            m = c | (c << 1) | (lo >> 31) | (c >> 1) | (hi << 31);
+            const int rem = C.B - (wd << 5);
+            if (rem < 32) m &= (1u << rem) - 1u;
         } else {
             docc[wd] = 0u;
             for (int s = 0; s < n; ++s) {
@@ -178,11 +207,10 @@ __global__ void __launch_bounds__(128) reuse_units_kernel(const __grid_constant_
         for (uint32_t k = 0; k < nvalid; ++k) {
             int b = (wd << 5) + __ffs(mm) - 1;
             mm &= mm - 1;
-            for (int s = 1; s < n; ++s) {
-                const ResDev* R = slot_res(a, s);
-                if (occ_get(*R, sp[s], b)) ++nf_tot;
-            }
-            if (n > 1 && occ_get(a.src, pix, b)) ni_tot += (uint32_t)(n - 1);
+            for (int s = 1; s < n; ++s)
+                if (slot_occ(a, s, sp[s], b)) ++nf_tot;
+            if (n > 1 && occ_get(a.src, pix, b))
+                for (int j = 1; j < n; ++j) ni_tot += slot_present(a, j, b) ? 1u : 0u;
         }
     }
     uint32_t fb = reserve(&w.counters[1], nf_tot);
@@ -192,12 +220,11 @@ __global__ void __launch_bounds__(128) reuse_units_kernel(const __grid_constant_
         m &= m - 1;
         uint32_t u = ubase + k;
         w.units[u] = make_int2(pix, b);
-        for (int s = 1; s < n; ++s) {
-            const ResDev* R = slot_res(a, s);
-            if (occ_get(*R, sp[s], b)) w.fwd[fb++] = (u << 4) | (uint32_t)s;
-        }
+        for (int s = 1; s < n; ++s)
+            if (slot_occ(a, s, sp[s], b)) w.fwd[fb++] = (u << 4) | (uint32_t)s;
         if (n > 1 && occ_get(a.src, pix, b)) {
-            for (int j = 1; j < n; ++j) w.inv[ib++] = (u << 8) | (uint32_t)j;
+            for (int j = 1; j < n; ++j)
+                if (slot_present(a, j, b)) w.inv[ib++] = (u << 8) | (uint32_t)j;
         }
     }
     // gated (one word per pixel): pixels that form a unit get their value from the merge
@@ -223,8 +250,9 @@ __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant
         const ResDev* Rs = slot_res(a, s);
         int Bs = Fs->B > 0 ? Fs->B : 1;
         Rec x;
-        rec_load(*Rs, (size_t)q * Bs + b, x);
-        Domain Ds = pix_domain(Fs, q, b);
+        const int sb = slot_bin(a, s, b);
+        rec_load(*Rs, (size_t)q * Bs + sb, x);
+        Domain Ds = pix_domain(Fs, q, sb);
         Domain D0 = pix_domain(&a.cur, pix, b);
         Rec y;
         float py = 0.f, J = 1.f;
@@ -373,13 +401,16 @@ __global__ void __launch_bounds__(128) emit_inv_kernel(const __grid_constant__ R
         uint32_t task = w.fwd[t];
         uint32_t u = task >> 4;
         int s = (int)(task & 15u);
-        int pix = w.units[u].x;
+        int2 ub = w.units[u];
+        const int pix = ub.x, b = ub.y;
         const int n = w.nslot[pix];
         const bool ok = w.py[(size_t)u * S + s] > 0.f;
-        const uint32_t ne = (ok && n > 2 && !pairwise) ? (uint32_t)(n - 2) : 0u;
+        uint32_t ne = 0u;
+        if (ok && n > 2 && !pairwise)
+            for (int j = 1; j < n; ++j) ne += (j != s && slot_present(a, j, b)) ? 1u : 0u;
         uint32_t ib = reserve_coalesced(&w.counters[2], ne);
         for (int j = 1; j < n && ne; ++j)
-            if (j != s) w.inv[ib++] = (u << 8) | ((uint32_t)s << 4) | (uint32_t)j;
+            if (j != s && slot_present(a, j, b)) w.inv[ib++] = (u << 8) | ((uint32_t)s << 4) | (uint32_t)j;
     }
 }
 
@@ -410,7 +441,7 @@ __global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant
         }
         int q = w.slot_pix[(size_t)pix * S + j];
         Domain D0 = pix_domain(&a.cur, pix, b);
-        Domain Dj = pix_domain(slot_frame(a, j), q, b);
+        Domain Dj = pix_domain(slot_frame(a, j), q, slot_bin(a, j, b));
         bool geom_static = (a.temporal && j == 1) ? a.geom_static != 0 : true;
         Rec tmp;
         float pj = 0.f, Jj = 1.f;
@@ -418,7 +449,8 @@ __global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant
         const size_t ti = ((size_t)u * S + s) * S + j;
         VisQ vq;
         vq.rays = w.rays; vq.counter = &w.counters[5]; vq.cap = w.ray_cap; vq.target = (uint32_t)ti;
-        if (shift_rec<false, kWalk>(y, D0, Dj, a.P, geom_static, tmp, pj, Jj, nullptr, &vq)) term = w.slot_M[(size_t)pix * S + j] * pj * Jj;
+        if (slot_present(a, j, b) && shift_rec<false, kWalk>(y, D0, Dj, a.P, geom_static, tmp, pj, Jj, nullptr, &vq))
+            term = w.slot_M[(size_t)pix * S + j] * pj * Jj;
         w.terms[ti] = term;
     }
     if (a.stats) {
@@ -446,15 +478,16 @@ __global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant_
         float py[kMaxSlots], J[kMaxSlots], ph[kMaxSlots], Wx[kMaxSlots], M[kMaxSlots], wv[kMaxSlots];
         bool ok[kMaxSlots];
         for (int s = 0; s < n; ++s) {
-            M[s] = w.slot_M[(size_t)pix * S + s];
+            // an absent domain (a bin outside the histogram) takes no part in the MIS
+            M[s] = slot_present(a, s, b) ? w.slot_M[(size_t)pix * S + s] : 0.f;
             ok[s] = false;
             wv[s] = 0.f;
             const ResDev* R = slot_res(a, s);
             int q = w.slot_pix[(size_t)pix * S + s];
-            if (!occ_get(*R, q, b)) continue;
+            if (!slot_occ(a, s, q, b)) continue;
             const FrameDev* Fs = slot_frame(a, s);
             int Bs = Fs->B > 0 ? Fs->B : 1;
-            float4 p0 = *res_at(*R, 0, (size_t)q * Bs + b);
+            float4 p0 = *res_at(*R, 0, (size_t)q * Bs + slot_bin(a, s, b));
             ph[s] = p0.y; Wx[s] = p0.x;
             if (s == 0) { py[0] = p0.y; J[0] = 1.f; ok[0] = py[0] > 0.f; }
             else { py[s] = w.py[(size_t)u * S + s]; J[s] = w.jac[(size_t)u * S + s]; ok[s] = py[s] > 0.f; }
@@ -475,7 +508,7 @@ __global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant_
                     const float pc = __fmul_rn(Mck, py[0]);
                     for (int i = 1; i < n; ++i) {
                         float alpha = __fdiv_rn(__fadd_rn(M[i], Mck), Msum);
-                        float ti = w.terms[((size_t)u * S + 0) * S + i];
+                        float ti = slot_present(a, i, b) ? w.terms[((size_t)u * S + 0) * S + i] : 0.f;
                         m = __fadd_rn(m, __fmul_rn(alpha, __fdiv_rn(pc, __fadd_rn(pc, ti))));
                     }
                 } else {
@@ -492,7 +525,8 @@ __global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant_
             float num = s == 0 ? __fmul_rn(M[0], py[0]) : __fdiv_rn(__fmul_rn(M[s], ph[s]), J[s]);
             float den = __fmul_rn(M[0], py[s]);
             for (int j = 1; j < n; ++j)
-                den = __fadd_rn(den, (j == s) ? __fdiv_rn(__fmul_rn(M[s], ph[s]), J[s]) : w.terms[((size_t)u * S + s) * S + j]);
+                den = __fadd_rn(den, (j == s) ? __fdiv_rn(__fmul_rn(M[s], ph[s]), J[s])
+                                              : slot_present(a, j, b) ? w.terms[((size_t)u * S + s) * S + j] : 0.f);
             float m = den > 0.f ? __fdiv_rn(num, den) : 0.f;
             wv[s] = m * py[s] * Wx[s] * J[s];
             if (!(wv[s] > 0.f) || !isfinite(wv[s])) wv[s] = 0.f;

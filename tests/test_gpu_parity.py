@@ -238,3 +238,19 @@ def test_triangle_walk(case):
     g = gpu_render(sc, frames)
     for f in range(len(frames)):
         _check(g[f], o[f], min_nonzero=50)
+
+
+@pytest.mark.parametrize("nsp,flags", [(0, scenes.FLAG_BIN_REUSE), (2, scenes.FLAG_BIN_REUSE),
+                                       (2, scenes.FLAG_BIN_REUSE | scenes.FLAG_PAIRWISE_MIS)])
+def test_transient_bin_reuse(nsp, flags):
+    """Bin reuse (Sec. 4.5): each bin also reuses the same pixel's neighbouring bins, shifted by one
+    bin width, with absent bins at the histogram's ends; temporal, optional spatial and pairwise
+    MIS; same histograms as the oracle."""
+    sc = scenes.box_icosphere(W=24, H=24, frames=2)
+    sc.params.n_spatial, sc.params.radius, sc.params.temporal = nsp, 4, 1
+    sc.params.flags = flags
+    sc.bins = (4.4, 0.1, 40)
+    o, ok, st, _ = oracle_render(sc, [0, 1], B=40)
+    g = gpu_render(sc, [0, 1], B=40)
+    for f in range(2):
+        _check(g[f], o[f])

@@ -183,3 +183,19 @@ def test_pairwise_mis_unbiased(oracle_lib):
     sc.params.flags = 0
     b = O.render_frame(O.View(32, 32, 0), g, sc, 0, seed=5, nthreads=8)[0]
     assert not np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("spatial", [0, 2])
+def test_transient_bin_reuse_unbiased(oracle_lib, spatial):
+    """Bin reuse (Sec. 4.5's extra reuse axis): each bin's reservoir also reuses the same pixel's
+    neighbouring bins, shifted by one bin width; absent bins (outside the histogram) take no part in
+    the MIS.  The histogram stays unbiased per bin."""
+    O = oracle_lib
+    sc = scenes.box_icosphere(W=16, H=16, frames=2)
+    sc.params.n_spatial, sc.params.radius, sc.params.temporal = spatial, 4, 1
+    sc.params.flags = scenes.FLAG_BIN_REUSE
+    sc.bins = (4.4, 0.1, 16)
+    gz, rel, z = _unbiased(O, sc, 2, nseeds=128, nbatches=32, spp=64, B=16)
+    assert abs(gz) < 3.5, (gz, rel)
+    assert abs(rel) < 0.03
+    assert np.max(np.abs(z)) < 4.5, z
