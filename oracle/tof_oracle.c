@@ -757,7 +757,7 @@ static void point_to_xi(const oframe2* f, v3 p, double xi[2]) {
  * motion, under which the average-gradient gauge is invariant, so the walk keeps the shift
  * reversible.
  * ==========================================================================================*/
-#define MAX_CROSS 8
+#define MAX_CROSS 3
 typedef struct { int tri; oframe2 f; double q[3][2]; } owalk;   /* f: chart -> 3-D on tri; q: its corners */
 
 static void walk_init(const ogeom* g, int tri, owalk* W) {
