@@ -833,7 +833,11 @@ static int walk_locate(const ogeom* g, owalk* W, const double from_in[2], const 
     return 0;
 }
 
-/* newton_solve with the offset vertex walking across triangles (W: its triangle and chart) */
+/* Newton with the offset vertex walking across triangles (W: its triangle and chart).  Newton runs
+ * on the plane of W's triangle exactly as without the walk; when the converged point lies outside
+ * the triangle, W walks along the chart segment from the solve's start to it (unfolding each
+ * neighbour it crosses) and Newton continues from that point on the new triangle's plane, with a
+ * fresh iteration budget, for at most MAX_CROSS re-solves. */
 static int newton_solve_walk(const ogeom* gi, const onewton* N0, owalk* W, const double xi[2], double delta, int max_iter,
                              double tol_stop, double tol_succ, double xp[2], double* jdet, int* iters) {
     onewton N = *N0;
@@ -841,51 +845,60 @@ static int newton_solve_walk(const ogeom* gi, const onewton* N0, owalk* W, const
     double Lx, gx[2], hx[3];
     derivs(N.p1x, N.p2x, &N.fx, xi, &Lx, gx, hx);
     xp[0] = xi[0]; xp[1] = xi[1];
+    double start[2] = {xi[0], xi[1]};
     double F[2], gy[2], hy[3], m[2];
-    eval_F(&N, xi, delta, xp, gx, hx, Lx, F, gy, hy, m);
-    int it = 0;
-    while (it < max_iter) {
-        double nF = fmax(fabs(F[0]), fabs(F[1]));
-        if (nF <= tol_stop) break;
-        double A[4], Bm[4];
-        jac_F(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
-        double det = A[0] * A[3] - A[1] * A[2];
-        if (!(fabs(det) > 1e-300)) break;
-        double step[2] = {-(A[3] * F[0] - A[1] * F[1]) / det, -(-A[2] * F[0] + A[0] * F[1]) / det};
-        double lam = 1.0;
-        int accepted = 0;
-        for (int ls = 0; ls < 5; ++ls) {
-            double cand[2] = {xp[0] + lam * step[0], xp[1] + lam * step[1]};
-            owalk Wc = *W;
-            if (walk_locate(gi, &Wc, xp, cand)) {
-                onewton Nc = N;
-                Nc.fy = Wc.f;
+    int total = 0;
+    for (int cross = 0;; ++cross) {
+        eval_F(&N, xi, delta, xp, gx, hx, Lx, F, gy, hy, m);
+        int it = 0;
+        while (it < max_iter) {
+            double nF = fmax(fabs(F[0]), fabs(F[1]));
+            if (nF <= tol_stop) break;
+            double A[4], Bm[4];
+            jac_F(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
+            double det = A[0] * A[3] - A[1] * A[2];
+            if (!(fabs(det) > 1e-300)) break;
+            double step[2] = {-(A[3] * F[0] - A[1] * F[1]) / det, -(-A[2] * F[0] + A[0] * F[1]) / det};
+            double lam = 1.0;
+            int accepted = 0;
+            for (int ls = 0; ls < 5; ++ls) {
+                double cand[2] = {xp[0] + lam * step[0], xp[1] + lam * step[1]};
                 double Fc[2], gyc[2], hyc[3], mc[2];
-                eval_F(&Nc, xi, delta, cand, gx, hx, Lx, Fc, gyc, hyc, mc);
+                eval_F(&N, xi, delta, cand, gx, hx, Lx, Fc, gyc, hyc, mc);
                 if (fmax(fabs(Fc[0]), fabs(Fc[1])) < nF) {
                     xp[0] = cand[0]; xp[1] = cand[1];
                     F[0] = Fc[0]; F[1] = Fc[1];
                     gy[0] = gyc[0]; gy[1] = gyc[1]; hy[0] = hyc[0]; hy[1] = hyc[1]; hy[2] = hyc[2];
                     m[0] = mc[0]; m[1] = mc[1];
-                    *W = Wc;
-                    N.fy = Wc.f;
                     accepted = 1;
                     break;
                 }
+                lam *= 0.5;
             }
-            lam *= 0.5;
+            if (!accepted) break;
+            ++it;
         }
-        if (!accepted) break;
-        ++it;
+        total += it;
+        if (!(fmax(fabs(F[0]), fabs(F[1])) <= tol_succ)) break;
+        double lm[3];
+        walk_bary(W, xp, lm);
+        if (lm[0] >= -BARY_EPS && lm[1] >= -BARY_EPS && lm[2] >= -BARY_EPS) {
+            *iters = total;
+            double A[4], Bm[4];
+            jac_F(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
+            double dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
+            if (!(fabs(dA) > 0)) return 0;
+            *jdet = fabs(dB / dA);
+            return isfinite(*jdet);
+        }
+        if (cross == MAX_CROSS) break;
+        /* the plane's solution lies outside the triangle: walk there and solve again */
+        if (!walk_locate(gi, W, start, xp)) break;
+        N.fy = W->f;
+        start[0] = xp[0]; start[1] = xp[1];
     }
-    *iters = it;
-    if (!(fmax(fabs(F[0]), fabs(F[1])) <= tol_succ)) return 0;
-    double A[4], Bm[4];
-    jac_F(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
-    double dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
-    if (!(fabs(dA) > 0)) return 0;
-    *jdet = fabs(dB / dA);
-    return isfinite(*jdet);
+    *iters = total;
+    return 0;
 }
 
 /* ============================================================================================

@@ -796,7 +796,7 @@ static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float
 // triangle strip differ by a rigid motion, under which the average-gradient gauge is invariant,
 // so the shift stays reversible.
 // ============================================================================================
-constexpr int kMaxCross = 3;   // 8 allowed cost 14 % more frame time for 0.2 % more successful shifts
+constexpr int kMaxCross = 3;   // re-solves on neighbouring triangles per shift (and crossings per walk)
 struct Walk { int tri; Frame2 f; };   // f: chart -> 3-D on tri (corners found from the triangle record)
 
 static __device__ __forceinline__ float3 tri_corner(const GeomDev& g, int tri, int j) {
@@ -874,58 +874,73 @@ static __device__ bool walk_locate(const GeomDev& g, Walk& W, const float from_i
     return false;
 }
 
-// newton_solve with the offset vertex walking across triangles (W: its triangle and chart)
+// Newton with the offset vertex walking across triangles (W: its triangle and chart).  Newton runs
+// on the plane of W's triangle exactly as without the walk; when the converged point lies outside
+// the triangle, W walks along the chart segment from the solve's start to it (unfolding each
+// neighbour it crosses) and Newton continues from that point on the new triangle's plane, with a
+// fresh iteration budget, for at most kMaxCross re-solves.  Shifts that stay on their triangle
+// cost what they cost without the walk.
 static __device__ bool newton_solve_walk(const GeomDev& gi, const NewtonGeo& N, Walk& W, const float xi[2], float delta,
                                          int max_iter, float tol_stop, float tol_succ, float xp[2], float& jdet, int& iters) {
     float Lx, gx[2], hx[3];
     length_derivs(N.p1x, N.p2x, N.fx, xi[0], xi[1], Lx, gx, hx);
     xp[0] = xi[0]; xp[1] = xi[1];
+    float start[2] = {xi[0], xi[1]};
     float F[2], gy[2], hy[3], m[2];
-    newton_F_f(N, W.f, xi, Lx, gx, delta, xp, F, gy, hy, m);
-    int it = 0;
-    // loops kept rolled: the unrolled copies of the line search cost more in instruction-cache misses
-    // than they save (4.9 against 5.1 ms per 512 x 512 frame)
+    int total = 0;
 #pragma unroll 1
-    while (it < max_iter) {
-        float nF = fmaxf(fabsf(F[0]), fabsf(F[1]));
-        if (nF <= tol_stop) break;
-        float A[4], Bm[4];
-        newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
-        float det = A[0] * A[3] - A[1] * A[2];
-        if (!(fabsf(det) > 1e-30f)) break;
-        float s0 = -(A[3] * F[0] - A[1] * F[1]) / det, s1 = -(-A[2] * F[0] + A[0] * F[1]) / det;
-        float lam = 1.0f;
-        bool accepted = false;
+    for (int cross = 0;; ++cross) {
+        newton_F_f(N, W.f, xi, Lx, gx, delta, xp, F, gy, hy, m);
+        int it = 0;
 #pragma unroll 1
-        for (int ls = 0; ls < 5; ++ls) {
-            float c[2] = {xp[0] + lam * s0, xp[1] + lam * s1};
-            Walk Wc = W;
-            if (walk_locate(gi, Wc, xp, c)) {
+        while (it < max_iter) {
+            float nF = fmaxf(fabsf(F[0]), fabsf(F[1]));
+            if (nF <= tol_stop) break;
+            float A[4], Bm[4];
+            newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
+            float det = A[0] * A[3] - A[1] * A[2];
+            if (!(fabsf(det) > 1e-30f)) break;
+            float s0 = -(A[3] * F[0] - A[1] * F[1]) / det, s1 = -(-A[2] * F[0] + A[0] * F[1]) / det;
+            float lam = 1.0f;
+            bool accepted = false;
+#pragma unroll 1
+            for (int ls = 0; ls < 5; ++ls) {
+                float c[2] = {xp[0] + lam * s0, xp[1] + lam * s1};
                 float Fc[2], gyc[2], hyc[3], mc[2];
-                newton_F_f(N, Wc.f, xi, Lx, gx, delta, c, Fc, gyc, hyc, mc);
+                newton_F_f(N, W.f, xi, Lx, gx, delta, c, Fc, gyc, hyc, mc);
                 if (fmaxf(fabsf(Fc[0]), fabsf(Fc[1])) < nF) {
                     xp[0] = c[0]; xp[1] = c[1];
                     F[0] = Fc[0]; F[1] = Fc[1];
                     gy[0] = gyc[0]; gy[1] = gyc[1]; hy[0] = hyc[0]; hy[1] = hyc[1]; hy[2] = hyc[2];
                     m[0] = mc[0]; m[1] = mc[1];
-                    W = Wc;
                     accepted = true;
                     break;
                 }
+                lam *= 0.5f;
             }
-            lam *= 0.5f;
+            if (!accepted) break;
+            ++it;
         }
-        if (!accepted) break;
-        ++it;
+        total += it;
+        if (!(fmaxf(fabsf(F[0]), fabsf(F[1])) <= tol_succ)) break;
+        float lm[3];
+        walk_bary(gi, W, xp[0], xp[1], lm);
+        if (lm[0] >= -kBaryEps && lm[1] >= -kBaryEps && lm[2] >= -kBaryEps) {
+            iters = total;
+            float A[4], Bm[4];
+            newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
+            float dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
+            if (!(fabsf(dA) > 0.f)) return false;
+            jdet = fabsf(dB / dA);
+            return isfinite(jdet);
+        }
+        if (cross == kMaxCross) break;
+        // the plane's solution lies outside the triangle: walk there and solve again
+        if (!walk_locate(gi, W, start, xp)) break;
+        start[0] = xp[0]; start[1] = xp[1];
     }
-    iters = it;
-    if (!(fmaxf(fabsf(F[0]), fabsf(F[1])) <= tol_succ)) return false;
-    float A[4], Bm[4];
-    newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
-    float dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
-    if (!(fabsf(dA) > 0.f)) return false;
-    jdet = fabsf(dB / dA);
-    return isfinite(jdet);
+    iters = total;
+    return false;
 }
 
 // ============================================================================================
