@@ -290,10 +290,14 @@ def run_ours(args, rank, world):
                 nobj=len(sc.object_material))
 
 
+_REF_CACHE = {}
+
+
 def _quality(args, ctx, sid, sc, p, kept, ms_frame, stream, extra=None):
     """relMSE of the kept frames {frame: image} against args.ref_spp-spp plain path-traced references,
     and of plain path tracing at (about) the frame time `ms_frame` on the same frames; the frames'
-    geometry is rebuilt here.  extra: more {frame: image} scored against the same references."""
+    geometry is rebuilt here.  extra: more {frame: image} scored against the same references.
+    References are kept per (scene, materials, frame) and shared by every configuration scored."""
     import torch
     from paper_2605_11536_gb300 import tof
     sptr = stream.cuda_stream
@@ -308,14 +312,18 @@ def _quality(args, ctx, sid, sc, p, kept, ms_frame, stream, extra=None):
             fq = f % nf
             tof.tof_bvh_build(ctx, sid, np.ascontiguousarray(sc.xforms[fq].reshape(-1), dtype=np.float32), refit_only=0,
                               stream=sptr)
-            acc = torch.zeros(H * W, device="cuda", dtype=torch.float64)
-            chunk = 64
-            for c0 in range(0, args.ref_spp, chunk):
-                tof.tof_render_pt(ctx, sid, sc.sensors[fq], sc.emitters[fq], sc.gates[fq], None, p, 9000 + c0, fq, chunk,
-                                  ref.data_ptr(), sptr)
-                acc += ref.double()
-            stream.synchronize()
-            refimg = (acc / (args.ref_spp // chunk)).cpu().numpy().reshape(H, W)
+            key = (sc.name, sc.seed, np.asarray(sc.materials).tobytes(), fq, args.ref_spp, tuple(sc.gates[fq]))
+            refimg = _REF_CACHE.get(key)
+            if refimg is None:
+                acc = torch.zeros(H * W, device="cuda", dtype=torch.float64)
+                chunk = 64
+                for c0 in range(0, args.ref_spp, chunk):
+                    tof.tof_render_pt(ctx, sid, sc.sensors[fq], sc.emitters[fq], sc.gates[fq], None, p, 9000 + c0, fq, chunk,
+                                      ref.data_ptr(), sptr)
+                    acc += ref.double()
+                stream.synchronize()
+                refimg = (acc / (args.ref_spp // chunk)).cpu().numpy().reshape(H, W)
+                _REF_CACHE[key] = refimg
             # plain PT at (approximately) equal time: grow spp until one render takes a frame's time
             for _ in range(8):
                 pt_ev[0].record(stream)
@@ -838,7 +846,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-spp", type=int, default=4096)
-    ap.add_argument("--quality-frames", type=int, default=4, help="frames whose relMSE is averaged")
+    ap.add_argument("--quality-frames", type=int, default=8, help="frames whose relMSE is averaged")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-pairwise", action="store_true", help="skip the pairwise-MIS line")
     ap.add_argument("--no-cpu", action="store_true")
@@ -939,6 +947,7 @@ def main():
         for key, mut in (("quality_walk", _walk), ("quality_shrink_K10_R1", _shrink(10.0, 0)),
                          ("quality_shrink_K10_R1_walk", _shrink(10.0, 0, walk=True)),
                          ("quality_shrink_K3_R1_walk", _shrink(3.0, 0, walk=True)),
+                         ("quality_shrink_K2_R1_walk", _shrink(2.0, 0, walk=True)),
                          ("quality_shrink_K10_R05", _shrink(10.0, 2)), ("quality_shrink_K10_R05_walk", _shrink(10.0, 2, walk=True)),
                          ("quality_shrink_K3_R05_walk", _shrink(3.0, 2, walk=True)),
                          ("quality_all_rough_variant", _all_rough)):
