@@ -348,6 +348,12 @@ def _quality(args, ctx, sid, sc, p, kept, ms_frame, stream, extra=None):
          "mean_vs_reference_per_frame": mean_ratio,
          "pt_spp": spp, "pt_ms": pm, "restir_ms": ms_frame,
          "restir_vs_pt_inv_mse_time": (1.0 / (er * ms_frame)) / (1.0 / (ep * pm)) if er > 0 and ep > 0 else None}
+    # relMSE is dominated by a few firefly pixels, so a single frame can move the mean by orders of
+    # magnitude: the medians over the frames are reported beside it
+    mr, mp = float(np.median(e_restir)), float(np.median(e_pt))
+    q["relmse_restir_median"], q["relmse_pt_median"] = mr, mp
+    q["restir_vs_pt_inv_mse_time_median"] = (mp * pm) / (mr * ms_frame) if mr > 0 and mp > 0 else None
+    q["mean_vs_reference"] = float(np.mean([x for x in mean_ratio if x is not None])) if mean_ratio else None
     return q, e_extra
 
 
