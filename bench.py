@@ -950,7 +950,9 @@ def main():
                                  "spatial_inverse_segments": pf["spatial_inv_rays"]},
             "wall_s": r["wall"]}
     if not args.no_quality:
-        for key, mut in (("quality_walk", _walk), ("quality_shrink_K10_R1", _shrink(10.0, 0)),
+        for key, mut in (("quality_headline_24_frames", lambda sc: "the headline configuration over the variants' 24-frame "
+                                                                    "sequence (the headline's own quality has 248 frames of history)"),
+                         ("quality_walk", _walk), ("quality_shrink_K10_R1", _shrink(10.0, 0)),
                          ("quality_shrink_K10_R1_walk", _shrink(10.0, 0, walk=True)),
                          ("quality_shrink_K3_R1_walk", _shrink(3.0, 0, walk=True)),
                          ("quality_shrink_K2_R1_walk", _shrink(2.0, 0, walk=True)),
