@@ -433,6 +433,16 @@ def _shrink(K, fine, walk=False):
     return mutate
 
 
+def _pairwise_walk(ncand=4):
+    def mutate(sc):
+        from paper_2605_11536_gb300 import scenes
+        sc.params = type(sc.params)(**vars(sc.params))
+        sc.params.flags |= scenes.FLAG_PAIRWISE_MIS | scenes.FLAG_TRIANGLE_WALK
+        sc.params.n_cand = ncand
+        return "pairwise MIS (2k shifts per merge) and the cross-triangle walk, %d path trees; unbiased" % ncand
+    return mutate
+
+
 def _walk(sc):
     from paper_2605_11536_gb300 import scenes
     sc.params = type(sc.params)(**vars(sc.params))
@@ -952,7 +962,8 @@ def main():
     if not args.no_quality:
         for key, mut in (("quality_headline_24_frames", lambda sc: "the headline configuration over the variants' 24-frame "
                                                                     "sequence (the headline's own quality has 248 frames of history)"),
-                         ("quality_walk", _walk), ("quality_shrink_K10_R1", _shrink(10.0, 0)),
+                         ("quality_walk", _walk), ("quality_pairwise_walk", _pairwise_walk()),
+                         ("quality_pairwise_walk_8_trees", _pairwise_walk(8)), ("quality_shrink_K10_R1", _shrink(10.0, 0)),
                          ("quality_shrink_K10_R1_walk", _shrink(10.0, 0, walk=True)),
                          ("quality_shrink_K3_R1_walk", _shrink(3.0, 0, walk=True)),
                          ("quality_shrink_K2_R1_walk", _shrink(2.0, 0, walk=True)),
