@@ -210,7 +210,7 @@ tof_status tof_render_transient(tof_ctx* ctx, tof_scene scene, tof_view view, co
                                 const tof_emitter* emitter, const tof_bins* bins, const tof_params* params,
                                 uint64_t seed, uint32_t frame, float* out_hist_dev, void* stream);
 
-/* One render job of a batch (configs[3]-style batched rendering): a gated (transient == 0) or
+/* One render job of a batch (batched rendering of many independent instances): a gated (transient == 0) or
  * transient frame of one view, exactly as tof_render_gated / tof_render_transient would render it. */
 typedef struct {
     tof_scene scene;
@@ -268,7 +268,7 @@ tof_status tof_view_get_tuning(tof_ctx* ctx, tof_view view, tof_tuning* out);
  * NULL, written to out[i].  Synchronises `stream`; not for use during stream capture. */
 tof_status tof_autotune(tof_ctx* ctx, const tof_job* jobs, uint32_t n, int32_t frames, void* stream, tof_tuning* out);
 
-/* Served form (configs[4]): a request scheduler over several dynamic streams.
+/* Served form: a request scheduler over several dynamic streams.
  *   A stream is a scene plus a fixed sensor resolution (and bin count for transient streams); its
  *   view -- reservoirs, G-buffers, confidences -- is created on first admission and stays resident,
  *   so frames of a stream reuse their predecessors temporally.

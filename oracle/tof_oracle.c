@@ -19,8 +19,8 @@
  *   Sec. 5    reservoir stores the vertex after the reconnection vertex; delta light sources
  *             (point light with NEE, collimated laser spot)
  *
- * Readings where the paper is silent, garbled or inconsistent are listed in the design doc; the ones
- * that change arithmetic are repeated at the function that applies them.
+ * Readings where the paper is silent, garbled or inconsistent are stated at the function that
+ * applies them.
  *
  * Everything is double precision.  Random numbers come from Philox4x32-10 (Salmon et al. 2011)
  * keyed by (seed) and counted by (pixel, frame, stream, purpose), so the CUDA path and this

@@ -1,4 +1,4 @@
-// tof_server.cu -- served form of the ToF ReSTIR path (configs[4]): continuous batching of frame
+// tof_server.cu -- served form of the ToF ReSTIR path (8 dynamic streams, mixed gated and transient): continuous batching of frame
 // requests from several dynamic streams on one GPU.
 //
 // Host-side scheduler over the C ABI: it never waits on the GPU (completion is observed with

@@ -44,7 +44,7 @@ def test_initial_only_box():
 
 
 def test_box_icosphere_64_spatial():
-    """configs[0]: 64x64 box + icosphere, depth 3, L0 = 5, dL = 0.05, 4 trees, 1 neighbour within 8 px."""
+    """The small box workload: 64x64 box + icosphere, depth 3, L0 = 5, dL = 0.05, 4 trees, 1 neighbour within 8 px."""
     sc = scenes.box_icosphere()
     o, ok, st, _ = oracle_render(sc, [0])
     (g,), gst = gpu_render(sc, [0], collect_stats=True)
@@ -117,7 +117,7 @@ def test_heightfield_small_temporal_spatial():
 
 
 def test_confocal_transient_moving_device():
-    """configs[2]'s confocal NLOS setup at reduced size: 32x32 scan, ~4.6k-triangle displaced
+    """The 256x256 x 1024-bin confocal NLOS setup at reduced size: 32x32 scan, ~4.6k-triangle displaced
     sphere behind an occluder, 160 bins of 5 mm, temporal + 3 spatial neighbours over 3 frames
     while the device moves (per-pixel laser spots: the reconnection suffix is re-evaluated)."""
     sc = scenes.confocal_nlos(W=32, H=32, frames=3, B=160, stacks=48, slices=48)
