@@ -101,6 +101,11 @@ def _declare(L):
     L.or_shift_roundtrip.argtypes = [C.c_void_p, C.POINTER(OParams), C.c_uint64, C.c_int, C.c_int, _dp]
     L.or_shrink_roundtrip.restype = C.c_int
     L.or_shrink_roundtrip.argtypes = [C.c_void_p, C.POINTER(OParams), C.c_uint64, C.c_int, C.c_double, _dp]
+    L.or_ell_sample.restype = C.c_int
+    L.or_ell_sample.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_double, _u32p, _dp]
+    L.or_ell_pdf.restype = C.c_double
+    L.or_ell_pdf.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double]
+    L.or_ell_tri_probs.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
 
 
 def _d(a):
@@ -306,3 +311,28 @@ def shrink_roundtrip(view: View, params, seed, pix, K):
     pp = params_struct(params)
     rc = lib().or_shrink_roundtrip(view.ptr, C.byref(pp), seed, pix, float(K), out.ctypes.data_as(_dp))
     return rc, out
+
+
+def ell_sample(geom: Geom, x, q, la, lb, u):
+    """One ellipsoidal-connection placement (Sec. 4.4, Sec. 5) from point x toward the light position
+    q with l = |x - z| + |z - q| drawn in [la, lb) from the 24 draws u.  Returns None or
+    (tri, b1, b2, pdf, z) with pdf the area density of z."""
+    out = np.zeros(7)
+    (xx, xp), (qq, qp), (uu, up) = _d(x), _d(q), _u(u)
+    if not lib().or_ell_sample(geom.ptr, xp, qp, float(la), float(lb), up, out.ctypes.data_as(_dp)):
+        return None
+    return int(out[0]), out[1], out[2], out[3], out[4:7].copy()
+
+
+def ell_pdf(geom: Geom, x, q, la, lb, tri, b1, b2):
+    """Area density with which the ellipsoidal connection places the point (tri, b1, b2)."""
+    (xx, xp), (qq, qp) = _d(x), _d(q)
+    return lib().or_ell_pdf(geom.ptr, xp, qp, float(la), float(lb), int(tri), float(b1), float(b2))
+
+
+def ell_tri_probs(geom: Geom, x, q, ell, nt):
+    """Probability of each triangle under the hierarchy walk for the ellipsoid of major axis ell."""
+    out = np.zeros(nt)
+    (xx, xp), (qq, qp) = _d(x), _d(q)
+    lib().or_ell_tri_probs(geom.ptr, xp, qp, float(ell), out.ctypes.data_as(_dp))
+    return out

@@ -72,7 +72,9 @@ void or_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
 }
 
 /* purposes (low byte of the 4th counter word) */
-enum { P_JITTER = 1, P_BSDF = 2, P_RIS = 3, P_NEIGHBOR = 4, P_MERGE = 5 };
+enum { P_JITTER = 1, P_BSDF = 2, P_RIS = 3, P_NEIGHBOR = 4, P_MERGE = 5,
+       P_ELL_RIS = 6,   /* selection of an ellipsoidal candidate */
+       P_ELL = 7 };     /* P_ELL + q, q = 0..5: the ellipsoidal connection's draws */
 
 static double u01(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
@@ -200,6 +202,8 @@ typedef struct {
     int nnodes;
     onode* nodes;
     int* prim;
+    int eP;         /* leaves of the triangle-index hierarchy of the ellipsoidal connection */
+    double* enode;  /* 2*eP nodes in heap order, 8 doubles each: lo[3], hi[3], area, radius */
     int* adj;       /* nt*3: across the edge opposite vertex i of t, 4 * neighbour + the neighbour's
                        vertex opposite that edge, or -1 (boundary, non-manifold or another object) */
 } ogeom;
@@ -279,6 +283,45 @@ static void build_adjacency(ogeom* g, const uint32_t* tris, const uint32_t* tri_
     free(E);
 }
 
+/* The hierarchy the ellipsoidal connection walks (Sec. 5 "Ellipsoidal Path Connection": BVH
+ * nodes weighted by the area of the triangles below them).  It is the implicit binary tree over
+ * triangle index ranges: eP = the smallest power of two >= nt leaves, node n (1 <= n < 2 eP) has
+ * children 2n and 2n + 1, triangle t is leaf eP + t, padding leaves are empty.  Its shape depends
+ * on the scene alone, not on how a ray-tracing hierarchy was built. */
+#define ELL_MAX_LEVELS 22
+static void etree_build(ogeom* g) {
+    int P = 1;
+    while (P < g->nt) P <<= 1;
+    g->eP = P;
+    g->enode = (double*)malloc(sizeof(double) * 8 * 2 * (size_t)P);
+    for (int i = 0; i < P; ++i) {
+        double* e = g->enode + 8 * (size_t)(P + i);
+        for (int k = 0; k < 3; ++k) { e[k] = 1e300; e[3 + k] = -1e300; }
+        e[6] = 0.0;
+        if (i < g->nt) {
+            const double* v = tri_v(g, i);
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k) {
+                    if (v[3 * c + k] < e[k]) e[k] = v[3 * c + k];
+                    if (v[3 * c + k] > e[3 + k]) e[3 + k] = v[3 * c + k];
+                }
+            v3 v0 = vload(v);
+            e[6] = 0.5 * vlen(vcross(vsub(vload(v + 3), v0), vsub(vload(v + 6), v0)));
+        }
+    }
+    for (int n = P - 1; n >= 1; --n) {
+        double* e = g->enode + 8 * (size_t)n;
+        const double* a = g->enode + 8 * (size_t)(2 * n);
+        const double* b = g->enode + 8 * (size_t)(2 * n + 1);
+        for (int k = 0; k < 3; ++k) { e[k] = fmin(a[k], b[k]); e[3 + k] = fmax(a[3 + k], b[3 + k]); }
+        e[6] = a[6] + b[6];
+    }
+    for (int n = 1; n < 2 * P; ++n) {
+        double* e = g->enode + 8 * (size_t)n;
+        e[7] = e[6] > 0 ? 0.5 * vlen(V(e[3] - e[0], e[4] - e[1], e[5] - e[2])) : 0.0;
+    }
+}
+
 /* verts: object-local vertices; xforms: nobj row-major 3x4 object-to-world matrices */
 ogeom* or_geom_create(const double* verts, int nv, const uint32_t* tris, int nt, const uint32_t* tri_obj,
                       const uint32_t* obj_mat, int nobj, const double* mats, int nmat, const double* xforms) {
@@ -312,12 +355,13 @@ ogeom* or_geom_create(const double* verts, int nv, const uint32_t* tris, int nt,
     if (nt > 0) bvh_build_rec(g, cent, 0, nt);
     free(cent);
     build_adjacency(g, tris, tri_obj, nt);
+    etree_build(g);
     return g;
 }
 
 void or_geom_destroy(ogeom* g) {
     if (!g) return;
-    free(g->tv); free(g->tmat); free(g->mats); free(g->xf); free(g->nodes); free(g->prim); free(g->adj); free(g);
+    free(g->tv); free(g->tmat); free(g->mats); free(g->xf); free(g->nodes); free(g->prim); free(g->adj); free(g->enode); free(g);
 }
 
 /* Moller-Trumbore ray/triangle test (Moller, Trumbore 1997); t in (tmin, tmax).  The barycentric
@@ -460,7 +504,7 @@ typedef struct {
     int shrink_fine;     /* trees kept in the gate itself (canonical samples); 0 = all trees widened */
 } oparams;
 enum { F_DIRECT = 1, F_NAIVE = 2, F_PAIRWISE = 4, F_GAUGE_AXIS_T = 8, F_GAUGE_AXIS_B = 16, F_GAUGE_START = 32,
-       F_WALK = 64, F_BIN_REUSE = 128 };
+       F_WALK = 64, F_BIN_REUSE = 128, F_ELLIPSOID = 256 };
 /* gauge of the Newton system (Sec. 4.3 "Selecting a Good Gauge Condition") */
 enum { G_AVERAGE = 0, G_AXIS_T = 1, G_AXIS_B = 2, G_START = 3 };
 static int gauge_of(uint32_t flags) {
@@ -1244,6 +1288,273 @@ static odomain make_domain(const oframe* F, int pix, const oparams* P, double L0
     return D;
 }
 
+
+/* ============================================================================================
+ * ellipsoidal path connection for NEE (Sec. 4.4 "Initialization with Ellipsoidal Path
+ * Connection", Sec. 5 "Ellipsoidal Path Connection"; Pediredla et al. 2019).  From a rough
+ * vertex x whose prefix has length len, a vertex z is placed so that the path x -> z -> light
+ * lands in the gate:
+ *   (1) l = |x - z| + |z - q| (q the light position) uniform on [l_a, l_b), the interval the gate
+ *       leaves (l_a raised to |x - q|);
+ *   (2) a triangle by a top-down walk of the index hierarchy above: at each node the child is
+ *       taken with probability proportional to its weight, the area below it, or zero where the
+ *       node's box cannot meet the ellipsoid with foci x, q and major axis l (the paper's
+ *       heuristic weights; the test is conservative: distance of x and of q to the box <= l <=
+ *       distance of x and of q to the box centre plus the box diagonal);
+ *   (3) on the triangle's plane the ellipsoid cuts an ellipse; z is uniform in the ellipse's
+ *       parametric angle phi over the arcs inside the triangle (total angle Phi).
+ * Area density of z (coarea formula: dA = dl ds / |grad_plane l|, ds = |dz/dphi| dphi):
+ *   p_ell(z) = P(tri | l) / (l_b - l_a) / Phi * |grad_plane l(z)| / |dz/dphi|.
+ * Ellipsoids thinner than b = 0.01 a (a the semi-major axis) place no vertex, in the sampler and
+ * in the density alike; the MIS with the path tree covers them.
+ * ==========================================================================================*/
+static double enode_w(const double* e, v3 x, v3 q, double ell) {
+    if (!(e[6] > 0)) return 0.0;
+    double px[3] = {x.x, x.y, x.z}, pq[3] = {q.x, q.y, q.z};
+    double dx2 = 0.0, dq2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double cx = fmin(fmax(px[k], e[k]), e[3 + k]), cq = fmin(fmax(pq[k], e[k]), e[3 + k]);
+        dx2 += (px[k] - cx) * (px[k] - cx);
+        dq2 += (pq[k] - cq) * (pq[k] - cq);
+    }
+    double lb = sqrt(dx2) + sqrt(dq2);
+    if (lb > ell) return 0.0;
+    double ub = 0.0;   /* l(z) is convex: its maximum over the box is at a corner */
+    for (int k = 0; k < 8; ++k) {
+        v3 c = V(e[(k & 1) ? 3 : 0], e[(k & 2) ? 4 : 1], e[(k & 4) ? 5 : 2]);
+        ub = fmax(ub, vlen(vsub(x, c)) + vlen(vsub(q, c)));
+    }
+    return ell <= ub ? e[6] : 0.0;
+}
+
+static int elog2(int P) { int L = 0; while ((1 << L) < P) ++L; return L; }
+
+/* step (2): the triangle (or -1) and its probability; u: one uniform per level */
+static int etree_pick(const ogeom* g, v3 x, v3 q, double ell, const double* u, double* prob) {
+    int n = 1, lvl = 0;
+    double p = 1.0;
+    while (n < g->eP) {
+        double w0 = enode_w(g->enode + 8 * (size_t)(2 * n), x, q, ell);
+        double w1 = enode_w(g->enode + 8 * (size_t)(2 * n + 1), x, q, ell);
+        double s = w0 + w1;
+        if (!(s > 0)) return -1;
+        if (u[lvl] * s < w0) { n = 2 * n; p *= w0 / s; }
+        else { n = 2 * n + 1; p *= w1 / s; }
+        ++lvl;
+    }
+    *prob = p;
+    return n - g->eP;
+}
+/* P(tri | l) of step (2), walking the root-to-leaf path of tri */
+static double etree_prob(const ogeom* g, int tri, v3 x, v3 q, double ell) {
+    const int L = elog2(g->eP), leaf = g->eP + tri;
+    double p = 1.0;
+    for (int i = 0; i < L; ++i) {
+        int n = leaf >> (L - i), next = leaf >> (L - i - 1);
+        double w0 = enode_w(g->enode + 8 * (size_t)(2 * n), x, q, ell);
+        double w1 = enode_w(g->enode + 8 * (size_t)(2 * n + 1), x, q, ell);
+        double s = w0 + w1, w = next == 2 * n ? w0 : w1;
+        if (!(s > 0) || !(w > 0)) return 0.0;
+        p *= w / s;
+    }
+    return p;
+}
+
+/* step (3): the ellipse the ellipsoid (foci x, q; major axis l) cuts from the plane of tri, in the
+ * triangle's frame (o = v0, t, b):  xi = xo + w0 + R1 cos(phi) g1 + R2 sin(phi) g2, and the arcs
+ * of phi inside the triangle.  With m the centre, a = l/2, c = |q - x|/2, b^2 = a^2 - c^2,
+ * d = (q - x)/|q - x|, n the normal, h = (m - v0).n, the plane's points m - h n + w1 t + w2 b
+ * satisfy |r|^2 + beta (r.d)^2 = b^2 (beta = -c^2/a^2), i.e. w^T (I + beta g g^T) w
+ * - 2 beta h (d.n) g.w + h^2 (1 + beta (d.n)^2) - b^2 = 0 with g = (d.t, d.b): centre
+ * w0 = beta h (d.n) g / gamma, gamma = 1 + beta |g|^2, and (w - w0)^T A (w - w0) = kappa =
+ * b^2 (1 - h^2 / (a^2 gamma)); radii sqrt(kappa / gamma) along g, sqrt(kappa) across it. */
+typedef struct {
+    double xo[2], w0[2], g1[2], g2[2], R1, R2;
+    int narc;
+    double a0[6], alen[6];
+    double Phi;
+} oellip;
+
+static int ellip_inside(const double c[3][2], double orient, double px, double py) {
+    for (int i = 0; i < 3; ++i) {
+        const double* a = c[i];
+        const double* b = c[(i + 1) % 3];
+        double cr = (b[0] - a[0]) * (py - a[1]) - (b[1] - a[1]) * (px - a[0]);
+        if (cr * orient < 0) return 0;
+    }
+    return 1;
+}
+
+static int ellip_on_tri(const ogeom* g, int tri, v3 x, v3 q, double ell, oellip* E) {
+    oframe2 f = tri_frame(g, tri);
+    v3 n = vcross(f.t, f.b);
+    v3 m = vmul(vadd(x, q), 0.5);
+    double a = 0.5 * ell, c = 0.5 * vlen(vsub(q, x));
+    double b2 = a * a - c * c;
+    if (!(b2 >= 1e-4 * a * a)) return 0;
+    v3 d = c > 0 ? vmul(vsub(q, x), 0.5 / c) : V(0, 0, 0);
+    double beta = -(c * c) / (a * a);
+    double dt = vdot(d, f.t), db = vdot(d, f.b), dn = vdot(d, n);
+    double h = vdot(vsub(m, f.o), n);
+    double gamma = 1.0 + beta * (dt * dt + db * db);
+    double kappa = b2 * (1.0 - h * h / (a * a * gamma));
+    if (!(kappa > 0)) return 0;
+    E->xo[0] = vdot(vsub(m, f.o), f.t);
+    E->xo[1] = vdot(vsub(m, f.o), f.b);
+    E->w0[0] = beta * h * dn * dt / gamma;
+    E->w0[1] = beta * h * dn * db / gamma;
+    double gl = sqrt(dt * dt + db * db);
+    if (gl > 1e-12) { E->g1[0] = dt / gl; E->g1[1] = db / gl; }
+    else { E->g1[0] = 1.0; E->g1[1] = 0.0; }
+    E->g2[0] = -E->g1[1]; E->g2[1] = E->g1[0];
+    E->R1 = sqrt(kappa / gamma);
+    E->R2 = sqrt(kappa);
+    /* corners in the unit-circle coordinates of the ellipse */
+    const double* v = tri_v(g, tri);
+    v3 v0 = vload(v);
+    double cc[3][2];
+    for (int i = 0; i < 3; ++i) {
+        v3 dv = vsub(vload(v + 3 * i), v0);
+        double w[2] = {vdot(dv, f.t) - E->xo[0] - E->w0[0], vdot(dv, f.b) - E->xo[1] - E->w0[1]};
+        cc[i][0] = (w[0] * E->g1[0] + w[1] * E->g1[1]) / E->R1;
+        cc[i][1] = (w[0] * E->g2[0] + w[1] * E->g2[1]) / E->R2;
+    }
+    double orient = (cc[1][0] - cc[0][0]) * (cc[2][1] - cc[0][1]) - (cc[1][1] - cc[0][1]) * (cc[2][0] - cc[0][0]);
+    if (orient == 0.0) return 0;
+    /* crossings of the unit circle with the edges */
+    double ph[6];
+    int np = 0;
+    for (int i = 0; i < 3; ++i) {
+        const double* P0 = cc[i];
+        const double* P1 = cc[(i + 1) % 3];
+        double e0 = P1[0] - P0[0], e1 = P1[1] - P0[1];
+        double A2 = e0 * e0 + e1 * e1, B2 = P0[0] * e0 + P0[1] * e1, C2 = P0[0] * P0[0] + P0[1] * P0[1] - 1.0;
+        double disc = B2 * B2 - A2 * C2;
+        if (!(disc > 0) || !(A2 > 0)) continue;
+        double sq = sqrt(disc);
+        double sr[2] = {(-B2 - sq) / A2, (-B2 + sq) / A2};
+        for (int k = 0; k < 2; ++k)
+            if (sr[k] >= 0.0 && sr[k] <= 1.0) ph[np++] = atan2(P0[1] + sr[k] * e1, P0[0] + sr[k] * e0);
+    }
+    for (int i = 1; i < np; ++i)
+        for (int j = i; j > 0 && ph[j - 1] > ph[j]; --j) { double t = ph[j]; ph[j] = ph[j - 1]; ph[j - 1] = t; }
+    E->narc = 0;
+    E->Phi = 0.0;
+    if (np == 0) {
+        if (ellip_inside(cc, orient, 1.0, 0.0)) { E->narc = 1; E->a0[0] = 0.0; E->alen[0] = 2.0 * OPI; E->Phi = 2.0 * OPI; }
+    } else {
+        for (int i = 0; i < np; ++i) {
+            double s0 = ph[i], s1 = i + 1 < np ? ph[i + 1] : ph[0] + 2.0 * OPI;
+            if (!(s1 > s0)) continue;
+            double mid = 0.5 * (s0 + s1);
+            if (!ellip_inside(cc, orient, cos(mid), sin(mid))) continue;
+            E->a0[E->narc] = s0; E->alen[E->narc] = s1 - s0; E->narc++;
+            E->Phi += s1 - s0;
+        }
+    }
+    return E->Phi > 0;
+}
+
+/* interval [l_a, l_b) of l = |x - z| + |z - q| that puts the path in [glo, ghi); 0 if empty */
+static int ell_range(const odomain* D, v3 x, double len, double glo, double ghi, v3* q, double* la, double* lb) {
+    if (D->light.kind == 0) return 0;
+    *q = D->light.kind == 2 ? D->light.s.p : D->light.pos;
+    double e = D->light.kind == 2 ? D->light.emit_len : 0.0;
+    *la = fmax(glo + D->o - len - e, vlen(vsub(x, *q)));
+    *lb = ghi + D->o - len - e;
+    return *lb > *la;
+}
+
+/* density factor |grad_plane l(z)| / |dz/dphi| and P(tri | l) (1/(l_b - l_a) and 1/Phi apart) */
+static double ell_point_factor(const oellip* E, const oframe2* f, v3 z, v3 x, v3 q) {
+    v3 n = vcross(f->t, f->b);
+    v3 gr = vadd(dir_to(x, z), dir_to(q, z));
+    double gn = vdot(gr, n);
+    double gp = sqrt(fmax(vdot(gr, gr) - gn * gn, 0.0));
+    double w[2] = {vdot(vsub(z, f->o), f->t) - E->xo[0] - E->w0[0], vdot(vsub(z, f->o), f->b) - E->xo[1] - E->w0[1]};
+    double c0 = (w[0] * E->g1[0] + w[1] * E->g1[1]) / E->R1, c1 = (w[0] * E->g2[0] + w[1] * E->g2[1]) / E->R2;
+    double cl = sqrt(c0 * c0 + c1 * c1);
+    if (!(cl > 0)) return 0.0;
+    c0 /= cl; c1 /= cl;
+    double dz = sqrt(E->R1 * E->R1 * c1 * c1 + E->R2 * E->R2 * c0 * c0);
+    return dz > 0 ? gp / dz : 0.0;
+}
+
+/* steps (2)-(3) for l_a <= l < l_b given the draws u (u[0] -> l, u[1] -> phi, u[2..] -> the levels) */
+static int ell_sample_core(const ogeom* g, v3 x, v3 q, double la, double lb, const uint32_t u[24], osurf* z, double* pdf) {
+    if (g->nt < 1 || elog2(g->eP) > ELL_MAX_LEVELS || !(lb > la)) return 0;
+    double ell = la + u01(u[0]) * (lb - la);
+    double ul[ELL_MAX_LEVELS];
+    for (int k = 0; k < ELL_MAX_LEVELS; ++k) ul[k] = u01(u[2 + k]);
+    double ptri;
+    int tri = etree_pick(g, x, q, ell, ul, &ptri);
+    if (tri < 0) return 0;
+    oellip E;
+    if (!ellip_on_tri(g, tri, x, q, ell, &E)) return 0;
+    double t = u01(u[1]) * E.Phi, cum = 0.0, phi = 0.0;
+    for (int i = 0; i < E.narc; ++i) {
+        if (t < cum + E.alen[i] || i == E.narc - 1) { phi = E.a0[i] + fmin(t - cum, E.alen[i]); break; }
+        cum += E.alen[i];
+    }
+    double cp = cos(phi), sp = sin(phi);
+    double xi[2] = {E.xo[0] + E.w0[0] + E.R1 * cp * E.g1[0] + E.R2 * sp * E.g2[0],
+                    E.xo[1] + E.w0[1] + E.R1 * cp * E.g1[1] + E.R2 * sp * E.g2[1]};
+    oframe2 f = tri_frame(g, tri);
+    double b1, b2;
+    xi_to_bary(g, tri, &f, xi, &b1, &b2);
+    *z = surf_at(g, tri, b1, b2);
+    *pdf = ptri / (lb - la) / E.Phi * ell_point_factor(&E, &f, z->p, x, q);
+    return *pdf > 0;
+}
+static double ell_pdf_core(const ogeom* g, v3 x, v3 q, double la, double lb, const osurf* z) {
+    if (g->nt < 1 || elog2(g->eP) > ELL_MAX_LEVELS || !(lb > la)) return 0.0;
+    double ell = vlen(vsub(z->p, x)) + vlen(vsub(q, z->p));
+    if (!(ell >= la && ell < lb)) return 0.0;
+    double ptri = etree_prob(g, z->tri, x, q, ell);
+    if (!(ptri > 0)) return 0.0;
+    oellip E;
+    if (!ellip_on_tri(g, z->tri, x, q, ell, &E)) return 0.0;
+    oframe2 f = tri_frame(g, z->tri);
+    return ptri / (lb - la) / E.Phi * ell_point_factor(&E, &f, z->p, x, q);
+}
+
+/* sample z from vertex x (prefix length len, path tree `tree`, vertex index d); 1 if placed */
+static int ell_sample(const ogeom* g, const odomain* D, uint64_t seed, uint32_t px, uint32_t frame, int tree, int d,
+                      const osurf* x, double len, double glo, double ghi, osurf* z, double* pdf) {
+    v3 q;
+    double la, lb;
+    if (!ell_range(D, x->p, len, glo, ghi, &q, &la, &lb)) return 0;
+    uint32_t u[24];
+    for (int k = 0; k < 6; ++k) rng4(seed, px, frame, ((uint32_t)tree << 8) | (uint32_t)d, P_ELL + k, u + 4 * k);
+    return ell_sample_core(g, x->p, q, la, lb, u, z, pdf);
+}
+
+/* p_ell(z) of a vertex z reached from x by other means (0 where the sampler cannot place it) */
+static double ell_pdf(const ogeom* g, const odomain* D, const osurf* x, double len, double glo, double ghi, const osurf* z) {
+    v3 q;
+    double la, lb;
+    if (!ell_range(D, x->p, len, glo, ghi, &q, &la, &lb)) return 0.0;
+    return ell_pdf_core(g, x->p, q, la, lb, z);
+}
+
+/* test access: one ellipsoidal placement from x toward light position q on [la, lb) with the draws
+ * u[24]; out = (tri, b1, b2, pdf, z.xyz); returns 1 if placed.  And the density at (tri, b1, b2). */
+int or_ell_sample(const ogeom* g, const double* x, const double* q, double la, double lb, const uint32_t* u, double out[7]) {
+    osurf z;
+    double pdf = 0.0;
+    if (!ell_sample_core(g, vload(x), vload(q), la, lb, u, &z, &pdf)) return 0;
+    out[0] = z.tri; out[1] = z.b1; out[2] = z.b2; out[3] = pdf; out[4] = z.p.x; out[5] = z.p.y; out[6] = z.p.z;
+    return 1;
+}
+double or_ell_pdf(const ogeom* g, const double* x, const double* q, double la, double lb, int tri, double b1, double b2) {
+    osurf z = surf_at(g, tri, b1, b2);
+    return ell_pdf_core(g, vload(x), vload(q), la, lb, &z);
+}
+/* P(tri | l) of the hierarchy walk, for every triangle (out[nt]) */
+void or_ell_tri_probs(const ogeom* g, const double* x, const double* q, double ell, double* out) {
+    for (int t = 0; t < g->nt; ++t) out[t] = etree_prob(g, t, vload(x), vload(q), ell);
+}
+
 /* ============================================================================================
  * initial candidates (Sec. 3.2 RIS, stage (1); Sec. 4.5 per-bin deposit for transients)
  * Path trees: BSDF-sampled paths with NEE to the delta light at every vertex; the candidate of
@@ -1309,11 +1620,16 @@ static void build_rec(const ogeom* g, const odomain* D, const opathbuf* pb, int 
 }
 
 /* One path tree; calls the candidate sink for every NEE path of length k in [kmin, depth].
- * The sink receives (k, c = f/p without the gate, tau). */
-typedef void (*cand_sink)(void* ctx, int k, double c, double tau, const opathbuf* pb);
+ * The sink receives (k, c = f/p without the gate, tau, the strategy: 0 the tree's own NEE, 1 the
+ * ellipsoidal connection).  With `ell`, every rough vertex x_d (d < depth) also places a vertex z
+ * by the ellipsoidal connection, a candidate of length d + 1; it and the tree's NEE candidate of
+ * the same length (whose last vertex x_{d+1} the tree sampled from x_d) are combined by the
+ * balance heuristic over the two densities of that vertex (Sec. 5: MIS between the direct and the
+ * ellipsoidal connection):  c_tree *= p_tree / (p_tree + p_ell),  c_ell = f / (p_tree + p_ell). */
+typedef void (*cand_sink)(void* ctx, int k, double c, double tau, const opathbuf* pb, int strategy);
 
 static void trace_tree(const ogeom* g, const odomain* D, const oparams* P, uint64_t seed, uint32_t px, uint32_t frame,
-                       int tree, int gated_lo_hi, double glo, double ghi, cand_sink sink, void* ctx) {
+                       int tree, int gated_lo_hi, double glo, double ghi, int ell, cand_sink sink, void* ctx) {
     opathbuf pb;
     pb.v[1] = D->y1;
     pb.cls[1] = mat_class(&g->mats[D->y1.mat]);
@@ -1321,6 +1637,8 @@ static void trace_tree(const ogeom* g, const odomain* D, const oparams* P, uint6
     double len = vlen(vsub(D->x0, D->y1.p));
     double beta = 1.0;
     int kmin = (P->flags & F_DIRECT) ? 1 : 2;
+    int ell_prev = 0;        /* the ellipsoidal connection was available at x_{d-1} */
+    double len_prev = 0.0;
     for (int d = 1; d <= P->depth; ++d) {
         const osurf* x = &pb.v[d];
         const omat* m = &g->mats[x->mat];
@@ -1332,9 +1650,44 @@ static void trace_tree(const ogeom* g, const odomain* D, const oparams* P, uint6
             if (fs > 0) {
                 double tau = len + seg - D->o;
                 int in = gated_lo_hi ? (tau >= glo && tau < ghi) : 1;
-                if (in && light_visible(g, &D->light, x, P->ray_eps)) sink(ctx, d, beta * fs * lt, tau, &pb);
+                if (in && light_visible(g, &D->light, x, P->ray_eps)) {
+                    double c = beta * fs * lt;
+                    if (ell_prev) {
+                        double pt = pb.pdfA[d], pe = ell_pdf(g, D, &pb.v[d - 1], len_prev, glo, ghi, x);
+                        c *= pt / (pt + pe);
+                    }
+                    sink(ctx, d, c, tau, &pb, 0);
+                }
             }
         }
+        const int ell_here = ell && gated_lo_hi && d < P->depth && mat_class(m) != C_DELTA && D->light.kind != 0;
+        if (ell_here) {
+            osurf z;
+            double pe;
+            if (ell_sample(g, D, seed, px, frame, tree, d, x, len, glo, ghi, &z, &pe)) {
+                const omat* mz = &g->mats[z.mat];
+                v3 wz = dir_to(x->p, z.p);
+                double dist = vlen(vsub(z.p, x->p));
+                double fx = bsdf_f(m, x->n, wi, wz);
+                if (fx > 0 && dist > 0 && mat_class(mz) != C_DELTA) {
+                    v3 wl; double seg;
+                    double lt = light_term(g, &D->light, &z, &wl, &seg);
+                    double fz = lt > 0 ? bsdf_f(mz, z.n, vmul(wz, -1.0), wl) : 0.0;
+                    double tau = len + dist + seg - D->o;
+                    if (fz > 0 && tau >= glo && tau < ghi && visible(g, x->p, x->n, z.p, &z.n, P->ray_eps) &&
+                        light_visible(g, &D->light, &z, P->ray_eps)) {
+                        double pt = bsdf_pdf(m, x->n, wi, wz) * fabs(vdot(z.n, wz)) / (dist * dist);
+                        double c = beta * fx * Gterm(x, &z) * fz * lt / (pt + pe);
+                        pb.v[d + 1] = z;
+                        pb.cls[d + 1] = mat_class(mz);
+                        pb.pdfA[d + 1] = pt;
+                        sink(ctx, d + 1, c, tau, &pb, 1);
+                    }
+                }
+            }
+        }
+        ell_prev = ell_here;
+        len_prev = len;
         if (d == P->depth) break;
         uint32_t u[4];
         rng4(seed, px, frame, ((uint32_t)tree << 8) | (uint32_t)d, P_BSDF, u);
@@ -1358,7 +1711,7 @@ typedef struct {
     double invN;
 } oinit_ctx;
 
-static void init_sink(void* vctx, int k, double c, double tau, const opathbuf* pb) {
+static void init_sink(void* vctx, int k, double c, double tau, const opathbuf* pb, int strategy) {
     oinit_ctx* C = (oinit_ctx*)vctx;
     double w = C->invN * c;
     if (!(w > 0)) return;
@@ -1369,7 +1722,7 @@ static void init_sink(void* vctx, int k, double c, double tau, const opathbuf* p
         b = (int)fb;
     }
     uint32_t u[4];
-    rng4(C->seed, C->px, C->frame, ((uint32_t)C->tree << 8) | (uint32_t)k, P_RIS, u);
+    rng4(C->seed, C->px, C->frame, ((uint32_t)C->tree << 8) | (uint32_t)k, strategy ? P_ELL_RIS : P_RIS, u);
     C->S[b] += w;
     if (u01(u[0]) * C->S[b] < w)
         build_rec(C->g, C->D, pb, k, C->tree, C->px, C->frame, tau, C->P, &C->out[b]);
@@ -1399,8 +1752,8 @@ static void initial_shrink(const ogeom* g, const odomain* D, const oparams* P, u
     oinit_ctx Ca = {g, D, P, seed, px, frame, 0, 0, L0, dL, &xa, &Sa, NA > 0 ? 1.0 / NA : 0.0};
     oinit_ctx Cb = {g, D, P, seed, px, frame, 0, 0, L0, dL, &xb, &Sb, 1.0 / NB};
     for (int t = 0; t < P->n_cand; ++t) {
-        if (t < NA) { Ca.tree = t; trace_tree(g, D, P, seed, px, frame, t, 1, L0, L0 + dL, init_sink, &Ca); }
-        else { Cb.tree = t; trace_tree(g, D, P, seed, px, frame, t, 1, c - half, c + half, init_sink, &Cb); }
+        if (t < NA) { Ca.tree = t; trace_tree(g, D, P, seed, px, frame, t, 1, L0, L0 + dL, 0, init_sink, &Ca); }
+        else { Cb.tree = t; trace_tree(g, D, P, seed, px, frame, t, 1, c - half, c + half, 0, init_sink, &Cb); }
     }
     const double Wa = (xa.valid && xa.phat > 0) ? Sa / xa.phat : 0.0;
     const double Wb = (xb.valid && xb.phat > 0) ? Sb / xb.phat : 0.0;
@@ -1566,6 +1919,7 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
     const int Bn = B > 0 ? B : 1;
     if (Bn != v->Bn || s->W != W || s->H != H) return -1;
     if (P->depth < 1 || P->depth > MAXD - 2 || P->n_cand < 1 || P->n_spatial > 15) return -1;
+    if ((P->flags & F_ELLIPSOID) && B == 0 && P->shrink_k > 1.0) return -1;   /* one initial sampler at a time */
     int prev = v->cur;
     int cur = v->has_prev ? 1 - v->cur : v->cur;
     oframe* F = &v->fr[cur];
@@ -1624,8 +1978,9 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
         oinit_ctx C = {g, &D, P, seed, (uint32_t)pix, frame, 0, B, L0, dL, rr, S, 1.0 / P->n_cand};
         for (int t = 0; t < P->n_cand; ++t) {
             C.tree = t;
-            if (B > 0) trace_tree(g, &D, P, seed, (uint32_t)pix, frame, t, 1, L0, L0 + B * dL, init_sink, &C);
-            else trace_tree(g, &D, P, seed, (uint32_t)pix, frame, t, 1, L0, L0 + dL, init_sink, &C);
+            const int ell = (P->flags & F_ELLIPSOID) != 0;
+            if (B > 0) trace_tree(g, &D, P, seed, (uint32_t)pix, frame, t, 1, L0, L0 + B * dL, ell, init_sink, &C);
+            else trace_tree(g, &D, P, seed, (uint32_t)pix, frame, t, 1, L0, L0 + dL, ell, init_sink, &C);
         }
         for (int b = 0; b < Bn; ++b) {
             if (rr[b].valid && rr[b].phat > 0) { rr[b].W = S[b] / rr[b].phat; rr[b].M = P->n_cand; }
@@ -1815,8 +2170,8 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
  * f / p into the gate (B == 0) or its bin.
  * ==========================================================================================*/
 typedef struct { int B; double t0, w; double* acc; double scale; } opt_ctx;
-static void pt_sink(void* vctx, int k, double c, double tau, const opathbuf* pb) {
-    (void)k; (void)pb;
+static void pt_sink(void* vctx, int k, double c, double tau, const opathbuf* pb, int strategy) {
+    (void)k; (void)pb; (void)strategy;
     opt_ctx* C = (opt_ctx*)vctx;
     if (C->B > 0) {
         double fb = floor((tau - C->t0) / C->w);
@@ -1871,8 +2226,8 @@ int or_render_pt(const ogeom* g, const osensor* s, const oemitter* e, double L0,
                 D.light.emit_len = vlen(vsub(vload(e->pos), D.y1.p)); D.light.pos = D.y1.p;
             }
             opt_ctx C = {B, L0, dL, acc, 1.0 / spp};
-            if (B > 0) trace_tree(g, &D, P, seed, (uint32_t)pix, frame, sm, 1, L0, L0 + B * dL, pt_sink, &C);
-            else trace_tree(g, &D, P, seed, (uint32_t)pix, frame, sm, 1, L0, L0 + dL, pt_sink, &C);
+            if (B > 0) trace_tree(g, &D, P, seed, (uint32_t)pix, frame, sm, 1, L0, L0 + B * dL, 0, pt_sink, &C);
+            else trace_tree(g, &D, P, seed, (uint32_t)pix, frame, sm, 1, L0, L0 + dL, 0, pt_sink, &C);
         }
     }
     return 0;

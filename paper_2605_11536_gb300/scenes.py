@@ -40,6 +40,7 @@ FLAG_GAUGE_AXIS_B = 16   # comparison gauge: fixed axis, the reconnection vertex
 FLAG_GAUGE_START = 32    # comparison gauge: gradient at the start point only (not reversible)
 FLAG_TRIANGLE_WALK = 64  # the reconnection vertex may walk across triangle edges during Newton
 FLAG_BIN_REUSE = 128     # transient: one pass reusing each pixel's neighbouring bins (Sec. 4.5)
+FLAG_ELLIPSOID = 256     # initial candidates also by ellipsoidal path connection, MIS with the path tree
 
 
 @dataclass
