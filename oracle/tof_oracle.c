@@ -203,7 +203,7 @@ typedef struct {
     onode* nodes;
     int* prim;
     int eP;         /* leaves of the triangle-index hierarchy of the ellipsoidal connection */
-    double* enode;  /* 2*eP nodes in heap order, 8 doubles each: lo[3], hi[3], area, radius */
+    double* enode;  /* 2*eP nodes in heap order, 8 doubles each: lo[3], hi[3], area, unused */
     int* adj;       /* nt*3: across the edge opposite vertex i of t, 4 * neighbour + the neighbour's
                        vertex opposite that edge, or -1 (boundary, non-manifold or another object) */
 } ogeom;
@@ -297,7 +297,7 @@ static void etree_build(ogeom* g) {
     for (int i = 0; i < P; ++i) {
         double* e = g->enode + 8 * (size_t)(P + i);
         for (int k = 0; k < 3; ++k) { e[k] = 1e300; e[3 + k] = -1e300; }
-        e[6] = 0.0;
+        e[6] = e[7] = 0.0;
         if (i < g->nt) {
             const double* v = tri_v(g, i);
             for (int c = 0; c < 3; ++c)
@@ -315,10 +315,7 @@ static void etree_build(ogeom* g) {
         const double* b = g->enode + 8 * (size_t)(2 * n + 1);
         for (int k = 0; k < 3; ++k) { e[k] = fmin(a[k], b[k]); e[3 + k] = fmax(a[3 + k], b[3 + k]); }
         e[6] = a[6] + b[6];
-    }
-    for (int n = 1; n < 2 * P; ++n) {
-        double* e = g->enode + 8 * (size_t)n;
-        e[7] = e[6] > 0 ? 0.5 * vlen(V(e[3] - e[0], e[4] - e[1], e[5] - e[2])) : 0.0;
+        e[7] = 0.0;
     }
 }
 
@@ -1299,8 +1296,8 @@ static odomain make_domain(const oframe* F, int pix, const oparams* P, double L0
  *   (2) a triangle by a top-down walk of the index hierarchy above: at each node the child is
  *       taken with probability proportional to its weight, the area below it, or zero where the
  *       node's box cannot meet the ellipsoid with foci x, q and major axis l (the paper's
- *       heuristic weights; the test is conservative: distance of x and of q to the box <= l <=
- *       distance of x and of q to the box centre plus the box diagonal);
+ *       heuristic weights; the test is conservative: the distances of x and of q to the box bound
+ *       l from below, their distances to the box's farthest points bound it from above);
  *   (3) on the triangle's plane the ellipsoid cuts an ellipse; z is uniform in the ellipse's
  *       parametric angle phi over the arcs inside the triangle (total angle Phi).
  * Area density of z (coarea formula: dA = dl ds / |grad_plane l|, ds = |dz/dphi| dphi):
@@ -1319,11 +1316,12 @@ static double enode_w(const double* e, v3 x, v3 q, double ell) {
     }
     double lb = sqrt(dx2) + sqrt(dq2);
     if (lb > ell) return 0.0;
-    double ub = 0.0;   /* l(z) is convex: its maximum over the box is at a corner */
-    for (int k = 0; k < 8; ++k) {
-        v3 c = V(e[(k & 1) ? 3 : 0], e[(k & 2) ? 4 : 1], e[(k & 4) ? 5 : 2]);
-        ub = fmax(ub, vlen(vsub(x, c)) + vlen(vsub(q, c)));
+    double fx2 = 0.0, fq2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double a = fmax(fabs(px[k] - e[k]), fabs(px[k] - e[3 + k])), b = fmax(fabs(pq[k] - e[k]), fabs(pq[k] - e[3 + k]));
+        fx2 += a * a; fq2 += b * b;
     }
+    double ub = sqrt(fx2) + sqrt(fq2);
     return ell <= ub ? e[6] : 0.0;
 }
 
