@@ -443,6 +443,22 @@ def _pairwise_walk(ncand=4):
     return mutate
 
 
+def _ellipsoid(extra=0, ncand=None):
+    def mutate(sc):
+        from paper_2605_11536_gb300 import scenes
+        sc.params = type(sc.params)(**vars(sc.params))
+        sc.params.flags |= scenes.FLAG_ELLIPSOID | extra
+        if ncand:
+            sc.params.n_cand = ncand
+        names = ["ellipsoidal connection (Sec. 4.4, Sec. 5) for the initial candidates"]
+        if extra & scenes.FLAG_PAIRWISE_MIS:
+            names.append("pairwise MIS")
+        if extra & scenes.FLAG_TRIANGLE_WALK:
+            names.append("the cross-triangle walk")
+        return ", ".join(names) + (", %d path trees" % ncand if ncand else "") + "; unbiased"
+    return mutate
+
+
 def _walk(sc):
     from paper_2605_11536_gb300 import scenes
     sc.params = type(sc.params)(**vars(sc.params))
@@ -963,7 +979,10 @@ def main():
         for key, mut in (("quality_headline_24_frames", lambda sc: "the headline configuration over the variants' 24-frame "
                                                                     "sequence (the headline's own quality has 248 frames of history)"),
                          ("quality_walk", _walk), ("quality_pairwise_walk", _pairwise_walk()),
-                         ("quality_pairwise_walk_8_trees", _pairwise_walk(8)), ("quality_shrink_K10_R1", _shrink(10.0, 0)),
+                         ("quality_pairwise_walk_8_trees", _pairwise_walk(8)), ("quality_ellipsoid", _ellipsoid()),
+                         ("quality_ellipsoid_pairwise", _ellipsoid(4)),
+                         ("quality_ellipsoid_pairwise_walk", _ellipsoid(4 | 64)),
+                         ("quality_shrink_K10_R1", _shrink(10.0, 0)),
                          ("quality_shrink_K10_R1_walk", _shrink(10.0, 0, walk=True)),
                          ("quality_shrink_K3_R1_walk", _shrink(3.0, 0, walk=True)),
                          ("quality_shrink_K2_R1_walk", _shrink(2.0, 0, walk=True)),

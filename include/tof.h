@@ -112,6 +112,19 @@ typedef struct { float t0, width; int32_t B; } tof_bins;
  * temporal reuse in which the reservoir of bin b also reuses the same pixel's bins b - 1 and
  * b + 1, shifted into bin b's gate by one bin width; bins outside the histogram are no domains. */
 #define TOF_FLAG_BIN_REUSE 128u
+/* ellipsoidal path connection for the initial candidates (Sec. 4.4 "Initialization with
+ * Ellipsoidal Path Connection", Sec. 5 "Ellipsoidal Path Connection"): every rough vertex x of a
+ * path tree below the maximum depth also places a vertex z with |x - z| + |z - light| drawn
+ * uniformly in the interval the gate (or the histogram's range) leaves, so that the NEE path
+ * through z lies in it.  z's triangle comes from an area-weighted walk of the binary hierarchy over
+ * triangle index ranges (nodes whose box cannot meet the ellipsoid weigh zero; built by
+ * tof_bvh_build for scenes of up to 2^22 triangles, else the flag is rejected), z itself uniformly
+ * in the parametric angle of the ellipse the ellipsoid cuts from the triangle, over its arcs inside
+ * the triangle.  Each such candidate and the path tree's own candidate of the same length are
+ * combined by the balance heuristic over the two densities of the last vertex (the paper's MIS
+ * between direct and ellipsoidal connection), so the estimate stays unbiased.  Excludes the shrink
+ * mapping. */
+#define TOF_FLAG_ELLIPSOID 256u
 
 /* reuse / sampling parameters (Sec. 6: path depth, candidates, neighbours, radius, M-cap;
  * Newton tolerance 1 % of the gate width with at most 5 iterations) */

@@ -32,6 +32,7 @@ cudaError_t launch_xform(int nt, const float* vloc, const uint32_t* tris, const 
 cudaError_t launch_build_topology(int n, const float4* cent, uint32_t* bb, uint32_t* keys, uint32_t* vals, uint32_t* keys2,
                                   uint32_t* vals2, uint32_t* hist, int* child, int* parent_int, int* parent_leaf,
                                   uint32_t** prim_out, cudaStream_t s);
+cudaError_t launch_etree(int nt, int P, const float4* tri, float4* node, cudaStream_t s);
 cudaError_t launch_refit(int n, const uint32_t* prim, const float4* tri, float4* leaf, float4* nodes, const int* child,
                          const int* parent_int, const int* parent_leaf, uint32_t* counter, cudaStream_t s);
 }  // namespace tof
@@ -61,6 +62,8 @@ struct SceneH {
     float4* tri[2] = {nullptr, nullptr};
     float4* leaf[2] = {nullptr, nullptr};
     float4* nodes[2] = {nullptr, nullptr};
+    float4* enode[2] = {nullptr, nullptr};   // ellipsoidal-connection hierarchy (null above 2^22 triangles)
+    int eP = 0;
     uint32_t version[2] = {0, 0};
     std::vector<float> xfh[2];
     int cur = 0;
@@ -206,7 +209,8 @@ static tof_status check_params(tof_ctx* c, const tof_params* p, int transient) {
     if (p->radius < 1 || p->radius > 255) return fail(c, TOF_EINVAL, "radius %d outside [1, 255]", p->radius);
     if (p->n_spatial_iters < 0 || p->n_spatial_iters > 4) return fail(c, TOF_EINVAL, "n_spatial_iters outside [0, 4]");
     const uint32_t gauges = p->flags & (TOF_FLAG_GAUGE_AXIS_T | TOF_FLAG_GAUGE_AXIS_B | TOF_FLAG_GAUGE_START);
-    if (p->flags & ~(TOF_FLAG_DIRECT | TOF_FLAG_NAIVE_SHIFT | TOF_FLAG_PAIRWISE_MIS | TOF_FLAG_TRIANGLE_WALK | TOF_FLAG_BIN_REUSE | gauges))
+    if (p->flags & ~(TOF_FLAG_DIRECT | TOF_FLAG_NAIVE_SHIFT | TOF_FLAG_PAIRWISE_MIS | TOF_FLAG_TRIANGLE_WALK | TOF_FLAG_BIN_REUSE |
+                     TOF_FLAG_ELLIPSOID | gauges))
         return fail(c, TOF_EINVAL, "unknown flag bits 0x%x", p->flags);
     if (gauges & (gauges - 1)) return fail(c, TOF_EINVAL, "at most one gauge flag");
     if ((p->flags & TOF_FLAG_BIN_REUSE) && !transient) return fail(c, TOF_EINVAL, "bin reuse applies to transient rendering");
@@ -217,12 +221,14 @@ static tof_status check_params(tof_ctx* c, const tof_params* p, int transient) {
         return fail(c, TOF_EINVAL, "shrink_k must be finite and at most 1000");
     if (p->shrink_k > 1.f) {
         if (transient) return fail(c, TOF_EINVAL, "the shrink mapping applies to gated rendering only");
+        if (p->flags & TOF_FLAG_ELLIPSOID) return fail(c, TOF_EINVAL, "the shrink mapping and the ellipsoidal connection exclude each other");
         if (p->shrink_fine < 0 || p->shrink_fine >= p->n_cand)
             return fail(c, TOF_EINVAL, "shrink_fine %d outside [0, n_cand - 1]", p->shrink_fine);
     }
     if (transient) {
         int kmin = (p->flags & TOF_FLAG_DIRECT) ? 1 : 2;
         int lengths = p->depth - kmin + 1;
+        if (p->flags & TOF_FLAG_ELLIPSOID) lengths += p->depth - 1;   // one ellipsoidal candidate per vertex below depth
         if (lengths > 0 && p->n_cand * lengths > kMaxBinsPerPixel)
             return fail(c, TOF_EINVAL, "transient: n_cand * path lengths = %d exceeds %d candidates per pixel",
                         p->n_cand * lengths, kMaxBinsPerPixel);
@@ -244,6 +250,7 @@ static FrameDev make_frame(const SceneH& S, int slot, const tof_sensor* s, const
     memset(&F, 0, sizeof(F));
     F.g.tri = S.tri[slot]; F.g.leaf = S.leaf[slot]; F.g.nodes = S.nodes[slot]; F.g.mats = S.mats; F.g.nt = S.nt;
     F.g.adj = S.adj;
+    F.g.enode = S.enode[slot]; F.g.eP = S.eP;
     F.g.version = S.version[slot];
     F.mode = s->mode; F.W = s->W; F.H = s->H;
     F.pos = v3f(s->pos); F.fwd = v3f(s->fwd); F.up = v3f(s->up); F.fov_y = s->fov_y;
@@ -410,6 +417,11 @@ tof_status tof_scene_upload(tof_ctx* c, const float* verts, uint32_t nv, const u
         TRY(dalloc(c, &S.leaf[k], sizeof(float4) * 3 * nt, "leaf records"));
         TRY(dalloc(c, &S.nodes[k], sizeof(float4) * 4 * (size_t)(nt > 1 ? nt - 1 : 1), "nodes"));
     }
+    if (nt <= (1u << kEllMaxLevels)) {
+        S.eP = 1;
+        while ((uint32_t)S.eP < nt) S.eP <<= 1;
+        for (int k = 0; k < 2; ++k) TRY(dalloc(c, &S.enode[k], sizeof(float4) * 4 * (size_t)S.eP, "ellipsoid hierarchy"));
+    }
     CK(cudaMemcpy(S.vloc, verts, sizeof(float) * 3 * nv, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(S.tris, tris, sizeof(uint32_t) * 3 * nt, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(S.triobj, tri_object, sizeof(uint32_t) * nt, cudaMemcpyHostToDevice));
@@ -453,7 +465,7 @@ tof_status tof_scene_destroy(tof_ctx* c, tof_scene id) {
     SceneH& S = c->scenes[id];
     void* ps[] = {S.vloc, S.tris, S.triobj, S.objmat, S.mats, S.xf, S.cent, S.keys, S.vals, S.keys2, S.vals2, S.hist, S.bb,
                   S.child, S.parent_int, S.parent_leaf, S.counter, S.tri[0], S.tri[1], S.leaf[0], S.leaf[1], S.nodes[0], S.nodes[1],
-                  S.adj};
+                  S.adj, S.enode[0], S.enode[1]};
     for (void* p : ps) dfree(c, p);
     S = SceneH();
     return TOF_OK;
@@ -478,6 +490,7 @@ tof_status tof_bvh_build(tof_ctx* c, tof_scene id, const float* xf, int refit_on
                                  S.parent_leaf, &S.prim, s));
     }
     CK(launch_refit(S.nt, S.prim, S.tri[slot], S.leaf[slot], S.nodes[slot], S.child, S.parent_int, S.parent_leaf, S.counter, s));
+    if (S.enode[slot]) CK(launch_etree(S.nt, S.eP, S.tri[slot], S.enode[slot], s));
     S.version[slot] = ++c->version_counter;
     S.xfh[slot] = xv;
     S.cur = slot;
@@ -652,6 +665,8 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     if ((B > 0) != (V.B > 0) || (B > 0 && B != V.B)) return fail(c, TOF_EINVAL, "bins %d do not match the view (%d)", B, V.B);
     TRY(check_sensor(c, sensor, V.W, V.H));
     TRY(check_params(c, params, B > 0));
+    if ((params->flags & TOF_FLAG_ELLIPSOID) && !S.enode[0])
+        return fail(c, TOF_EINVAL, "the ellipsoidal connection supports scenes of up to 2^%d triangles", kEllMaxLevels);
     if (!emitter || emitter->type < 0 || emitter->type > 2 || !(emitter->power >= 0))
         return fail(c, TOF_EINVAL, "bad emitter");
     if (!(dL > 0) || !std::isfinite(L0)) return fail(c, TOF_EINVAL, "gate / bin width must be positive and finite");
@@ -854,6 +869,8 @@ tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* s
         if (!c->scenes[J.scene].built) return fail(c, TOF_ESTATE, "job %u: scene %d has no BVH", i, J.scene);
         ViewH& V = c->views[J.view];
         TRY(check_params(c, &J.params, J.transient != 0));
+        if ((J.params.flags & TOF_FLAG_ELLIPSOID) && !c->scenes[J.scene].enode[0])
+            return fail(c, TOF_EINVAL, "job %u: the ellipsoidal connection supports scenes of up to 2^%d triangles", i, kEllMaxLevels);
         TRY(check_sensor(c, &J.sensor, V.W, V.H));
         if (!J.out_dev) return fail(c, TOF_EINVAL, "job %u: output pointer is NULL", i);
         const size_t npix = (size_t)V.W * V.H, Bn = V.B > 0 ? (size_t)V.B : 1;

@@ -8,6 +8,8 @@
 //   karras_kernel   binary radix tree over the sorted codes (Karras, HPG 2012), ties broken by index
 //   refit_kernel    leaf records in leaf order and bottom-up child boxes (one atomic per node;
 //                   the second arriving thread continues, no thread waits)
+//   etree_*_kernel  the ellipsoidal connection's hierarchy over triangle index ranges (boxes and
+//                   areas, bottom-up: 8 levels per block in shared memory, then one block)
 #include <cstdio>
 
 #include "tof_internal.h"
@@ -254,6 +256,66 @@ __global__ void refit_kernel(int n, const uint32_t* __restrict__ prim, const flo
     }
 }
 
+// ---- ellipsoidal-connection hierarchy (Sec. 5 "Ellipsoidal Path Connection": nodes weighted by
+// the area of the triangles below them).  The implicit binary tree over triangle index ranges
+// (GeomDev::enode): eP leaves (a power of two >= nt), node n with children 2n and 2n + 1.
+constexpr int kEllBlock = 256;
+
+__device__ __forceinline__ void enode_merge(float4 alo, float4 ahi, float4 blo, float4 bhi, float4& lo, float4& hi) {
+    lo = make_float4(fminf(alo.x, blo.x), fminf(alo.y, blo.y), fminf(alo.z, blo.z), alo.w + blo.w);
+    hi = make_float4(fmaxf(ahi.x, bhi.x), fmaxf(ahi.y, bhi.y), fmaxf(ahi.z, bhi.z), 0.f);
+}
+
+// leaves and the `levels` levels above them, one block per blockDim.x leaves (blockDim.x divides P)
+__global__ void __launch_bounds__(kEllBlock) etree_low_kernel(int nt, int P, int levels, const float4* __restrict__ tri,
+                                                              float4* __restrict__ node) {
+    __shared__ float4 slo[kEllBlock], shi[kEllBlock];
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + t;
+    float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f), hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.f);
+    if (i < nt) {
+        float4 a = tri[3 * (size_t)i], b = tri[3 * (size_t)i + 1], c = tri[3 * (size_t)i + 2];
+        float3 v0 = make_float3(a.x, a.y, a.z), e1 = make_float3(b.x, b.y, b.z), e2 = make_float3(c.x, c.y, c.z);
+        float3 v1 = make_float3(v0.x + e1.x, v0.y + e1.y, v0.z + e1.z), v2 = make_float3(v0.x + e2.x, v0.y + e2.y, v0.z + e2.z);
+        float cx = e1.y * e2.z - e1.z * e2.y, cy = e1.z * e2.x - e1.x * e2.z, cz = e1.x * e2.y - e1.y * e2.x;
+        lo = make_float4(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)),
+                         0.5f * sqrtf(cx * cx + cy * cy + cz * cz));
+        hi = make_float4(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)), 0.f);
+    }
+    node[2 * (size_t)(P + i)] = lo;
+    node[2 * (size_t)(P + i) + 1] = hi;
+    slo[t] = lo;
+    shi[t] = hi;
+    for (int h = 1; h <= levels; ++h) {
+        __syncthreads();
+        const int cnt = (int)blockDim.x >> h;
+        float4 nlo, nhi;
+        if (t < cnt) enode_merge(slo[2 * t], shi[2 * t], slo[2 * t + 1], shi[2 * t + 1], nlo, nhi);
+        __syncthreads();
+        if (t < cnt) {
+            slo[t] = nlo;
+            shi[t] = nhi;
+            const size_t n = (size_t)((P + (int)(blockIdx.x * blockDim.x)) >> h) + t;
+            node[2 * n] = nlo;
+            node[2 * n + 1] = nhi;
+        }
+    }
+}
+
+// the levels above: nodes [cnt, 2 cnt) for cnt = lowest / 2, ..., 1, one block
+__global__ void __launch_bounds__(1024) etree_top_kernel(int lowest, float4* node) {
+    for (int cnt = lowest >> 1; cnt >= 1; cnt >>= 1) {
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const size_t n = (size_t)cnt + t;
+            float4 lo, hi;
+            enode_merge(node[4 * n], node[4 * n + 1], node[4 * n + 2], node[4 * n + 3], lo, hi);
+            node[2 * n] = lo;
+            node[2 * n + 1] = hi;
+        }
+        __syncthreads();
+    }
+}
+
 // ---- host launchers --------------------------------------------------------------------------
 static inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -295,6 +357,15 @@ cudaError_t launch_refit(int n, const uint32_t* prim, const float4* tri, float4*
         if (e != cudaSuccess) return e;
     }
     refit_kernel<<<blocks(n, 256), 256, 0, s>>>(n, prim, tri, leaf, nodes, child, parent_int, parent_leaf, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_etree(int nt, int P, const float4* tri, float4* node, cudaStream_t s) {
+    const int bs = P < kEllBlock ? P : kEllBlock;
+    int levels = 0;
+    while ((1 << levels) < bs) ++levels;
+    etree_low_kernel<<<P / bs, bs, 0, s>>>(nt, P, levels, tri, node);
+    if (P / bs > 1) etree_top_kernel<<<1, 1024, 0, s>>>(P / bs, node);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,9 @@ static __device__ __forceinline__ float3 dir_to(float3 from, float3 to) { return
 // Philox4x32-10 (Salmon et al., SC 2011) counter-based streams.  Key = 64-bit seed; counter =
 // (pixel, frame, stream word, purpose word).  Uniform u = (x >> 8) * 2^-24.
 // ============================================================================================
-enum : uint32_t { P_JITTER = 1, P_BSDF = 2, P_RIS = 3, P_NEIGHBOR = 4, P_MERGE = 5 };
+enum : uint32_t { P_JITTER = 1, P_BSDF = 2, P_RIS = 3, P_NEIGHBOR = 4, P_MERGE = 5,
+                  P_ELL_RIS = 6,   // selection of an ellipsoidal candidate
+                  P_ELL = 7 };     // P_ELL + q, q = 0..5: the ellipsoidal connection's draws
 
 static __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t seed) {
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
@@ -941,6 +943,246 @@ static __device__ bool newton_solve_walk(const GeomDev& gi, const NewtonGeo& N, 
     }
     iters = total;
     return false;
+}
+
+// ============================================================================================
+// ellipsoidal path connection for NEE (Sec. 4.4 "Initialization with Ellipsoidal Path
+// Connection", Sec. 5 "Ellipsoidal Path Connection"; Pediredla et al. 2019).  From a rough vertex
+// x whose prefix has length len, a vertex z is placed so that x -> z -> light lands in the gate:
+//   (1) l = |x - z| + |z - q| (q the light position) uniform on [l_a, l_b), the interval the gate
+//       leaves (l_a raised to |x - q|);
+//   (2) a triangle by a top-down walk of the implicit binary hierarchy over triangle index ranges
+//       (GeomDev::enode): at each node the child is taken with probability proportional to its
+//       weight, the area below it, or zero where its box cannot meet the ellipsoid with foci x, q
+//       and major axis l (the paper's heuristic weights; the distances of x and q to the box bound
+//       l from below, their distances to the box's farthest points from above);
+//   (3) on the triangle's plane the ellipsoid cuts an ellipse; z is uniform in its parametric
+//       angle phi over the arcs inside the triangle (total angle Phi).
+// Area density (coarea formula, dA = dl ds / |grad_plane l|, ds = |dz/dphi| dphi):
+//   p(z) = P(tri | l) / (l_b - l_a) / Phi * |grad_plane l(z)| / |dz/dphi|.
+// Ellipsoids thinner than b = 0.01 a place no vertex, in the sampler and the density alike (the
+// MIS with the path tree covers those paths).  The hierarchy depends on the scene alone, so the
+// density is a function of the scene, not of how the ray-tracing hierarchy was built.
+// ============================================================================================
+
+static __device__ __forceinline__ float enode_w(const float4* node, int n, float3 x, float3 q, float ell) {
+    const float4 lo = __ldg(&node[2 * n]), hi = __ldg(&node[2 * n + 1]);
+    if (!(lo.w > 0.f)) return 0.f;
+    float ax = x.x - fminf(fmaxf(x.x, lo.x), hi.x), ay = x.y - fminf(fmaxf(x.y, lo.y), hi.y), az = x.z - fminf(fmaxf(x.z, lo.z), hi.z);
+    float bx = q.x - fminf(fmaxf(q.x, lo.x), hi.x), by = q.y - fminf(fmaxf(q.y, lo.y), hi.y), bz = q.z - fminf(fmaxf(q.z, lo.z), hi.z);
+    float lb = sqrtf(ax * ax + ay * ay + az * az) + sqrtf(bx * bx + by * by + bz * bz);
+    if (lb > ell) return 0.f;
+    float fx = fmaxf(fabsf(x.x - lo.x), fabsf(x.x - hi.x)), fy = fmaxf(fabsf(x.y - lo.y), fabsf(x.y - hi.y)),
+          fz = fmaxf(fabsf(x.z - lo.z), fabsf(x.z - hi.z));
+    float gx = fmaxf(fabsf(q.x - lo.x), fabsf(q.x - hi.x)), gy = fmaxf(fabsf(q.y - lo.y), fabsf(q.y - hi.y)),
+          gz = fmaxf(fabsf(q.z - lo.z), fabsf(q.z - hi.z));
+    float ub = sqrtf(fx * fx + fy * fy + fz * fz) + sqrtf(gx * gx + gy * gy + gz * gz);
+    return ell <= ub ? lo.w : 0.f;
+}
+
+static __device__ __forceinline__ int elog2(int P) { return 31 - __clz(P); }   // P a power of two
+
+// step (2): the triangle (or -1) and its probability; u: the draws of the levels (u[2..])
+static __device__ int etree_pick(const GeomDev& g, float3 x, float3 q, float ell, const uint32_t* u, float& prob) {
+    int n = 1, lvl = 0;
+    float p = 1.0f;
+#pragma unroll 1
+    while (n < g.eP) {
+        float w0 = enode_w(g.enode, 2 * n, x, q, ell), w1 = enode_w(g.enode, 2 * n + 1, x, q, ell);
+        float s = w0 + w1;
+        if (!(s > 0.f)) return -1;
+        if (u01(u[2 + lvl]) * s < w0) { n = 2 * n; p *= w0 / s; }
+        else { n = 2 * n + 1; p *= w1 / s; }
+        ++lvl;
+    }
+    prob = p;
+    return n - g.eP;
+}
+// P(tri | l) of step (2) along the root-to-leaf path of tri
+static __device__ float etree_prob(const GeomDev& g, int tri, float3 x, float3 q, float ell) {
+    const int L = elog2(g.eP), leaf = g.eP + tri;
+    float p = 1.0f;
+#pragma unroll 1
+    for (int i = 0; i < L; ++i) {
+        int n = leaf >> (L - i), next = leaf >> (L - i - 1);
+        float w0 = enode_w(g.enode, 2 * n, x, q, ell), w1 = enode_w(g.enode, 2 * n + 1, x, q, ell);
+        float s = w0 + w1, w = next == 2 * n ? w0 : w1;
+        if (!(s > 0.f) || !(w > 0.f)) return 0.f;
+        p *= w / s;
+    }
+    return p;
+}
+
+// step (3): the ellipse in the triangle's frame (o = v0, t, b): xi = xo + w0 + R1 cos(phi) g1 +
+// R2 sin(phi) g2, and its arcs inside the triangle.  With m the centre, a = l/2, c = |q - x|/2,
+// b^2 = a^2 - c^2, d the focal axis, n the normal and h = (m - v0).n, the plane's points
+// m - h n + w1 t + w2 b satisfy |r|^2 + beta (r.d)^2 = b^2 (beta = -c^2/a^2): centre
+// w0 = beta h (d.n) g / gamma with g = (d.t, d.b), gamma = 1 + beta |g|^2, level
+// kappa = b^2 (1 - h^2 / (a^2 gamma)), radii sqrt(kappa / gamma) along g, sqrt(kappa) across.
+struct Ellip {
+    float xo0, xo1, w00, w01, g10, g11, R1, R2;
+    int narc;
+    float a0[6], alen[6];
+    float Phi;
+};
+
+static __device__ __forceinline__ bool ellip_inside(const float c[3][2], float orient, float px, float py) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = i == 2 ? 0 : i + 1;
+        float cr = (c[j][0] - c[i][0]) * (py - c[i][1]) - (c[j][1] - c[i][1]) * (px - c[i][0]);
+        if (cr * orient < 0.f) return false;
+    }
+    return true;
+}
+
+static __device__ bool ellip_on_tri(const GeomDev& g, int tri, float3 x, float3 q, float ell, const Frame2& f, Ellip& E) {
+    float3 n = cross3(f.t, f.b);
+    float3 m = (x + q) * 0.5f;
+    float a = 0.5f * ell, c = 0.5f * len3(q - x);
+    float b2 = a * a - c * c;
+    if (!(b2 >= 1e-4f * a * a)) return false;
+    float3 d = c > 0.f ? (q - x) * (0.5f / c) : f3(0.f, 0.f, 0.f);
+    float beta = -(c * c) / (a * a);
+    float dt = dot3(d, f.t), db = dot3(d, f.b), dn = dot3(d, n);
+    float3 mo = m - f.o;
+    float h = dot3(mo, n);
+    float gamma = 1.0f + beta * (dt * dt + db * db);
+    float kappa = b2 * (1.0f - h * h / (a * a * gamma));
+    if (!(kappa > 0.f)) return false;
+    E.xo0 = dot3(mo, f.t);
+    E.xo1 = dot3(mo, f.b);
+    E.w00 = beta * h * dn * dt / gamma;
+    E.w01 = beta * h * dn * db / gamma;
+    float gl = sqrtf(dt * dt + db * db);
+    if (gl > 1e-12f) { E.g10 = dt / gl; E.g11 = db / gl; }
+    else { E.g10 = 1.0f; E.g11 = 0.0f; }
+    E.R1 = sqrtf(kappa / gamma);
+    E.R2 = sqrtf(kappa);
+    // corners in the unit-circle coordinates of the ellipse (g2 = (-g11, g10))
+    float cc[3][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float3 dv = tri_corner(g, tri, i) - f.o;
+        float w0 = dot3(dv, f.t) - E.xo0 - E.w00, w1 = dot3(dv, f.b) - E.xo1 - E.w01;
+        cc[i][0] = (w0 * E.g10 + w1 * E.g11) / E.R1;
+        cc[i][1] = (-w0 * E.g11 + w1 * E.g10) / E.R2;
+    }
+    float orient = (cc[1][0] - cc[0][0]) * (cc[2][1] - cc[0][1]) - (cc[1][1] - cc[0][1]) * (cc[2][0] - cc[0][0]);
+    if (orient == 0.f) return false;
+    float ph[6];
+    int np = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = i == 2 ? 0 : i + 1;
+        float e0 = cc[j][0] - cc[i][0], e1 = cc[j][1] - cc[i][1];
+        float A2 = e0 * e0 + e1 * e1, B2 = cc[i][0] * e0 + cc[i][1] * e1, C2 = cc[i][0] * cc[i][0] + cc[i][1] * cc[i][1] - 1.0f;
+        float disc = B2 * B2 - A2 * C2;
+        if (!(disc > 0.f) || !(A2 > 0.f)) continue;
+        float sq = sqrtf(disc);
+        float s0 = (-B2 - sq) / A2, s1 = (-B2 + sq) / A2;
+        if (s0 >= 0.f && s0 <= 1.f) ph[np++] = atan2f(cc[i][1] + s0 * e1, cc[i][0] + s0 * e0);
+        if (s1 >= 0.f && s1 <= 1.f) ph[np++] = atan2f(cc[i][1] + s1 * e1, cc[i][0] + s1 * e0);
+    }
+    for (int i = 1; i < np; ++i)
+        for (int j = i; j > 0 && ph[j - 1] > ph[j]; --j) { float t = ph[j]; ph[j] = ph[j - 1]; ph[j - 1] = t; }
+    E.narc = 0;
+    E.Phi = 0.f;
+    if (np == 0) {
+        if (ellip_inside(cc, orient, 1.0f, 0.0f)) { E.narc = 1; E.a0[0] = 0.f; E.alen[0] = 2.0f * kPi; E.Phi = 2.0f * kPi; }
+    } else {
+        for (int i = 0; i < np; ++i) {
+            float s0 = ph[i], s1 = i + 1 < np ? ph[i + 1] : ph[0] + 2.0f * kPi;
+            if (!(s1 > s0)) continue;
+            float mid = 0.5f * (s0 + s1);
+            if (!ellip_inside(cc, orient, cosf(mid), sinf(mid))) continue;
+            E.a0[E.narc] = s0; E.alen[E.narc] = s1 - s0; E.narc++;
+            E.Phi += s1 - s0;
+        }
+    }
+    return E.Phi > 0.f;
+}
+
+// [l_a, l_b) of l = |x - z| + |z - q| that puts the path in [glo, ghi); false if empty
+static __device__ __forceinline__ bool ell_range(const Domain& D, float3 x, float len, float glo, float ghi, float3& q,
+                                                 float& la, float& lb) {
+    if (D.light.kind == 0) return false;
+    q = D.light.pos;
+    float e = D.light.kind == 2 ? D.light.emit_len : 0.f;
+    la = fmaxf(glo + D.o - len - e, len3(x - q));
+    lb = ghi + D.o - len - e;
+    return lb > la;
+}
+
+// |grad_plane l(z)| / |dz/dphi| at z on the ellipse E of frame f
+static __device__ float ell_point_factor(const Ellip& E, const Frame2& f, float3 z, float3 x, float3 q) {
+    float3 n = cross3(f.t, f.b);
+    float3 gr = dir_to(x, z) + dir_to(q, z);
+    float gn = dot3(gr, n);
+    float gp = sqrtf(fmaxf(dot3(gr, gr) - gn * gn, 0.f));
+    float3 dz = z - f.o;
+    float w0 = dot3(dz, f.t) - E.xo0 - E.w00, w1 = dot3(dz, f.b) - E.xo1 - E.w01;
+    float c0 = (w0 * E.g10 + w1 * E.g11) / E.R1, c1 = (-w0 * E.g11 + w1 * E.g10) / E.R2;
+    float cl = sqrtf(c0 * c0 + c1 * c1);
+    if (!(cl > 0.f)) return 0.f;
+    c0 /= cl; c1 /= cl;
+    float dphi = sqrtf(E.R1 * E.R1 * c1 * c1 + E.R2 * E.R2 * c0 * c0);
+    return dphi > 0.f ? gp / dphi : 0.f;
+}
+
+// place z from vertex x (prefix length len) of path tree `tree` at vertex index d; true if placed
+static __device__ bool ell_sample(const Domain& D, const ParamsDev& P, uint32_t px, uint32_t frame, int tree, int d,
+                                  const Surf& x, float len, float glo, float ghi, Surf& z, float& pdf) {
+    const GeomDev& g = D.F->g;
+    if (g.nt < 1 || elog2(g.eP) > kEllMaxLevels) return false;
+    float3 q;
+    float la, lb;
+    if (!ell_range(D, x.p, len, glo, ghi, q, la, lb)) return false;
+    uint32_t u[24];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        uint4 r = philox(px, frame, ((uint32_t)tree << 8) | (uint32_t)d, P_ELL + k, P.seed);
+        u[4 * k] = r.x; u[4 * k + 1] = r.y; u[4 * k + 2] = r.z; u[4 * k + 3] = r.w;
+    }
+    float ell = la + u01(u[0]) * (lb - la);
+    float ptri;
+    int tri = etree_pick(g, x.p, q, ell, u, ptri);
+    if (tri < 0) return false;
+    Frame2 f = tri_frame(g, tri);
+    Ellip E;
+    if (!ellip_on_tri(g, tri, x.p, q, ell, f, E)) return false;
+    float t = u01(u[1]) * E.Phi, cum = 0.f, phi = 0.f;
+    for (int i = 0; i < E.narc; ++i) {
+        if (t < cum + E.alen[i] || i == E.narc - 1) { phi = E.a0[i] + fminf(t - cum, E.alen[i]); break; }
+        cum += E.alen[i];
+    }
+    float cp = cosf(phi), sp = sinf(phi);
+    float xi0 = E.xo0 + E.w00 + E.R1 * cp * E.g10 - E.R2 * sp * E.g11;
+    float xi1 = E.xo1 + E.w01 + E.R1 * cp * E.g11 + E.R2 * sp * E.g10;
+    float4 e1v = __ldg(&g.tri[3 * tri + 1]), e2v = __ldg(&g.tri[3 * tri + 2]);
+    float3 e1 = xyz(e1v), e2 = xyz(e2v);
+    float e1t = dot3(e1, f.t), e2t = dot3(e2, f.t), e2b = dot3(e2, f.b);
+    float b2 = xi1 / e2b, b1 = (xi0 - b2 * e2t) / e1t;
+    z = surf_at(g, tri, b1, b2);
+    pdf = ptri / (lb - la) / E.Phi * ell_point_factor(E, f, z.p, x.p, q);
+    return pdf > 0.f;
+}
+
+// p_ell(z) of a vertex z reached from x by other means (0 where the sampler cannot place it)
+static __device__ float ell_pdf(const Domain& D, const Surf& x, float len, float glo, float ghi, const Surf& z) {
+    const GeomDev& g = D.F->g;
+    if (g.nt < 1 || elog2(g.eP) > kEllMaxLevels) return 0.f;
+    float3 q;
+    float la, lb;
+    if (!ell_range(D, x.p, len, glo, ghi, q, la, lb)) return 0.f;
+    float ell = len3(z.p - x.p) + len3(q - z.p);
+    if (!(ell >= la && ell < lb)) return 0.f;
+    float ptri = etree_prob(g, z.tri, x.p, q, ell);
+    if (!(ptri > 0.f)) return 0.f;
+    Frame2 f = tri_frame(g, z.tri);
+    Ellip E;
+    if (!ellip_on_tri(g, z.tri, x.p, q, ell, f, E)) return 0.f;
+    return ptri / (lb - la) / E.Phi * ell_point_factor(E, f, z.p, x.p, q);
 }
 
 // ============================================================================================

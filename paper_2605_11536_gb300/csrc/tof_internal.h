@@ -18,6 +18,8 @@ constexpr int kMaxBinsPerPixel = 32;  // distinct transient bins a pixel's initi
 constexpr uint32_t kNoHit = 0xFFFFFFFFu;
 constexpr uint32_t kFlagPairwiseMis = 4u;  // TOF_FLAG_PAIRWISE_MIS
 constexpr uint32_t kFlagTriangleWalk = 64u;  // TOF_FLAG_TRIANGLE_WALK
+constexpr uint32_t kFlagEllipsoid = 256u;    // TOF_FLAG_ELLIPSOID
+constexpr int kEllMaxLevels = 22;           // ellipsoidal-connection hierarchies of up to 2^22 triangles
 
 // material record: (type, albedo, alpha, unused)
 // triangle record (original order): 3 float4 = (v0.xyz, material id bits), (e1.xyz, 0), (e2.xyz, 0)
@@ -27,12 +29,18 @@ constexpr uint32_t kFlagTriangleWalk = 64u;  // TOF_FLAG_TRIANGLE_WALK
 //                child >= 0: internal node, child < 0: leaf ~child.
 // adjacency (original order), nt * 3: across the edge opposite vertex i of triangle t,
 // 4 * neighbour + the neighbour's vertex opposite that edge, or -1
+// ellipsoidal-connection hierarchy: the implicit binary tree over triangle index ranges, eP (a
+// power of two >= nt) leaves, node n in [1, 2 eP) with children 2n, 2n + 1, triangle t at leaf
+// eP + t; 2 float4 per node = (lo.xyz, area of the triangles below), (hi.xyz, 0); padding leaves
+// have area 0
 struct GeomDev {
     const float4* tri;
     const float4* leaf;
     const float4* nodes;
     const float4* mats;
     const int* adj;
+    const float4* enode;
+    int eP;
     int nt;
     uint32_t version;
 };

@@ -16,9 +16,14 @@ namespace tof {
 // --------------------------------------------------------------------------------------------
 __device__ __forceinline__ float gate_L0(const FrameDev& F, int b) { return F.B > 0 ? F.L0 + b * F.dL : F.L0; }
 
-// One path tree; Sink(k, c, tau, T) receives each NEE candidate of length k in [kmin, depth]
-// whose tau lies in [glo, ghi) and whose light segment is unoccluded (c = f / p, no gate).
-template <class Sink>
+// One path tree; Sink(k, c, tau, T, strategy) receives each NEE candidate of length k in
+// [kmin, depth] whose tau lies in [glo, ghi) and whose light segment is unoccluded (c = f / p, no
+// gate; strategy 0).  With kEll every rough vertex x_d (d < depth) also places a vertex z by the
+// ellipsoidal connection, a candidate of length d + 1 (strategy 1); it and the tree's NEE
+// candidate of the same length (whose last vertex x_{d+1} the tree sampled from x_d) are combined
+// by the balance heuristic over the two densities of that vertex (Sec. 5: MIS between the direct
+// and the ellipsoidal connection):  c_tree *= p_tree / (p_tree + p_ell),  c_ell = f / (p_tree + p_ell).
+template <bool kEll = false, class Sink>
 __device__ void trace_tree(const Domain& D, const ParamsDev& P, uint32_t px, uint32_t frame, int tree, float glo, float ghi,
                            TreeVerts& T, Sink& sink) {
     const GeomDev& g = D.F->g;
@@ -28,6 +33,8 @@ __device__ void trace_tree(const Domain& D, const ParamsDev& P, uint32_t px, uin
     float len = len3(D.x0 - D.y1.p);
     float beta = 1.0f;
     const int kmin = (P.flags & 1u) ? 1 : 2;
+    bool ell_prev = false;   // the ellipsoidal connection was available at x_{d-1}
+    float len_prev = 0.f;
     for (int d = 1; d <= P.depth; ++d) {
         const Surf& x = T.v[d];
         Mat m = load_mat(g, x.mat);
@@ -38,8 +45,43 @@ __device__ void trace_tree(const Domain& D, const ParamsDev& P, uint32_t px, uin
             float fs = lt > 0.f ? bsdf_f(m, x.n, wi, wl) : 0.f;
             if (fs > 0.f) {
                 float tau = len + seg - D.o;
-                if (tau >= glo && tau < ghi && light_visible(D, g, x, P.ray_eps)) sink(d, beta * fs * lt, tau, T);
+                if (tau >= glo && tau < ghi && light_visible(D, g, x, P.ray_eps)) {
+                    float c = beta * fs * lt;
+                    if (kEll && ell_prev) {
+                        float pt = T.pdfA[d], pe = ell_pdf(D, T.v[d - 1], len_prev, glo, ghi, x);
+                        c *= pt / (pt + pe);
+                    }
+                    sink(d, c, tau, T, 0);
+                }
             }
+        }
+        if constexpr (kEll) {
+            const bool ell_here = d < P.depth && mat_class(m) != C_DELTA && D.light.kind != 0;
+            Surf z;
+            float pe;
+            if (ell_here && ell_sample(D, P, px, frame, tree, d, x, len, glo, ghi, z, pe)) {
+                Mat mz = load_mat(g, z.mat);
+                float3 wz = dir_to(x.p, z.p);
+                float dist = len3(z.p - x.p);
+                float fx = bsdf_f(m, x.n, wi, wz);
+                if (fx > 0.f && dist > 0.f && mat_class(mz) != C_DELTA) {
+                    float3 wl; float seg;
+                    float lt = light_term(D, z, wl, seg);
+                    float fz = lt > 0.f ? bsdf_f(mz, z.n, wz * -1.0f, wl) : 0.f;
+                    float tau = len + dist + seg - D.o;
+                    if (fz > 0.f && tau >= glo && tau < ghi && visible(g, x.p, x.n, z.p, &z.n, P.ray_eps) &&
+                        light_visible(D, g, z, P.ray_eps)) {
+                        float pt = bsdf_pdf(m, x.n, wi, wz) * fabsf(dot3(z.n, wz)) / (dist * dist);
+                        float c = beta * fx * Gterm(x, z) * fz * lt / (pt + pe);
+                        T.v[d + 1] = z;
+                        T.cls[d + 1] = mat_class(mz);
+                        T.pdfA[d + 1] = pt;
+                        sink(d + 1, c, tau, T, 1);
+                    }
+                }
+            }
+            ell_prev = ell_here;
+            len_prev = len;
         }
         if (d == P.depth) break;
         uint4 u = philox(px, frame, ((uint32_t)tree << 8) | (uint32_t)d, P_BSDF, P.seed);
@@ -120,7 +162,7 @@ struct InitSink {
     int bin[kMaxBinsPerPixel];
     float S[kMaxBinsPerPixel], phat[kMaxBinsPerPixel], tau[kMaxBinsPerPixel], Lsuf[kMaxBinsPerPixel];
     bool overflow;
-    __device__ void operator()(int k, float c, float tauv, const TreeVerts& T) {
+    __device__ void operator()(int k, float c, float tauv, const TreeVerts& T, int strategy) {
         float wv = invN * c;
         if (!(wv > 0.f)) return;
         int b = 0;
@@ -135,7 +177,7 @@ struct InitSink {
             if (n == kMaxBinsPerPixel) { overflow = true; return; }
             bin[n] = b; S[n] = 0.f; phat[n] = 0.f; ++n;
         }
-        uint4 u = philox(px, frame, ((uint32_t)tree << 8) | (uint32_t)k, P_RIS, P->seed);
+        uint4 u = philox(px, frame, ((uint32_t)tree << 8) | (uint32_t)k, strategy ? P_ELL_RIS : P_RIS, P->seed);
         S[e] += wv;
         if (u01(u.x) * S[e] < wv) {
             Rec r;
@@ -148,8 +190,10 @@ struct InitSink {
 };
 
 // 6 resident blocks per SM (80 registers): 1.08 against 1.11 ms at 5 blocks (96 registers) on the
-// 512 x 512 dynamic workload; 8 blocks (64 registers, more spills) were slower
-__global__ void __launch_bounds__(128, 6) initial_kernel(const __grid_constant__ InitArgs a, int* err) {
+// 512 x 512 dynamic workload; 8 blocks (64 registers, more spills) were slower.  kEll: with the
+// ellipsoidal connection (TOF_FLAG_ELLIPSOID), compiled apart so the default keeps its registers.
+template <bool kEll>
+__global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_kernel(const __grid_constant__ InitArgs a, int* err) {
     const FrameDev& F = a.F;
     int ix, iy;
     tile_pixel(a.tile_w, ix, iy);
@@ -174,7 +218,7 @@ __global__ void __launch_bounds__(128, 6) initial_kernel(const __grid_constant__
     TreeVerts T;
     for (int t = 0; t < P.n_cand; ++t) {
         sink.tree = t;
-        trace_tree(D, P, (uint32_t)pix, F.frame, t, glo, ghi, T, sink);
+        trace_tree<kEll>(D, P, (uint32_t)pix, F.frame, t, glo, ghi, T, sink);
     }
     if (sink.overflow && err) atomicOr(err, 1);
     float outv = 0.f;
@@ -207,7 +251,8 @@ struct ShrinkSink {
     float invN, S;
     bool has;
     Rec rec;
-    __device__ void operator()(int k, float c, float tauv, const TreeVerts& T) {
+    __device__ void operator()(int k, float c, float tauv, const TreeVerts& T, int strategy) {
+        (void)strategy;
         float wv = invN * c;
         if (!(wv > 0.f)) return;
         uint4 u = philox(px, frame, ((uint32_t)tree << 8) | (uint32_t)k, P_RIS, P->seed);
@@ -320,8 +365,8 @@ struct PtSink {
     float* row;
     int B;
     float t0, w, scale;
-    __device__ void operator()(int k, float c, float tau, const TreeVerts& T) {
-        (void)k; (void)T;
+    __device__ void operator()(int k, float c, float tau, const TreeVerts& T, int strategy) {
+        (void)k; (void)T; (void)strategy;
         if (B > 0) {
             float fb = floorf((tau - t0) / w);
             if (!(fb >= 0.f && fb < (float)B)) return;
@@ -390,7 +435,10 @@ cudaError_t launch_gbuffer(const GbufArgs& a, int tile_h, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_initial(const InitArgs& a, int tile_h, int* err, cudaStream_t s) {
-    initial_kernel<<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, err);
+    if (a.P.flags & kFlagEllipsoid)
+        initial_kernel<true><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, err);
+    else
+        initial_kernel<false><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, err);
     return cudaGetLastError();
 }
 cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s) {

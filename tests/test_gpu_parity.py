@@ -254,3 +254,56 @@ def test_transient_bin_reuse(nsp, flags):
     g = gpu_render(sc, [0, 1], B=40)
     for f in range(2):
         _check(g[f], o[f])
+
+
+@pytest.mark.parametrize("case", ["box_initial", "box_spatial_temporal", "materials_moving", "heightfield_temporal",
+                                  "heightfield_pairwise_walk", "transient_box"])
+def test_ellipsoidal_connection(case):
+    """TOF_FLAG_ELLIPSOID (Sec. 4.4, Sec. 5): initial candidates also by ellipsoidal path connection,
+    MIS with the path tree, then temporal and spatial reuse; gated and transient; Lambertian, glossy
+    and mirror surfaces; with pairwise MIS and the cross-triangle walk.  Same images as the oracle."""
+    B, frames = 0, [0]
+    if case.startswith("box"):
+        sc = scenes.box_icosphere(W=72 if case == "box_initial" else 48, H=40, frames=2)
+        sc.gates = [(5.0, 0.25)] * 2
+        if case == "box_initial":
+            sc.params.n_spatial = 0
+        else:
+            sc.params.n_spatial, sc.params.radius, sc.params.temporal = 3, 8, 1
+            frames = [0, 1]
+    elif case == "materials_moving":
+        sc = scenes.box_materials(W=48, H=40, frames=2, moving=True)
+        sc.params.temporal = 1
+        frames = [0, 1]
+    elif case.startswith("heightfield"):
+        sc = scenes.heightfield_spheres(W=96, H=80, frames=3)
+        sc.params.radius = 8
+        frames = [0, 1, 2]
+    else:
+        sc = scenes.box_icosphere(W=24, H=24, frames=2)
+        sc.params.n_spatial, sc.params.radius, sc.params.temporal = 2, 4, 1
+        sc.bins = (4.4, 0.1, 40)
+        B, frames = 40, [0, 1]
+    sc.params.flags |= scenes.FLAG_ELLIPSOID
+    if case == "heightfield_pairwise_walk":
+        sc.params.flags |= scenes.FLAG_PAIRWISE_MIS | scenes.FLAG_TRIANGLE_WALK
+    o, ok, st, _ = oracle_render(sc, frames, B=B)
+    g = gpu_render(sc, frames, B=B)
+    for f in range(len(frames)):
+        _check(g[f], o[f], min_nonzero=50)
+
+
+def test_ellipsoidal_connection_full_size_center_region():
+    """The dynamic 512x512 workload with the ellipsoidal connection, rendered at full size in the
+    bench's launch configuration; the oracle computes a central region covering the dependency cone
+    of its inner pixels over 2 frames, and every untainted pixel is compared."""
+    sc = scenes.heightfield_spheres(W=512, H=512, frames=2)
+    sc.params.flags |= scenes.FLAG_ELLIPSOID
+    frames = [0, 1]
+    half = 110
+    roi = (256 - half, 256 - half, 256 + half, 256 + half)
+    o, oks, st, _ = oracle_render(sc, frames, roi=roi, nthreads=0)
+    g = gpu_render(sc, frames)
+    for f in frames:
+        assert oks[f].sum() >= 40 * 40
+        _check(g[f], o[f], mask=oks[f], min_nonzero=30)
