@@ -1302,8 +1302,10 @@ static odomain make_domain(const oframe* F, int pix, const oparams* P, double L0
  *       parametric angle phi over the arcs inside the triangle (total angle Phi).
  * Area density of z (coarea formula: dA = dl ds / |grad_plane l|, ds = |dz/dphi| dphi):
  *   p_ell(z) = P(tri | l) / (l_b - l_a) / Phi * |grad_plane l(z)| / |dz/dphi|.
- * Ellipsoids thinner than b = 0.01 a (a the semi-major axis) place no vertex, in the sampler and
- * in the density alike; the MIS with the path tree covers them.
+ * Ellipsoids thinner than b = 0.05 a (a the semi-major axis: l within about 1.25e-3 l of |x - q|)
+ * place no vertex, in the sampler and in the density alike; the MIS with the path tree covers them.
+ * (There z depends on l - |x - q|, a difference of path lengths that single precision resolves to
+ * ~1e-6 m; the cut keeps the GPU's FP32 placement within ~5e-5 of this FP64 one.)
  * ==========================================================================================*/
 static double enode_w(const double* e, v3 x, v3 q, double ell) {
     if (!(e[6] > 0)) return 0.0;
@@ -1389,7 +1391,7 @@ static int ellip_on_tri(const ogeom* g, int tri, v3 x, v3 q, double ell, oellip*
     v3 m = vmul(vadd(x, q), 0.5);
     double a = 0.5 * ell, c = 0.5 * vlen(vsub(q, x));
     double b2 = a * a - c * c;
-    if (!(b2 >= 1e-4 * a * a)) return 0;
+    if (!(b2 >= 2.5e-3 * a * a)) return 0;
     v3 d = c > 0 ? vmul(vsub(q, x), 0.5 / c) : V(0, 0, 0);
     double beta = -(c * c) / (a * a);
     double dt = vdot(d, f.t), db = vdot(d, f.b), dn = vdot(d, n);
@@ -1671,9 +1673,10 @@ static void trace_tree(const ogeom* g, const odomain* D, const oparams* P, uint6
                     v3 wl; double seg;
                     double lt = light_term(g, &D->light, &z, &wl, &seg);
                     double fz = lt > 0 ? bsdf_f(mz, z.n, vmul(wz, -1.0), wl) : 0.0;
+                    /* tau lies in [glo, ghi) by construction (z is on the ellipsoid of the drawn l); it is
+                     * not tested again, so that rounding cannot decide it */
                     double tau = len + dist + seg - D->o;
-                    if (fz > 0 && tau >= glo && tau < ghi && visible(g, x->p, x->n, z.p, &z.n, P->ray_eps) &&
-                        light_visible(g, &D->light, &z, P->ray_eps)) {
+                    if (fz > 0 && visible(g, x->p, x->n, z.p, &z.n, P->ray_eps) && light_visible(g, &D->light, &z, P->ray_eps)) {
                         double pt = bsdf_pdf(m, x->n, wi, wz) * fabs(vdot(z.n, wz)) / (dist * dist);
                         double c = beta * fx * Gterm(x, &z) * fz * lt / (pt + pe);
                         pb.v[d + 1] = z;

@@ -960,8 +960,9 @@ static __device__ bool newton_solve_walk(const GeomDev& gi, const NewtonGeo& N, 
 //       angle phi over the arcs inside the triangle (total angle Phi).
 // Area density (coarea formula, dA = dl ds / |grad_plane l|, ds = |dz/dphi| dphi):
 //   p(z) = P(tri | l) / (l_b - l_a) / Phi * |grad_plane l(z)| / |dz/dphi|.
-// Ellipsoids thinner than b = 0.01 a place no vertex, in the sampler and the density alike (the
-// MIS with the path tree covers those paths).  The hierarchy depends on the scene alone, so the
+// Ellipsoids thinner than b = 0.05 a (l within about 1.25e-3 l of |x - q|) place no vertex, in the
+// sampler and the density alike (the MIS with the path tree covers those paths): there z depends on
+// l - |x - q|, a difference of path lengths FP32 resolves to ~1e-6 m.  The hierarchy depends on the scene alone, so the
 // density is a function of the scene, not of how the ray-tracing hierarchy was built.
 // ============================================================================================
 
@@ -1041,7 +1042,7 @@ static __device__ bool ellip_on_tri(const GeomDev& g, int tri, float3 x, float3 
     float3 m = (x + q) * 0.5f;
     float a = 0.5f * ell, c = 0.5f * len3(q - x);
     float b2 = a * a - c * c;
-    if (!(b2 >= 1e-4f * a * a)) return false;
+    if (!(b2 >= 2.5e-3f * a * a)) return false;
     float3 d = c > 0.f ? (q - x) * (0.5f / c) : f3(0.f, 0.f, 0.f);
     float beta = -(c * c) / (a * a);
     float dt = dot3(d, f.t), db = dot3(d, f.b), dn = dot3(d, n);

@@ -68,9 +68,10 @@ __device__ void trace_tree(const Domain& D, const ParamsDev& P, uint32_t px, uin
                     float3 wl; float seg;
                     float lt = light_term(D, z, wl, seg);
                     float fz = lt > 0.f ? bsdf_f(mz, z.n, wz * -1.0f, wl) : 0.f;
+                    // tau lies in [glo, ghi) by construction (z is on the ellipsoid of the drawn l); it is
+                    // not tested again, so that rounding cannot decide it
                     float tau = len + dist + seg - D.o;
-                    if (fz > 0.f && tau >= glo && tau < ghi && visible(g, x.p, x.n, z.p, &z.n, P.ray_eps) &&
-                        light_visible(D, g, z, P.ray_eps)) {
+                    if (fz > 0.f && visible(g, x.p, x.n, z.p, &z.n, P.ray_eps) && light_visible(D, g, z, P.ray_eps)) {
                         float pt = bsdf_pdf(m, x.n, wi, wz) * fabsf(dot3(z.n, wz)) / (dist * dist);
                         float c = beta * fx * Gterm(x, z) * fz * lt / (pt + pe);
                         T.v[d + 1] = z;
