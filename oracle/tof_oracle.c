@@ -1385,7 +1385,11 @@ static int ellip_inside(const double c[3][2], double orient, double px, double p
     return 1;
 }
 
-static int ellip_on_tri(const ogeom* g, int tri, v3 x, v3 q, double ell, oellip* E) {
+/* zp: a point known to lie on the ellipse (the density evaluated at a vertex placed by other
+ * means), or NULL.  With a point, kappa is the ellipse's quadratic form at it, which equals the
+ * expression above without its cancellation where the plane nearly touches the ellipsoid (the point
+ * near the plane's mirror point of x and q, where l is minimal). */
+static int ellip_on_tri(const ogeom* g, int tri, v3 x, v3 q, double ell, oellip* E, const v3* zp) {
     oframe2 f = tri_frame(g, tri);
     v3 n = vcross(f.t, f.b);
     v3 m = vmul(vadd(x, q), 0.5);
@@ -1397,12 +1401,19 @@ static int ellip_on_tri(const ogeom* g, int tri, v3 x, v3 q, double ell, oellip*
     double dt = vdot(d, f.t), db = vdot(d, f.b), dn = vdot(d, n);
     double h = vdot(vsub(m, f.o), n);
     double gamma = 1.0 + beta * (dt * dt + db * db);
-    double kappa = b2 * (1.0 - h * h / (a * a * gamma));
-    if (!(kappa > 0)) return 0;
     E->xo[0] = vdot(vsub(m, f.o), f.t);
     E->xo[1] = vdot(vsub(m, f.o), f.b);
     E->w0[0] = beta * h * dn * dt / gamma;
     E->w0[1] = beta * h * dn * db / gamma;
+    double kappa;
+    if (zp) {
+        double d0 = vdot(vsub(*zp, f.o), f.t) - E->xo[0] - E->w0[0], d1 = vdot(vsub(*zp, f.o), f.b) - E->xo[1] - E->w0[1];
+        double gd = dt * d0 + db * d1;
+        kappa = d0 * d0 + d1 * d1 + beta * gd * gd;
+    } else {
+        kappa = b2 * (1.0 - h * h / (a * a * gamma));
+    }
+    if (!(kappa > 0)) return 0;
     double gl = sqrt(dt * dt + db * db);
     if (gl > 1e-12) { E->g1[0] = dt / gl; E->g1[1] = db / gl; }
     else { E->g1[0] = 1.0; E->g1[1] = 0.0; }
@@ -1467,10 +1478,9 @@ static int ell_range(const odomain* D, v3 x, double len, double glo, double ghi,
 
 /* density factor |grad_plane l(z)| / |dz/dphi| and P(tri | l) (1/(l_b - l_a) and 1/Phi apart) */
 static double ell_point_factor(const oellip* E, const oframe2* f, v3 z, v3 x, v3 q) {
-    v3 n = vcross(f->t, f->b);
     v3 gr = vadd(dir_to(x, z), dir_to(q, z));
-    double gn = vdot(gr, n);
-    double gp = sqrt(fmax(vdot(gr, gr) - gn * gn, 0.0));
+    double gt = vdot(gr, f->t), gb = vdot(gr, f->b);
+    double gp = sqrt(gt * gt + gb * gb);
     double w[2] = {vdot(vsub(z, f->o), f->t) - E->xo[0] - E->w0[0], vdot(vsub(z, f->o), f->b) - E->xo[1] - E->w0[1]};
     double c0 = (w[0] * E->g1[0] + w[1] * E->g1[1]) / E->R1, c1 = (w[0] * E->g2[0] + w[1] * E->g2[1]) / E->R2;
     double cl = sqrt(c0 * c0 + c1 * c1);
@@ -1490,7 +1500,7 @@ static int ell_sample_core(const ogeom* g, v3 x, v3 q, double la, double lb, con
     int tri = etree_pick(g, x, q, ell, ul, &ptri);
     if (tri < 0) return 0;
     oellip E;
-    if (!ellip_on_tri(g, tri, x, q, ell, &E)) return 0;
+    if (!ellip_on_tri(g, tri, x, q, ell, &E, NULL)) return 0;
     double t = u01(u[1]) * E.Phi, cum = 0.0, phi = 0.0;
     for (int i = 0; i < E.narc; ++i) {
         if (t < cum + E.alen[i] || i == E.narc - 1) { phi = E.a0[i] + fmin(t - cum, E.alen[i]); break; }
@@ -1513,7 +1523,7 @@ static double ell_pdf_core(const ogeom* g, v3 x, v3 q, double la, double lb, con
     double ptri = etree_prob(g, z->tri, x, q, ell);
     if (!(ptri > 0)) return 0.0;
     oellip E;
-    if (!ellip_on_tri(g, z->tri, x, q, ell, &E)) return 0.0;
+    if (!ellip_on_tri(g, z->tri, x, q, ell, &E, &z->p)) return 0.0;
     oframe2 f = tri_frame(g, z->tri);
     return ptri / (lb - la) / E.Phi * ell_point_factor(&E, &f, z->p, x, q);
 }

@@ -1037,7 +1037,12 @@ static __device__ __forceinline__ bool ellip_inside(const float c[3][2], float o
     return true;
 }
 
-static __device__ bool ellip_on_tri(const GeomDev& g, int tri, float3 x, float3 q, float ell, const Frame2& f, Ellip& E) {
+// zp: a point known to lie on the ellipse (the density at a vertex placed by other means), or
+// null.  With a point, kappa is the ellipse's quadratic form at it: the same value without the
+// cancellation of the expression above where the plane nearly touches the ellipsoid (the point near
+// the plane's mirror point of x and q, where l is minimal), which FP32 cannot resolve.
+static __device__ bool ellip_on_tri(const GeomDev& g, int tri, float3 x, float3 q, float ell, const Frame2& f, Ellip& E,
+                                    const float3* zp = nullptr) {
     float3 n = cross3(f.t, f.b);
     float3 m = (x + q) * 0.5f;
     float a = 0.5f * ell, c = 0.5f * len3(q - x);
@@ -1049,12 +1054,20 @@ static __device__ bool ellip_on_tri(const GeomDev& g, int tri, float3 x, float3 
     float3 mo = m - f.o;
     float h = dot3(mo, n);
     float gamma = 1.0f + beta * (dt * dt + db * db);
-    float kappa = b2 * (1.0f - h * h / (a * a * gamma));
-    if (!(kappa > 0.f)) return false;
     E.xo0 = dot3(mo, f.t);
     E.xo1 = dot3(mo, f.b);
     E.w00 = beta * h * dn * dt / gamma;
     E.w01 = beta * h * dn * db / gamma;
+    float kappa;
+    if (zp) {
+        float3 dz = *zp - f.o;
+        float d0 = dot3(dz, f.t) - E.xo0 - E.w00, d1 = dot3(dz, f.b) - E.xo1 - E.w01;
+        float gd = dt * d0 + db * d1;
+        kappa = d0 * d0 + d1 * d1 + beta * gd * gd;
+    } else {
+        kappa = b2 * (1.0f - h * h / (a * a * gamma));
+    }
+    if (!(kappa > 0.f)) return false;
     float gl = sqrtf(dt * dt + db * db);
     if (gl > 1e-12f) { E.g10 = dt / gl; E.g11 = db / gl; }
     else { E.g10 = 1.0f; E.g11 = 0.0f; }
@@ -1117,10 +1130,9 @@ static __device__ __forceinline__ bool ell_range(const Domain& D, float3 x, floa
 
 // |grad_plane l(z)| / |dz/dphi| at z on the ellipse E of frame f
 static __device__ float ell_point_factor(const Ellip& E, const Frame2& f, float3 z, float3 x, float3 q) {
-    float3 n = cross3(f.t, f.b);
     float3 gr = dir_to(x, z) + dir_to(q, z);
-    float gn = dot3(gr, n);
-    float gp = sqrtf(fmaxf(dot3(gr, gr) - gn * gn, 0.f));
+    float gt = dot3(gr, f.t), gb = dot3(gr, f.b);
+    float gp = sqrtf(gt * gt + gb * gb);
     float3 dz = z - f.o;
     float w0 = dot3(dz, f.t) - E.xo0 - E.w00, w1 = dot3(dz, f.b) - E.xo1 - E.w01;
     float c0 = (w0 * E.g10 + w1 * E.g11) / E.R1, c1 = (-w0 * E.g11 + w1 * E.g10) / E.R2;
@@ -1182,7 +1194,7 @@ static __device__ float ell_pdf(const Domain& D, const Surf& x, float len, float
     if (!(ptri > 0.f)) return 0.f;
     Frame2 f = tri_frame(g, z.tri);
     Ellip E;
-    if (!ellip_on_tri(g, z.tri, x.p, q, ell, f, E)) return 0.f;
+    if (!ellip_on_tri(g, z.tri, x.p, q, ell, f, E, &z.p)) return 0.f;
     return ptri / (lb - la) / E.Phi * ell_point_factor(E, f, z.p, x.p, q);
 }
 
