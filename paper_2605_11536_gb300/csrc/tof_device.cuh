@@ -983,18 +983,25 @@ static __device__ __forceinline__ float enode_w(const float4* node, int n, float
 
 static __device__ __forceinline__ int elog2(int P) { return 31 - __clz(P); }   // P a power of two
 
-// step (2): the triangle (or -1) and its probability; u: the draws of the levels (u[2..])
-static __device__ int etree_pick(const GeomDev& g, float3 x, float3 q, float ell, const uint32_t* u, float& prob) {
-    int n = 1, lvl = 0;
+// step (2): the triangle (or -1) and its probability.  The draws are the words 2, 3, ... of the
+// Philox blocks P_ELL + k (4 words each); r0 is block 0, the later blocks are generated as the walk
+// reaches them (one rolled call per 4 levels keeps the code small).
+static __device__ int etree_pick(const GeomDev& g, float3 x, float3 q, float ell, uint4 r0, uint32_t c0, uint32_t c1,
+                                 uint32_t c2, uint64_t seed, float& prob) {
+    int n = 1;
+    uint32_t j = 2;   // word index of the next draw
+    uint4 r = r0;
     float p = 1.0f;
 #pragma unroll 1
     while (n < g.eP) {
+        if ((j & 3u) == 0u) r = philox(c0, c1, c2, P_ELL + (j >> 2), seed);
+        const uint32_t w = (j & 3u) == 0u ? r.x : (j & 3u) == 1u ? r.y : (j & 3u) == 2u ? r.z : r.w;
+        ++j;
         float w0 = enode_w(g.enode, 2 * n, x, q, ell), w1 = enode_w(g.enode, 2 * n + 1, x, q, ell);
         float s = w0 + w1;
         if (!(s > 0.f)) return -1;
-        if (u01(u[2 + lvl]) * s < w0) { n = 2 * n; p *= w0 / s; }
+        if (u01(w) * s < w0) { n = 2 * n; p *= w0 / s; }
         else { n = 2 * n + 1; p *= w1 / s; }
-        ++lvl;
     }
     prob = p;
     return n - g.eP;
@@ -1143,28 +1150,26 @@ static __device__ float ell_point_factor(const Ellip& E, const Frame2& f, float3
     return dphi > 0.f ? gp / dphi : 0.f;
 }
 
-// place z from vertex x (prefix length len) of path tree `tree` at vertex index d; true if placed
-static __device__ bool ell_sample(const Domain& D, const ParamsDev& P, uint32_t px, uint32_t frame, int tree, int d,
-                                  const Surf& x, float len, float glo, float ghi, Surf& z, float& pdf) {
+// place z from vertex x (prefix length len) of path tree `tree` at vertex index d; true if placed.
+// Kept out of line (with ell_pdf): inlined into the path-tree loop, the walk and the ellipse code
+// thrash the instruction cache of the divergent warps.
+static __device__ __noinline__ bool ell_sample(const Domain& D, const ParamsDev& P, uint32_t px, uint32_t frame, int tree, int d,
+                                               const Surf& x, float len, float glo, float ghi, Surf& z, float& pdf) {
     const GeomDev& g = D.F->g;
     if (g.nt < 1 || elog2(g.eP) > kEllMaxLevels) return false;
     float3 q;
     float la, lb;
     if (!ell_range(D, x.p, len, glo, ghi, q, la, lb)) return false;
-    uint32_t u[24];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        uint4 r = philox(px, frame, ((uint32_t)tree << 8) | (uint32_t)d, P_ELL + k, P.seed);
-        u[4 * k] = r.x; u[4 * k + 1] = r.y; u[4 * k + 2] = r.z; u[4 * k + 3] = r.w;
-    }
-    float ell = la + u01(u[0]) * (lb - la);
+    const uint32_t c2 = ((uint32_t)tree << 8) | (uint32_t)d;
+    const uint4 r0 = philox(px, frame, c2, P_ELL, P.seed);
+    float ell = la + u01(r0.x) * (lb - la);
     float ptri;
-    int tri = etree_pick(g, x.p, q, ell, u, ptri);
+    int tri = etree_pick(g, x.p, q, ell, r0, px, frame, c2, P.seed, ptri);
     if (tri < 0) return false;
     Frame2 f = tri_frame(g, tri);
     Ellip E;
     if (!ellip_on_tri(g, tri, x.p, q, ell, f, E)) return false;
-    float t = u01(u[1]) * E.Phi, cum = 0.f, phi = 0.f;
+    float t = u01(r0.y) * E.Phi, cum = 0.f, phi = 0.f;
     for (int i = 0; i < E.narc; ++i) {
         if (t < cum + E.alen[i] || i == E.narc - 1) { phi = E.a0[i] + fminf(t - cum, E.alen[i]); break; }
         cum += E.alen[i];
@@ -1182,7 +1187,7 @@ static __device__ bool ell_sample(const Domain& D, const ParamsDev& P, uint32_t 
 }
 
 // p_ell(z) of a vertex z reached from x by other means (0 where the sampler cannot place it)
-static __device__ float ell_pdf(const Domain& D, const Surf& x, float len, float glo, float ghi, const Surf& z) {
+static __device__ __noinline__ float ell_pdf(const Domain& D, const Surf& x, float len, float glo, float ghi, const Surf& z) {
     const GeomDev& g = D.F->g;
     if (g.nt < 1 || elog2(g.eP) > kEllMaxLevels) return 0.f;
     float3 q;
