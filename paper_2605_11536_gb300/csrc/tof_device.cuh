@@ -611,8 +611,10 @@ static __device__ float path_f(const Domain& D, const TreeVerts& T, int k) {
     return f;
 }
 
-// reservoir record of the candidate of length k from tree `tree` (P0's W is filled later)
-static __device__ void build_rec(const Domain& D, const TreeVerts& T, int k, int tree, uint32_t px, uint32_t frame, float tau,
+// reservoir record of the candidate of length k from tree `tree` (P0's W is filled later); out of
+// line: every RIS selection calls it, and inlined at each candidate site it bloats the path-tree
+// loop (0.25 ms of the ellipsoidal initial kernel on the 512 x 512 workload)
+static __device__ __noinline__ void build_rec(const Domain& D, const TreeVerts& T, int k, int tree, uint32_t px, uint32_t frame, float tau,
                           const ParamsDev& P, Rec& R) {
     const GeomDev& g = D.F->g;
     R.W = 0.f;
@@ -1093,7 +1095,7 @@ static __device__ bool ellip_on_tri(const GeomDev& g, int tri, float3 x, float3 
     if (orient == 0.f) return false;
     float ph[6];
     int np = 0;
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < 3; ++i) {
         const int j = i == 2 ? 0 : i + 1;
         float e0 = cc[j][0] - cc[i][0], e1 = cc[j][1] - cc[i][1];

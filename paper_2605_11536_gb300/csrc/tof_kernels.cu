@@ -16,6 +16,34 @@ namespace tof {
 // --------------------------------------------------------------------------------------------
 __device__ __forceinline__ float gate_L0(const FrameDev& F, int b) { return F.B > 0 ? F.L0 + b * F.dL : F.L0; }
 
+// The ellipsoidal candidate from vertex x (material m, incident direction wi, prefix length len):
+// places z and returns f / (p_tree + p_ell) without the prefix throughput (cf), its tau and the
+// tree's density of z (pt).  Out of line: inlined, its BSDF, light and visibility code doubles the
+// path-tree loop and thrashes the instruction cache of the divergent warps.
+static __device__ __noinline__ bool ell_connect(const Domain& D, const ParamsDev& P, uint32_t px, uint32_t frame, int tree, int d,
+                                                const Surf& x, float3 wi, float len, float glo, float ghi, Surf& z, float& cf,
+                                                float& tau, float& pt) {
+    const GeomDev& g = D.F->g;
+    float pe;
+    if (!ell_sample(D, P, px, frame, tree, d, x, len, glo, ghi, z, pe)) return false;
+    Mat m = load_mat(g, x.mat), mz = load_mat(g, z.mat);
+    float3 wz = dir_to(x.p, z.p);
+    float dist = len3(z.p - x.p);
+    float fx = bsdf_f(m, x.n, wi, wz);
+    if (!(fx > 0.f) || !(dist > 0.f) || mat_class(mz) == C_DELTA) return false;
+    float3 wl; float seg;
+    float lt = light_term(D, z, wl, seg);
+    float fz = lt > 0.f ? bsdf_f(mz, z.n, wz * -1.0f, wl) : 0.f;
+    if (!(fz > 0.f)) return false;
+    // tau lies in [glo, ghi) by construction (z is on the ellipsoid of the drawn l); it is not tested
+    // again, so that rounding cannot decide it
+    tau = len + dist + seg - D.o;
+    if (!visible(g, x.p, x.n, z.p, &z.n, P.ray_eps) || !light_visible(D, g, z, P.ray_eps)) return false;
+    pt = bsdf_pdf(m, x.n, wi, wz) * fabsf(dot3(z.n, wz)) / (dist * dist);
+    cf = fx * Gterm(x, z) * fz * lt / (pt + pe);
+    return true;
+}
+
 // One path tree; Sink(k, c, tau, T, strategy) receives each NEE candidate of length k in
 // [kmin, depth] whose tau lies in [glo, ghi) and whose light segment is unoccluded (c = f / p, no
 // gate; strategy 0).  With kEll every rough vertex x_d (d < depth) also places a vertex z by the
@@ -58,28 +86,12 @@ __device__ void trace_tree(const Domain& D, const ParamsDev& P, uint32_t px, uin
         if constexpr (kEll) {
             const bool ell_here = d < P.depth && mat_class(m) != C_DELTA && D.light.kind != 0;
             Surf z;
-            float pe;
-            if (ell_here && ell_sample(D, P, px, frame, tree, d, x, len, glo, ghi, z, pe)) {
-                Mat mz = load_mat(g, z.mat);
-                float3 wz = dir_to(x.p, z.p);
-                float dist = len3(z.p - x.p);
-                float fx = bsdf_f(m, x.n, wi, wz);
-                if (fx > 0.f && dist > 0.f && mat_class(mz) != C_DELTA) {
-                    float3 wl; float seg;
-                    float lt = light_term(D, z, wl, seg);
-                    float fz = lt > 0.f ? bsdf_f(mz, z.n, wz * -1.0f, wl) : 0.f;
-                    // tau lies in [glo, ghi) by construction (z is on the ellipsoid of the drawn l); it is
-                    // not tested again, so that rounding cannot decide it
-                    float tau = len + dist + seg - D.o;
-                    if (fz > 0.f && visible(g, x.p, x.n, z.p, &z.n, P.ray_eps) && light_visible(D, g, z, P.ray_eps)) {
-                        float pt = bsdf_pdf(m, x.n, wi, wz) * fabsf(dot3(z.n, wz)) / (dist * dist);
-                        float c = beta * fx * Gterm(x, z) * fz * lt / (pt + pe);
-                        T.v[d + 1] = z;
-                        T.cls[d + 1] = mat_class(mz);
-                        T.pdfA[d + 1] = pt;
-                        sink(d + 1, c, tau, T, 1);
-                    }
-                }
+            float cf, tau, pt;
+            if (ell_here && ell_connect(D, P, px, frame, tree, d, x, wi, len, glo, ghi, z, cf, tau, pt)) {
+                T.v[d + 1] = z;
+                T.cls[d + 1] = mat_class(load_mat(g, z.mat));
+                T.pdfA[d + 1] = pt;
+                sink(d + 1, beta * cf, tau, T, 1);
             }
             ell_prev = ell_here;
             len_prev = len;
