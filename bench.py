@@ -156,16 +156,21 @@ def aggregate(dev_s_max: float, steps: int, world: int) -> dict:
     return {"value": world * steps / dev_s_max, "ms_per_step": dev_s_max * 1e3 / steps}
 
 
-def workload(W=512, H=512, frames=32, seed=1):
+def workload(W=512, H=512, frames=32, seed=1, flags=0):
+    """The dynamic gated workload; `flags` are method flags OR-ed into its parameters."""
     from paper_2605_11536_gb300 import scenes
-    return scenes.heightfield_spheres(W=W, H=H, frames=frames, seed=seed)
+    sc = scenes.heightfield_spheres(W=W, H=H, frames=frames, seed=seed)
+    if flags:
+        sc.params = type(sc.params)(**vars(sc.params))
+        sc.params.flags |= flags
+    return sc
 
 
 def run_ours(args, rank, world):
     import torch
     from paper_2605_11536_gb300 import scenes, tof
     dev = torch.device("cuda", torch.cuda.current_device())
-    sc = workload(seed=1 + rank)
+    sc = workload(seed=1 + rank, flags=args.flags)
     p = sc.params
     W, H = sc.sensors[0]["W"], sc.sensors[0]["H"]
     nf = sc.n_frames
@@ -828,7 +833,7 @@ def cpu_baseline(args, crop=None, frames=3):
     the workload at full resolution (or on a crop of it, with the margin the spatial reuse needs),
     timing the frames after the first (temporal + spatial reuse), extrapolated per pixel for a crop."""
     import oracle as O
-    sc = workload()
+    sc = workload(flags=args.flags)
     W, H = sc.sensors[0]["W"], sc.sensors[0]["H"]
     if crop:
         R = sc.params.radius * max(1, sc.params.n_spatial_iters)
@@ -865,7 +870,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / fps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "dynamic gated 512x512, 66k tris, depth 4, temporal + 5 spatial (frame 0 crop)"},
+            "config": {"workload": "dynamic gated 512x512, 66k tris, depth 4, temporal + 5 spatial (frame 0 crop)",
+                       "flags": args.flags},
             "cpu_baseline": {"value": fps, "kind": "oracle", "cores": cb["cores"], "sample": cb["sample"]},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -879,6 +885,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-spp", type=int, default=4096)
     ap.add_argument("--quality-frames", type=int, default=8, help="frames whose relMSE is averaged")
+    ap.add_argument("--flags", type=int, default=0,
+                    help="method flags OR-ed into the timed configuration (tof.h TOF_FLAG_*; e.g. 324 = ellipsoidal "
+                         "connection + pairwise MIS + cross-triangle walk, the best unbiased equal-time setting)")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-pairwise", action="store_true", help="skip the pairwise-MIS line")
     ap.add_argument("--no-cpu", action="store_true")
@@ -953,15 +962,17 @@ def main():
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "dynamic gated 512x512 x 32 frames, 66k tris (200x125 fBm heightfield + 20 rotating "
                                    "spheres), depth 4, 4 trees, temporal + 5 spatial within 30 px, L0 8 m dL 0.03 m",
+                       "flags": args.flags,
                        "l2": "256 MiB flush between timed frames", "parallelism": "replicas x%d" % world},
             "latency_ms": {"p50": p50, "p99": p99},
             "stage_ms": st,
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 12 * 4 * r["nobj"],
                     "d2h_bytes_per_step": 4 * r["npix"]},
-            # per frame: LBVH (xform, bounds, morton, 4 x 3 radix-sort, karras, refit = 17), gbuffer,
-            # initial, 8 temporal-pass and 8 spatial-pass kernels (slots, units, forward shifts,
-            # visibility, inverse-task emission, inverse shifts, visibility, merge)
-            "gpu_launches": 35 * K,
+            # per frame: LBVH (xform, bounds, morton, 4 x 3 radix-sort, karras, refit = 17), the
+            # ellipsoidal connection's hierarchy (2), gbuffer, initial, 8 temporal-pass and 8
+            # spatial-pass kernels (slots, units, forward shifts, visibility, inverse-task emission,
+            # inverse shifts, visibility, merge)
+            "gpu_launches": 37 * K,
             "roofline": roof,
             "kernel_rooflines": per_kernel,
             "clocks": r["clocks"],
