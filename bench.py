@@ -62,7 +62,8 @@ BYTES = {
 # kernel as it is now, on the dynamic gated workload; None for kernels whose launches vary too much
 # from frame to frame for one capture to stand for the mean launch (task counts grow over the
 # first frames).  Must be retaken whenever the kernel changes.
-NCU_TRAFFIC = {"initial_kernel": 30.859264e6 + 34.762496e6, "reuse_merge_kernel": 85.374208e6 + 9.837824e6}
+NCU_TRAFFIC = {"initial_kernel<0>": 28.644864e6 + 30.080512e6, "initial_kernel<1>": 42.868224e6 + 47.666432e6,
+               "reuse_merge_kernel": 85.374208e6 + 9.837824e6}
 
 
 def _peaks():
@@ -934,9 +935,10 @@ def main():
              "spatial_inv_shift": "%.0f tasks + %.0f segments" % (pf["spatial_inv_calls"], pf["spatial_inv_rays"]),
              "spatial_fwd_vis": "%.0f segments" % pf["spatial_fwd_rays"], "spatial_inv_vis": "%.0f segments" % pf["spatial_inv_rays"],
              "spatial_merge": "%d px" % r["npix"]}
-    kernels = {"gbuffer": "gbuffer_kernel", "initial": "initial_kernel", "temporal": "temporal pass (8 kernels)",
-               "spatial_setup": "reuse_slots_kernel + reuse_units_kernel", "spatial_fwd_shift": "shift_fwd_kernel",
-               "spatial_fwd_vis": "vis_kernel (forward segments) + emit_inv_kernel", "spatial_inv_shift": "shift_inv_kernel",
+    ell, walk = int(bool(args.flags & 256)), int(bool(args.flags & 64))
+    kernels = {"gbuffer": "gbuffer_kernel", "initial": "initial_kernel<%d>" % ell, "temporal": "temporal pass (8 kernels)",
+               "spatial_setup": "reuse_slots_kernel + reuse_units_kernel", "spatial_fwd_shift": "shift_fwd_kernel<%d>" % walk,
+               "spatial_fwd_vis": "vis_kernel (forward segments) + emit_inv_kernel", "spatial_inv_shift": "shift_inv_kernel<%d>" % walk,
                "spatial_inv_vis": "vis_kernel (inverse segments)", "spatial_merge": "reuse_merge_kernel"}
 
     def roofline(k):
