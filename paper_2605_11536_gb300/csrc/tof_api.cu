@@ -20,6 +20,9 @@
 namespace tof {
 cudaError_t launch_gbuffer(const GbufArgs& a, int tile_h, cudaStream_t s);
 cudaError_t launch_initial(const InitArgs& a, int tile_h, int* err, cudaStream_t s);
+cudaError_t launch_initial_ell_wave(const InitArgs& a, const EllWaveDev& w, int tile_h, int place_blocks, int vis_blocks,
+                                    cudaStream_t s);
+cudaError_t ell_place_blocks(int* out);
 cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s);
 cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, int vis_blocks,
                               cudaEvent_t* ev, cudaStream_t s);
@@ -109,6 +112,10 @@ struct ViewH {
     std::vector<cudaEvent_t> kev;   // kReuseEvents events per timed spatial launch group
     size_t kev_used = 0;
     void* wave_ptrs[12] = {nullptr};
+    // the ellipsoidal connection's initial wavefront (gated views; sized on first use)
+    EllWaveDev ell;
+    size_t ell_slots = 0;        // pixels x trees x depth it holds
+    void* ell_ptrs[9] = {nullptr};
     tof_tuning tune = {16, 8, 0, TOF_LAYOUT_SOA};   // launch shapes and reservoir layout (autotuner)
 };
 
@@ -126,6 +133,7 @@ struct tof_ctx {
     int* d_err = nullptr;
     float* d_scratch = nullptr;  // laser spot of plain PT renders
     int persist_blocks = 0;      // resident blocks of the persistent reuse kernels (all SMs)
+    int ell_blocks = 0;          // resident blocks of the ellipsoidal placement kernel (all SMs)
     int vis_blocks = 0;          // resident blocks of the visibility kernel (all SMs)
     int sms = 0;                 // streaming multiprocessors
     // batched rendering: stream pool, fork / join events, and the instantiated graph
@@ -536,6 +544,7 @@ tof_status tof_view_destroy(tof_ctx* c, tof_view id) {
     for (int k = 0; k < 2; ++k) { dfree(c, V.gb[k]); dfree(c, V.laser[k]); }
     for (int k = 0; k < 3; ++k) { dfree(c, V.res[k].planes); dfree(c, V.res[k].M); dfree(c, V.res[k].occ); }
     for (void* p : V.wave_ptrs) dfree(c, p);
+    for (void* p : V.ell_ptrs) dfree(c, p);
     dfree(c, V.stats);
     for (int k = 0; k < 7; ++k)
         if (V.ev[k]) cudaEventDestroy(V.ev[k]);
@@ -570,8 +579,44 @@ constexpr int kReuseEvents = 7;   // events around the kernels of one reuse laun
 static tof_status persist_init(tof_ctx* c) {
     if (c->persist_blocks) return TOF_OK;
     CK(reuse_persist_blocks(&c->persist_blocks, &c->vis_blocks));
+    CK(ell_place_blocks(&c->ell_blocks));
     CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     return TOF_OK;
+}
+
+// (re)allocate the scratch of the ellipsoidal connection's initial wavefront for nc trees of the
+// given depth: per (pixel, tree, vertex) 64 B of vertex, candidate and placement records, a request
+// and two queued visibility segments (450 MB for 512 x 512, 4 trees, depth 4)
+static tof_status ensure_ell_wave(tof_ctx* c, ViewH& V, int nc, int depth) {
+    const size_t npix = (size_t)V.W * V.H, slots = npix * (size_t)nc * (size_t)depth;
+    if (V.ell_slots >= slots && V.ell.nc == nc && V.ell.depth == depth) return TOF_OK;
+    for (void*& p : V.ell_ptrs) { dfree(c, p); p = nullptr; }
+    V.ell_slots = 0;
+    EllWaveDev& w = V.ell;
+    w.nc = nc; w.depth = depth;
+    const size_t reqs = npix * (size_t)nc * (size_t)(depth > 1 ? depth - 1 : 1);
+    TRY(dalloc(c, &w.vtx, sizeof(float4) * slots, "ellipsoid wave vertices"));
+    TRY(dalloc(c, &w.vtx2, sizeof(float2) * slots, "ellipsoid wave throughputs"));
+    TRY(dalloc(c, &w.acand, sizeof(float2) * slots, "ellipsoid wave tree candidates"));
+    TRY(dalloc(c, &w.bw, sizeof(float) * slots, "ellipsoid wave weights"));
+    TRY(dalloc(c, &w.bz, sizeof(float4) * slots, "ellipsoid wave vertices placed"));
+    TRY(dalloc(c, &w.bpt, sizeof(float) * slots, "ellipsoid wave densities"));
+    TRY(dalloc(c, &w.req, sizeof(uint32_t) * reqs, "ellipsoid wave requests"));
+    w.req_cap = (uint32_t)reqs;
+    TRY(dalloc(c, &w.rays, sizeof(float4) * 4 * reqs, "ellipsoid wave visibility queue"));
+    w.ray_cap = (uint32_t)(2 * reqs);
+    TRY(dalloc(c, &w.counters, sizeof(uint32_t) * 4, "ellipsoid wave counters"));
+    void* ps[9] = {w.vtx, w.vtx2, w.acand, w.bw, w.bz, w.bpt, w.req, w.rays, w.counters};
+    for (int k = 0; k < 9; ++k) V.ell_ptrs[k] = ps[k];
+    V.ell_slots = slots;
+    return TOF_OK;
+}
+
+// the initial stage runs as the ellipsoidal wavefront: gated, ellipsoidal connection, not the
+// allocation-free form, and slot indices that fit 32 bits
+static bool use_ell_wave(const ViewH& V, int B, const tof_params* p, bool fixed) {
+    if (fixed || B > 0 || !(p->flags & TOF_FLAG_ELLIPSOID) || p->shrink_k > 1.f) return false;
+    return (double)V.W * V.H * p->n_cand * p->depth * 2.0 < 4294967295.0;
 }
 
 // (re)allocate the view's wavefront scratch for S slots per pixel and cap merge units
@@ -704,8 +749,20 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     ia.F = F; ia.dst = V.res[out_of(stage)].dev(); ia.P = P;
     ia.out = (stage == stages - 1 && B == 0) ? out : nullptr;
     ia.tile_w = V.tune.tile_w;
-    if (B == 0 && params->shrink_k > 1.f) CK(launch_initial_shrink(ia, V.tune.tile_h, s));
-    else CK(launch_initial(ia, V.tune.tile_h, c->d_err, s));
+    if (B == 0 && params->shrink_k > 1.f) {
+        CK(launch_initial_shrink(ia, V.tune.tile_h, s));
+    } else if (use_ell_wave(V, B, params, fixed_wave != nullptr)) {
+        TRY(ensure_ell_wave(c, V, params->n_cand, params->depth));
+        TRY(persist_init(c));
+        int vb = c->vis_blocks, eb = c->ell_blocks;
+        if (V.tune.packet > 0) {
+            vb = std::min(vb, c->sms * V.tune.packet);
+            eb = std::min(eb, c->sms * V.tune.packet);
+        }
+        CK(launch_initial_ell_wave(ia, V.ell, V.tune.tile_h, eb, vb, s));
+    } else {
+        CK(launch_initial(ia, V.tune.tile_h, c->d_err, s));
+    }
     mark(V, 2, s);
     V.ran[1] = true;
     int src = out_of(stage);
@@ -879,6 +936,7 @@ tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* s
         int S = 1 + J.params.n_spatial > 2 ? 1 + J.params.n_spatial : 2;
         if (J.transient && (J.params.flags & TOF_FLAG_BIN_REUSE) && S < 3) S = 3;
         TRY(ensure_wave(c, V, S, (int)cap));
+        if (use_ell_wave(V, J.transient ? V.B : 0, &J.params, false)) TRY(ensure_ell_wave(c, V, J.params.n_cand, J.params.depth));
     }
     TRY(persist_init(c));
     const uint32_t P = n < 16 ? n : 16;

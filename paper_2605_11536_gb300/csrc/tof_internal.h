@@ -154,6 +154,26 @@ struct WaveDev {
 };
 constexpr int kWaveCounters = 8;
 
+// wavefront of the gated initial stage with the ellipsoidal connection (tof_kernels.cu): the path
+// trees record their vertices, their NEE candidates and the ellipsoidal requests; the vertices are
+// placed in one pass over the requests, their visibility segments traced by vis_kernel, and the
+// streaming RIS replayed per pixel in the trees' candidate order.  Slot (pixel, tree, vertex d) =
+// (pixel * nc + tree) * depth + d - 1.
+struct EllWaveDev {
+    int nc, depth;
+    float4* vtx;            // (tri bits, b1, b2, area pdf) of vertex d
+    float2* vtx2;           // (prefix throughput beta, prefix length) at vertex d
+    float2* acand;          // (f / p, tau) of the tree's NEE candidate ending at vertex d (0: none)
+    float* bw;              // f / p of the ellipsoidal candidate from vertex d (0: none; zeroed when occluded)
+    float4* bz;             // (z tri bits, b1, b2, tau) of that candidate
+    float* bpt;             // the tree's area density of z (its pdf entry in the record)
+    uint32_t* req;          // ellipsoidal requests (slot indices)
+    uint32_t req_cap;
+    float4* rays;           // 2 * ray_cap: their visibility segments (VisQ, target = slot)
+    uint32_t ray_cap;
+    uint32_t* counters;     // requests, request fetch, segments, segment fetch
+};
+
 struct SplatArgs {
     ResDev src;
     int npix, B;

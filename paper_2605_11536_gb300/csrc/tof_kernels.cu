@@ -16,13 +16,14 @@ namespace tof {
 // --------------------------------------------------------------------------------------------
 __device__ __forceinline__ float gate_L0(const FrameDev& F, int b) { return F.B > 0 ? F.L0 + b * F.dL : F.L0; }
 
-// The ellipsoidal candidate from vertex x (material m, incident direction wi, prefix length len):
-// places z and returns f / (p_tree + p_ell) without the prefix throughput (cf), its tau and the
-// tree's density of z (pt).  Out of line: inlined, its BSDF, light and visibility code doubles the
-// path-tree loop and thrashes the instruction cache of the divergent warps.
+// The ellipsoidal candidate from vertex x (incident direction wi, prefix length len): places z and
+// returns f / (p_tree + p_ell) without the prefix throughput (cf), its tau and the tree's density of
+// z (pt).  Out of line: inlined, its BSDF, light and visibility code doubles the path-tree loop and
+// thrashes the instruction cache of the divergent warps.  q: its two visibility segments are queued
+// there (vis_kernel zeroes the guarded weight when one is occluded) instead of traced in place.
 static __device__ __noinline__ bool ell_connect(const Domain& D, const ParamsDev& P, uint32_t px, uint32_t frame, int tree, int d,
                                                 const Surf& x, float3 wi, float len, float glo, float ghi, Surf& z, float& cf,
-                                                float& tau, float& pt) {
+                                                float& tau, float& pt, const VisQ* q = nullptr) {
     const GeomDev& g = D.F->g;
     float pe;
     if (!ell_sample(D, P, px, frame, tree, d, x, len, glo, ghi, z, pe)) return false;
@@ -38,7 +39,7 @@ static __device__ __noinline__ bool ell_connect(const Domain& D, const ParamsDev
     // tau lies in [glo, ghi) by construction (z is on the ellipsoid of the drawn l); it is not tested
     // again, so that rounding cannot decide it
     tau = len + dist + seg - D.o;
-    if (!visible(g, x.p, x.n, z.p, &z.n, P.ray_eps) || !light_visible(D, g, z, P.ray_eps)) return false;
+    if (!visible_q(q, g, x.p, x.n, z.p, &z.n, P.ray_eps) || !light_visible(D, g, z, P.ray_eps, q)) return false;
     pt = bsdf_pdf(m, x.n, wi, wz) * fabsf(dot3(z.n, wz)) / (dist * dist);
     cf = fx * Gterm(x, z) * fz * lt / (pt + pe);
     return true;
@@ -51,7 +52,9 @@ static __device__ __noinline__ bool ell_connect(const Domain& D, const ParamsDev
 // candidate of the same length (whose last vertex x_{d+1} the tree sampled from x_d) are combined
 // by the balance heuristic over the two densities of that vertex (Sec. 5: MIS between the direct
 // and the ellipsoidal connection):  c_tree *= p_tree / (p_tree + p_ell),  c_ell = f / (p_tree + p_ell).
-template <bool kEll = false, class Sink>
+// kEll = 1 places the ellipsoidal vertex in place; kEll = 2 (the wavefront) only records every
+// vertex (sink.vertex) and the ellipsoidal requests (sink.request) for a later pass.
+template <int kEll = 0, class Sink>
 __device__ void trace_tree(const Domain& D, const ParamsDev& P, uint32_t px, uint32_t frame, int tree, float glo, float ghi,
                            TreeVerts& T, Sink& sink) {
     const GeomDev& g = D.F->g;
@@ -67,6 +70,7 @@ __device__ void trace_tree(const Domain& D, const ParamsDev& P, uint32_t px, uin
         const Surf& x = T.v[d];
         Mat m = load_mat(g, x.mat);
         float3 wi = dir_to(x.p, d == 1 ? D.x0 : T.v[d - 1].p);
+        if constexpr (kEll == 2) sink.vertex(d, T, beta, len);
         if (d >= kmin && mat_class(m) != C_DELTA) {
             float3 wl; float seg;
             float lt = light_term(D, x, wl, seg);
@@ -75,7 +79,7 @@ __device__ void trace_tree(const Domain& D, const ParamsDev& P, uint32_t px, uin
                 float tau = len + seg - D.o;
                 if (tau >= glo && tau < ghi && light_visible(D, g, x, P.ray_eps)) {
                     float c = beta * fs * lt;
-                    if (kEll && ell_prev) {
+                    if (kEll != 0 && ell_prev) {
                         float pt = T.pdfA[d], pe = ell_pdf(D, T.v[d - 1], len_prev, glo, ghi, x);
                         c *= pt / (pt + pe);
                     }
@@ -83,15 +87,19 @@ __device__ void trace_tree(const Domain& D, const ParamsDev& P, uint32_t px, uin
                 }
             }
         }
-        if constexpr (kEll) {
+        if constexpr (kEll != 0) {
             const bool ell_here = d < P.depth && mat_class(m) != C_DELTA && D.light.kind != 0;
-            Surf z;
-            float cf, tau, pt;
-            if (ell_here && ell_connect(D, P, px, frame, tree, d, x, wi, len, glo, ghi, z, cf, tau, pt)) {
-                T.v[d + 1] = z;
-                T.cls[d + 1] = mat_class(load_mat(g, z.mat));
-                T.pdfA[d + 1] = pt;
-                sink(d + 1, beta * cf, tau, T, 1);
+            if constexpr (kEll == 2) {
+                if (ell_here) sink.request(d);
+            } else {
+                Surf z;
+                float cf, tau, pt;
+                if (ell_here && ell_connect(D, P, px, frame, tree, d, x, wi, len, glo, ghi, z, cf, tau, pt)) {
+                    T.v[d + 1] = z;
+                    T.cls[d + 1] = mat_class(load_mat(g, z.mat));
+                    T.pdfA[d + 1] = pt;
+                    sink(d + 1, beta * cf, tau, T, 1);
+                }
             }
             ell_prev = ell_here;
             len_prev = len;
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_kernel(const __grid
     TreeVerts T;
     for (int t = 0; t < P.n_cand; ++t) {
         sink.tree = t;
-        trace_tree<kEll>(D, P, (uint32_t)pix, F.frame, t, glo, ghi, T, sink);
+        trace_tree<kEll ? 1 : 0>(D, P, (uint32_t)pix, F.frame, t, glo, ghi, T, sink);
     }
     if (sink.overflow && err) atomicOr(err, 1);
     float outv = 0.f;
@@ -242,6 +250,169 @@ __global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_kernel(const __grid
         *res_at(a.dst, 0, idx) = make_float4(W, sink.phat[e], sink.tau[e], sink.Lsuf[e]);
         occ[sink.bin[e] >> 5] |= 1u << (sink.bin[e] & 31);
         outv = sink.phat[e] * W;
+    }
+    if (a.out) a.out[pix] = outv;
+}
+
+// --------------------------------------------------------------------------------------------
+// gated initial candidates with the ellipsoidal connection as a wavefront (EllWaveDev): the same
+// candidates, weights, uniforms and order as initial_kernel<true>, so the same reservoirs, but the
+// ellipsoidal vertices are placed in one coherent pass instead of inside the divergent path-tree
+// loop (whose mixed tree / walk / traversal code stalled on instruction fetch):
+//   ell_trees_kernel   the path trees: every vertex, every NEE candidate (with its MIS weight),
+//                      every ellipsoidal request
+//   ell_place_kernel   one thread per request: the walk, the ellipse clip, the candidate's weight;
+//                      its two visibility segments queued for vis_kernel (which zeroes the weight of
+//                      an occluded one)
+//   ell_select_kernel  the streaming RIS per pixel in the trees' order (tree-major; at vertex d the
+//                      NEE candidate, then the ellipsoidal one), then the winner's record alone
+// --------------------------------------------------------------------------------------------
+struct RecordSink {
+    const EllWaveDev* w;
+    size_t base;   // slot of (pixel, tree, vertex 1)
+    __device__ void operator()(int k, float c, float tauv, const TreeVerts& T, int strategy) {
+        (void)T; (void)strategy;   // only the tree's own NEE candidates arrive here
+        w->acand[base + k - 1] = make_float2(c, tauv);
+    }
+    __device__ void vertex(int d, const TreeVerts& T, float beta, float len) {
+        const Surf& v = T.v[d];
+        w->vtx[base + d - 1] = make_float4(__int_as_float(v.tri), v.b1, v.b2, T.pdfA[d]);
+        w->vtx2[base + d - 1] = make_float2(beta, len);
+    }
+    __device__ void request(int d) {
+        const uint32_t i = reserve_coalesced(&w->counters[0], 1u);
+        if (i < w->req_cap) w->req[i] = (uint32_t)(base + d - 1);
+    }
+};
+
+__global__ void __launch_bounds__(128, 6) ell_trees_kernel(const __grid_constant__ InitArgs a, const EllWaveDev w) {
+    const FrameDev& F = a.F;
+    int ix, iy;
+    tile_pixel(a.tile_w, ix, iy);
+    if (ix >= F.W || iy >= F.H) return;
+    const int pix = iy * F.W + ix;
+    const ParamsDev& P = a.P;
+    float4 gb = F.gb[pix];
+    uint32_t tri = __float_as_uint(gb.x);
+    Domain D = make_domain_hit(&F, tri != kNoHit, (int)tri, gb.y, gb.z, gb.w, F.L0, F.dL);
+    if (!D.valid) return;
+    RecordSink sink;
+    sink.w = &w;
+    TreeVerts T;
+    for (int t = 0; t < P.n_cand; ++t) {
+        sink.base = ((size_t)pix * w.nc + t) * w.depth;
+        for (int d = 0; d < w.depth; ++d) {
+            w.acand[sink.base + d] = make_float2(0.f, 0.f);
+            w.bw[sink.base + d] = 0.f;
+        }
+        trace_tree<2>(D, P, (uint32_t)pix, F.frame, t, F.L0, F.L0 + F.dL, T, sink);
+    }
+}
+
+__global__ void __launch_bounds__(128) ell_place_kernel(const __grid_constant__ InitArgs a, const EllWaveDev w) {
+    const FrameDev& F = a.F;
+    const ParamsDev& P = a.P;
+    const uint32_t n = min(w.counters[0], w.req_cap);
+    const uint32_t per = (uint32_t)(w.nc * w.depth);
+    VisQ q;
+    q.rays = w.rays; q.counter = &w.counters[2]; q.cap = w.ray_cap;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t slot = w.req[i];
+        const int pix = (int)(slot / per), t = (int)((slot / (uint32_t)w.depth) % (uint32_t)w.nc), d = (int)(slot % (uint32_t)w.depth) + 1;
+        float4 gb = F.gb[pix];
+        Domain D = make_domain_hit(&F, true, (int)__float_as_uint(gb.x), gb.y, gb.z, gb.w, F.L0, F.dL);
+        float4 v = w.vtx[slot];
+        Surf x = surf_at(F.g, __float_as_int(v.x), v.y, v.z);
+        float3 prev = D.x0;
+        if (d > 1) {
+            float4 u = w.vtx[slot - 1];
+            prev = surf_at(F.g, __float_as_int(u.x), u.y, u.z).p;
+        }
+        const float2 bl = w.vtx2[slot];
+        q.target = slot;
+        Surf z;
+        float cf, tau, pt;
+        if (ell_connect(D, P, (uint32_t)pix, F.frame, t, d, x, dir_to(x.p, prev), bl.y, F.L0, F.L0 + F.dL, z, cf, tau, pt, &q)) {
+            w.bw[slot] = bl.x * cf;
+            w.bz[slot] = make_float4(__int_as_float(z.tri), z.b1, z.b2, tau);
+            w.bpt[slot] = pt;
+        } else {
+            w.bw[slot] = 0.f;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) ell_select_kernel(const __grid_constant__ InitArgs a, const EllWaveDev w) {
+    const FrameDev& F = a.F;
+    int ix, iy;
+    tile_pixel(a.tile_w, ix, iy);
+    if (ix >= F.W || iy >= F.H) return;
+    const int pix = iy * F.W + ix;
+    const ParamsDev& P = a.P;
+    a.dst.occ[pix] = 0u;
+    a.dst.M[pix] = (float)P.n_cand;
+    float4 gb = F.gb[pix];
+    uint32_t tri = __float_as_uint(gb.x);
+    Domain D = make_domain_hit(&F, tri != kNoHit, (int)tri, gb.y, gb.z, gb.w, F.L0, F.dL);
+    float outv = 0.f;
+    if (D.valid) {
+        const int kmin = (P.flags & 1u) ? 1 : 2;
+        const float invN = 1.0f / (float)P.n_cand;
+        float S = 0.f, sel_tau = 0.f;
+        int sel_t = -1, sel_k = 0, sel_s = 0;
+        for (int t = 0; t < P.n_cand; ++t) {
+            const size_t base = ((size_t)pix * w.nc + t) * w.depth;
+            for (int d = 1; d <= P.depth; ++d) {
+                if (d >= kmin) {
+                    const float2 ac = w.acand[base + d - 1];
+                    const float wv = invN * ac.x;
+                    if (wv > 0.f) {
+                        uint4 u = philox((uint32_t)pix, F.frame, ((uint32_t)t << 8) | (uint32_t)d, P_RIS, P.seed);
+                        S += wv;
+                        if (u01(u.x) * S < wv) { sel_t = t; sel_k = d; sel_s = 0; sel_tau = ac.y; }
+                    }
+                }
+                if (d < P.depth) {
+                    const float wv = invN * w.bw[base + d - 1];
+                    if (wv > 0.f) {
+                        uint4 u = philox((uint32_t)pix, F.frame, ((uint32_t)t << 8) | (uint32_t)(d + 1), P_ELL_RIS, P.seed);
+                        S += wv;
+                        if (u01(u.x) * S < wv) { sel_t = t; sel_k = d + 1; sel_s = 1; sel_tau = w.bz[base + d - 1].w; }
+                    }
+                }
+            }
+        }
+        if (sel_t >= 0) {
+            // the winner's path as the tree held it when the candidate streamed by
+            const GeomDev& g = F.g;
+            const size_t base = ((size_t)pix * w.nc + sel_t) * w.depth;
+            TreeVerts T;
+            T.v[1] = D.y1;
+            T.cls[1] = mat_class(load_mat(g, D.y1.mat));
+            T.pdfA[1] = 1.0f;
+            const int ntree = sel_s ? sel_k - 1 : sel_k;   // vertices from the tree itself
+            for (int j = 2; j <= ntree; ++j) {
+                float4 v = w.vtx[base + j - 1];
+                T.v[j] = surf_at(g, __float_as_int(v.x), v.y, v.z);
+                T.cls[j] = mat_class(load_mat(g, T.v[j].mat));
+                T.pdfA[j] = v.w;
+            }
+            if (sel_s) {
+                float4 zb = w.bz[base + sel_k - 2];
+                T.v[sel_k] = surf_at(g, __float_as_int(zb.x), zb.y, zb.z);
+                T.cls[sel_k] = mat_class(load_mat(g, T.v[sel_k].mat));
+                T.pdfA[sel_k] = w.bpt[base + sel_k - 2];
+            }
+            Rec r;
+            build_rec(D, T, sel_k, sel_t, (uint32_t)pix, F.frame, sel_tau, P, r);
+            if (r.phat > 0.f) {
+                const float W = S / r.phat;
+                store_tail(a.dst, (size_t)pix, r);
+                *res_at(a.dst, 0, (size_t)pix) = make_float4(W, r.phat, sel_tau, r.Lsuf);
+                a.dst.occ[pix] = 1u;
+                outv = r.phat * W;
+            }
+        }
     }
     if (a.out) a.out[pix] = outv;
 }
@@ -452,6 +623,33 @@ cudaError_t launch_initial(const InitArgs& a, int tile_h, int* err, cudaStream_t
         initial_kernel<true><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, err);
     else
         initial_kernel<false><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, err);
+    return cudaGetLastError();
+}
+cudaError_t launch_vis_queue(const GeomDev& g, const float4* rays, const uint32_t* counter, uint32_t cap, uint32_t* fetch,
+                             float* target, int blocks, cudaStream_t s);   // tof_reuse.cu
+
+// resident blocks of ell_place_kernel on every SM (its grid strides over the requests)
+cudaError_t ell_place_blocks(int* out) {
+    int dev = 0, sms = 0, b = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ell_place_kernel, 128, 0);
+    *out = sms * (b > 0 ? b : 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_initial_ell_wave(const InitArgs& a, const EllWaveDev& w, int tile_h, int place_blocks, int vis_blocks,
+                                    cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(w.counters, 0, 4 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const dim3 grid = tile_grid(a.F.W, a.F.H, a.tile_w, tile_h);
+    const int threads = a.tile_w * tile_h;
+    ell_trees_kernel<<<grid, threads, 0, s>>>(a, w);
+    ell_place_kernel<<<place_blocks, 128, 0, s>>>(a, w);
+    e = launch_vis_queue(a.F.g, w.rays, &w.counters[2], w.ray_cap, &w.counters[3], w.bw, vis_blocks, s);
+    if (e != cudaSuccess) return e;
+    ell_select_kernel<<<grid, threads, 0, s>>>(a, w);
     return cudaGetLastError();
 }
 cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s) {

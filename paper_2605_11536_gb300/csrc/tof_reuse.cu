@@ -593,6 +593,13 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
     return cudaGetLastError();
 }
 
+// visibility segments queued by another stage (the ellipsoidal connection's initial wavefront)
+cudaError_t launch_vis_queue(const GeomDev& g, const float4* rays, const uint32_t* counter, uint32_t cap, uint32_t* fetch,
+                             float* target, int blocks, cudaStream_t s) {
+    vis_kernel<<<blocks, 128, 0, s>>>(g, rays, counter, cap, fetch, target, nullptr, -1, -1);
+    return cudaGetLastError();
+}
+
 cudaError_t reuse_persist_blocks(int* out, int* vis_out) {
     int dev = 0, sms = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0;
     cudaError_t e = cudaGetDevice(&dev);
