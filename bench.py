@@ -995,6 +995,7 @@ def main():
                          ("quality_pairwise_walk_8_trees", _pairwise_walk(8)), ("quality_ellipsoid", _ellipsoid()),
                          ("quality_ellipsoid_pairwise", _ellipsoid(4)),
                          ("quality_ellipsoid_pairwise_walk", _ellipsoid(4 | 64)),
+                         ("quality_ellipsoid_pairwise_walk_6_trees", _ellipsoid(4 | 64, 6)),
                          ("quality_shrink_K10_R1", _shrink(10.0, 0)),
                          ("quality_shrink_K10_R1_walk", _shrink(10.0, 0, walk=True)),
                          ("quality_shrink_K3_R1_walk", _shrink(3.0, 0, walk=True)),
