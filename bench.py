@@ -62,7 +62,10 @@ BYTES = {
 # kernel as it is now, on the dynamic gated workload; None for kernels whose launches vary too much
 # from frame to frame for one capture to stand for the mean launch (task counts grow over the
 # first frames).  Must be retaken whenever the kernel changes.
+ELL_WAVE = "ell_trees_kernel + ell_place_kernel + ell_select_kernel"
 NCU_TRAFFIC = {"initial_kernel<0>": 28.644864e6 + 30.080512e6, "initial_kernel<1>": 42.868224e6 + 47.666432e6,
+               # the three kernels of the ellipsoidal wavefront (its vis_kernel launch not included)
+               ELL_WAVE: 125.222912e6 + 225.113344e6 + 129.852160e6 + 40.145152e6 + 80.166912e6 + 27.827968e6,
                "reuse_merge_kernel": 85.374208e6 + 9.837824e6}
 
 
@@ -936,7 +939,7 @@ def main():
              "spatial_fwd_vis": "%.0f segments" % pf["spatial_fwd_rays"], "spatial_inv_vis": "%.0f segments" % pf["spatial_inv_rays"],
              "spatial_merge": "%d px" % r["npix"]}
     ell, walk = int(bool(args.flags & 256)), int(bool(args.flags & 64))
-    kernels = {"gbuffer": "gbuffer_kernel", "initial": "initial_kernel<%d>" % ell, "temporal": "temporal pass (8 kernels)",
+    kernels = {"gbuffer": "gbuffer_kernel", "initial": ELL_WAVE if ell else "initial_kernel<0>", "temporal": "temporal pass (8 kernels)",
                "spatial_setup": "reuse_slots_kernel + reuse_units_kernel", "spatial_fwd_shift": "shift_fwd_kernel<%d>" % walk,
                "spatial_fwd_vis": "vis_kernel (forward segments) + emit_inv_kernel", "spatial_inv_shift": "shift_inv_kernel<%d>" % walk,
                "spatial_inv_vis": "vis_kernel (inverse segments)", "spatial_merge": "reuse_merge_kernel"}
