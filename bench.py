@@ -976,8 +976,9 @@ def main():
             # per frame: LBVH (xform, bounds, morton, 4 x 3 radix-sort, karras, refit = 17), the
             # ellipsoidal connection's hierarchy (2), gbuffer, initial, 8 temporal-pass and 8
             # spatial-pass kernels (slots, units, forward shifts, visibility, inverse-task emission,
-            # inverse shifts, visibility, merge)
-            "gpu_launches": 37 * K,
+            # inverse shifts, visibility, merge); the ellipsoidal wavefront replaces the initial
+            # kernel by 4 (trees, placement, visibility, selection)
+            "gpu_launches": (37 + (3 if ell else 0)) * K,
             "roofline": roof,
             "kernel_rooflines": per_kernel,
             "clocks": r["clocks"],
