@@ -1011,6 +1011,15 @@ def main():
                 line[key] = run_quality_variant(args, mut)
             except Exception as e:
                 line[key] = {"error": str(e)[:300]}
+    best = line.get("quality_ellipsoid_pairwise_walk")
+    if isinstance(best, dict) and "restir_ms" in best:
+        line["best_unbiased_configuration"] = {
+            "flags": 324, "what": "ellipsoidal connection + pairwise MIS + cross-triangle walk, 4 path trees, "
+                                  "otherwise the headline workload (time it alone with --flags 324)",
+            "ms_per_frame": best["restir_ms"], "frames_per_s": 1e3 / best["restir_ms"],
+            "vs_pt_equal_time_median": best.get("restir_vs_pt_inv_mse_time_median"),
+            "vs_pt_equal_time_mean": best.get("restir_vs_pt_inv_mse_time"),
+            "mean_vs_reference": best.get("mean_vs_reference")}
     if not args.no_sweep:
         try:
             line["gate_width_sweep"] = run_gate_sweep(args)
