@@ -31,10 +31,11 @@ def _sensor(sc, f, W, H):
     return dict(sc.sensors[f], W=W, H=H)
 
 
-def _run(batched, tune=None, chosen=None):
+def _run(batched, tune=None, chosen=None, flags=0):
     """Render the spec's jobs over two frames, batched or one launch per job.  tune: None (default
     tuning), a dict of tof_view_set_tuning fields for every view, or "auto" (tof_autotune on the
-    first frame's jobs, chosen tunings appended to `chosen`)."""
+    first frame's jobs, chosen tunings appended to `chosen`).  flags: method flags added to the
+    gated jobs."""
     import torch
     from paper_2605_11536_gb300 import tof
     spec = _jobs_spec()
@@ -52,6 +53,8 @@ def _run(batched, tune=None, chosen=None):
             bufs.append(torch.zeros(W * H * max(B, 1), device="cuda"))
             p = scenes.Params(**vars(sc.params))
             p.depth, p.n_spatial, p.radius, p.temporal = depth, nsp, rad, temporal
+            if not transient:
+                p.flags |= flags
             params.append(p)
             if isinstance(tune, dict):
                 tof.tof_view_set_tuning(ctx, views[-1], **tune)
@@ -92,6 +95,19 @@ def _run(batched, tune=None, chosen=None):
 def test_batch_equals_individual_renders_over_two_frames():
     ind = _run(False)
     bat = _run(True)
+    for f in range(2):
+        for i, (a, b) in enumerate(zip(ind[f], bat[f])):
+            assert np.count_nonzero(a) > 0, (f, i)
+            frac, relmse, _ = compare(b, a)
+            assert frac >= 0.999 and relmse <= 1e-6, (f, i, frac, relmse)
+
+
+def test_batch_with_ellipsoid_pairwise_walk_equals_individual_renders():
+    """The gated jobs with the ellipsoidal connection (its initial wavefront's scratch is allocated
+    before the graph is captured), pairwise MIS and the walk: batched as rendered one by one."""
+    flags = scenes.FLAG_ELLIPSOID | scenes.FLAG_PAIRWISE_MIS | scenes.FLAG_TRIANGLE_WALK
+    ind = _run(False, flags=flags)
+    bat = _run(True, flags=flags)
     for f in range(2):
         for i, (a, b) in enumerate(zip(ind[f], bat[f])):
             assert np.count_nonzero(a) > 0, (f, i)
