@@ -613,10 +613,11 @@ static tof_status ensure_ell_wave(tof_ctx* c, ViewH& V, int nc, int depth) {
 }
 
 // the initial stage runs as the ellipsoidal wavefront: gated, ellipsoidal connection, not the
-// allocation-free form, and slot indices that fit 32 bits
+// allocation-free form, and at most 32M (pixel, tree, vertex) slots (~2.5 GB of scratch; larger
+// views or tree counts keep the single kernel, which needs none)
 static bool use_ell_wave(const ViewH& V, int B, const tof_params* p, bool fixed) {
     if (fixed || B > 0 || !(p->flags & TOF_FLAG_ELLIPSOID) || p->shrink_k > 1.f) return false;
-    return (double)V.W * V.H * p->n_cand * p->depth * 2.0 < 4294967295.0;
+    return (double)V.W * V.H * p->n_cand * p->depth <= 32.0 * 1024.0 * 1024.0;
 }
 
 // (re)allocate the view's wavefront scratch for S slots per pixel and cap merge units
