@@ -96,6 +96,12 @@ def _declare(L):
                                            C.POINTER(C.c_int), _dp, C.c_int]
     L.or_stream_select.restype = C.c_int
     L.or_stream_select.argtypes = [_dp, _dp, C.c_int, _dp]
+    L.or_ris_accept.restype = C.c_int
+    L.or_ris_accept.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
+    L.or_ris_W.restype = C.c_double
+    L.or_ris_W.argtypes = [C.c_double, C.c_double]
+    L.or_gris_mis.restype = C.c_double
+    L.or_gris_mis.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int]
     L.or_view_reservoir.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, C.POINTER(C.c_int)]
     L.or_shift_roundtrip.restype = C.c_int
     L.or_shift_roundtrip.argtypes = [C.c_void_p, C.POINTER(OParams), C.c_uint64, C.c_int, C.c_int, _dp]
@@ -294,6 +300,25 @@ def stream_select(w, u):
     S = C.c_double()
     sel = lib().or_stream_select(wp, up, len(wa), C.byref(S))
     return sel, S.value
+
+
+def ris_accept(S, w, u):
+    """One streaming-resampling step of the pipeline: (accepted, new running sum)."""
+    So = C.c_double()
+    a = lib().or_ris_accept(float(S), float(w), float(u), C.byref(So))
+    return bool(a), So.value
+
+
+def ris_W(S, phat):
+    """The pipeline's unbiased contribution weight of a selected sample: sum of weights / p_hat(y)."""
+    return lib().or_ris_W(float(S), float(phat))
+
+
+def gris_mis(M, T, s, pairwise=False):
+    """The pipeline's MIS weight of candidate s in a GRIS merge (confidences M, T_j = p_hat_{<-j}(y_s))."""
+    Ma, Mp = _d(M)
+    Ta, Tp = _d(T)
+    return lib().or_gris_mis(Mp, Tp, len(Ma), int(s), int(bool(pairwise)))
 
 
 def shift_roundtrip(view: View, params, seed, src, dst):

@@ -789,8 +789,9 @@ static void point_to_xi(const oframe2* f, v3 p, double xi[2]) {
 }
 
 /* ============================================================================================
- * cross-triangle walk of the reconnection vertex (reading R25; the paper parameterises p on the
- * surface, Sec. 4.2, without saying what happens at a triangle's edge).  The Newton unknown xi'
+ * cross-triangle walk of the reconnection vertex (opt-in; the paper parameterises p on the
+ * surface, Sec. 4.2, without saying what happens at a triangle's edge, and this walk is one answer:
+ * the vertex continues on the neighbouring triangle instead of failing the shift).  The Newton unknown xi'
  * lives in a 2-D chart: the plane of p's triangle, into which each neighbour entered is unfolded
  * about the shared edge (an isometry, so lengths, gradients and |det| carry over).  A candidate
  * that leaves the current triangle crosses its exit edge into the neighbour; the walk fails at a
@@ -1566,6 +1567,51 @@ void or_ell_tri_probs(const ogeom* g, const double* x, const double* q, double e
 }
 
 /* ============================================================================================
+ * resampling primitives shared by every RIS / GRIS step of the pipeline (Sec. 3.2)
+ * ==========================================================================================*/
+/* One step of streaming resampling: the running weight sum S grows by the candidate's resampling
+ * weight w > 0, and the candidate replaces the current selection when u S < w (u uniform in
+ * [0, 1)).  Over a stream of candidates the last replacement is the selection, which picks
+ * candidate i with probability w_i / sum_j w_j (basic RIS and the GRIS merge alike). */
+static int ris_accept(double* S, double w, double u) {
+    *S += w;
+    return u * *S < w;
+}
+/* unbiased contribution weight of the selected sample y: the sum of the resampling weights over
+ * the target at y, W_y = (sum_j w_j) / p_hat(y) (Sec. 3.2, RIS and GRIS estimators) */
+static double ris_W(double S, double phat) { return S / phat; }
+/* MIS weight of candidate s in a GRIS merge of n domains with confidences M, given
+ * T_j = p_hat_{<-j}(y_s), the target of domain j at y_s carried back by the inverse shift with its
+ * Jacobian (0 where that shift fails), T_0 = p_hat_0(y_s) of the canonical domain, T_s the
+ * candidate's own domain term.  Generalized balance heuristic (eq. GRIS_MIS_weight, every term
+ * evaluated at the same y_s): m_s = M_s T_s / sum_j M_j T_j.  Pairwise (an opt-in from the
+ * ReSTIR literature): the canonical domain pairs with each reused domain i as a two-technique
+ * balance heuristic with confidences M_0/k and M_i, weighted by a_i = (M_i + M_0/k) / sum_j M_j;
+ * m_0 = sum_i a_i (M_0/k) T_0 / ((M_0/k) T_0 + M_i T_i), m_s = a_s M_s T_s / (M_s T_s + (M_0/k) T_0).
+ * Either way the weights of one y over the domains that can produce it sum to 1. */
+static double gris_mis(const double* M, const double* T, int n, int s, int pairwise) {
+    if (pairwise && n > 1) {
+        const int k = n - 1;
+        double Msum = 0.0;
+        for (int j = 0; j < n; ++j) Msum += M[j];
+        const double Mck = M[0] / k;
+        if (s == 0) {
+            double m = 0.0;
+            for (int i = 1; i < n; ++i) {
+                double pc = Mck * T[0], ti = M[i] * T[i];
+                m += (M[i] + Mck) / Msum * (pc / (pc + ti));
+            }
+            return m;
+        }
+        double pi = M[s] * T[s], pc = Mck * T[0];
+        return (M[s] + Mck) / Msum * (pi / (pi + pc));
+    }
+    double den = 0.0;
+    for (int j = 0; j < n; ++j) den += M[j] * T[j];
+    return den > 0 ? M[s] * T[s] / den : 0.0;
+}
+
+/* ============================================================================================
  * initial candidates (Sec. 3.2 RIS, stage (1); Sec. 4.5 per-bin deposit for transients)
  * Path trees: BSDF-sampled paths with NEE to the delta light at every vertex; the candidate of
  * length k is the NEE path ending at x_k.  w = (1/N) p_hat / p with p_hat = f 1[tau in gate].
@@ -1734,8 +1780,7 @@ static void init_sink(void* vctx, int k, double c, double tau, const opathbuf* p
     }
     uint32_t u[4];
     rng4(C->seed, C->px, C->frame, ((uint32_t)C->tree << 8) | (uint32_t)k, strategy ? P_ELL_RIS : P_RIS, u);
-    C->S[b] += w;
-    if (u01(u[0]) * C->S[b] < w)
+    if (ris_accept(&C->S[b], w, u01(u[0])))
         build_rec(C->g, C->D, pb, k, C->tree, C->px, C->frame, tau, C->P, &C->out[b]);
 }
 
@@ -1766,8 +1811,8 @@ static void initial_shrink(const ogeom* g, const odomain* D, const oparams* P, u
         if (t < NA) { Ca.tree = t; trace_tree(g, D, P, seed, px, frame, t, 1, L0, L0 + dL, 0, init_sink, &Ca); }
         else { Cb.tree = t; trace_tree(g, D, P, seed, px, frame, t, 1, c - half, c + half, 0, init_sink, &Cb); }
     }
-    const double Wa = (xa.valid && xa.phat > 0) ? Sa / xa.phat : 0.0;
-    const double Wb = (xb.valid && xb.phat > 0) ? Sb / xb.phat : 0.0;
+    const double Wa = (xa.valid && xa.phat > 0) ? ris_W(Sa, xa.phat) : 0.0;
+    const double Wb = (xb.valid && xb.phat > 0) ? ris_W(Sb, xb.phat) : 0.0;
     const ogatemap to_gate = {1.0 / K, c, L0, L0 + dL}, to_wide = {K, c, c - half, c + half};
     orec yb = EMPTY_REC;
     double pyb = 0.0, Jb = 0.0;
@@ -1795,12 +1840,11 @@ static void initial_shrink(const ogeom* g, const odomain* D, const oparams* P, u
         if (!(w[s] > 0) || !isfinite(w[s])) continue;
         uint32_t u[4];
         rng4(seed, px, frame, (0xFFu << 8) | (uint32_t)s, P_MERGE, u);
-        S += w[s];
-        if (u01(u[0]) * S < w[s]) sel = s;
+        if (ris_accept(&S, w[s], u01(u[0]))) sel = s;
     }
     *out = EMPTY_REC;
-    if (sel == 0) { *out = xa; out->valid = 1; out->W = S / xa.phat; }
-    else if (sel == 1) { *out = yb; out->valid = 1; out->W = S / pyb; }
+    if (sel == 0) { *out = xa; out->valid = 1; out->W = ris_W(S, xa.phat); }
+    else if (sel == 1) { *out = yb; out->valid = 1; out->W = ris_W(S, pyb); }
     out->M = P->n_cand;
 }
 
@@ -1825,45 +1869,25 @@ static double merge(const oslot* sl, int n, const oparams* P, uint64_t seed, uin
         if (s == 0) { y[0] = *sl[0].x; py[0] = sl[0].x->phat; J[0] = 1.0; ok[0] = py[0] > 0; continue; }
         ok[s] = shift_rec(sl[s].x, sl[s].D, sl[0].D, P, seed, sl[s].geom_static, &y[s], &py[s], &J[s], st);
     }
-    if ((P->flags & F_PAIRWISE) && n > 1) {
-        /* pairwise MIS: pair i = {canonical with confidence M_0/k, domain i with confidence M_i},
-         * a two-technique balance heuristic at the same y, weighted by
-         * alpha_i = (M_i + M_0/k) / sum_t M_t; the weights over all techniques sum to one. */
-        const int k = n - 1;
-        const double Mck = sl[0].M / k;
-        for (int s = 0; s < n; ++s) {
-            if (!ok[s]) continue;
-            double m = 0.0;
-            if (s == 0) {
-                for (int i = 1; i < n; ++i) {
-                    double alpha = (sl[i].M + Mck) / Msum;
-                    double ti = 0.0;
-                    orec tmp; double pj, Jj;
-                    if (shift_rec(&y[0], sl[0].D, sl[i].D, P, seed, sl[i].geom_static, &tmp, &pj, &Jj, NULL))
-                        ti = sl[i].M * pj * Jj;
-                    double pc = Mck * py[0];
-                    m += alpha * (pc / (pc + ti));
-                }
-            } else {
-                double alpha = (sl[s].M + Mck) / Msum;
-                double pi = sl[s].M * sl[s].x->phat / J[s];
-                double pc = Mck * py[s];
-                m = alpha * (pi / (pi + pc));
-            }
-            w[s] = m * py[s] * sl[s].x->W * J[s];
-            if (!(w[s] > 0) || !isfinite(w[s])) w[s] = 0.0;
-        }
-    } else for (int s = 0; s < n; ++s) {
+    /* MIS weight of each candidate from the targets of every domain at its own y_s (gris_mis):
+     * T_0 = p_hat_0(y_s); T_s = p_hat_s(x_s) / |dS_s/dx_s| (the candidate's own domain); T_j for the
+     * other domains by the inverse shift of y_s into j with its Jacobian (0 if it fails).  Pairwise
+     * MIS needs only T_0 and T_s for a reused candidate, and every T_i for the canonical one. */
+    const int pairwise = (P->flags & F_PAIRWISE) && n > 1;
+    double Mv[16], T[16];
+    for (int j = 0; j < n; ++j) Mv[j] = sl[j].M;
+    for (int s = 0; s < n; ++s) {
         if (!ok[s]) continue;
-        double num = s == 0 ? sl[0].M * py[0] : sl[s].M * sl[s].x->phat / J[s];
-        double den = sl[0].M * py[s];
+        T[0] = py[s];
         for (int j = 1; j < n; ++j) {
-            if (j == s) { den += sl[s].M * sl[s].x->phat / J[s]; continue; }
+            T[j] = 0.0;
+            if (j == s) { T[j] = sl[s].x->phat / J[s]; continue; }
+            if (pairwise && s != 0) continue;
             orec tmp; double pj, Jj;
             if (shift_rec(&y[s], sl[0].D, sl[j].D, P, seed, sl[j].geom_static, &tmp, &pj, &Jj, NULL))
-                den += sl[j].M * pj * Jj;
+                T[j] = pj * Jj;
         }
-        double m = den > 0 ? num / den : 0.0;
+        double m = gris_mis(Mv, T, n, s, pairwise);
         w[s] = m * py[s] * sl[s].x->W * J[s];
         if (!(w[s] > 0) || !isfinite(w[s])) w[s] = 0.0;
     }
@@ -1873,13 +1897,12 @@ static double merge(const oslot* sl, int n, const oparams* P, uint64_t seed, uin
         if (!(w[s] > 0)) continue;
         uint32_t u[4];
         rng4(seed, px, frame, ((uint32_t)pass << 8) | (uint32_t)s, P_MERGE | ((uint32_t)bin << 8), u);
-        S += w[s];
-        if (u01(u[0]) * S < w[s]) sel = s;
+        if (ris_accept(&S, w[s], u01(u[0]))) sel = s;
     }
     if (sel >= 0) {
         *out = y[sel];
         out->valid = 1;
-        out->W = S / py[sel];
+        out->W = ris_W(S, py[sel]);
     } else {
         *out = EMPTY_REC;
     }
@@ -1994,7 +2017,7 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
             else trace_tree(g, &D, P, seed, (uint32_t)pix, frame, t, 1, L0, L0 + dL, ell, init_sink, &C);
         }
         for (int b = 0; b < Bn; ++b) {
-            if (rr[b].valid && rr[b].phat > 0) { rr[b].W = S[b] / rr[b].phat; rr[b].M = P->n_cand; }
+            if (rr[b].valid && rr[b].phat > 0) { rr[b].W = ris_W(S[b], rr[b].phat); rr[b].M = P->n_cand; }
             else { rr[b] = EMPTY_REC; rr[b].M = P->n_cand; }
         }
         free(S);
@@ -2253,11 +2276,22 @@ int or_stream_select(const double* w, const double* u, int n, double* S_out) {
     int sel = -1;
     for (int i = 0; i < n; ++i) {
         if (!(w[i] > 0)) continue;
-        S += w[i];
-        if (u[i] * S < w[i]) sel = i;
+        if (ris_accept(&S, w[i], u[i])) sel = i;
     }
     *S_out = S;
     return sel;
+}
+/* the pipeline's resampling primitives on explicit inputs (exhaustive-enumeration pins) */
+int or_ris_accept(double S_in, double w, double u, double* S_out) {
+    double S = S_in;
+    int a = ris_accept(&S, w, u);
+    *S_out = S;
+    return a;
+}
+double or_ris_W(double S, double phat) { return ris_W(S, phat); }
+double or_gris_mis(const double* M, const double* T, int n, int s, int pairwise) {
+    if (n < 1 || n > 16 || s < 0 || s >= n) return -1.0;
+    return gris_mis(M, T, n, s, pairwise);
 }
 
 /* BSDF sampling hook: returns ok; wo[3], pdf, thr */
