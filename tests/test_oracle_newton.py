@@ -9,7 +9,9 @@
 * reversibility of the average-gradient gauge: solving back from xi' with -delta returns xi and
   the two determinants multiply to 1;
 * the printed sign of the 0.5 H R (xi' - xi) term in the second row of dF/dxi' disagrees with
-  the finite differences while the derivative of the stated F agrees (reading c1).
+  the finite differences while the derivative of the stated F agrees: differentiating
+  (R m)^T (xi' - xi) with R^T = -R gives R m - 0.5 H(xi') R (xi' - xi), so the printed + is taken
+  as a sign slip and the derivative is used.
 """
 import numpy as np
 import pytest

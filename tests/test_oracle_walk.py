@@ -1,4 +1,6 @@
-"""Pins of the cross-triangle walk of the reconnection vertex (reading R25) in the oracle.
+"""Pins of the cross-triangle walk of the reconnection vertex in the oracle (opt-in: when Newton
+moves the vertex off its triangle -- an edge case Sec. 4.2 does not address -- it continues on the
+neighbour across the crossed edge, unfolded into the triangle's plane, instead of failing).
 
 * Tessellation invariance: on planar surfaces the walk unfolds coplanar neighbours without
   change, so the box scene renders the same whether its walls are 2 or 32 triangles each (without
