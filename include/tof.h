@@ -12,6 +12,11 @@
  * Conventions for every entry point
  *   - Return value: TOF_OK (0) or a negative tof_status; never aborts.  tof_last_error() gives a
  *     one-line message for the last failure on that context.
+ *   - Device-side errors (a BVH traversal that overflows its stack or exceeds its visit budget,
+ *     a transient pixel whose candidates overflow its bin table) set bits of the context's error
+ *     word instead of faulting.  The word is read back asynchronously after every render and
+ *     reported (TOF_ECUDA, message naming the cause, word cleared) by the context's next render or
+ *     batch call, by tof_view_stats, and by tof_sync, which waits for the stream first.
  *   - Host pointers (const T*) are read during the call only and stay owned by the caller.
  *   - Device pointers (out_*_dev) are caller-owned device memory on the context's GPU, written
  *     asynchronously on `stream` (a cudaStream_t passed as void*, NULL = legacy default stream);
@@ -158,7 +163,7 @@ typedef struct {
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
  * context may allocate for scenes and views (0 = no bound); allocations beyond it fail with
- * TOF_EBUDGET. */
+ * TOF_EBUDGET.  Not in the paper: library plumbing (the paper's renderer runs inside Falcor). */
 tof_status tof_create(tof_ctx** out, int device, uint64_t hbm_budget_bytes);
 tof_status tof_destroy(tof_ctx* ctx);
 const char* tof_last_error(tof_ctx* ctx);
@@ -175,7 +180,9 @@ tof_status tof_scene_upload(tof_ctx* ctx, const float* verts, uint32_t nv, const
 tof_status tof_scene_destroy(tof_ctx* ctx, tof_scene scene);
 
 /* Place the objects (row-major 3x4 object-to-world matrices, nobj*12 floats) and build the GPU
- * LBVH (Morton codes, radix sort, hierarchy, bounds).  refit_only = 1 keeps the hierarchy and
+ * LBVH (Morton codes, radix sort, hierarchy, bounds).  Not in the paper, which traces rays with
+ * the GPU's ray-tracing hardware through DXR (Sec. 6); GB300 has no such units, so the library
+ * builds its own hierarchy (Karras 2012 construction over 30-bit Morton codes).  refit_only = 1 keeps the hierarchy and
  * refits bounds after rigid motion: cheaper to build, but the hierarchy's quality decays as objects
  * move away from where it was built (a full build of 66k triangles takes about 0.2 ms on GB300 and
  * pays for itself within a few frames of motion).  Call once per frame before rendering it: the library keeps
@@ -210,7 +217,10 @@ tof_status tof_render_gated(tof_ctx* ctx, tof_scene scene, tof_view view, const 
  *   - The static array (about 15.6 MiB) belongs to the library's device image: every GPU that
  *     loads libtof.so holds it until the process exits.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress with
- *     that device current); make that first call before any stream capture.
+ *     that device current).  Under CUDA's lazy module loading (the default) that lookup is also
+ *     what loads the library's host-side module and commits the array's device memory, so the
+ *     first call does take memory once; later calls take none.  Make that first call at set-up,
+ *     before any stream capture.
  *   - Every call shares the one array and each call overwrites it (its task counters are reset on
  *     the stream at the start of each reuse pass): calls whose work overlaps on the GPU -- on
  *     different streams, or from different threads -- race and must be serialised by the caller.
@@ -284,17 +294,25 @@ tof_status tof_view_get_tuning(tof_ctx* ctx, tof_view view, tof_tuning* out);
  * NULL, written to out[i].  Synchronises `stream`; not for use during stream capture. */
 tof_status tof_autotune(tof_ctx* ctx, const tof_job* jobs, uint32_t n, int32_t frames, void* stream, tof_tuning* out);
 
-/* Served form: a request scheduler over several dynamic streams.
+/* Served form: a request scheduler over several dynamic streams (continuous batching).  Not in the
+ * paper (its renderer serves one view); the method's real-time intent (Sec. 6) served as a system.
  *   A stream is a scene plus a fixed sensor resolution (and bin count for transient streams); its
- *   view -- reservoirs, G-buffers, confidences -- is created on first admission and stays resident,
- *   so frames of a stream reuse their predecessors temporally.
+ *   view -- reservoirs, G-buffers, confidences, reuse scratch -- is created on admission and stays
+ *   resident, so frames of a stream reuse their predecessors temporally.
  *   tof_server_submit queues one frame request: the job (view field ignored) and the frame's
  *   object transforms (nobj * 12 floats, copied).  tof_server_step retires batches whose GPU work
- *   has finished, admits pending requests in arrival order -- at most one frame in flight per stream,
- *   and a stream's first admission only if its view fits the server's HBM budget -- applies each
- *   admitted stream's transforms (tof_bvh_build, full build), and launches all admitted frames as one
- *   batch (tof_render_batch) on `stream`.  Requests arriving while a batch runs join the next step
- *   (continuous batching).  Times are host wall-clock: submit -> observed completion. */
+ *   has finished and admits pending requests in arrival order: at most one frame in flight per
+ *   stream and per scene (streams may share a scene; its BVH is rebuilt only while no frame reads
+ *   it).  A stream's first admission creates its view and scratch, measures the device bytes they
+ *   took and keeps them only if the resident views fit the server's HBM budget, evicting the least
+ *   recently used idle views (no frame in flight, none queued; an evicted stream's next frame
+ *   renders without temporal reuse) to make room; otherwise the request waits.  The step applies
+ *   each admitted stream's transforms (tof_bvh_build, full build) and launches all admitted frames
+ *   as one batch graph on the next of the server's own streams (4, round robin), ordered after the
+ *   work already queued on `stream`; batches of successive steps therefore overlap on the device.
+ *   Requests arriving while batches run join the next step.  Times are host wall-clock:
+ *   submit -> observed completion.  The server's results are those of tof_render_gated /
+ *   tof_render_transient on the same views (every random number is keyed by pixel and frame). */
 typedef struct tof_server tof_server;
 tof_status tof_server_create(tof_ctx* ctx, uint64_t hbm_budget_bytes, tof_server** out);
 tof_status tof_server_destroy(tof_server* srv);
@@ -314,7 +332,19 @@ tof_status tof_render_pt(tof_ctx* ctx, tof_scene scene, const tof_sensor* sensor
                          const tof_gate* gate, const tof_bins* bins, const tof_params* params, uint64_t seed,
                          uint32_t frame, int32_t spp, float* out_dev, void* stream);
 
-/* Forget the view's history (the next frame renders without temporal reuse). */
+/* Wait for `stream` and report any device-side error recorded since the last check (TOF_ECUDA
+ * with a message naming the cause; the error word is cleared).  Outputs written on `stream`
+ * before the call are valid when it returns TOF_OK.  Not in the paper: error plumbing. */
+tof_status tof_sync(tof_ctx* ctx, void* stream);
+
+/* Kernel launches the library has issued in this process, across every context (a kernel recorded
+ * into a batch graph counts once, when it is recorded; graph replays add nothing).  Not in the
+ * paper: instrumentation for launch accounting. */
+uint64_t tof_kernel_launches(void);
+
+/* Forget the view's history (the next frame renders without temporal reuse).  Not in the paper:
+ * a restart of the reservoir sequence (e.g. after a scene cut), which the method leaves to the
+ * renderer. */
 tof_status tof_reservoirs_reset(tof_ctx* ctx, tof_view view);
 
 /* Shift statistics accumulated by the view since creation (Table "Newton statistics", Sec. 6):

@@ -19,7 +19,7 @@
 
 namespace tof {
 cudaError_t launch_gbuffer(const GbufArgs& a, int tile_h, cudaStream_t s);
-cudaError_t launch_initial(const InitArgs& a, int tile_h, int* err, cudaStream_t s);
+cudaError_t launch_initial(const InitArgs& a, int tile_h, unsigned* err, cudaStream_t s);
 cudaError_t launch_initial_ell_wave(const InitArgs& a, const EllWaveDev& w, int tile_h, int place_blocks, int vis_blocks,
                                     cudaStream_t s);
 cudaError_t ell_place_blocks(int* out);
@@ -121,6 +121,8 @@ struct ViewH {
 
 }  // namespace
 
+constexpr int kBatchSlots = 8;   // batch graphs that may be in flight at once (launches of one graph serialise)
+
 struct tof_ctx {
     int device = 0;
     uint64_t budget = 0;
@@ -130,7 +132,8 @@ struct tof_ctx {
     std::vector<ViewH> views;
     std::vector<DevAlloc> allocs;
     uint32_t version_counter = 0;
-    int* d_err = nullptr;
+    unsigned* d_err = nullptr;   // device error word (kErr* bits), set by kernels
+    unsigned* h_err = nullptr;   // pinned host mirror of it, copied after every render on its stream
     float* d_scratch = nullptr;  // laser spot of plain PT renders
     int persist_blocks = 0;      // resident blocks of the persistent reuse kernels (all SMs)
     int ell_blocks = 0;          // resident blocks of the ellipsoidal placement kernel (all SMs)
@@ -141,7 +144,7 @@ struct tof_ctx {
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
     cudaStream_t capture = nullptr;
-    cudaGraphExec_t batch_exec = nullptr;
+    cudaGraphExec_t batch_exec[kBatchSlots] = {};   // one instantiated graph per batch slot
     bool in_batch = false;
 };
 
@@ -199,6 +202,28 @@ static void dfree(tof_ctx* c, void* p) {
 
 static float3 v3f(const float* p) { return make_float3(p[0], p[1], p[2]); }
 
+// turn error-word bits into a status: TOF_ECUDA naming every cause, the word cleared (on the device
+// too) so that each error is reported once
+static tof_status report_err_bits(tof_ctx* c, unsigned bits) {
+    if (!bits) return TOF_OK;
+    cudaMemset(c->d_err, 0, sizeof(unsigned));
+    c->h_err[0] = 0u;
+    return fail(c, TOF_ECUDA, "device error word 0x%x:%s%s%s (results since the last check are unreliable)", bits,
+                (bits & kErrBinOverflow) ? " transient bin table overflow;" : "",
+                (bits & kErrStackOverflow) ? " BVH traversal stack overflow (a subtree was skipped);" : "",
+                (bits & kErrVisitBudget) ? " BVH traversal visit budget exhausted (malformed hierarchy);" : "");
+}
+// errors of earlier renders whose mirror copy has already landed (no wait)
+static tof_status pending_err(tof_ctx* c) {
+    const unsigned bits = c->h_err ? *(volatile unsigned*)c->h_err : 0u;
+    return report_err_bits(c, bits);
+}
+// queue the mirror copy of the error word after a render (not while a batch graph is captured:
+// the next direct render or tof_sync reads the word)
+static void mirror_err(tof_ctx* c, cudaStream_t s, bool capturing) {
+    if (!capturing) cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+}
+
 static ParamsDev to_dev(const tof_params* p, uint64_t seed) {
     ParamsDev d;
     d.depth = p->depth; d.n_cand = p->n_cand; d.n_spatial = p->n_spatial; d.radius = p->radius;
@@ -253,13 +278,14 @@ static tof_status check_sensor(tof_ctx* c, const tof_sensor* s, int W, int H) {
 }
 
 static FrameDev make_frame(const SceneH& S, int slot, const tof_sensor* s, const tof_emitter* e, float L0, float dL, int B,
-                           uint32_t frame, float4* gb, LightDev* laser) {
+                           uint32_t frame, float4* gb, LightDev* laser, unsigned* err) {
     FrameDev F;
     memset(&F, 0, sizeof(F));
     F.g.tri = S.tri[slot]; F.g.leaf = S.leaf[slot]; F.g.nodes = S.nodes[slot]; F.g.mats = S.mats; F.g.nt = S.nt;
     F.g.adj = S.adj;
     F.g.enode = S.enode[slot]; F.g.eP = S.eP;
     F.g.version = S.version[slot];
+    F.g.err = err;
     F.mode = s->mode; F.W = s->W; F.H = s->H;
     F.pos = v3f(s->pos); F.fwd = v3f(s->fwd); F.up = v3f(s->up); F.fov_y = s->fov_y;
     F.wall_o = v3f(s->wall_o); F.wall_u = v3f(s->wall_u); F.wall_v = v3f(s->wall_v);
@@ -355,6 +381,13 @@ tof_status tof_create(tof_ctx** out, int device, uint64_t hbm_budget_bytes) {
     c->budget = hbm_budget_bytes;
     if (dalloc(c, &c->d_err, 64, "error word") != TOF_OK) { delete c; return TOF_ENOMEM; }
     cudaMemset(c->d_err, 0, 64);
+    if (cudaHostAlloc((void**)&c->h_err, 64, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        for (auto& a : c->allocs) cudaFree(a.p);
+        delete c;
+        return TOF_ENOMEM;
+    }
+    memset(c->h_err, 0, 64);
     *out = c;
     return TOF_OK;
 }
@@ -363,12 +396,14 @@ tof_status tof_destroy(tof_ctx* c) {
     if (!c) return TOF_EINVAL;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+    for (cudaGraphExec_t& x : c->batch_exec)
+        if (x) cudaGraphExecDestroy(x);
     for (cudaStream_t q : c->pool) cudaStreamDestroy(q);
     for (cudaEvent_t e : c->join) cudaEventDestroy(e);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->capture) cudaStreamDestroy(c->capture);
     for (auto& a : c->allocs) cudaFree(a.p);
+    if (c->h_err) cudaFreeHost(c->h_err);
     delete c;
     return TOF_OK;
 }
@@ -569,7 +604,9 @@ tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[10]) {
     CK(cudaStreamSynchronize(V.last_stream));
     CK(cudaMemcpy(&h, V.stats, sizeof(h), cudaMemcpyDeviceToHost));
     for (int i = 0; i < 10; ++i) out[i] = (double)h.v[i];
-    return TOF_OK;
+    unsigned bits = 0;
+    CK(cudaMemcpy(&bits, c->d_err, sizeof(bits), cudaMemcpyDeviceToHost));
+    return report_err_bits(c, bits);
 }
 
 static bool g_no_marks = false;   // set while a batch is being captured (no profiling events)
@@ -718,11 +755,12 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     if (!(dL > 0) || !std::isfinite(L0)) return fail(c, TOF_EINVAL, "gate / bin width must be positive and finite");
     if (!out) return fail(c, TOF_EINVAL, "output pointer is NULL");
     cudaSetDevice(c->device);
+    if (!g_no_marks) TRY(pending_err(c));
     cudaStream_t s = (cudaStream_t)stream;
     V.last_stream = s;
 
     const int fc = V.has_prev ? 1 - V.cur : V.cur;
-    FrameDev F = make_frame(S, S.cur, sensor, emitter, L0, dL, B, frame, V.gb[fc], V.laser[fc]);
+    FrameDev F = make_frame(S, S.cur, sensor, emitter, L0, dL, B, frame, V.gb[fc], V.laser[fc], c->d_err);
     ParamsDev P = to_dev(params, seed);
     for (int k = 0; k < 5; ++k) V.ran[k] = false;
     V.kev_used = 0;
@@ -822,6 +860,7 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     }
     mark(V, 5, s);
     mark(V, 6, s);
+    mirror_err(c, s, g_no_marks);
     V.fd[fc] = F;
     V.geom_slot[fc] = S.cur;
     V.geom_version[fc] = S.version[S.cur];
@@ -908,36 +947,52 @@ __attribute__((visibility("hidden"))) int tof_internal_scene_objects(tof_ctx* c,
     return c->scenes[id].nobj;
 }
 
-tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* stream) {
+// validate one job of a batch and allocate its view's scratch (allocation is not allowed inside the
+// capture)
+static tof_status prepare_job(tof_ctx* c, const tof_job& J, uint32_t i) {
+    if (J.view < 0 || J.view >= (int)c->views.size() || !c->views[J.view].alive)
+        return fail(c, TOF_EINVAL, "job %u: bad view handle", i);
+    if (J.scene < 0 || J.scene >= (int)c->scenes.size() || !c->scenes[J.scene].alive)
+        return fail(c, TOF_EINVAL, "job %u: bad scene handle", i);
+    if (!c->scenes[J.scene].built) return fail(c, TOF_ESTATE, "job %u: scene %d has no BVH", i, J.scene);
+    ViewH& V = c->views[J.view];
+    TRY(check_params(c, &J.params, J.transient != 0));
+    if ((J.params.flags & TOF_FLAG_ELLIPSOID) && !c->scenes[J.scene].enode[0])
+        return fail(c, TOF_EINVAL, "job %u: the ellipsoidal connection supports scenes of up to 2^%d triangles", i, kEllMaxLevels);
+    TRY(check_sensor(c, &J.sensor, V.W, V.H));
+    if (!J.out_dev) return fail(c, TOF_EINVAL, "job %u: output pointer is NULL", i);
+    const size_t npix = (size_t)V.W * V.H, Bn = V.B > 0 ? (size_t)V.B : 1;
+    size_t cap = npix * Bn < ((size_t)1 << 22) ? npix * Bn : ((size_t)1 << 22);
+    if (cap < npix && V.B == 0) cap = npix;
+    int S = 1 + J.params.n_spatial > 2 ? 1 + J.params.n_spatial : 2;
+    if (J.transient && (J.params.flags & TOF_FLAG_BIN_REUSE) && S < 3) S = 3;
+    TRY(ensure_wave(c, V, S, (int)cap));
+    if (use_ell_wave(V, J.transient ? V.B : 0, &J.params, false)) TRY(ensure_ell_wave(c, V, J.params.n_cand, J.params.depth));
+    return TOF_OK;
+}
+
+// allocate the scratch a job's view needs (as the first batch with that job would), for callers that
+// account device memory per view before launching (the served form's admission)
+__attribute__((visibility("hidden"))) tof_status tof_internal_prepare_job(tof_ctx* c, const tof_job* job) {
+    if (!c || !job) return TOF_EINVAL;
+    cudaSetDevice(c->device);
+    return prepare_job(c, *job, 0);
+}
+
+static tof_status render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* stream, int slot) {
     if (!c) return TOF_EINVAL;
     if (!jobs || n == 0) return fail(c, TOF_EINVAL, "empty batch");
+    if (slot < 0 || slot >= kBatchSlots) return fail(c, TOF_EINVAL, "batch slot %d outside [0, %d)", slot, kBatchSlots);
     if (c->in_batch) return fail(c, TOF_ESTATE, "tof_render_batch is not re-entrant");
     cudaSetDevice(c->device);
-    // validate and prepare every job outside the capture (allocation is not allowed inside it)
+    TRY(pending_err(c));
     std::vector<int> seen;
     for (uint32_t i = 0; i < n; ++i) {
         const tof_job& J = jobs[i];
-        if (J.view < 0 || J.view >= (int)c->views.size() || !c->views[J.view].alive)
-            return fail(c, TOF_EINVAL, "job %u: bad view handle", i);
         for (int v : seen)
             if (v == J.view) return fail(c, TOF_EINVAL, "job %u: view %d used by two jobs of one batch", i, J.view);
         seen.push_back(J.view);
-        if (J.scene < 0 || J.scene >= (int)c->scenes.size() || !c->scenes[J.scene].alive)
-            return fail(c, TOF_EINVAL, "job %u: bad scene handle", i);
-        if (!c->scenes[J.scene].built) return fail(c, TOF_ESTATE, "job %u: scene %d has no BVH", i, J.scene);
-        ViewH& V = c->views[J.view];
-        TRY(check_params(c, &J.params, J.transient != 0));
-        if ((J.params.flags & TOF_FLAG_ELLIPSOID) && !c->scenes[J.scene].enode[0])
-            return fail(c, TOF_EINVAL, "job %u: the ellipsoidal connection supports scenes of up to 2^%d triangles", i, kEllMaxLevels);
-        TRY(check_sensor(c, &J.sensor, V.W, V.H));
-        if (!J.out_dev) return fail(c, TOF_EINVAL, "job %u: output pointer is NULL", i);
-        const size_t npix = (size_t)V.W * V.H, Bn = V.B > 0 ? (size_t)V.B : 1;
-        size_t cap = npix * Bn < ((size_t)1 << 22) ? npix * Bn : ((size_t)1 << 22);
-        if (cap < npix && V.B == 0) cap = npix;
-        int S = 1 + J.params.n_spatial > 2 ? 1 + J.params.n_spatial : 2;
-        if (J.transient && (J.params.flags & TOF_FLAG_BIN_REUSE) && S < 3) S = 3;
-        TRY(ensure_wave(c, V, S, (int)cap));
-        if (use_ell_wave(V, J.transient ? V.B : 0, &J.params, false)) TRY(ensure_ell_wave(c, V, J.params.n_cand, J.params.depth));
+        TRY(prepare_job(c, J, i));
     }
     TRY(persist_init(c));
     const uint32_t P = n < 16 ? n : 16;
@@ -1006,29 +1061,41 @@ tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* s
         cudaGetLastError();
         return fail(c, TOF_ECUDA, "batch capture failed: %s", cudaGetErrorString(e));
     }
-    // reuse the instantiated graph when only node parameters changed
+    // reuse the slot's instantiated graph when only node parameters changed
+    cudaGraphExec_t& X = c->batch_exec[slot];
     bool updated = false;
-    if (c->batch_exec) {
+    if (X) {
         cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(c->batch_exec, graph, &info) == cudaSuccess) updated = true;
+        if (cudaGraphExecUpdate(X, graph, &info) == cudaSuccess) updated = true;
         else {
             cudaGetLastError();
-            cudaGraphExecDestroy(c->batch_exec);
-            c->batch_exec = nullptr;
+            cudaGraphExecDestroy(X);
+            X = nullptr;
         }
     }
     if (!updated) {
-        e = cudaGraphInstantiate(&c->batch_exec, graph, 0);
+        e = cudaGraphInstantiate(&X, graph, 0);
         if (e != cudaSuccess) {
             cudaGraphDestroy(graph);
-            c->batch_exec = nullptr;
+            X = nullptr;
             return fail(c, TOF_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
         }
     }
     cudaGraphDestroy(graph);
-    CK(cudaGraphLaunch(c->batch_exec, (cudaStream_t)stream));
+    CK(cudaGraphLaunch(X, (cudaStream_t)stream));
+    mirror_err(c, (cudaStream_t)stream, false);
     for (uint32_t i = 0; i < n; ++i) c->views[jobs[i].view].last_stream = (cudaStream_t)stream;
     return TOF_OK;
+}
+
+tof_status tof_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* stream) {
+    return render_batch(c, jobs, n, stream, 0);
+}
+
+// batch on graph slot `slot` (the served form keeps several batches in flight, one slot each)
+__attribute__((visibility("hidden"))) tof_status tof_internal_render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n,
+                                                                         void* stream, int slot) {
+    return render_batch(c, jobs, n, stream, slot);
 }
 
 static tof_status check_tuning(tof_ctx* c, const tof_tuning* t) {
@@ -1206,19 +1273,32 @@ tof_status tof_render_pt(tof_ctx* c, tof_scene scene, const tof_sensor* sensor, 
     if (bins && B < 1) return fail(c, TOF_EINVAL, "B < 1");
     if (!(dL > 0)) return fail(c, TOF_EINVAL, "gate / bin width must be positive");
     cudaSetDevice(c->device);
+    TRY(pending_err(c));
     cudaStream_t s = (cudaStream_t)stream;
     LightDev* laser = nullptr;
     if (emitter->type == TOF_EMIT_LASER) {
         if (!c->d_scratch) TRY(dalloc(c, &c->d_scratch, 256, "laser scratch"));
         laser = (LightDev*)c->d_scratch;
     }
-    FrameDev F = make_frame(S, S.cur, sensor, emitter, L0, dL, B, frame, nullptr, laser);
+    FrameDev F = make_frame(S, S.cur, sensor, emitter, L0, dL, B, frame, nullptr, laser, c->d_err);
     ParamsDev P = to_dev(params, seed);
     if (laser) CK(launch_laser(F.g, v3f(emitter->pos), v3f(emitter->dir), emitter->power, laser, s));
     PtArgs pa;
     pa.F = F; pa.P = P; pa.spp = spp; pa.out = out_dev;
     CK(launch_pt(pa, s));
+    mirror_err(c, s, false);
     return TOF_OK;
 }
+
+tof_status tof_sync(tof_ctx* c, void* stream) {
+    if (!c) return TOF_EINVAL;
+    cudaSetDevice(c->device);
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned bits = 0;
+    CK(cudaMemcpy(&bits, c->d_err, sizeof(bits), cudaMemcpyDeviceToHost));
+    return report_err_bits(c, bits);
+}
+
+uint64_t tof_kernel_launches(void) { return (uint64_t)g_kernel_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

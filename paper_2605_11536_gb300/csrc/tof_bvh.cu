@@ -321,6 +321,7 @@ static inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1
 
 cudaError_t launch_xform(int nt, const float* vloc, const uint32_t* tris, const uint32_t* triobj, const uint32_t* objmat,
                          const float* xf, float4* tri_out, float4* cent, cudaStream_t s) {
+    note_launch();
     xform_kernel<<<blocks(nt, 256), 256, 0, s>>>(nt, vloc, tris, triobj, objmat, xf, tri_out, cent);
     return cudaGetLastError();
 }
@@ -333,19 +334,24 @@ cudaError_t launch_build_topology(int n, const float4* cent, uint32_t* bb, uint3
     cudaError_t e = cudaMemsetAsync(bb, 0xFF, 3 * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(bb + 3, 0, 3 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
+    note_launch();
     bounds_kernel<<<min(1024u, blocks(n, 256)), 256, 0, s>>>(n, cent, bb);
+    note_launch();
     morton_kernel<<<blocks(n, 256), 256, 0, s>>>(n, cent, bb, keys, vals);
     int ntiles = (n + kTile - 1) / kTile;
     uint32_t *ki = keys, *vi = vals, *ko = keys2, *vo = vals2;
     for (int shift = 0; shift < 32; shift += 8) {
+        note_launch();
         radix_hist_kernel<<<ntiles, 256, 0, s>>>(ki, n, shift, hist, ntiles);
+        note_launch();
         scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * ntiles);
+        note_launch();
         radix_scatter_kernel<<<ntiles, 256, 0, s>>>(ki, vi, ko, vo, n, shift, hist, ntiles);
         uint32_t* t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
     }
     // after 4 passes the sorted keys / prims are back in keys / vals
-    if (n > 1) karras_kernel<<<blocks(n - 1, 256), 256, 0, s>>>(n, ki, child, parent_int, parent_leaf);
+    if (n > 1) { note_launch(); karras_kernel<<<blocks(n - 1, 256), 256, 0, s>>>(n, ki, child, parent_int, parent_leaf); }
     *prim_out = vi;
     return cudaGetLastError();
 }
@@ -356,6 +362,7 @@ cudaError_t launch_refit(int n, const uint32_t* prim, const float4* tri, float4*
         cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(uint32_t) * (size_t)(n - 1), s);
         if (e != cudaSuccess) return e;
     }
+    note_launch();
     refit_kernel<<<blocks(n, 256), 256, 0, s>>>(n, prim, tri, leaf, nodes, child, parent_int, parent_leaf, counter);
     return cudaGetLastError();
 }
@@ -364,8 +371,9 @@ cudaError_t launch_etree(int nt, int P, const float4* tri, float4* node, cudaStr
     const int bs = P < kEllBlock ? P : kEllBlock;
     int levels = 0;
     while ((1 << levels) < bs) ++levels;
+    note_launch();
     etree_low_kernel<<<P / bs, bs, 0, s>>>(nt, P, levels, tri, node);
-    if (P / bs > 1) etree_top_kernel<<<1, 1024, 0, s>>>(P / bs, node);
+    if (P / bs > 1) { note_launch(); etree_top_kernel<<<1, 1024, 0, s>>>(P / bs, node); }
     return cudaGetLastError();
 }
 

@@ -204,12 +204,17 @@ static __device__ __forceinline__ bool closer(bool found, float t, int id, float
 // keeps the shift kernels' code small and lets lanes from different call sites share it.
 template <bool kAny>
 static __device__ __noinline__ bool traverse(const GeomDev& g, float3 o, float3 d, float tmax, int& tri, float& b1, float& b2, float& tout) {
-    if (g.nt <= 0) return false;
+    // the loop reads the hierarchy through these copies and makes no store that could alias them;
+    // an overflow is only noted here and published in the error word after the loop
+    const float4* __restrict__ nodes = g.nodes;
+    const float4* __restrict__ leaf = g.leaf;
+    const int nt = g.nt;
+    if (nt <= 0) return false;
     bool found = false;
     float best = tmax;
-    if (g.nt == 1) {
+    if (nt == 1) {
         int orig;
-        if (tri_test(g.leaf, 0, o, d, best, tout, b1, b2, orig) && tout < tmax) { tri = orig; return true; }
+        if (tri_test(leaf, 0, o, d, best, tout, b1, b2, orig) && tout < tmax) { tri = orig; return true; }
         return false;
     }
     float3 id = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
@@ -217,12 +222,16 @@ static __device__ __noinline__ bool traverse(const GeomDev& g, float3 o, float3 
     int stack[kStack];
     int sp = 0;
     int node = 0;
+    unsigned fault = 0u;
     // a valid hierarchy visits each of its nt - 1 internal nodes at most once per ray; the cap
-    // only guards against a malformed one
-    int budget = g.nt + 64;
+    // only guards against a malformed one, and running into it is reported in the error word
+    int budget = nt + 64;
     while (true) {
-        if (--budget < 0) break;
-        const float4* N = g.nodes + 4 * node;
+        if (--budget < 0) {
+            fault |= kErrVisitBudget;
+            break;
+        }
+        const float4* N = nodes + 4 * node;
         float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
         float a0 = n0.x * id.x - ood.x, a1 = n0.y * id.x - ood.x;
         float b0 = n0.z * id.y - ood.y, bb1 = n0.w * id.y - ood.y;
@@ -238,7 +247,7 @@ static __device__ __noinline__ bool traverse(const GeomDev& g, float3 o, float3 
         int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
         if (h0 && ch0 < 0) {
             float t, u, w; int orig;
-            if (tri_test(g.leaf, ~ch0, o, d, best, t, u, w, orig) && (found || t < tmax) && closer(found, t, orig, best, tri)) {
+            if (tri_test(leaf, ~ch0, o, d, best, t, u, w, orig) && (found || t < tmax) && closer(found, t, orig, best, tri)) {
                 best = t; tri = orig; b1 = u; b2 = w; found = true;
                 if (kAny) { tout = t; return true; }
             }
@@ -246,7 +255,7 @@ static __device__ __noinline__ bool traverse(const GeomDev& g, float3 o, float3 
         }
         if (h1 && ch1 < 0) {
             float t, u, w; int orig;
-            if (tri_test(g.leaf, ~ch1, o, d, best, t, u, w, orig) && (found || t < tmax) && closer(found, t, orig, best, tri)) {
+            if (tri_test(leaf, ~ch1, o, d, best, t, u, w, orig) && (found || t < tmax) && closer(found, t, orig, best, tri)) {
                 best = t; tri = orig; b1 = u; b2 = w; found = true;
                 if (kAny) { tout = t; return true; }
             }
@@ -255,6 +264,7 @@ static __device__ __noinline__ bool traverse(const GeomDev& g, float3 o, float3 
         if (h0 && h1) {
             int nearc = lo0 <= lo1 ? ch0 : ch1, farc = lo0 <= lo1 ? ch1 : ch0;
             if (sp < kStack) stack[sp++] = farc;
+            else fault |= kErrStackOverflow;   // the far subtree is skipped: reported below
             node = nearc;
         } else if (h0) {
             node = ch0;
@@ -265,6 +275,7 @@ static __device__ __noinline__ bool traverse(const GeomDev& g, float3 o, float3 
             node = stack[--sp];
         }
     }
+    if (fault && g.err) atomicOr(g.err, fault);
     if (found) tout = best;
     return found;
 }

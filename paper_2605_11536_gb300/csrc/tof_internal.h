@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 // number of objects of a scene (server -> context); hidden from the library's exports
 extern "C" __attribute__((visibility("hidden"))) int tof_internal_scene_objects(struct tof_ctx* c, int32_t scene);
 
@@ -20,6 +22,16 @@ constexpr uint32_t kFlagPairwiseMis = 4u;  // TOF_FLAG_PAIRWISE_MIS
 constexpr uint32_t kFlagTriangleWalk = 64u;  // TOF_FLAG_TRIANGLE_WALK
 constexpr uint32_t kFlagEllipsoid = 256u;    // TOF_FLAG_ELLIPSOID
 constexpr int kEllMaxLevels = 22;           // ellipsoidal-connection hierarchies of up to 2^22 triangles
+
+// bits of the context's device error word (read back by the host at the next synchronising call)
+constexpr unsigned kErrBinOverflow = 1u;    // a pixel's initial candidates hit more distinct bins than it holds
+constexpr unsigned kErrStackOverflow = 2u;  // a BVH traversal stack was full (a far child would have been dropped)
+constexpr unsigned kErrVisitBudget = 4u;    // a BVH traversal visited more nodes than a valid hierarchy has
+
+// kernel launches issued by the library in this process (every launch wrapper counts its kernels;
+// a kernel recorded into a graph counts once, when it is recorded)
+inline std::atomic<unsigned long long> g_kernel_launches{0};
+inline void note_launch(unsigned n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // material record: (type, albedo, alpha, unused)
 // triangle record (original order): 3 float4 = (v0.xyz, material id bits), (e1.xyz, 0), (e2.xyz, 0)
@@ -43,6 +55,7 @@ struct GeomDev {
     int eP;
     int nt;
     uint32_t version;
+    unsigned* err;           // the context's device error word (kErr* bits), or null
 };
 
 // resolved light of one domain (Sec. 5 "Light Source")

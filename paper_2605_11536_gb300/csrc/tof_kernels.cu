@@ -210,11 +210,74 @@ struct InitSink {
     }
 };
 
+// gated sink: one running reservoir in registers (the transient sink's per-bin tables live in
+// local memory, which every candidate of a gated pixel paid for)
+struct GatedSink {
+    const ResDev* R;
+    const Domain* D;
+    const ParamsDev* P;
+    uint32_t px, frame;
+    int tree;
+    float invN;
+    float S, phat, tau, Lsuf;
+    __device__ void operator()(int k, float c, float tauv, const TreeVerts& T, int strategy) {
+        float wv = invN * c;
+        if (!(wv > 0.f)) return;
+        uint4 u = philox(px, frame, ((uint32_t)tree << 8) | (uint32_t)k, strategy ? P_ELL_RIS : P_RIS, P->seed);
+        S += wv;
+        if (u01(u.x) * S < wv) {
+            Rec r;
+            build_rec(*D, T, k, tree, px, frame, tauv, *P, r);
+            store_tail(*R, (size_t)px, r);
+            phat = r.phat; tau = tauv; Lsuf = r.Lsuf;
+        }
+    }
+};
+
+// gated views: the same trees, candidates, order and uniforms as initial_kernel, into GatedSink
+template <bool kEll>
+__global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_gated_kernel(const __grid_constant__ InitArgs a) {
+    const FrameDev& F = a.F;
+    int ix, iy;
+    tile_pixel(a.tile_w, ix, iy);
+    if (ix >= F.W || iy >= F.H) return;
+    const int pix = iy * F.W + ix;
+    const ParamsDev& P = a.P;
+    a.dst.M[pix] = (float)P.n_cand;
+    float4 gb = F.gb[pix];
+    uint32_t tri = __float_as_uint(gb.x);
+    Domain D = make_domain_hit(&F, tri != kNoHit, (int)tri, gb.y, gb.z, gb.w, F.L0, F.dL);
+    if (!D.valid) {
+        a.dst.occ[pix] = 0u;
+        if (a.out) a.out[pix] = 0.f;
+        return;
+    }
+    GatedSink sink;
+    sink.R = &a.dst; sink.D = &D; sink.P = &P; sink.px = (uint32_t)pix; sink.frame = F.frame;
+    sink.invN = 1.0f / (float)P.n_cand;
+    sink.S = 0.f; sink.phat = 0.f; sink.tau = 0.f; sink.Lsuf = 0.f;
+    TreeVerts T;
+    for (int t = 0; t < P.n_cand; ++t) {
+        sink.tree = t;
+        trace_tree<kEll ? 1 : 0>(D, P, (uint32_t)pix, F.frame, t, F.L0, F.L0 + F.dL, T, sink);
+    }
+    float outv = 0.f;
+    uint32_t occ = 0u;
+    if (sink.phat > 0.f) {
+        const float W = sink.S / sink.phat;
+        *res_at(a.dst, 0, (size_t)pix) = make_float4(W, sink.phat, sink.tau, sink.Lsuf);
+        occ = 1u;
+        outv = sink.phat * W;
+    }
+    a.dst.occ[pix] = occ;
+    if (a.out) a.out[pix] = outv;
+}
+
 // 6 resident blocks per SM (80 registers): 1.08 against 1.11 ms at 5 blocks (96 registers) on the
 // 512 x 512 dynamic workload; 8 blocks (64 registers, more spills) were slower.  kEll: with the
 // ellipsoidal connection (TOF_FLAG_ELLIPSOID), compiled apart so the default keeps its registers.
 template <bool kEll>
-__global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_kernel(const __grid_constant__ InitArgs a, int* err) {
+__global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_kernel(const __grid_constant__ InitArgs a, unsigned* err) {
     const FrameDev& F = a.F;
     int ix, iy;
     tile_pixel(a.tile_w, ix, iy);
@@ -241,7 +304,7 @@ __global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_kernel(const __grid
         sink.tree = t;
         trace_tree<kEll ? 1 : 0>(D, P, (uint32_t)pix, F.frame, t, glo, ghi, T, sink);
     }
-    if (sink.overflow && err) atomicOr(err, 1);
+    if (sink.overflow && err) atomicOr(err, kErrBinOverflow);
     float outv = 0.f;
     for (int e = 0; e < sink.n; ++e) {
         if (!(sink.phat[e] > 0.f)) continue;
@@ -617,14 +680,21 @@ static inline dim3 tile_grid(int W, int H, int tw, int th) { return dim3((W + tw
 
 // tile_w x tile_h pixel tiles, tile_w a power of two in [4, 32], tile_w * tile_h = 64 or 128
 cudaError_t launch_gbuffer(const GbufArgs& a, int tile_h, cudaStream_t s) {
+    note_launch();
     gbuffer_kernel<<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_initial(const InitArgs& a, int tile_h, int* err, cudaStream_t s) {
-    if (a.P.flags & kFlagEllipsoid)
-        initial_kernel<true><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, err);
-    else
-        initial_kernel<false><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, err);
+cudaError_t launch_initial(const InitArgs& a, int tile_h, unsigned* err, cudaStream_t s) {
+    note_launch();
+    const dim3 grid = tile_grid(a.F.W, a.F.H, a.tile_w, tile_h);
+    const int threads = a.tile_w * tile_h;
+    if (a.F.B == 0) {
+        if (a.P.flags & kFlagEllipsoid) initial_gated_kernel<true><<<grid, threads, 0, s>>>(a);
+        else initial_gated_kernel<false><<<grid, threads, 0, s>>>(a);
+    } else {
+        if (a.P.flags & kFlagEllipsoid) initial_kernel<true><<<grid, threads, 0, s>>>(a, err);
+        else initial_kernel<false><<<grid, threads, 0, s>>>(a, err);
+    }
     return cudaGetLastError();
 }
 cudaError_t launch_vis_queue(const GeomDev& g, const float4* rays, const uint32_t* counter, uint32_t cap, uint32_t* fetch,
@@ -647,14 +717,18 @@ cudaError_t launch_initial_ell_wave(const InitArgs& a, const EllWaveDev& w, int 
     if (e != cudaSuccess) return e;
     const dim3 grid = tile_grid(a.F.W, a.F.H, a.tile_w, tile_h);
     const int threads = a.tile_w * tile_h;
+    note_launch();
     ell_trees_kernel<<<grid, threads, 0, s>>>(a, w);
+    note_launch();
     ell_place_kernel<<<place_blocks, 128, 0, s>>>(a, w);
     e = launch_vis_queue(a.F.g, w.rays, &w.counters[2], w.ray_cap, &w.counters[3], w.bw, vis_blocks, s);
     if (e != cudaSuccess) return e;
+    note_launch();
     ell_select_kernel<<<grid, threads, 0, s>>>(a, w);
     return cudaGetLastError();
 }
 cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s) {
+    note_launch();
     if (a.P.flags & kFlagTriangleWalk)
         initial_shrink_kernel<true><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a);
     else
@@ -663,14 +737,17 @@ cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s)
 }
 cudaError_t launch_splat(const SplatArgs& a, cudaStream_t s) {
     long long threads = (long long)a.npix * 32;
+    note_launch();
     splat_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_pt(const PtArgs& a, cudaStream_t s) {
+    note_launch();
     pt_kernel<<<pix_grid(a.F.W, a.F.H), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_laser(const GeomDev& g, float3 o, float3 d, float power, LightDev* out, cudaStream_t s) {
+    note_launch();
     laser_kernel<<<1, 32, 0, s>>>(g, o, d, power, out);
     return cudaGetLastError();
 }

@@ -292,13 +292,14 @@ __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant
 // --------------------------------------------------------------------------------------------
 constexpr int kVisSteps = 32;   // 8: 4.63, 16: 4.52, 32: 4.49-4.51, 64 / 128: 4.50 ms per 512 x 512 frame
 
-__global__ void __launch_bounds__(128) vis_kernel(const GeomDev g, const float4* __restrict__ rays, const uint32_t* counter,
+__global__ void __launch_bounds__(128, 8) vis_kernel(const GeomDev g, const float4* __restrict__ rays, const uint32_t* counter,
                                                   uint32_t cap, uint32_t* fetch, float* target, StatsDev* stats, int stat,
                                                   int ray_stat) {
     const uint32_t n = min(*counter, cap);
     if (stats && ray_stat >= 0 && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(&stats->v[ray_stat], (unsigned long long)n);
     const int lane = threadIdx.x & 31;
     unsigned long long lost = 0;
+    unsigned fault = 0u;         // traversal overflows of this lane, published after the loop
     bool has = false, done = false;
     float3 o = f3(0.f, 0.f, 0.f), d = o, id = o, ood = o;
     float tmax = 0.f;
@@ -338,7 +339,11 @@ __global__ void __launch_bounds__(128) vis_kernel(const GeomDev g, const float4*
                 has = false;
                 break;
             }
-            if (--budget < 0) { has = false; break; }
+            if (--budget < 0) {
+                fault |= kErrVisitBudget;
+                has = false;
+                break;
+            }
             const float4* N = g.nodes + 4 * node;
             float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
             float a0 = n0.x * id.x - ood.x, a1 = n0.y * id.x - ood.x;
@@ -366,6 +371,7 @@ __global__ void __launch_bounds__(128) vis_kernel(const GeomDev g, const float4*
             if (h0 && h1) {
                 int nearc = lo0 <= lo1 ? ch0 : ch1, farc = lo0 <= lo1 ? ch1 : ch0;
                 if (sp < kStack) stack[sp++] = farc;
+                else fault |= kErrStackOverflow;   // the far subtree is skipped: reported after the loop
                 node = nearc;
             } else if (h0) {
                 node = ch0;
@@ -381,6 +387,7 @@ __global__ void __launch_bounds__(128) vis_kernel(const GeomDev g, const float4*
             if (old != 0.f) ++lost;
         }
     }
+    if (fault && g.err) atomicOr(g.err, fault);
     if (stats && stat >= 0) {
         unsigned long long x = lost;
         for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o2);
@@ -567,27 +574,33 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
     int np = p1 - p0;
     if (np <= 0) return cudaSuccess;
     if (ev) cudaEventRecord(ev[0], s);
+    note_launch();
     reuse_slots_kernel<<<(np + 127) / 128, 128, 0, s>>>(a, w, p0, p1);
     const long long nw = (long long)np * a.dst.words;
+    note_launch();
     reuse_units_kernel<<<(unsigned)((nw + 127) / 128), 128, 0, s>>>(a, w, p0, p1);
     if (ev) cudaEventRecord(ev[1], s);
     const bool walk = (a.P.flags & kFlagTriangleWalk) != 0u;
-    if (walk) shift_fwd_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w);
-    else shift_fwd_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w);
+    if (walk) { note_launch(); shift_fwd_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w); }
+    else { note_launch(); shift_fwd_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w); }
     if (ev) cudaEventRecord(ev[2], s);
     // forward shifts land in the current frame; counter 4 of the stats counted them as successes
+    note_launch();
     vis_kernel<<<vis_blocks, 128, 0, s>>>(a.cur.g, w.rays, &w.counters[4], w.ray_cap, &w.counters[6], w.py, a.stats, 4,
                                           a.temporal ? -1 : 8);
+    note_launch();
     emit_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
     if (ev) cudaEventRecord(ev[3], s);
-    if (walk) shift_inv_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w);
-    else shift_inv_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w);
+    if (walk) { note_launch(); shift_inv_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w); }
+    else { note_launch(); shift_inv_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w); }
     if (ev) cudaEventRecord(ev[4], s);
     // inverse shifts land in the reused domain: the previous frame for the temporal pass (its one
     // reused slot), the current frame for spatial passes
+    note_launch();
     vis_kernel<<<vis_blocks, 128, 0, s>>>(a.temporal ? a.prev.g : a.cur.g, w.rays, &w.counters[5], w.ray_cap, &w.counters[7],
                                           w.terms, a.stats, -1, a.temporal ? -1 : 9);
     if (ev) cudaEventRecord(ev[5], s);
+    note_launch();
     reuse_merge_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
     if (ev) cudaEventRecord(ev[6], s);
     return cudaGetLastError();
@@ -596,6 +609,7 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
 // visibility segments queued by another stage (the ellipsoidal connection's initial wavefront)
 cudaError_t launch_vis_queue(const GeomDev& g, const float4* rays, const uint32_t* counter, uint32_t cap, uint32_t* fetch,
                              float* target, int blocks, cudaStream_t s) {
+    note_launch();
     vis_kernel<<<blocks, 128, 0, s>>>(g, rays, counter, cap, fetch, target, nullptr, -1, -1);
     return cudaGetLastError();
 }

@@ -67,7 +67,7 @@ EXPORTS = ["tof_create", "tof_destroy", "tof_last_error", "tof_device_bytes", "t
            "tof_render_pt", "tof_reservoirs_reset", "tof_view_stats", "tof_view_profile", "tof_view_stage_ms",
            "tof_render_gated_noalloc", "tof_render_batch", "tof_server_create", "tof_server_destroy",
            "tof_server_open_stream", "tof_server_submit", "tof_server_step", "tof_server_poll", "tof_server_stats",
-           "tof_view_set_tuning", "tof_view_get_tuning", "tof_autotune"]
+           "tof_view_set_tuning", "tof_view_get_tuning", "tof_autotune", "tof_sync", "tof_kernel_launches"]
 
 _vp, _fp, _u32p = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_uint32)
 
@@ -112,8 +112,11 @@ def _declare(L):
     L.tof_view_stats.argtypes = [_vp, C.c_int32, C.POINTER(C.c_double)]
     L.tof_view_profile.argtypes = [_vp, C.c_int32, C.c_int]
     L.tof_view_stage_ms.argtypes = [_vp, C.c_int32, C.POINTER(C.c_float)]
+    L.tof_sync.argtypes = [_vp, _vp]
+    L.tof_kernel_launches.argtypes = []
+    L.tof_kernel_launches.restype = C.c_uint64
     for name in EXPORTS:
-        if name not in ("tof_last_error", "tof_device_bytes"):
+        if name not in ("tof_last_error", "tof_device_bytes", "tof_kernel_launches"):
             getattr(L, name).restype = C.c_int32
 
 
@@ -257,6 +260,15 @@ def tof_render_pt(ctx, scene, sensor_d, emitter_d, gate, bins, params_p, seed, f
     rc = lib().tof_render_pt(ctx, scene, C.byref(s), C.byref(e), C.byref(g) if g else None, C.byref(b) if b else None,
                              C.byref(p), int(seed), int(frame), int(spp), C.c_void_p(out_ptr), C.c_void_p(stream))
     _check(ctx, rc, "tof_render_pt")
+
+
+def tof_sync(ctx, stream: int = 0):
+    """Wait for `stream`; raises TofError if a kernel recorded a device-side error since the last check."""
+    _check(ctx, lib().tof_sync(ctx, C.c_void_p(stream)), "tof_sync")
+
+
+def tof_kernel_launches() -> int:
+    return int(lib().tof_kernel_launches())
 
 
 def tof_reservoirs_reset(ctx, view: int):
