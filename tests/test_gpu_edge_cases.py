@@ -93,3 +93,30 @@ def test_invalid_arguments_are_rejected_and_context_survives():
         assert torch.isfinite(out).all()
     finally:
         tof.tof_destroy(ctx)
+
+
+def test_deep_hierarchy_of_coincident_triangles():
+    """4096 copies of one triangle inside the box: identical Morton codes, so the LBVH splits them by
+    index alone.  The render either matches the oracle or reports the traversal's device error word
+    (stack overflow, visit budget) through tof_sync -- never a silent wrong image."""
+    from paper_2605_11536_gb300 import tof
+    sc = scenes.box_icosphere(W=40, H=32)
+    sc.gates = [(4.5, 1.0)]
+    sc.params.n_spatial, sc.params.radius = 2, 6
+    n = 4096
+    tri = np.array([[-0.6, -0.5, -1.5], [0.6, -0.5, -1.5], [0.0, 0.6, -1.5]])   # faces the camera (+z)
+    nv0, nobj = len(sc.verts), len(sc.object_material)
+    sc.verts = np.concatenate([sc.verts, np.tile(tri, (n, 1))])
+    sc.tris = np.concatenate([sc.tris, (nv0 + np.arange(3 * n)).reshape(n, 3)]).astype(np.uint32)
+    sc.tri_object = np.concatenate([sc.tri_object, np.full(n, nobj)]).astype(np.uint32)
+    sc.object_material = np.concatenate([sc.object_material, [0]]).astype(np.uint32)
+    sc.xforms = np.concatenate([sc.xforms, sc.xforms[:, :1, :]], axis=1)
+    try:
+        g = gpu_render(sc, [0])
+    except tof.TofError as e:
+        assert "device error word" in str(e), str(e)
+        return
+    o, ok, st, _ = oracle_render(sc, [0])
+    frac, relmse, _ = compare(g[0], o[0])
+    assert np.count_nonzero(o[0]) > 50
+    assert frac >= 0.995 and relmse <= 1e-4, (frac, relmse)

@@ -11,11 +11,9 @@ import pytest
 
 from paper_2605_11536_gb300 import scenes
 
-from tests.harness import compare, gpu_pt, gpu_render, oracle_render
+from tests.harness import PARITY_FRAC as FRAC, PARITY_RELMSE as RELMSE, compare, gpu_pt, gpu_render, oracle_render
 
 pytestmark = pytest.mark.gpu
-
-FRAC, RELMSE = 0.995, 1e-4
 
 
 def _check(g, o, mask=None, frac=FRAC, relmse=RELMSE, min_nonzero=20):
