@@ -702,8 +702,10 @@ static void jac_F(int gauge, const double xi[2], const double xp[2], const doubl
 }
 
 /* Newton iteration of Sec. 4.3 with backtracking (step halved up to 4 times when |F|_inf does
- * not decrease).  Stops when |F|_inf <= tol_stop or after max_iter iterations.
- * Success: |F|_inf <= tol_succ.  Returns 1 on success; xp = xi', *jdet = |det(dxi'/dxi)| =
+ * not decrease).  Stops when |F|_inf <= tol_stop -- after one more full step at that point, kept
+ * if |F|_inf does not grow -- or after max_iter iterations, extended by up to max_iter more while
+ * |F|_inf is already within tol_succ (the paper's success band, 1 % of the gate width).
+ * Success: converged, |F|_inf <= tol_stop.  Returns 1 on success; xp = xi', *jdet = |det(dxi'/dxi)| =
  * |det(dF/dxi)| / |det(dF/dxi')| (implicit differentiation), *iters = iterations used. */
 static int newton_solve(const onewton* N, const double xi[2], double delta, int max_iter, double tol_stop,
                         double tol_succ, double xp[2], double* jdet, int* iters) {
@@ -712,10 +714,21 @@ static int newton_solve(const onewton* N, const double xi[2], double delta, int 
     xp[0] = xi[0]; xp[1] = xi[1];
     double F[2], gy[2], hy[3], m[2];
     eval_F(N, xi, delta, xp, gx, hx, Lx, F, gy, hy, m);
-    int it = 0;
-    while (it < max_iter) {
+    int it = 0, polished = 0;
+    /* the paper's budget is max_iter iterations; a solve that spends it inside the success band
+     * (|F| <= tol_succ) short of convergence continues toward the root, at most max_iter more, so
+     * that an accepted shift is the root F = 0 and not a point of the band */
+    while (it < 2 * max_iter) {
         double nF = fmax(fabs(F[0]), fabs(F[1]));
-        if (nF <= tol_stop) break;
+        if (it >= max_iter && !(nF <= tol_succ)) break;
+        int polish = 0;
+        if (nF <= tol_stop) {
+            /* converged: one more full Newton step at the root, kept if |F| does not grow, so that
+             * the result is the root itself and not the first iterate under the tolerance (not
+             * counted as an iteration) */
+            if (polished || !(nF > 0)) break;
+            polish = polished = 1;
+        }
         double A[4], Bm[4];
         jac_F(N->gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
         double det = A[0] * A[3] - A[1] * A[2];
@@ -723,11 +736,11 @@ static int newton_solve(const onewton* N, const double xi[2], double delta, int 
         double step[2] = {-(A[3] * F[0] - A[1] * F[1]) / det, -(-A[2] * F[0] + A[0] * F[1]) / det};
         double lam = 1.0;
         int accepted = 0;
-        for (int ls = 0; ls < 5; ++ls) {
+        for (int ls = 0; ls < (polish ? 1 : 5); ++ls) {
             double cand[2] = {xp[0] + lam * step[0], xp[1] + lam * step[1]};
             double Fc[2], gyc[2], hyc[3], mc[2];
             eval_F(N, xi, delta, cand, gx, hx, Lx, Fc, gyc, hyc, mc);
-            if (fmax(fabs(Fc[0]), fabs(Fc[1])) < nF) {
+            if (polish ? fmax(fabs(Fc[0]), fabs(Fc[1])) <= nF : fmax(fabs(Fc[0]), fabs(Fc[1])) < nF) {
                 xp[0] = cand[0]; xp[1] = cand[1];
                 F[0] = Fc[0]; F[1] = Fc[1];
                 gy[0] = gyc[0]; gy[1] = gyc[1]; hy[0] = hyc[0]; hy[1] = hyc[1]; hy[2] = hyc[2];
@@ -738,10 +751,12 @@ static int newton_solve(const onewton* N, const double xi[2], double delta, int 
             lam *= 0.5;
         }
         if (!accepted) break;
-        ++it;
+        if (!polish) ++it;
     }
     *iters = it;
-    if (!(fmax(fabs(F[0]), fabs(F[1])) <= tol_succ)) return 0;
+    /* success: converged (|F| <= tol_stop), so that the shift satisfies its constraint and stays
+     * invertible; a solve stalled inside the band is rejected */
+    if (!(fmax(fabs(F[0]), fabs(F[1])) <= tol_stop)) return 0;
     double A[4], Bm[4];
     jac_F(N->gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
     double dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
@@ -892,10 +907,18 @@ static int newton_solve_walk(const ogeom* gi, const onewton* N0, owalk* W, const
     int total = 0;
     for (int cross = 0;; ++cross) {
         eval_F(&N, xi, delta, xp, gx, hx, Lx, F, gy, hy, m);
-        int it = 0;
-        while (it < max_iter) {
+        int it = 0, polished = 0;
+        while (it < 2 * max_iter) {   /* budget as in newton_solve */
             double nF = fmax(fabs(F[0]), fabs(F[1]));
-            if (nF <= tol_stop) break;
+            if (it >= max_iter && !(nF <= tol_succ)) break;
+            int polish = 0;
+            if (nF <= tol_stop) {
+                /* converged: one more full Newton step at the root, kept if |F| does not grow, so that
+                 * the result is the root itself and not the first iterate under the tolerance (not
+                 * counted as an iteration) */
+                if (polished || !(nF > 0)) break;
+                polish = polished = 1;
+            }
             double A[4], Bm[4];
             jac_F(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
             double det = A[0] * A[3] - A[1] * A[2];
@@ -903,11 +926,11 @@ static int newton_solve_walk(const ogeom* gi, const onewton* N0, owalk* W, const
             double step[2] = {-(A[3] * F[0] - A[1] * F[1]) / det, -(-A[2] * F[0] + A[0] * F[1]) / det};
             double lam = 1.0;
             int accepted = 0;
-            for (int ls = 0; ls < 5; ++ls) {
+            for (int ls = 0; ls < (polish ? 1 : 5); ++ls) {
                 double cand[2] = {xp[0] + lam * step[0], xp[1] + lam * step[1]};
                 double Fc[2], gyc[2], hyc[3], mc[2];
                 eval_F(&N, xi, delta, cand, gx, hx, Lx, Fc, gyc, hyc, mc);
-                if (fmax(fabs(Fc[0]), fabs(Fc[1])) < nF) {
+                if (polish ? fmax(fabs(Fc[0]), fabs(Fc[1])) <= nF : fmax(fabs(Fc[0]), fabs(Fc[1])) < nF) {
                     xp[0] = cand[0]; xp[1] = cand[1];
                     F[0] = Fc[0]; F[1] = Fc[1];
                     gy[0] = gyc[0]; gy[1] = gyc[1]; hy[0] = hyc[0]; hy[1] = hyc[1]; hy[2] = hyc[2];
@@ -918,10 +941,10 @@ static int newton_solve_walk(const ogeom* gi, const onewton* N0, owalk* W, const
                 lam *= 0.5;
             }
             if (!accepted) break;
-            ++it;
+            if (!polish) ++it;
         }
         total += it;
-        if (!(fmax(fabs(F[0]), fabs(F[1])) <= tol_succ)) break;
+        if (!(fmax(fabs(F[0]), fabs(F[1])) <= tol_stop)) break;   /* converged, as in newton_solve */
         double lm[3];
         walk_bary(W, xp, lm);
         if (lm[0] >= -BARY_EPS && lm[1] >= -BARY_EPS && lm[2] >= -BARY_EPS) {

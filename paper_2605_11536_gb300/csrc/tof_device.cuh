@@ -751,7 +751,9 @@ static __device__ __forceinline__ void newton_J(int gauge, const float xi[2], co
 }
 
 // Newton iteration with backtracking (Sec. 4.3); returns success, xi', |det(dxi'/dxi)| and the
-// iteration count.  Stops at |F|_inf <= tol_stop or after max_iter; success if |F|_inf <= tol_succ.
+// iteration count.  Stops at |F|_inf <= tol_stop (after one polishing step there) or after
+// max_iter (up to 2 max_iter while |F|_inf <= tol_succ, the paper's 1 %-of-the-gate band);
+// success if converged, |F|_inf <= tol_stop.
 static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float delta, int max_iter, float tol_stop,
                              float tol_succ, float xp[2], float& jdet, int& iters) {
     float Lx, gx[2], hx[3];
@@ -760,12 +762,24 @@ static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float
     float F[2], gy[2], hy[3], m[2];
     newton_F(N, xi, Lx, gx, delta, xp, F, gy, hy, m);
     int it = 0;
+    bool polished = false;
     // loops kept rolled: the unrolled copies of the line search cost more in instruction-cache misses
     // than they save (4.9 against 5.1 ms per 512 x 512 frame)
+    // the paper's budget is max_iter iterations; a solve that spends it inside the success band
+    // (|F| <= tol_succ) short of convergence continues toward the root, at most max_iter more, so
+    // that an accepted shift is the root F = 0 and not a point of the band that depends on rounding
 #pragma unroll 1
-    while (it < max_iter) {
+    while (it < 2 * max_iter) {
         float nF = fmaxf(fabsf(F[0]), fabsf(F[1]));
-        if (nF <= tol_stop) break;
+        if (it >= max_iter && !(nF <= tol_succ)) break;
+        bool polish = false;
+        if (nF <= tol_stop) {
+            // converged: one more full Newton step at the root, kept if |F| does not grow, so that the
+            // result is the root itself (to FP32 rounding) and not the first iterate under the
+            // tolerance, which FP32 and FP64 reach at different distances from it (not counted)
+            if (polished || !(nF > 0.f)) break;
+            polish = polished = true;
+        }
         float A[4], Bm[4];
         newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
         float det = A[0] * A[3] - A[1] * A[2];
@@ -774,11 +788,11 @@ static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float
         float lam = 1.0f;
         bool accepted = false;
 #pragma unroll 1
-        for (int ls = 0; ls < 5; ++ls) {
+        for (int ls = 0; ls < (polish ? 1 : 5); ++ls) {
             float c[2] = {xp[0] + lam * s0, xp[1] + lam * s1};
             float Fc[2], gyc[2], hyc[3], mc[2];
             newton_F(N, xi, Lx, gx, delta, c, Fc, gyc, hyc, mc);
-            if (fmaxf(fabsf(Fc[0]), fabsf(Fc[1])) < nF) {
+            if (polish ? fmaxf(fabsf(Fc[0]), fabsf(Fc[1])) <= nF : fmaxf(fabsf(Fc[0]), fabsf(Fc[1])) < nF) {
                 xp[0] = c[0]; xp[1] = c[1];
                 F[0] = Fc[0]; F[1] = Fc[1];
                 gy[0] = gyc[0]; gy[1] = gyc[1]; hy[0] = hyc[0]; hy[1] = hyc[1]; hy[2] = hyc[2];
@@ -789,10 +803,13 @@ static __device__ bool newton_solve(const NewtonGeo& N, const float xi[2], float
             lam *= 0.5f;
         }
         if (!accepted) break;
-        ++it;
+        if (!polish) ++it;
     }
     iters = it;
-    if (!(fmaxf(fabsf(F[0]), fabsf(F[1])) <= tol_succ)) return false;
+    // success: converged (|F| <= tol_stop), so that the shift satisfies its constraint and stays
+    // invertible; a solve stalled inside the band (ill-conditioned: L nearly stationary at the
+    // vertex) is rejected, in FP32 as in FP64, instead of ending at a rounding-dependent point
+    if (!(fmaxf(fabsf(F[0]), fabsf(F[1])) <= tol_stop)) return false;
     float A[4], Bm[4];
     newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
     float dA = A[0] * A[3] - A[1] * A[2], dB = Bm[0] * Bm[3] - Bm[1] * Bm[2];
@@ -909,10 +926,16 @@ static __device__ bool newton_solve_walk(const GeomDev& gi, const NewtonGeo& N, 
     for (int cross = 0;; ++cross) {
         newton_F_f(N, W.f, xi, Lx, gx, delta, xp, F, gy, hy, m);
         int it = 0;
+        bool polished = false;
 #pragma unroll 1
-        while (it < max_iter) {
+        while (it < 2 * max_iter) {   // budget as in newton_solve
             float nF = fmaxf(fabsf(F[0]), fabsf(F[1]));
-            if (nF <= tol_stop) break;
+            if (it >= max_iter && !(nF <= tol_succ)) break;
+            bool polish = false;
+            if (nF <= tol_stop) {   // converged: one polishing step, as in newton_solve
+                if (polished || !(nF > 0.f)) break;
+                polish = polished = true;
+            }
             float A[4], Bm[4];
             newton_J(N.gauge, xi, xp, gx, hx, gy, hy, m, A, Bm);
             float det = A[0] * A[3] - A[1] * A[2];
@@ -921,11 +944,11 @@ static __device__ bool newton_solve_walk(const GeomDev& gi, const NewtonGeo& N, 
             float lam = 1.0f;
             bool accepted = false;
 #pragma unroll 1
-            for (int ls = 0; ls < 5; ++ls) {
+            for (int ls = 0; ls < (polish ? 1 : 5); ++ls) {
                 float c[2] = {xp[0] + lam * s0, xp[1] + lam * s1};
                 float Fc[2], gyc[2], hyc[3], mc[2];
                 newton_F_f(N, W.f, xi, Lx, gx, delta, c, Fc, gyc, hyc, mc);
-                if (fmaxf(fabsf(Fc[0]), fabsf(Fc[1])) < nF) {
+                if (polish ? fmaxf(fabsf(Fc[0]), fabsf(Fc[1])) <= nF : fmaxf(fabsf(Fc[0]), fabsf(Fc[1])) < nF) {
                     xp[0] = c[0]; xp[1] = c[1];
                     F[0] = Fc[0]; F[1] = Fc[1];
                     gy[0] = gyc[0]; gy[1] = gyc[1]; hy[0] = hyc[0]; hy[1] = hyc[1]; hy[2] = hyc[2];
@@ -936,10 +959,10 @@ static __device__ bool newton_solve_walk(const GeomDev& gi, const NewtonGeo& N, 
                 lam *= 0.5f;
             }
             if (!accepted) break;
-            ++it;
+            if (!polish) ++it;
         }
         total += it;
-        if (!(fmaxf(fabsf(F[0]), fabsf(F[1])) <= tol_succ)) break;
+        if (!(fmaxf(fabsf(F[0]), fabsf(F[1])) <= tol_stop)) break;   // converged, as in newton_solve
         float lm[3];
         walk_bary(gi, W, xp[0], xp[1], lm);
         if (lm[0] >= -kBaryEps && lm[1] >= -kBaryEps && lm[2] >= -kBaryEps) {
