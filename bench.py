@@ -930,22 +930,29 @@ def run_transient(args, frames=None):
                 stages.append(tof.tof_view_stage_ms(ctx, vid))
         nnz = int(torch.count_nonzero(out).item())
         st = tof.tof_view_stats(ctx, vid)
-        # the same sequence with bin reuse (Sec. 4.5): frame times only
-        p_bin = type(sc.params)(**vars(sc.params))
-        p_bin.flags |= scenes.FLAG_BIN_REUSE
-        vid2 = tof.tof_view_create(ctx, sid, W, H, B)
-        ms_bin = []
-        with torch.cuda.stream(stream):
-            for f in range(frames):
-                tof.tof_bvh_build(ctx, sid, sc.xforms[f].reshape(-1), refit_only=0, stream=sptr)
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                tof.tof_render_transient(ctx, sid, vid2, sc.sensors[f], sc.emitters[f], sc.bins, p_bin, sc.seed, f,
-                                         out.data_ptr(), sptr)
-                e1.record(stream)
-                stream.synchronize()
-                ms_bin.append(e0.elapsed_time(e1))
+        # the same sequence with bin reuse (Sec. 4.5), with pairwise MIS (2k instead of k + k^2
+        # shifts per merged bin) and with temporal reuse only: frame times only
+        def variant(mut):
+            pv = type(sc.params)(**vars(sc.params))
+            mut(pv)
+            v = tof.tof_view_create(ctx, sid, W, H, B)
+            tms = []
+            with torch.cuda.stream(stream):
+                for f in range(frames):
+                    tof.tof_bvh_build(ctx, sid, sc.xforms[f].reshape(-1), refit_only=0, stream=sptr)
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    tof.tof_render_transient(ctx, sid, v, sc.sensors[f], sc.emitters[f], sc.bins, pv, sc.seed, f,
+                                             out.data_ptr(), sptr)
+                    e1.record(stream)
+                    stream.synchronize()
+                    tms.append(e0.elapsed_time(e1))
+            tof.tof_view_destroy(ctx, v)
+            return tms
+        ms_bin = variant(lambda q: setattr(q, "flags", q.flags | scenes.FLAG_BIN_REUSE))
+        ms_pw = variant(lambda q: setattr(q, "flags", q.flags | scenes.FLAG_PAIRWISE_MIS))
+        ms_tonly = variant(lambda q: setattr(q, "n_spatial", 0))
     finally:
         tof.tof_destroy(ctx)
     hbm, hbm_kind = _peaks()
@@ -958,6 +965,8 @@ def run_transient(args, frames=None):
                         "spatial within 10 px, %d frames" % (W, H, frames),
             "value": frames / (sum(ms) / 1e3), "unit": "frames/s", "ms_per_frame": ms,
             "bin_reuse": {"value": frames / (sum(ms_bin) / 1e3), "unit": "frames/s", "ms_per_frame": ms_bin},
+            "pairwise_mis": {"value": frames / (sum(ms_pw) / 1e3), "unit": "frames/s", "ms_per_frame": ms_pw},
+            "temporal_only": {"value": frames / (sum(ms_tonly) / 1e3), "unit": "frames/s", "ms_per_frame": ms_tonly},
             "stage_ms_mean": {k: float(np.mean([x[k] for x in stages])) for k in stages[0]},
             "nonzero_bins_last_frame_per_px": nnz / npix,
             "shifts_per_frame": {"forward": st["shift_calls"] / frames, "inverse": st["inv_calls"] / frames},

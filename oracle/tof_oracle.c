@@ -2023,9 +2023,12 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
 #pragma omp parallel for schedule(dynamic, 4)
 #endif
     for (int pix = 0; pix < W * H; ++pix) {
+        /* pixels outside the region of interest are never touched: their reservoirs stay zero
+         * (empty), and every result that depends on them is marked not-ok */
+        if (!F->ok[pix]) continue;
         orec* rr = &R0[(size_t)pix * Bn];
         for (int b = 0; b < Bn; ++b) { rr[b] = EMPTY_REC; rr[b].M = P->n_cand; }
-        if (!F->ok[pix] || !F->gb[pix].valid) continue;
+        if (!F->gb[pix].valid) continue;
         odomain D = make_domain(F, pix, P, L0, dL);
         if (shrink) {
             initial_shrink(g, &D, P, seed, (uint32_t)pix, frame, L0, dL, rr);
@@ -2065,10 +2068,11 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
 #pragma omp parallel for schedule(dynamic, 4)
 #endif
         for (int pix = 0; pix < W * H; ++pix) {
+            Mt[pix] = Mc[pix];
+            if (!F->ok[pix]) continue;
             orec* dst = &R1[(size_t)pix * Bn];
             memcpy(dst, &R0[(size_t)pix * Bn], sizeof(orec) * Bn);
-            Mt[pix] = Mc[pix];
-            if (!F->ok[pix] || !F->gb[pix].valid) continue;
+            if (!F->gb[pix].valid) continue;
             int q = -1;
             if (s->mode == 1) q = pix;
             else {
@@ -2109,11 +2113,12 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
 #pragma omp parallel for schedule(dynamic, 4)
 #endif
         for (int pix = 0; pix < W * H; ++pix) {
-            orec* dst = &Rb[(size_t)pix * Bn];
-            memcpy(dst, &R1[(size_t)pix * Bn], sizeof(orec) * Bn);
             const double Mn = fmin(Mc[pix], P->m_cap);
             Mb[pix] = Mc[pix] + 2.0 * Mn;
-            if (!ok1[pix] || !F->gb[pix].valid) continue;
+            if (!ok1[pix]) continue;
+            orec* dst = &Rb[(size_t)pix * Bn];
+            memcpy(dst, &R1[(size_t)pix * Bn], sizeof(orec) * Bn);
+            if (!F->gb[pix].valid) continue;
             for (int b = 0; b < Bn; ++b) {
                 const orec* xc = &R1[(size_t)pix * Bn + b];
                 int any = xc->valid;
@@ -2155,11 +2160,12 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
 #pragma omp parallel for schedule(dynamic, 4)
 #endif
         for (int pix = 0; pix < W * H; ++pix) {
-            orec* dst = &Rn[(size_t)pix * Bn];
-            memcpy(dst, &Rcur[(size_t)pix * Bn], sizeof(orec) * Bn);
             okn[pix] = okc[pix];
             Mn[pix] = Mc[pix];
-            if (!okc[pix] || !F->gb[pix].valid) continue;
+            if (!okc[pix]) continue;
+            orec* dst = &Rn[(size_t)pix * Bn];
+            memcpy(dst, &Rcur[(size_t)pix * Bn], sizeof(orec) * Bn);
+            if (!F->gb[pix].valid) continue;
             int nb[16], nn = 0;
             for (int sI = 1; sI <= P->n_spatial; ++sI) {
                 int q = pick_neighbor(seed, (uint32_t)pix, frame, 1 + it, sI, W, H, P->radius);
@@ -2202,11 +2208,12 @@ int or_render_frame(oview* v, const ogeom* g, const osensor* s, const oemitter* 
     for (int pix = 0; pix < W * H; ++pix) {
         for (int b = 0; b < Bn; ++b) {
             const orec* rr = &Rcur[(size_t)pix * Bn + b];
-            out[(size_t)pix * Bn + b] = (rr->valid && okc[pix]) ? rr->phat * rr->W : 0.0;
+            out[(size_t)pix * Bn + b] = (okc[pix] && rr->valid) ? rr->phat * rr->W : 0.0;
         }
         ok_out[pix] = okc[pix];
+        /* the frame's reservoirs (read by the next frame only where this frame is ok) */
+        if (okc[pix]) memcpy(&F->res[(size_t)pix * Bn], &Rcur[(size_t)pix * Bn], sizeof(orec) * Bn);
     }
-    memcpy(F->res, Rcur, sizeof(orec) * (size_t)W * H * Bn);
     memcpy(F->ok, okc, (size_t)W * H);
     memcpy(F->M, Mc, sizeof(double) * (size_t)W * H);
     free(Mc);

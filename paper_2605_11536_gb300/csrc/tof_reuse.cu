@@ -471,97 +471,166 @@ __global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant
 }
 
 // --------------------------------------------------------------------------------------------
-// merge: MIS weights, streaming selection, output record
+// merge: MIS weights, streaming selection, output record.  One group of G lanes per unit (G the
+// power of two >= slots, so 2, 4, 8 or 16 units per warp): lane s reads slot s's slot-table
+// entries, source P0 word, shifted target and Jacobian and its row of MIS terms (each unit's
+// arrays are contiguous, so a group's loads coalesce and are all in flight at once), computes its
+// candidate's weight, and the group forms the streaming selection by shuffles in slot order (the
+// same running sum and comparisons as one thread would make); the group then copies the selected
+// record plane by plane.
 // --------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
     const uint32_t nunits = min(w.counters[0], (uint32_t)w.cap_units);
     const int S = w.slots;
     const FrameDev& C = a.cur;
     const int Bn = C.B > 0 ? C.B : 1;
-    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < nunits; u += gridDim.x * blockDim.x) {
-        int2 ub = w.units[u];
-        int pix = ub.x, b = ub.y;
-        int n = w.nslot[pix];
-        float py[kMaxSlots], J[kMaxSlots], ph[kMaxSlots], Wx[kMaxSlots], M[kMaxSlots], wv[kMaxSlots];
-        bool ok[kMaxSlots];
-        for (int s = 0; s < n; ++s) {
-            // an absent domain (a bin outside the histogram) takes no part in the MIS
-            M[s] = slot_present(a, s, b) ? w.slot_M[(size_t)pix * S + s] : 0.f;
-            ok[s] = false;
-            wv[s] = 0.f;
-            const ResDev* R = slot_res(a, s);
-            int q = w.slot_pix[(size_t)pix * S + s];
-            if (!slot_occ(a, s, q, b)) continue;
-            const FrameDev* Fs = slot_frame(a, s);
-            int Bs = Fs->B > 0 ? Fs->B : 1;
-            float4 p0 = *res_at(*R, 0, (size_t)q * Bs + slot_bin(a, s, b));
-            ph[s] = p0.y; Wx[s] = p0.x;
-            if (s == 0) { py[0] = p0.y; J[0] = 1.f; ok[0] = py[0] > 0.f; }
-            else { py[s] = w.py[(size_t)u * S + s]; J[s] = w.jac[(size_t)u * S + s]; ok[s] = py[s] > 0.f; }
+    const bool pairwise = (a.P.flags & kFlagPairwiseMis) != 0u;
+    const int G = S <= 2 ? 2 : S <= 4 ? 4 : S <= 8 ? 8 : 16;
+    const int lane = threadIdx.x & 31;
+    const int s = lane & (G - 1);                 // this lane's slot
+    const int g0 = lane & ~(G - 1);               // first lane of the group
+    const unsigned gmask = (G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u)) << g0;
+    const uint32_t groups = gridDim.x * (blockDim.x / G);
+    const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    // every lane of a warp runs the same number of iterations (the group index advances by the same
+    // stride for all groups of the warp), so the warp-synchronous shuffles below see full groups
+    const uint32_t warp_first = (blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) / G;
+    for (uint32_t base = warp_first; base < nunits; base += groups) {
+        const uint32_t u = first + (base - warp_first);
+        const bool unit_ok = u < nunits;
+        // loads in three dependent rounds instead of five: everything indexed by the unit first
+        // (its pixel and bin, this slot's shifted target and Jacobian, this candidate's row of MIS
+        // terms), then the pixel's slot count with this slot's table entries, then the slot
+        // pixel's occupancy word with its P0 word
+        int2 ub = make_int2(0, 0);
+        float pyu = 0.f, ju = 0.f;
+        float Trow[kMaxSlots];
+#pragma unroll
+        for (int j = 0; j < kMaxSlots; ++j) Trow[j] = 0.f;
+        if (unit_ok) {
+            ub = w.units[u];
+            if (s < S) {
+                if (s > 0) { pyu = w.py[(size_t)u * S + s]; ju = w.jac[(size_t)u * S + s]; }
+                const float* T = w.terms + ((size_t)u * S + s) * S;
+#pragma unroll
+                for (int j = 0; j < kMaxSlots; ++j)
+                    if (j < S) Trow[j] = T[j];
+            }
         }
-        // MIS weights with explicitly rounded operations (no contraction into FMAs), so that
-        // pairwise MIS with one reused domain reproduces the balance heuristic bit for bit
-        if ((a.P.flags & kFlagPairwiseMis) && n > 1) {
-            // pairwise MIS: pair i = {canonical with confidence M_0/k, domain i with M_i}, a
-            // two-technique balance heuristic at the same y weighted by (M_i + M_0/k) / sum M
-            const int k = n - 1;
-            float Msum = 0.f;
-            for (int s = 0; s < n; ++s) Msum = __fadd_rn(Msum, M[s]);
-            const float Mck = __fdiv_rn(M[0], (float)k);
-            for (int s = 0; s < n; ++s) {
-                if (!ok[s]) continue;
-                float m = 0.f;
+        const int pix = ub.x, b = ub.y;
+        int n = 0, q = 0;
+        float Mraw = 0.f;
+        if (unit_ok) {
+            n = (int)w.nslot[pix];
+            if (s < S) { q = w.slot_pix[(size_t)pix * S + s]; Mraw = w.slot_M[(size_t)pix * S + s]; }
+        }
+        const bool mine = s < n;
+        // this lane's slot: confidence, source P0 word, shifted target and Jacobian
+        float M = 0.f, py = 0.f, J = 0.f, ph = 0.f, Wx = 0.f;
+        bool ok = false;
+        if (mine) {
+            // an absent domain (a bin outside the histogram) takes no part in the MIS
+            const bool present = slot_present(a, s, b);
+            M = present ? Mraw : 0.f;
+            const ResDev* R = slot_res(a, s);
+            const FrameDev* Fs = slot_frame(a, s);
+            const int Bs = Fs->B > 0 ? Fs->B : 1;
+            const int sb = slot_bin(a, s, b);
+            uint32_t word = 0u;
+            float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (present) {
+                word = R->occ[(size_t)q * R->words + (sb >> 5)];
+                p0 = *res_at(*R, 0, (size_t)q * Bs + sb);
+            }
+            if ((word >> (sb & 31)) & 1u) {
+                ph = p0.y; Wx = p0.x;
+                if (s == 0) { py = p0.y; J = 1.f; }
+                else { py = pyu; J = ju; }
+                ok = py > 0.f;
+            }
+        }
+        // every shuffle below runs on the whole warp in loops bounded by S (uniform per launch):
+        // the groups of a warp hold units with different slot counts n <= S
+        const float M0 = __shfl_sync(0xFFFFFFFFu, M, g0);
+        const float py0 = __shfl_sync(0xFFFFFFFFu, py, g0);
+        const bool pw = pairwise && n > 1;
+        // pairwise MIS: pair i = {canonical with confidence M_0/k, domain i with M_i}, a two-technique
+        // balance heuristic at the same y weighted by (M_i + M_0/k) / sum M.  Explicitly rounded
+        // operations (no contraction into FMAs), so that pairwise MIS with one reused domain
+        // reproduces the balance heuristic.
+        float Msum = 0.f;
+        for (int i = 0; i < S; ++i) {
+            const float Mi = __shfl_sync(0xFFFFFFFFu, M, g0 + i);
+            if (i < n) Msum = __fadd_rn(Msum, Mi);
+        }
+        const float Mck = pw ? __fdiv_rn(M0, (float)(n - 1)) : 0.f;
+        float mpw0 = 0.f;   // the canonical candidate's pairwise weight (lane 0 of the group)
+        for (int i = 1; i < S; ++i) {
+            const float Mi = __shfl_sync(0xFFFFFFFFu, M, g0 + i);
+            if (pw && s == 0 && ok && i < n) {
+                const float pc = __fmul_rn(Mck, py0);
+                float alpha = __fdiv_rn(__fadd_rn(Mi, Mck), Msum);
+                float ti = 0.f;
+#pragma unroll
+                for (int j = 1; j < kMaxSlots; ++j)
+                    if (j == i) ti = slot_present(a, i, b) ? Trow[j] : 0.f;
+                mpw0 = __fadd_rn(mpw0, __fmul_rn(alpha, __fdiv_rn(pc, __fadd_rn(pc, ti))));
+            }
+        }
+        float wv = 0.f;
+        if (ok) {
+            float m;
+            if (pw) {
                 if (s == 0) {
-                    const float pc = __fmul_rn(Mck, py[0]);
-                    for (int i = 1; i < n; ++i) {
-                        float alpha = __fdiv_rn(__fadd_rn(M[i], Mck), Msum);
-                        float ti = slot_present(a, i, b) ? w.terms[((size_t)u * S + 0) * S + i] : 0.f;
-                        m = __fadd_rn(m, __fmul_rn(alpha, __fdiv_rn(pc, __fadd_rn(pc, ti))));
-                    }
+                    m = mpw0;
                 } else {
-                    float alpha = __fdiv_rn(__fadd_rn(M[s], Mck), Msum);
-                    float pi = __fdiv_rn(__fmul_rn(M[s], ph[s]), J[s]);
-                    float pc = __fmul_rn(Mck, py[s]);
+                    float alpha = __fdiv_rn(__fadd_rn(M, Mck), Msum);
+                    float pi = __fdiv_rn(__fmul_rn(M, ph), J);
+                    float pc = __fmul_rn(Mck, py);
                     m = __fmul_rn(alpha, __fdiv_rn(pi, __fadd_rn(pc, pi)));
                 }
-                wv[s] = m * py[s] * Wx[s] * J[s];
-                if (!(wv[s] > 0.f) || !isfinite(wv[s])) wv[s] = 0.f;
+            } else {
+                // generalized balance heuristic: this candidate's row of inverse-shift terms
+                float num = s == 0 ? __fmul_rn(M0, py0) : __fdiv_rn(__fmul_rn(M, ph), J);
+                float den = __fmul_rn(M0, py);
+#pragma unroll
+                for (int j = 1; j < kMaxSlots; ++j)
+                    if (j < n)
+                        den = __fadd_rn(den, (j == s) ? __fdiv_rn(__fmul_rn(M, ph), J) : slot_present(a, j, b) ? Trow[j] : 0.f);
+                m = den > 0.f ? __fdiv_rn(num, den) : 0.f;
             }
-        } else for (int s = 0; s < n; ++s) {
-            if (!ok[s]) continue;
-            float num = s == 0 ? __fmul_rn(M[0], py[0]) : __fdiv_rn(__fmul_rn(M[s], ph[s]), J[s]);
-            float den = __fmul_rn(M[0], py[s]);
-            for (int j = 1; j < n; ++j)
-                den = __fadd_rn(den, (j == s) ? __fdiv_rn(__fmul_rn(M[s], ph[s]), J[s])
-                                              : slot_present(a, j, b) ? w.terms[((size_t)u * S + s) * S + j] : 0.f);
-            float m = den > 0.f ? __fdiv_rn(num, den) : 0.f;
-            wv[s] = m * py[s] * Wx[s] * J[s];
-            if (!(wv[s] > 0.f) || !isfinite(wv[s])) wv[s] = 0.f;
+            wv = m * py * Wx * J;
+            if (!(wv > 0.f) || !isfinite(wv)) wv = 0.f;
         }
-        float Ssum = 0.f;
-        int sel = -1;
-        for (int s = 0; s < n; ++s) {
-            if (!(wv[s] > 0.f)) continue;
-            uint4 r = philox((uint32_t)pix, C.frame, ((uint32_t)a.pass << 8) | (uint32_t)s, P_MERGE | ((uint32_t)b << 8), a.P.seed);
-            Ssum += wv[s];
-            if (u01(r.x) * Ssum < wv[s]) sel = s;
+        // streaming selection in slot order: every lane forms the running sum up to its own slot
+        float Ssum = 0.f, Sat = 0.f;
+        for (int i = 0; i < S; ++i) {
+            const float wi = __shfl_sync(0xFFFFFFFFu, wv, g0 + i);
+            if (i < n && wi > 0.f) Ssum += wi;
+            if (i == s) Sat = Ssum;
         }
-        float outv = 0.f;
-        if (sel >= 0) {
-            Rec y;
-            if (sel == 0) rec_load(a.src, (size_t)pix * Bn + b, y);
-            else {
-                ResDev R;
-                R.planes = w.yrec; R.stride = (size_t)w.cap_units * (S - 1); R.estride = 1;
-                rec_load(R, (size_t)u * (S - 1) + (sel - 1), y);
+        bool acc = false;
+        if (mine && wv > 0.f) {
+            const uint4 r = philox((uint32_t)pix, C.frame, ((uint32_t)a.pass << 8) | (uint32_t)s, P_MERGE | ((uint32_t)b << 8),
+                                   a.P.seed);
+            acc = u01(r.x) * Sat < wv;
+        }
+        const unsigned accm = __ballot_sync(0xFFFFFFFFu, acc) & gmask;
+        const int sel = accm ? 31 - __clz(accm) - g0 : -1;
+        const float pysel = __shfl_sync(0xFFFFFFFFu, py, g0 + (sel >= 0 ? sel : 0));
+        if (unit_ok && sel >= 0) {
+            // the selected record, planes s, s + G, ... copied by lane s (P0 takes the new W and target)
+            const size_t dst = (size_t)pix * Bn + b;
+            for (int k = s; k < 6; k += G) {
+                float4 v;
+                if (sel == 0) v = *res_at(a.src, k, dst);
+                else v = w.yrec[(size_t)k * ((size_t)w.cap_units * (S - 1)) + (size_t)u * (S - 1) + (sel - 1)];
+                if (k == 0) { v.x = Ssum / pysel; v.y = pysel; }
+                *res_at(a.dst, k, dst) = v;
             }
-            y.W = Ssum / py[sel];
-            y.phat = py[sel];
-            rec_store(a.dst, (size_t)pix * Bn + b, y);
-            atomicOr(&a.dst.occ[(size_t)pix * a.dst.words + (b >> 5)], 1u << (b & 31));
-            outv = y.phat * y.W;
+            if (s == 0) atomicOr(&a.dst.occ[(size_t)pix * a.dst.words + (b >> 5)], 1u << (b & 31));
         }
-        if (a.out) a.out[pix] = outv;
+        if (unit_ok && s == 0 && a.out) a.out[pix] = sel >= 0 ? pysel * (Ssum / pysel) : 0.f;
     }
 }
 

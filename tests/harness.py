@@ -101,3 +101,29 @@ def compare(gpu, ref, mask=None, tol=1e-3):
     s = float(np.sum(o * o))
     relmse = float(np.sum((g - o) ** 2) / s) if s > 0 else float(np.sum((g - o) ** 2))
     return frac_ok, relmse, rel
+
+
+def bin_moves(gpu, ref, mask=None, tol=1e-3):
+    """Transient histograms [H, W, B]: the (pixel, bin) values whose sample sits one bin apart on
+    the two sides -- g[b] nonzero where o[b] is zero and o[b -/+ 1] equals g[b] (within tol) while
+    g[b -/+ 1] is zero, and the mirror pair.  A path length within rounding of a bin boundary is
+    binned by floor((tau - t0) / w) in each side's own precision, so both answers are correct.
+    Returns a boolean array [H, W, B] marking both values of every such pair."""
+    g = np.asarray(gpu, dtype=np.float64)
+    o = np.asarray(ref, dtype=np.float64)
+    moved = np.zeros(g.shape, dtype=bool)
+    for d in (-1, 1):
+        gs = np.roll(g, d, axis=2)   # gs[..., b] = g[..., b - d]
+        os_ = np.roll(o, d, axis=2)
+        # the GPU's value at b - d is the oracle's at b: a move by +d
+        hit = (g == 0) & (os_ == 0) & (gs != 0) & (o != 0) & (np.abs(gs - o) <= tol * np.maximum(np.abs(gs), np.abs(o)))
+        if d == 1:
+            hit[..., 0] = False
+        else:
+            hit[..., -1] = False
+        moved |= hit
+        moved |= np.roll(hit, -d, axis=2)
+    if mask is not None:
+        moved &= np.asarray(mask, dtype=bool)[..., None]
+    return moved
+

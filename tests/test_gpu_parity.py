@@ -11,7 +11,7 @@ import pytest
 
 from paper_2605_11536_gb300 import scenes
 
-from tests.harness import PARITY_FRAC as FRAC, PARITY_RELMSE as RELMSE, compare, gpu_pt, gpu_render, oracle_render
+from tests.harness import PARITY_FRAC as FRAC, PARITY_RELMSE as RELMSE, bin_moves, compare, gpu_pt, gpu_render, oracle_render
 
 pytestmark = pytest.mark.gpu
 
@@ -125,6 +125,30 @@ def test_confocal_transient_moving_device():
     g = gpu_render(sc, [0, 1, 2], B=160)
     for f in range(3):
         _check(g[f], o[f], min_nonzero=100)
+
+
+def test_confocal_transient_full_size_center_region():
+    """The transient workload at full size: 256x256 confocal scan, 1024 bins of 1 mm, ~100k-triangle
+    hidden object, 8 trees, temporal + 3 spatial neighbours within 10 px, the device moving over 3
+    frames -- rendered on the GPU in the bench's launch configuration; the oracle computes a central
+    96x96 region, and every (pixel, bin) of the pixels whose dependency cone lies inside it is
+    compared."""
+    sc = scenes.confocal_nlos(W=256, H=256, frames=3, B=1024)
+    frames = [0, 1, 2]
+    half = 48
+    roi = (128 - half, 128 - half, 128 + half, 128 + half)
+    o, oks, st, _ = oracle_render(sc, frames, B=1024, roi=roi)
+    g = gpu_render(sc, frames, B=1024)
+    for f in frames:
+        assert oks[f].sum() >= 30 * 30
+        # with 1 mm bins a few samples lie within FP32 rounding of a bin boundary: the same value one
+        # bin apart on the two sides (both correct); they are counted, bounded and left out of the
+        # comparison of the rest
+        moved = bin_moves(g[f], o[f], oks[f])
+        nz = int(np.count_nonzero(o[f][oks[f]]))
+        assert moved.sum() <= max(8, 2e-3 * nz), (int(moved.sum()), nz)
+        keep = np.repeat(oks[f][..., None], o[f].shape[2], axis=2) & ~moved
+        _check(np.where(keep, g[f], 0.0), np.where(keep, o[f], 0.0), mask=oks[f], min_nonzero=1000)
 
 
 def test_laser_emitter_spatial_reuse():
