@@ -71,8 +71,10 @@ BYTES = {
 # from frame to frame for one capture to stand for the mean launch (task counts grow over the
 # first frames).  Must be retaken whenever the kernel changes.
 ELL_WAVE = "ell_trees_kernel + ell_place_kernel + ell_select_kernel"
-NCU_TRAFFIC_SRC = None   # _src_hash() of the sources the figures below were captured on
-NCU_TRAFFIC = {}
+NCU_TRAFFIC_SRC = "6131501fa04a"   # _src_hash() of the sources the figures below were captured on
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch (profiles/*_dynamic_gated_512.md)
+NCU_TRAFFIC = {"initial_gated_kernel<0>": 32.488960e6 + 31.040256e6, "reuse_merge_kernel": 109.030912e6 + 7.375872e6,
+               "shift_inv_kernel<0>": 167.921408e6 + 331.290880e6}
 
 
 def _peaks():
@@ -508,7 +510,7 @@ def run_quality_variant(args, mutate, frames=24):
     after 8 with CUDA events, L2 flushed), the last frames scored like the headline's quality."""
     import torch
     from paper_2605_11536_gb300 import tof
-    sc = workload(seed=1)
+    sc = workload(seed=1, flags=args.flags)
     note = mutate(sc)
     p = sc.params
     W, H = sc.sensors[0]["W"], sc.sensors[0]["H"]
@@ -1071,6 +1073,7 @@ def main():
     ap.add_argument("--converge-budget", type=float, default=5.0, help="device seconds per convergence run")
     ap.add_argument("--variants", action="store_true", help="also score the quality variants at equal time")
     ap.add_argument("--no-converge", action="store_true")
+    ap.add_argument("--no-quality", action="store_true", help="skip the per-frame equal-time quality section")
     ap.add_argument("--no-pairwise", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -1111,7 +1114,7 @@ def main():
             "spatial_inv_vis": BYTES["spatial_inv_vis"] * pf["spatial_inv_rays"],
             "spatial_merge": BYTES["spatial_merge"] * r["npix"]}
     ell, walk = int(bool(args.flags & 256)), int(bool(args.flags & 64))
-    kernels = {"gbuffer": "gbuffer_kernel", "initial": ELL_WAVE if ell else "initial_kernel<0>", "temporal": "temporal pass (8 kernels)",
+    kernels = {"gbuffer": "gbuffer_kernel", "initial": ELL_WAVE if ell else "initial_gated_kernel<0>", "temporal": "temporal pass (8 kernels)",
                "spatial_setup": "reuse_slots_kernel + reuse_units_kernel", "spatial_fwd_shift": "shift_fwd_kernel<%d>" % walk,
                "spatial_fwd_vis": "vis_kernel (forward segments) + emit_inv_kernel", "spatial_inv_shift": "shift_inv_kernel<%d>" % walk,
                "spatial_inv_vis": "vis_kernel (inverse segments)", "spatial_merge": "reuse_merge_kernel"}
@@ -1175,6 +1178,17 @@ def main():
                 "pt_over_restir": tp / tr if tr and tp else None, "pt_over_restir_ell_pw_walk": tp / tb if tb and tp else None,
                 "measured": [m.get(k, {}).get("measured") for k in ("restir", "restir_ellipsoid_pairwise_walk", "pt")],
                 "how": "frozen frame 16, images averaged over iterations, relMSE variance from 2 seeds; bench_detail.json"}
+    if not args.no_quality:
+        # per-frame quality against plain path tracing at equal time on the dynamic sequence: relMSE
+        # of frames 16-23 against 4096-spp references, the mean over those frames (fixed in advance)
+        eq = {}
+        for key, mut in (("restir", lambda sc: "the timed configuration"),
+                         ("restir_ell_pw_walk", _ellipsoid(4 | 64))):
+            q = _section(detail, "quality_" + key, run_quality_variant, args, mut)
+            if "restir_vs_pt_inv_mse_time" in q:
+                eq[key] = round(q["restir_vs_pt_inv_mse_time"], 3)
+        if eq:
+            line["equal_time_vs_pt_mean"] = eq
     if not args.no_pairwise:
         pw = _section(detail, "pairwise_mis", run_pairwise, args)
         if "value" in pw:
