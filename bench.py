@@ -168,13 +168,18 @@ def aggregate(dev_s_max: float, steps: int, world: int) -> dict:
     return {"value": world * steps / dev_s_max, "ms_per_step": dev_s_max * 1e3 / steps}
 
 
+TREES = None   # path trees per pixel of the timed configuration (--trees; None: the workload's 4)
+
+
 def workload(W=512, H=512, frames=32, seed=1, flags=0):
     """The dynamic gated workload; `flags` are method flags OR-ed into its parameters."""
     from paper_2605_11536_gb300 import scenes
     sc = scenes.heightfield_spheres(W=W, H=H, frames=frames, seed=seed)
-    if flags:
+    if flags or TREES:
         sc.params = type(sc.params)(**vars(sc.params))
         sc.params.flags |= flags
+        if TREES:
+            sc.params.n_cand = TREES
     return sc
 
 
@@ -411,7 +416,7 @@ def run_convergence(args, methods, frame=16, budget_s=5.0, kmax=4096, seeds=(101
     time per run; the time to 1e-2 is read where the curve crosses it (log-log interpolation) or else
     extrapolated from the last checkpoint along the slope fitted to the last four (|slope| <= 1, so
     the extrapolation never assumes faster than 1/time convergence).
-    methods: [(name, kind, flags)] with kind "restir" or "pt"."""
+    methods: [(name, kind, flags, trees)] with kind "restir" or "pt" (trees None: the workload's)."""
     import torch
     from paper_2605_11536_gb300 import tof
     sc = workload(seed=1)
@@ -428,9 +433,11 @@ def run_convergence(args, methods, frame=16, budget_s=5.0, kmax=4096, seeds=(101
         out = torch.zeros(H * W, device="cuda")
         ck = [1 << i for i in range(0, 13) if (1 << i) <= kmax]
         pt_spp = None
-        for name, kind, flags in methods:
+        for name, kind, flags, trees in methods:
             p = type(sc.params)(**vars(sc.params))
             p.flags = sc.params.flags | flags
+            if trees:
+                p.n_cand = trees
             if kind == "pt" and pt_spp is None:
                 # calibrate: spp per call close to the first ReSTIR method's frame time
                 target_ms = out_all[methods[0][0]]["ms_per_iter"] if out_all else 4.5
@@ -1068,6 +1075,7 @@ def main():
     ap.add_argument("--flags", type=int, default=0,
                     help="method flags OR-ed into the timed configuration (tof.h TOF_FLAG_*; e.g. 324 = ellipsoidal "
                          "connection + pairwise MIS + cross-triangle walk)")
+    ap.add_argument("--trees", type=int, default=None, help="path trees per pixel of the timed configuration")
     ap.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
                     help="file for every section beyond the headline line ('' to skip)")
     ap.add_argument("--converge-budget", type=float, default=5.0, help="device seconds per convergence run")
@@ -1085,6 +1093,8 @@ def main():
     ap.add_argument("--transient-frames", type=int, default=16)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    global TREES
+    TREES = args.trees
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
@@ -1149,7 +1159,8 @@ def main():
     line = {"metric": METRIC, "value": agg["value"], "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": agg["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "flags": args.flags, "l2": "256 MiB flush between timed frames",
+            "config": {"workload": WORKLOAD if not args.trees else WORKLOAD.replace("4 trees", "%d trees" % args.trees),
+                       "flags": args.flags, "l2": "256 MiB flush between timed frames",
                        "parallelism": "replicas x%d" % world},
             "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4)},
             "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 12 * 4 * r["nobj"],
@@ -1167,23 +1178,25 @@ def main():
     # streaming kernels against HBM (the merge of the spatial pass; the transient splat below)
     stream_fr = {"reuse_merge_kernel": per_kernel.get("reuse_merge_kernel", {}).get("frac")}
     if not args.no_converge:
-        methods = [("restir", "restir", args.flags), ("restir_ellipsoid_pairwise_walk", "restir", 324), ("pt", "pt", 0)]
+        # the timed configuration, the best unbiased one measured (ellipsoidal connection + pairwise
+        # MIS + cross-triangle walk, 6 path trees) and plain path tracing
+        methods = [("restir", "restir", args.flags, None), ("restir_ell_pw_walk_6", "restir", 324, 6), ("pt", "pt", 0, None)]
         cv = _section(detail, "convergence", run_convergence, args, methods, budget_s=args.converge_budget)
         if "methods" in cv:
             m = cv["methods"]
-            tr, tb, tp = (m.get(k, {}).get("time_to_relmse_1e-2_s") for k in ("restir", "restir_ellipsoid_pairwise_walk", "pt"))
+            tr, tb, tp = (m.get(k, {}).get("time_to_relmse_1e-2_s") for k in ("restir", "restir_ell_pw_walk_6", "pt"))
             line["at_relmse_1e-2"] = {
                 "restir_s": tr, "restir_frames_per_s": 1.0 / tr if tr else None,
-                "restir_ell_pw_walk_s": tb, "pt_s": tp,
-                "pt_over_restir": tp / tr if tr and tp else None, "pt_over_restir_ell_pw_walk": tp / tb if tb and tp else None,
-                "measured": [m.get(k, {}).get("measured") for k in ("restir", "restir_ellipsoid_pairwise_walk", "pt")],
+                "restir_ell_pw_walk_6_s": tb, "pt_s": tp,
+                "pt_over_restir": tp / tr if tr and tp else None, "pt_over_restir_ell_pw_walk_6": tp / tb if tb and tp else None,
+                "measured": [m.get(k, {}).get("measured") for k in ("restir", "restir_ell_pw_walk_6", "pt")],
                 "how": "frozen frame 16, images averaged over iterations, relMSE variance from 2 seeds; bench_detail.json"}
     if not args.no_quality:
         # per-frame quality against plain path tracing at equal time on the dynamic sequence: relMSE
         # of frames 16-23 against 4096-spp references, the mean over those frames (fixed in advance)
         eq = {}
         for key, mut in (("restir", lambda sc: "the timed configuration"),
-                         ("restir_ell_pw_walk", _ellipsoid(4 | 64))):
+                         ("restir_ell_pw_walk_6", _ellipsoid(4 | 64, 6))):
             q = _section(detail, "quality_" + key, run_quality_variant, args, mut)
             if "restir_vs_pt_inv_mse_time" in q:
                 eq[key] = round(q["restir_vs_pt_inv_mse_time"], 3)
