@@ -1136,7 +1136,11 @@ def main():
         a = algo[k] / (ms / 1e3) / 1e9
         t = traffic.get(kernels[k])
         d = {"bound": "hbm", "kernel": kernels[k], "achieved": round(a, 2), "peak": hbm, "unit": "GB/s",
-             "frac": round(a / hbm, 5), "traffic": t}
+             "frac": round(a / hbm, 5), "traffic": t,
+             # what limits it, from the kernel's ncu profile (profiles/): the traversal-bound kernels
+             # are far from any DRAM roofline; their figure of merit is work per second ("throughput")
+             "limiter": "load latency (dependent rounds)" if k == "spatial_merge" else
+                        "BVH traversal: lane divergence, L1/L2 latency, instruction fetch"}
         if full:
             d.update({"ms": ms, "algorithmic_bytes": algo[k],
                       "note": "achieved = algorithmic bytes per launch / mean CUDA-event launch time; peak = %s HBM "

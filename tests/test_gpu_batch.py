@@ -154,3 +154,44 @@ def test_autotune_chooses_valid_tunings_and_keeps_results():
         for i, (a, b) in enumerate(zip(ref[f], got[f])):
             frac, relmse, _ = compare(b, a)
             assert frac >= 0.999 and relmse <= 1e-6, (f, i, frac, relmse)
+
+
+def test_full_size_instance_in_a_batch_matches_the_oracle():
+    """A 512x512 instance of the dynamic gated workload rendered inside a batch with two small
+    instances of other scenes, over 2 frames; the oracle computes a central region covering the
+    dependency cone of its inner pixels, and every untainted pixel is compared at the common bar."""
+    import torch
+    from paper_2605_11536_gb300 import tof
+    from tests.harness import PARITY_FRAC, PARITY_RELMSE
+    big = scenes.heightfield_spheres(W=512, H=512, frames=2)
+    box = scenes.box_icosphere(W=64, H=64, frames=2)
+    box.gates = [(5.0, 0.25)] * 2
+    ctx = tof.tof_create(0)
+    imgs = []
+    try:
+        sb = tof.tof_scene_upload(ctx, big.verts, big.tris, big.tri_object, big.materials, big.object_material)
+        sx = tof.tof_scene_upload(ctx, box.verts, box.tris, box.tri_object, box.materials, box.object_material)
+        vb = tof.tof_view_create(ctx, sb, 512, 512, 0)
+        vx = [tof.tof_view_create(ctx, sx, 64, 64, 0) for _ in range(2)]
+        out = torch.zeros(512 * 512, device="cuda")
+        small = [torch.zeros(64 * 64, device="cuda") for _ in range(2)]
+        for f in range(2):
+            tof.tof_bvh_build(ctx, sb, big.xforms[f].reshape(-1), refit_only=0 if f == 0 else 1)
+            tof.tof_bvh_build(ctx, sx, box.xforms[f].reshape(-1), refit_only=0 if f == 0 else 1)
+            jobs = [tof.job(sb, vb, big.sensors[f], big.emitters[f], big.params, big.seed, f, out.data_ptr(), gate=big.gates[f])]
+            for k in range(2):
+                jobs.append(tof.job(sx, vx[k], box.sensors[f], box.emitters[f], box.params, 40 + k, f, small[k].data_ptr(),
+                                    gate=box.gates[f]))
+            tof.tof_render_batch(ctx, jobs)
+            tof.tof_sync(ctx)
+            imgs.append(out.cpu().numpy().astype(np.float64).reshape(512, 512))
+    finally:
+        tof.tof_destroy(ctx)
+    half = 110
+    roi = (256 - half, 256 - half, 256 + half, 256 + half)
+    o, oks, st, _ = oracle_render(big, [0, 1], roi=roi)
+    for f in range(2):
+        assert oks[f].sum() >= 40 * 40
+        frac, relmse, _ = compare(imgs[f], o[f], oks[f])
+        assert np.count_nonzero(o[f][oks[f]]) >= 30
+        assert frac >= PARITY_FRAC and relmse <= PARITY_RELMSE, (f, frac, relmse)

@@ -115,3 +115,63 @@ def test_budget_defers_admission():
         tof.tof_server_destroy(srv)
     finally:
         tof.tof_destroy(ctx)
+
+
+def test_idle_views_are_evicted_for_new_streams():
+    """A budget that holds one view: admitting a second stream evicts the first (idle) one, whose
+    next frame then renders without temporal history -- the same image as a direct render after
+    tof_reservoirs_reset; the resident bytes never exceed the budget."""
+    import torch
+    from paper_2605_11536_gb300 import tof
+    from tests.harness import gpu_render
+    scs = [_streams()[0], scenes.box_icosphere(W=48, H=40, frames=NF, seed=5)]
+    scs[1].gates = [(5.0, 0.25)] * NF
+    scs[1].params.n_spatial, scs[1].params.radius, scs[1].params.temporal = 3, 6, 1
+    ctx = tof.tof_create(0)
+    out = {}
+    try:
+        sids = []
+        for sc in scs:
+            sids.append(tof.tof_scene_upload(ctx, sc.verts, sc.tris, sc.tri_object, sc.materials, sc.object_material))
+            tof.tof_bvh_build(ctx, sids[-1], sc.xforms[0].reshape(-1))
+
+        def run(srv, streams, i, f):
+            sc = scs[i]
+            buf = torch.zeros(48 * 40, device="cuda")
+            j = tof.job(sids[i], 0, sc.sensors[f], sc.emitters[f], sc.params, 21 + i, f, buf.data_ptr(), gate=sc.gates[f])
+            t = tof.tof_server_submit(srv, streams[i], j, sc.xforms[f].reshape(-1))
+            for _ in range(1000):
+                tof.tof_server_step(srv)
+                torch.cuda.synchronize()
+                if tof.tof_server_poll(srv, t)[0] == 2:
+                    break
+            assert tof.tof_server_poll(srv, t)[0] == 2
+            return buf.cpu().numpy().astype(np.float64)
+
+        # the device bytes of one stream's view, measured by a server without a budget
+        srv = tof.tof_server_create(ctx, 0)
+        run(srv, [tof.tof_server_open_stream(srv, sids[0], 48, 40, 0)], 0, 0)
+        one = tof.tof_server_stats(srv)["resident_bytes"]
+        tof.tof_server_destroy(srv)
+        assert one > 0
+        budget = int(one * 1.5)
+        srv = tof.tof_server_create(ctx, budget)
+        streams = [tof.tof_server_open_stream(srv, sids[i], 48, 40, 0) for i in range(2)]
+        out[(0, 0)] = run(srv, streams, 0, 0)
+        out[(1, 0)] = run(srv, streams, 1, 0)      # evicts stream 0's view
+        assert tof.tof_server_stats(srv)["resident_bytes"] <= budget
+        out[(0, 1)] = run(srv, streams, 0, 1)      # evicts stream 1's; stream 0 starts without history
+        st = tof.tof_server_stats(srv)
+        assert st["resident_bytes"] <= budget and st["completed"] == 3 and st["queued"] == 0
+        tof.tof_server_destroy(srv)
+    finally:
+        tof.tof_destroy(ctx)
+    d0 = gpu_render(scs[0], [0, 1], seed=21, reset_each=True)
+    d1 = gpu_render(scs[1], [0], seed=22)
+    for key, ref in (((0, 0), d0[0]), ((1, 0), d1[0]), ((0, 1), d0[1])):
+        assert np.count_nonzero(ref) > 0, key
+        fr, rm, _ = compare(out[key], np.asarray(ref).ravel())
+        assert fr >= 0.999 and rm <= 1e-6, (key, fr, rm)
+    # and the evicted stream's frame 1 is not what it would have been with its history
+    with_history = gpu_render(scs[0], [0, 1], seed=21)[1]
+    assert not np.array_equal(out[(0, 1)], np.asarray(with_history).ravel())
