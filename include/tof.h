@@ -252,10 +252,15 @@ typedef struct {
     float* out_dev;           /* H*W (gated) or H*W*B (transient) floats, caller-owned device memory */
 } tof_job;
 
-/* Render n independent jobs as one CUDA graph launched on `stream`: every job's stage kernels form
- * their own branch of the graph, so small instances run concurrently and the whole batch costs one
- * launch.  Jobs must use distinct views.  Results equal those of rendering each job on its own.
- * Scratch for every view is allocated before the graph is captured (first use of a view). */
+/* Render n independent jobs as one CUDA graph launched on `stream`.  When every job is a gated view
+ * without the ellipsoidal connection, the triangle walk, the shrink mapping or a laser emitter, the
+ * jobs are split into 4 groups of similar estimated work and each group is one branch of the graph
+ * with one kernel launch per stage over all of its instances (per-pixel stages map each block to its
+ * instance; persistent stages pull every instance's tasks), ~20 launches per group whatever the
+ * number of instances; the stage arguments travel as tables copied at the head of the graph.
+ * Otherwise every job's stage kernels form their own branch (16 concurrent branches).  Jobs must
+ * use distinct views.  Results equal those of rendering each job on its own.  Scratch for every view
+ * is allocated before the graph is captured (first use of a view). */
 tof_status tof_render_batch(tof_ctx* ctx, const tof_job* jobs, uint32_t n, void* stream);
 
 /* Launch shapes and reservoir layout of a view (the batched form's per-instance-class tuning).

@@ -38,6 +38,10 @@ cudaError_t launch_build_topology(int n, const float4* cent, uint32_t* bb, uint3
 cudaError_t launch_etree(int nt, int P, const float4* tri, float4* node, cudaStream_t s);
 cudaError_t launch_refit(int n, const uint32_t* prim, const float4* tri, float4* leaf, float4* nodes, const int* child,
                          const int* parent_int, const int* parent_leaf, uint32_t* counter, cudaStream_t s);
+cudaError_t launch_gbuffer_batch(const GbufArgs* A, const int* blk0, int n, int blocks, cudaStream_t s);
+cudaError_t launch_initial_batch(const InitArgs* A, const int* blk0, int n, int blocks, cudaStream_t s);
+cudaError_t launch_reuse_batch(const ReuseJob* J, int n, const int* blk_slots, int nblk_slots, const int* blk_units,
+                               int nblk_units, int persist_blocks, int vis_blocks, cudaStream_t s);
 }  // namespace tof
 
 using namespace tof;
@@ -145,6 +149,13 @@ struct tof_ctx {
     cudaEvent_t fork = nullptr;
     cudaStream_t capture = nullptr;
     cudaGraphExec_t batch_exec[kBatchSlots] = {};   // one instantiated graph per batch slot
+    // staged batches: argument tables per slot (pinned host staging, device copy) and the event after
+    // the slot's last launch (the staging buffer is rewritten only once that launch has finished)
+    void* bstage[kBatchSlots] = {};
+    size_t bstage_bytes[kBatchSlots] = {};
+    unsigned char* btab[kBatchSlots] = {};
+    size_t btab_bytes[kBatchSlots] = {};
+    cudaEvent_t bdone[kBatchSlots] = {};
     bool in_batch = false;
 };
 
@@ -398,6 +409,10 @@ tof_status tof_destroy(tof_ctx* c) {
     cudaDeviceSynchronize();
     for (cudaGraphExec_t& x : c->batch_exec)
         if (x) cudaGraphExecDestroy(x);
+    for (int k = 0; k < kBatchSlots; ++k) {
+        if (c->bstage[k]) cudaFreeHost(c->bstage[k]);
+        if (c->bdone[k]) cudaEventDestroy(c->bdone[k]);
+    }
     for (cudaStream_t q : c->pool) cudaStreamDestroy(q);
     for (cudaEvent_t e : c->join) cudaEventDestroy(e);
     if (c->fork) cudaEventDestroy(c->fork);
@@ -610,6 +625,15 @@ tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[10]) {
 }
 
 static bool g_no_marks = false;   // set while a batch is being captured (no profiling events)
+
+// staged batches: while set, render() records each stage's arguments instead of launching them
+struct BatchRec {
+    std::vector<GbufArgs> gbuf;
+    std::vector<InitArgs> init;
+    std::vector<std::vector<ReuseJob>> pass;   // pass[q]: every instance's q-th reuse pass
+    size_t q = 0;                              // the current instance's next pass
+};
+static BatchRec* g_rec = nullptr;
 constexpr int kReuseEvents = 7;   // events around the kernels of one reuse launch group
 
 // resident-block counts of the persistent reuse kernels, once per context
@@ -719,6 +743,13 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
             ev = &V.kev[V.kev_used];
             V.kev_used += kReuseEvents;
         }
+        if (g_rec) {
+            if (g_rec->pass.size() <= g_rec->q) g_rec->pass.resize(g_rec->q + 1);
+            ReuseJob J;
+            J.a = ra; J.w = w; J.p0 = (int)p0; J.p1 = (int)p1;
+            g_rec->pass[g_rec->q].push_back(J);
+            continue;
+        }
         int pb = c->persist_blocks, vb = c->vis_blocks;
         if (V.tune.packet > 0) {
             pb = std::min(pb, c->sms * V.tune.packet);
@@ -726,6 +757,7 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
         }
         CK(launch_reuse_wave(ra, w, (int)p0, (int)p1, pb, vb, ev, s));
     }
+    if (g_rec) ++g_rec->q;
     return TOF_OK;
 }
 
@@ -768,7 +800,12 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     if (emitter->type == TOF_EMIT_LASER) CK(launch_laser(F.g, v3f(emitter->pos), v3f(emitter->dir), emitter->power, V.laser[fc], s));
     GbufArgs ga;
     ga.F = F; ga.gb = V.gb[fc]; ga.P = P; ga.tile_w = V.tune.tile_w;
-    CK(launch_gbuffer(ga, V.tune.tile_h, s));
+    if (g_rec) {
+        g_rec->q = 0;
+        g_rec->gbuf.push_back(ga);
+    } else {
+        CK(launch_gbuffer(ga, V.tune.tile_h, s));
+    }
     mark(V, 1, s);
     V.ran[0] = true;
 
@@ -799,6 +836,8 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
             eb = std::min(eb, c->sms * V.tune.packet);
         }
         CK(launch_initial_ell_wave(ia, V.ell, V.tune.tile_h, eb, vb, s));
+    } else if (g_rec) {
+        g_rec->init.push_back(ia);   // staged batches hold gated views without those options only
     } else {
         CK(launch_initial(ia, V.tune.tile_h, c->d_err, s));
     }
@@ -860,7 +899,7 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     }
     mark(V, 5, s);
     mark(V, 6, s);
-    mirror_err(c, s, g_no_marks);
+    if (!g_rec) mirror_err(c, s, g_no_marks);
     V.fd[fc] = F;
     V.geom_slot[fc] = S.cur;
     V.geom_version[fc] = S.version[S.cur];
@@ -979,6 +1018,207 @@ __attribute__((visibility("hidden"))) tof_status tof_internal_prepare_job(tof_ct
     return prepare_job(c, *job, 0);
 }
 
+// launch a captured batch graph through the slot's executable graph (updated in place when only node
+// parameters changed, else instantiated again); the graph itself is consumed
+static tof_status launch_batch_graph(tof_ctx* c, cudaGraph_t graph, int slot, cudaStream_t stream) {
+    cudaGraphExec_t& X = c->batch_exec[slot];
+    bool updated = false;
+    if (X) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(X, graph, &info) == cudaSuccess) updated = true;
+        else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(X);
+            X = nullptr;
+        }
+    }
+    if (!updated) {
+        cudaError_t e = cudaGraphInstantiate(&X, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            X = nullptr;
+            return fail(c, TOF_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaGraphDestroy(graph);
+    CK(cudaGraphLaunch(X, stream));
+    return TOF_OK;
+}
+
+// staged batches: jobs whose every stage has a batched kernel (gated views without the ellipsoidal
+// connection, the triangle walk, the shrink mapping or a laser emitter)
+static bool stageable(const tof_job& J) {
+    return !J.transient && !(J.params.flags & (TOF_FLAG_ELLIPSOID | TOF_FLAG_TRIANGLE_WALK)) && !(J.params.shrink_k > 1.f) &&
+           J.emitter.type != TOF_EMIT_LASER;
+}
+static size_t al256h(size_t b) { return (b + 255) / 256 * 256; }
+
+// argument tables of one group of a staged batch, laid out in the slot's staging buffer from `off`
+struct StagedGroup {
+    BatchRec rec;
+    std::vector<int> bpix;
+    std::vector<std::vector<int>> bs, bu;
+    size_t o_g = 0, o_i = 0, o_b = 0;
+    std::vector<size_t> o_p, o_s, o_u;
+};
+static size_t staged_layout(StagedGroup& G, size_t off) {
+    const size_t nj = G.rec.gbuf.size(), np = G.rec.pass.size();
+    G.bpix.assign(nj + 1, 0);
+    for (size_t j = 0; j < nj; ++j) {
+        const GbufArgs& g = G.rec.gbuf[j];
+        const int tw = g.tile_w, th = 128 / tw;
+        G.bpix[j + 1] = G.bpix[j] + ((g.F.W + tw - 1) / tw) * ((g.F.H + th - 1) / th);
+    }
+    G.o_g = off;
+    off = al256h(off + sizeof(GbufArgs) * nj);
+    G.o_i = off;
+    off = al256h(off + sizeof(InitArgs) * nj);
+    G.o_b = off;
+    off = al256h(off + sizeof(int) * (nj + 1));
+    G.o_p.assign(np, 0); G.o_s.assign(np, 0); G.o_u.assign(np, 0);
+    G.bs.assign(np, {}); G.bu.assign(np, {});
+    for (size_t q = 0; q < np; ++q) {
+        const std::vector<ReuseJob>& P = G.rec.pass[q];
+        G.bs[q].assign(P.size() + 1, 0);
+        G.bu[q].assign(P.size() + 1, 0);
+        for (size_t k = 0; k < P.size(); ++k) {
+            const long long npx = P[k].p1 - P[k].p0;
+            G.bs[q][k + 1] = G.bs[q][k] + (int)((npx + 127) / 128);
+            G.bu[q][k + 1] = G.bu[q][k] + (int)((npx * P[k].a.dst.words + 127) / 128);
+        }
+        G.o_p[q] = off;
+        off = al256h(off + sizeof(ReuseJob) * P.size());
+        G.o_s[q] = off;
+        off = al256h(off + sizeof(int) * (P.size() + 1));
+        G.o_u[q] = off;
+        off = al256h(off + sizeof(int) * (P.size() + 1));
+    }
+    return off;
+}
+static void staged_fill(const StagedGroup& G, unsigned char* h) {
+    const size_t nj = G.rec.gbuf.size();
+    memcpy(h + G.o_g, G.rec.gbuf.data(), sizeof(GbufArgs) * nj);
+    memcpy(h + G.o_i, G.rec.init.data(), sizeof(InitArgs) * nj);
+    memcpy(h + G.o_b, G.bpix.data(), sizeof(int) * (nj + 1));
+    for (size_t q = 0; q < G.rec.pass.size(); ++q) {
+        memcpy(h + G.o_p[q], G.rec.pass[q].data(), sizeof(ReuseJob) * G.rec.pass[q].size());
+        memcpy(h + G.o_s[q], G.bs[q].data(), sizeof(int) * G.bs[q].size());
+        memcpy(h + G.o_u[q], G.bu[q].data(), sizeof(int) * G.bu[q].size());
+    }
+}
+static cudaError_t staged_launch(tof_ctx* c, const StagedGroup& G, unsigned char* d, cudaStream_t q) {
+    const int nj = (int)G.rec.gbuf.size();
+    if (nj == 0) return cudaSuccess;
+    cudaError_t e = launch_gbuffer_batch((const GbufArgs*)(d + G.o_g), (const int*)(d + G.o_b), nj, G.bpix[nj], q);
+    if (e == cudaSuccess) e = launch_initial_batch((const InitArgs*)(d + G.o_i), (const int*)(d + G.o_b), nj, G.bpix[nj], q);
+    for (size_t k = 0; k < G.rec.pass.size() && e == cudaSuccess; ++k)
+        e = launch_reuse_batch((const ReuseJob*)(d + G.o_p[k]), (int)G.rec.pass[k].size(), (const int*)(d + G.o_s[k]),
+                               G.bs[k].back(), (const int*)(d + G.o_u[k]), G.bu[k].back(), c->persist_blocks, c->vis_blocks, q);
+    return e;
+}
+
+// One graph for the whole batch: the instances are split into kStagedGroups groups of similar
+// estimated work, and each group is a branch of the graph with one launch per stage over all its
+// instances (per-pixel stages map each block to its instance, persistent stages pull every
+// instance's tasks in turn).  render() records every instance's stage arguments (advancing the
+// views' state exactly as a direct render does); the tables are copied once at the head of the
+// graph.  The branches let different stages of different groups overlap on the device, which one
+// stage at a time over every instance would not (latency-bound stages leave the GPU half idle).
+constexpr uint32_t kStagedGroups = 4;
+static tof_status render_batch_staged(tof_ctx* c, const tof_job* jobs, uint32_t n, cudaStream_t stream, int slot) {
+    TRY(persist_init(c));
+    if (!c->capture) CK(cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+    if (!c->fork) CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    if (!c->bdone[slot]) CK(cudaEventCreateWithFlags(&c->bdone[slot], cudaEventDisableTiming));
+    else CK(cudaEventSynchronize(c->bdone[slot]));   // the slot's staging buffer is free again
+    const uint32_t NG = n < kStagedGroups ? n : kStagedGroups;
+    while (c->pool.size() < NG) {
+        cudaStream_t q;
+        cudaEvent_t e;
+        CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->pool.push_back(q);
+        c->join.push_back(e);
+    }
+    // groups: longest estimated work first onto the least loaded group
+    std::vector<double> cost(n), load(NG, 0.0);
+    std::vector<uint32_t> order(n), group(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        const tof_job& J = jobs[i];
+        const ViewH& V = c->views[J.view];
+        const double passes = 1.0 + (J.params.temporal ? 1.0 : 0.0) + J.params.n_spatial_iters * (1.0 + J.params.n_spatial);
+        cost[i] = (double)V.W * V.H * J.params.depth * (J.params.n_cand + passes);
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+    for (uint32_t i : order) {
+        uint32_t best = 0;
+        for (uint32_t g = 1; g < NG; ++g)
+            if (load[g] < load[best]) best = g;
+        group[i] = best;
+        load[best] += cost[i];
+    }
+    std::vector<StagedGroup> G(NG);
+    g_no_marks = true;
+    tof_status st = TOF_OK;
+    for (uint32_t i = 0; i < n && st == TOF_OK; ++i) {
+        const tof_job& J = jobs[i];
+        g_rec = &G[group[i]].rec;
+        st = render(c, J.scene, J.view, &J.sensor, &J.emitter, J.gate.L0, J.gate.dL, 0, &J.params, J.seed, J.frame, J.out_dev,
+                    stream);
+        if (st == TOF_OK && g_rec->init.size() != g_rec->gbuf.size())
+            st = fail(c, TOF_ESTATE, "staged batch: job %u recorded no initial stage", i);
+    }
+    g_rec = nullptr;
+    g_no_marks = false;
+    TRY(st);
+    size_t bytes = 0;
+    for (StagedGroup& g : G) bytes = staged_layout(g, bytes);
+    if (c->bstage_bytes[slot] < bytes) {
+        if (c->bstage[slot]) cudaFreeHost(c->bstage[slot]);
+        c->bstage[slot] = nullptr;
+        c->bstage_bytes[slot] = 0;
+        CK(cudaHostAlloc(&c->bstage[slot], bytes, cudaHostAllocDefault));
+        c->bstage_bytes[slot] = bytes;
+    }
+    if (c->btab_bytes[slot] < bytes) {
+        dfree(c, c->btab[slot]);
+        c->btab[slot] = nullptr;
+        c->btab_bytes[slot] = 0;
+        TRY(dalloc(c, &c->btab[slot], bytes, "batch argument tables"));
+        c->btab_bytes[slot] = bytes;
+    }
+    unsigned char* h = (unsigned char*)c->bstage[slot];
+    for (const StagedGroup& g : G) staged_fill(g, h);
+    unsigned char* d = c->btab[slot];
+    c->in_batch = true;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t r = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c->capture);
+        if (r == cudaSuccess) r = cudaEventRecord(c->fork, c->capture);
+        for (uint32_t g = 0; g < NG && r == cudaSuccess; ++g) {
+            r = cudaStreamWaitEvent(c->pool[g], c->fork, 0);
+            if (r == cudaSuccess) r = staged_launch(c, G[g], d, c->pool[g]);
+            if (r == cudaSuccess) r = cudaEventRecord(c->join[g], c->pool[g]);
+            if (r == cudaSuccess) r = cudaStreamWaitEvent(c->capture, c->join[g], 0);
+        }
+        e = cudaStreamEndCapture(c->capture, &graph);
+        if (r != cudaSuccess) e = r;
+    }
+    c->in_batch = false;
+    if (e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(c, TOF_ECUDA, "staged batch capture failed: %s", cudaGetErrorString(e));
+    }
+    TRY(launch_batch_graph(c, graph, slot, stream));
+    CK(cudaEventRecord(c->bdone[slot], stream));
+    mirror_err(c, stream, false);
+    for (uint32_t i = 0; i < n; ++i) c->views[jobs[i].view].last_stream = stream;
+    return TOF_OK;
+}
+
 static tof_status render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void* stream, int slot) {
     if (!c) return TOF_EINVAL;
     if (!jobs || n == 0) return fail(c, TOF_EINVAL, "empty batch");
@@ -994,6 +1234,9 @@ static tof_status render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void
         seen.push_back(J.view);
         TRY(prepare_job(c, J, i));
     }
+    bool staged = true;
+    for (uint32_t i = 0; i < n && staged; ++i) staged = stageable(jobs[i]);
+    if (staged) return render_batch_staged(c, jobs, n, (cudaStream_t)stream, slot);
     TRY(persist_init(c));
     const uint32_t P = n < 16 ? n : 16;
     while (c->pool.size() < P) {
@@ -1061,28 +1304,7 @@ static tof_status render_batch(tof_ctx* c, const tof_job* jobs, uint32_t n, void
         cudaGetLastError();
         return fail(c, TOF_ECUDA, "batch capture failed: %s", cudaGetErrorString(e));
     }
-    // reuse the slot's instantiated graph when only node parameters changed
-    cudaGraphExec_t& X = c->batch_exec[slot];
-    bool updated = false;
-    if (X) {
-        cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(X, graph, &info) == cudaSuccess) updated = true;
-        else {
-            cudaGetLastError();
-            cudaGraphExecDestroy(X);
-            X = nullptr;
-        }
-    }
-    if (!updated) {
-        e = cudaGraphInstantiate(&X, graph, 0);
-        if (e != cudaSuccess) {
-            cudaGraphDestroy(graph);
-            X = nullptr;
-            return fail(c, TOF_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
-        }
-    }
-    cudaGraphDestroy(graph);
-    CK(cudaGraphLaunch(X, (cudaStream_t)stream));
+    TRY(launch_batch_graph(c, graph, slot, (cudaStream_t)stream));
     mirror_err(c, (cudaStream_t)stream, false);
     for (uint32_t i = 0; i < n; ++i) c->views[jobs[i].view].last_stream = (cudaStream_t)stream;
     return TOF_OK;

@@ -1460,4 +1460,26 @@ static __device__ bool shift_rec(const Rec& x, const Domain& Dj, const Domain& D
     return true;
 }
 
+// --------------------------------------------------------------------------------------------
+// batched launches (tof_render_batch): the instance of this block, blk0[j] <= blockIdx.x < blk0[j + 1],
+// and its argument record copied to shared memory by the whole block
+__device__ __forceinline__ int batch_job(const int* __restrict__ blk0, int n) {
+    int lo = 0, hi = n - 1;
+    const int b = (int)blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&blk0[mid]) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+template <class T>
+__device__ __forceinline__ void block_copy(T* dst, const T* src) {
+    static_assert(sizeof(T) % 4 == 0, "4-byte words");
+    const uint32_t* s = (const uint32_t*)src;
+    uint32_t* d = (uint32_t*)dst;
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+
 }  // namespace tof

@@ -187,6 +187,14 @@ struct EllWaveDev {
     uint32_t* counters;     // requests, request fetch, segments, segment fetch
 };
 
+// one instance's reuse pass in a batched launch (tof_render_batch): its arguments, its wavefront
+// scratch and its pixel range
+struct ReuseJob {
+    ReuseArgs a;
+    WaveDev w;
+    int p0, p1;
+};
+
 struct SplatArgs {
     ResDev src;
     int npix, B;

@@ -139,20 +139,22 @@ __device__ __forceinline__ void store_tail(const ResDev& R, size_t idx, const Re
     }
 }
 
-// pixel of this thread in a tile_w x (blockDim.x / tile_w) tile (tile_w a power of two)
-__device__ __forceinline__ void tile_pixel(int tile_w, int& ix, int& iy) {
+// pixel of this thread in tile (bx, by) of tile_w x (blockDim.x / tile_w) pixels (tile_w a power of
+// two); a direct launch passes (blockIdx.x, blockIdx.y), a batched one the tile within its instance
+__device__ __forceinline__ void tile_pixel(int tile_w, int bx, int by, int& ix, int& iy) {
     const int sh = __ffs(tile_w) - 1;
-    ix = blockIdx.x * tile_w + (int)(threadIdx.x & (unsigned)(tile_w - 1));
-    iy = blockIdx.y * (int)(blockDim.x >> sh) + (int)(threadIdx.x >> sh);
+    ix = bx * tile_w + (int)(threadIdx.x & (unsigned)(tile_w - 1));
+    iy = by * (int)(blockDim.x >> sh) + (int)(threadIdx.x >> sh);
 }
+__device__ __forceinline__ void tile_pixel(int tile_w, int& ix, int& iy) { tile_pixel(tile_w, blockIdx.x, blockIdx.y, ix, iy); }
 
 // --------------------------------------------------------------------------------------------
 // G-buffer: one jittered primary ray per pixel -> (tri, b1, b2, |x1 - x0|)
 // --------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) gbuffer_kernel(const __grid_constant__ GbufArgs a) {
+__device__ __forceinline__ void gbuffer_body(const GbufArgs& a, int bx, int by) {
     const FrameDev& F = a.F;
     int ix, iy;
-    tile_pixel(a.tile_w, ix, iy);
+    tile_pixel(a.tile_w, bx, by, ix, iy);
     if (ix >= F.W || iy >= F.H) return;
     int pix = iy * F.W + ix;
     uint4 u = philox((uint32_t)pix, F.frame, 0u, P_JITTER, a.P.seed);
@@ -165,6 +167,17 @@ __global__ void __launch_bounds__(128) gbuffer_kernel(const __grid_constant__ Gb
         out = make_float4(__int_as_float(tri), b1, b2, len3(s.p - o));
     }
     a.gb[pix] = out;
+}
+__global__ void __launch_bounds__(128) gbuffer_kernel(const __grid_constant__ GbufArgs a) { gbuffer_body(a, blockIdx.x, blockIdx.y); }
+// all instances of a batch: blocks blk0[j] .. blk0[j + 1] - 1 tile instance j
+__global__ void __launch_bounds__(128) gbuffer_batch_kernel(const GbufArgs* __restrict__ A, const int* __restrict__ blk0, int n) {
+    __shared__ GbufArgs s;
+    const int j = batch_job(blk0, n);
+    block_copy(&s, &A[j]);
+    __syncthreads();
+    const int lb = (int)blockIdx.x - __ldg(&blk0[j]);
+    const int tx = (s.F.W + s.tile_w - 1) / s.tile_w;
+    gbuffer_body(s, lb % tx, lb / tx);
 }
 
 // --------------------------------------------------------------------------------------------
@@ -236,10 +249,10 @@ struct GatedSink {
 
 // gated views: the same trees, candidates, order and uniforms as initial_kernel, into GatedSink
 template <bool kEll>
-__global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_gated_kernel(const __grid_constant__ InitArgs a) {
+__device__ __forceinline__ void initial_gated_body(const InitArgs& a, int bx, int by) {
     const FrameDev& F = a.F;
     int ix, iy;
-    tile_pixel(a.tile_w, ix, iy);
+    tile_pixel(a.tile_w, bx, by, ix, iy);
     if (ix >= F.W || iy >= F.H) return;
     const int pix = iy * F.W + ix;
     const ParamsDev& P = a.P;
@@ -271,6 +284,20 @@ __global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_gated_kernel(const 
     }
     a.dst.occ[pix] = occ;
     if (a.out) a.out[pix] = outv;
+}
+template <bool kEll>
+__global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_gated_kernel(const __grid_constant__ InitArgs a) {
+    initial_gated_body<kEll>(a, blockIdx.x, blockIdx.y);
+}
+__global__ void __launch_bounds__(128, 6) initial_gated_batch_kernel(const InitArgs* __restrict__ A, const int* __restrict__ blk0,
+                                                                     int n) {
+    __shared__ InitArgs s;
+    const int j = batch_job(blk0, n);
+    block_copy(&s, &A[j]);
+    __syncthreads();
+    const int lb = (int)blockIdx.x - __ldg(&blk0[j]);
+    const int tx = (s.F.W + s.tile_w - 1) / s.tile_w;
+    initial_gated_body<false>(s, lb % tx, lb / tx);
 }
 
 // 6 resident blocks per SM (80 registers): 1.08 against 1.11 ms at 5 blocks (96 registers) on the
@@ -699,6 +726,19 @@ cudaError_t launch_initial(const InitArgs& a, int tile_h, unsigned* err, cudaStr
 }
 cudaError_t launch_vis_queue(const GeomDev& g, const float4* rays, const uint32_t* counter, uint32_t cap, uint32_t* fetch,
                              float* target, int blocks, cudaStream_t s);   // tof_reuse.cu
+
+// batched G-buffer and gated initial stages over the instances of a batch (device argument tables,
+// blk0: first block of each instance, `blocks` in all)
+cudaError_t launch_gbuffer_batch(const GbufArgs* A, const int* blk0, int n, int blocks, cudaStream_t s) {
+    note_launch();
+    gbuffer_batch_kernel<<<blocks, 128, 0, s>>>(A, blk0, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_initial_batch(const InitArgs* A, const int* blk0, int n, int blocks, cudaStream_t s) {
+    note_launch();
+    initial_gated_batch_kernel<<<blocks, 128, 0, s>>>(A, blk0, n);
+    return cudaGetLastError();
+}
 
 // resident blocks of ell_place_kernel on every SM (its grid strides over the requests)
 cudaError_t ell_place_blocks(int* out) {

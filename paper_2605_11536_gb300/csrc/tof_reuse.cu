@@ -99,10 +99,9 @@ __device__ __forceinline__ void store_rec(float4* P, size_t stride, size_t idx, 
 // --------------------------------------------------------------------------------------------
 // per pixel: slots (the pixel, its reused pixels) and capped confidences
 // --------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) reuse_slots_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w,
-                                                          int p0, int p1) {
+__device__ __forceinline__ void reuse_slots_body(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int blk) {
     const FrameDev& C = a.cur;
-    const int pix = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int pix = p0 + blk * blockDim.x + threadIdx.x;
     if (pix >= p1) return;
     const ParamsDev& P = a.P;
     int n = 1;
@@ -142,18 +141,21 @@ __global__ void __launch_bounds__(128) reuse_slots_kernel(const __grid_constant_
     w.nslot[pix] = (uint8_t)n;
     for (int s = 0; s < n; ++s) { w.slot_pix[(size_t)pix * S + s] = sp[s]; w.slot_M[(size_t)pix * S + s] = sM[s]; }
 }
+__global__ void __launch_bounds__(128) reuse_slots_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w,
+                                                          int p0, int p1) {
+    reuse_slots_body(a, w, p0, p1, blockIdx.x);
+}
 
 // --------------------------------------------------------------------------------------------
 // per (pixel, 32-bin occupancy word): merge units and their tasks. One thread per word keeps the
 // transient passes parallel over bins (a pixel may occupy hundreds of bins); gated views have one
 // word per pixel.
 // --------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) reuse_units_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w,
-                                                          int p0, int p1) {
+__device__ __forceinline__ void reuse_units_body(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int blk) {
     const FrameDev& C = a.cur;
     const int Bn = C.B > 0 ? C.B : 1;
     const int words = a.dst.words;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long t = (long long)blk * blockDim.x + threadIdx.x;
     const bool active = t < (long long)(p1 - p0) * words;
     const int pix = active ? p0 + (int)(t / words) : 0;
     const int wd = active ? (int)(t % words) : 0;
@@ -230,12 +232,16 @@ __global__ void __launch_bounds__(128) reuse_units_kernel(const __grid_constant_
     // gated (one word per pixel): pixels that form a unit get their value from the merge
     if (active && a.out) a.out[pix] = n == 1 ? outv : 0.f;
 }
+__global__ void __launch_bounds__(128) reuse_units_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w,
+                                                          int p0, int p1) {
+    reuse_units_body(a, w, p0, p1, blockIdx.x);
+}
 
 // --------------------------------------------------------------------------------------------
 // forward shifts: slot s's sample into the unit's domain
 // --------------------------------------------------------------------------------------------
 template <bool kWalk>
-__global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+__device__ __forceinline__ void shift_fwd_body(const ReuseArgs& a, const WaveDev& w) {
     ShiftStats st = {0, 0, 0, 0, 0};
     const uint32_t ntask = min(w.counters[1], (uint32_t)w.cap_units * (uint32_t)(w.slots - 1));
     const int S = w.slots;
@@ -280,6 +286,10 @@ __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant
         }
     }
 }
+template <bool kWalk>
+__global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+    shift_fwd_body<kWalk>(a, w);
+}
 
 // --------------------------------------------------------------------------------------------
 // visibility segments queued by a shift kernel; an occluded segment zeroes the result it guards.
@@ -292,9 +302,11 @@ __global__ void __launch_bounds__(128, 8) shift_fwd_kernel(const __grid_constant
 // --------------------------------------------------------------------------------------------
 constexpr int kVisSteps = 32;   // 8: 4.63, 16: 4.52, 32: 4.49-4.51, 64 / 128: 4.50 ms per 512 x 512 frame
 
-__global__ void __launch_bounds__(128, 8) vis_kernel(const GeomDev g, const float4* __restrict__ rays, const uint32_t* counter,
-                                                  uint32_t cap, uint32_t* fetch, float* target, StatsDev* stats, int stat,
-                                                  int ray_stat) {
+__device__ __forceinline__ void vis_body(const GeomDev& gref, const float4* __restrict__ rays, const uint32_t* counter,
+                                         uint32_t cap, uint32_t* fetch, float* target, StatsDev* stats, int stat, int ray_stat) {
+    // the hierarchy in registers (a batched launch passes the instance's GeomDev in shared memory)
+    GeomDev g;
+    g.nodes = gref.nodes; g.leaf = gref.leaf; g.nt = gref.nt; g.err = gref.err;
     const uint32_t n = min(*counter, cap);
     if (stats && ray_stat >= 0 && blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(&stats->v[ray_stat], (unsigned long long)n);
     const int lane = threadIdx.x & 31;
@@ -394,13 +406,18 @@ __global__ void __launch_bounds__(128, 8) vis_kernel(const GeomDev g, const floa
         if (lane == 0 && x) atomicAdd(&stats->v[stat], 0ull - x);
     }
 }
+__global__ void __launch_bounds__(128, 8) vis_kernel(const GeomDev g, const float4* __restrict__ rays, const uint32_t* counter,
+                                                  uint32_t cap, uint32_t* fetch, float* target, StatsDev* stats, int stat,
+                                                  int ray_stat) {
+    vis_body(g, rays, counter, cap, fetch, target, stats, stat, ray_stat);
+}
 
 // --------------------------------------------------------------------------------------------
 // after the forward shifts' visibility: each surviving shifted candidate's inverse shifts into
 // the other reused domains (pairwise MIS needs none: it pairs the canonical domain with each
 // reused one)
 // --------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) emit_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+__device__ __forceinline__ void emit_inv_body(const ReuseArgs& a, const WaveDev& w) {
     const uint32_t ntask = min(w.counters[1], (uint32_t)w.cap_units * (uint32_t)(w.slots - 1));
     const int S = w.slots;
     const bool pairwise = (a.P.flags & kFlagPairwiseMis) != 0u;
@@ -420,12 +437,15 @@ __global__ void __launch_bounds__(128) emit_inv_kernel(const __grid_constant__ R
             if (j != s && slot_present(a, j, b)) w.inv[ib++] = (u << 8) | ((uint32_t)s << 4) | (uint32_t)j;
     }
 }
+__global__ void __launch_bounds__(128) emit_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+    emit_inv_body(a, w);
+}
 
 // --------------------------------------------------------------------------------------------
 // inverse shifts: candidate s's offset path (in the unit's domain) into domain j
 // --------------------------------------------------------------------------------------------
 template <bool kWalk>
-__global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+__device__ __forceinline__ void shift_inv_body(const ReuseArgs& a, const WaveDev& w) {
     const uint32_t cap = (uint32_t)w.cap_units * (uint32_t)w.slots * (uint32_t)(w.slots - 1);
     const uint32_t ntask = min(w.counters[2], cap);
     const int S = w.slots;
@@ -469,6 +489,10 @@ __global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant
         }
     }
 }
+template <bool kWalk>
+__global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+    shift_inv_body<kWalk>(a, w);
+}
 
 // --------------------------------------------------------------------------------------------
 // merge: MIS weights, streaming selection, output record.  One group of G lanes per unit (G the
@@ -479,7 +503,7 @@ __global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant
 // same running sum and comparisons as one thread would make); the group then copies the selected
 // record plane by plane.
 // --------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+__device__ __forceinline__ void reuse_merge_body(const ReuseArgs& a, const WaveDev& w) {
     const uint32_t nunits = min(w.counters[0], (uint32_t)w.cap_units);
     const int S = w.slots;
     const FrameDev& C = a.cur;
@@ -632,6 +656,72 @@ __global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant_
         }
         if (unit_ok && s == 0 && a.out) a.out[pix] = sel >= 0 ? pysel * (Ssum / pysel) : 0.f;
     }
+}
+__global__ void __launch_bounds__(128) reuse_merge_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
+    reuse_merge_body(a, w);
+}
+
+// --------------------------------------------------------------------------------------------
+// a reuse pass over all instances of a batch (tof_render_batch): one launch per stage.  Per-pixel
+// stages map each block to its instance through blk0 (first block of each instance); persistent
+// stages run over the instances one after another, every block pulling its share of each instance's
+// tasks (the instances are independent, so no block waits for another).  Each block copies the
+// instance's argument record to shared memory.
+// --------------------------------------------------------------------------------------------
+__global__ void reuse_reset_batch_kernel(const ReuseJob* __restrict__ J, int n) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * kWaveCounters; t += gridDim.x * blockDim.x)
+        J[t / kWaveCounters].w.counters[t % kWaveCounters] = 0u;
+}
+__global__ void __launch_bounds__(128) reuse_slots_batch_kernel(const ReuseJob* __restrict__ J, const int* __restrict__ blk0, int n) {
+    __shared__ ReuseJob s;
+    const int j = batch_job(blk0, n);
+    block_copy(&s, &J[j]);
+    __syncthreads();
+    reuse_slots_body(s.a, s.w, s.p0, s.p1, (int)blockIdx.x - __ldg(&blk0[j]));
+}
+__global__ void __launch_bounds__(128) reuse_units_batch_kernel(const ReuseJob* __restrict__ J, const int* __restrict__ blk0, int n) {
+    __shared__ ReuseJob s;
+    const int j = batch_job(blk0, n);
+    block_copy(&s, &J[j]);
+    __syncthreads();
+    reuse_units_body(s.a, s.w, s.p0, s.p1, (int)blockIdx.x - __ldg(&blk0[j]));
+}
+// stage k of the persistent part: 0 forward shifts, 1 their visibility, 2 inverse-task emission,
+// 3 inverse shifts, 4 their visibility, 5 merge
+template <int kStage>
+__global__ void __launch_bounds__(128, 8) reuse_persist_batch_kernel(const ReuseJob* __restrict__ J, int n) {
+    __shared__ ReuseJob s;
+    for (int j = 0; j < n; ++j) {
+        __syncthreads();
+        block_copy(&s, &J[j]);
+        __syncthreads();
+        const ReuseArgs& a = s.a;
+        const WaveDev& w = s.w;
+        if constexpr (kStage == 0) shift_fwd_body<false>(a, w);
+        else if constexpr (kStage == 1)
+            vis_body(a.cur.g, w.rays, &w.counters[4], w.ray_cap, &w.counters[6], w.py, a.stats, 4, a.temporal ? -1 : 8);
+        else if constexpr (kStage == 2) emit_inv_body(a, w);
+        else if constexpr (kStage == 3) shift_inv_body<false>(a, w);
+        else if constexpr (kStage == 4)
+            vis_body(a.temporal ? a.prev.g : a.cur.g, w.rays, &w.counters[5], w.ray_cap, &w.counters[7], w.terms, a.stats, -1,
+                     a.temporal ? -1 : 9);
+        else reuse_merge_body(a, w);
+    }
+}
+
+cudaError_t launch_reuse_batch(const ReuseJob* J, int n, const int* blk_slots, int nblk_slots, const int* blk_units,
+                               int nblk_units, int persist_blocks, int vis_blocks, cudaStream_t s) {
+    note_launch(9);
+    reuse_reset_batch_kernel<<<(n * kWaveCounters + 127) / 128, 128, 0, s>>>(J, n);
+    reuse_slots_batch_kernel<<<nblk_slots, 128, 0, s>>>(J, blk_slots, n);
+    reuse_units_batch_kernel<<<nblk_units, 128, 0, s>>>(J, blk_units, n);
+    reuse_persist_batch_kernel<0><<<persist_blocks, 128, 0, s>>>(J, n);
+    reuse_persist_batch_kernel<1><<<vis_blocks, 128, 0, s>>>(J, n);
+    reuse_persist_batch_kernel<2><<<persist_blocks, 128, 0, s>>>(J, n);
+    reuse_persist_batch_kernel<3><<<persist_blocks, 128, 0, s>>>(J, n);
+    reuse_persist_batch_kernel<4><<<vis_blocks, 128, 0, s>>>(J, n);
+    reuse_persist_batch_kernel<5><<<persist_blocks, 128, 0, s>>>(J, n);
+    return cudaGetLastError();
 }
 
 // ev (optional): 7 events recorded around the stages (setup | forward shifts | their visibility and
