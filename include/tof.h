@@ -199,7 +199,11 @@ tof_status tof_view_destroy(tof_ctx* ctx, tof_view view);
 /* Render one time-gated frame (Sec. 3.2 stages (1)-(4)): G-buffer, initial path-tree RIS,
  * temporal reuse against the view's previous frame (params->temporal), params->n_spatial_iters
  * spatial passes, and the gated image out_image_dev[H*W] (row-major, float32) = f(y) W_y.
- * `frame` keys the random streams together with `seed`. */
+ * `frame` keys the random streams together with `seed`.  Without the ellipsoidal connection and
+ * the shrink mapping, views of up to 16M pixels x trees run the initial stage as a bounce
+ * wavefront whose scratch (about 240 MB for 512 x 512 x 4 trees at depth 4) the first such render
+ * allocates; it gives the same reservoirs as the single kernel that batches and the
+ * allocation-free form run. */
 tof_status tof_render_gated(tof_ctx* ctx, tof_scene scene, tof_view view, const tof_sensor* sensor,
                             const tof_emitter* emitter, const tof_gate* gate, const tof_params* params,
                             uint64_t seed, uint32_t frame, float* out_image_dev, void* stream);

@@ -22,6 +22,9 @@ cudaError_t launch_gbuffer(const GbufArgs& a, int tile_h, cudaStream_t s);
 cudaError_t launch_initial(const InitArgs& a, int tile_h, unsigned* err, cudaStream_t s);
 cudaError_t launch_initial_ell_wave(const InitArgs& a, const EllWaveDev& w, int tile_h, int place_blocks, int vis_blocks,
                                     cudaStream_t s);
+cudaError_t launch_initial_tree_wave(const InitArgs& a, const TreeWaveDev& w, int tile_h, int hit_blocks, int vis_blocks,
+                                     cudaStream_t s);
+cudaError_t tree_hit_blocks(int* out);
 cudaError_t ell_place_blocks(int* out);
 cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s);
 cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, int vis_blocks,
@@ -120,6 +123,9 @@ struct ViewH {
     EllWaveDev ell;
     size_t ell_slots = 0;        // pixels x trees x depth it holds
     void* ell_ptrs[9] = {nullptr};
+    TreeWaveDev tw;              // the gated initial stage's bounce wavefront
+    size_t tw_paths = 0;         // pixels x trees it holds
+    void* tw_ptrs[9] = {nullptr};
     tof_tuning tune = {16, 8, 0, TOF_LAYOUT_SOA};   // launch shapes and reservoir layout (autotuner)
 };
 
@@ -141,6 +147,7 @@ struct tof_ctx {
     float* d_scratch = nullptr;  // laser spot of plain PT renders
     int persist_blocks = 0;      // resident blocks of the persistent reuse kernels (all SMs)
     int ell_blocks = 0;          // resident blocks of the ellipsoidal placement kernel (all SMs)
+    int hit_blocks = 0;          // resident blocks of the wavefront closest-hit kernel (all SMs)
     int vis_blocks = 0;          // resident blocks of the visibility kernel (all SMs)
     int sms = 0;                 // streaming multiprocessors
     // batched rendering: stream pool, fork / join events, and the instantiated graph
@@ -595,6 +602,7 @@ tof_status tof_view_destroy(tof_ctx* c, tof_view id) {
     for (int k = 0; k < 3; ++k) { dfree(c, V.res[k].planes); dfree(c, V.res[k].M); dfree(c, V.res[k].occ); }
     for (void* p : V.wave_ptrs) dfree(c, p);
     for (void* p : V.ell_ptrs) dfree(c, p);
+    for (void* p : V.tw_ptrs) dfree(c, p);
     dfree(c, V.stats);
     for (int k = 0; k < 7; ++k)
         if (V.ev[k]) cudaEventDestroy(V.ev[k]);
@@ -641,6 +649,7 @@ static tof_status persist_init(tof_ctx* c) {
     if (c->persist_blocks) return TOF_OK;
     CK(reuse_persist_blocks(&c->persist_blocks, &c->vis_blocks));
     CK(ell_place_blocks(&c->ell_blocks));
+    CK(tree_hit_blocks(&c->hit_blocks));
     CK(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     return TOF_OK;
 }
@@ -671,6 +680,43 @@ static tof_status ensure_ell_wave(tof_ctx* c, ViewH& V, int nc, int depth) {
     for (int k = 0; k < 9; ++k) V.ell_ptrs[k] = ps[k];
     V.ell_slots = slots;
     return TOF_OK;
+}
+
+// (re)allocate the bounce wavefront of the gated initial stage for nc trees of the given depth: per
+// (pixel, tree) 24 B per vertex (record and candidate), 32 B of path state, 80 B of rays and hits
+// and a queued light segment (about 240 MB for 512 x 512, 4 trees, depth 4)
+static tof_status ensure_tree_wave(tof_ctx* c, ViewH& V, int nc, int depth) {
+    const size_t paths = (size_t)V.W * V.H * (size_t)nc, slots = paths * (size_t)depth;
+    if (V.tw_paths >= paths && V.tw.nc == nc && V.tw.depth == depth) return TOF_OK;
+    for (void*& p : V.tw_ptrs) { dfree(c, p); p = nullptr; }
+    V.tw_paths = 0;
+    TreeWaveDev& w = V.tw;
+    w.nc = nc; w.depth = depth;
+    TRY(dalloc(c, &w.vtx, sizeof(float4) * slots, "tree wave vertices"));
+    TRY(dalloc(c, &w.acand, sizeof(float2) * slots, "tree wave candidates"));
+    TRY(dalloc(c, &w.ps0, sizeof(float4) * paths, "tree wave path throughputs"));
+    TRY(dalloc(c, &w.ps1, sizeof(float4) * paths, "tree wave path vertices"));
+    TRY(dalloc(c, &w.rays[0], sizeof(float4) * 2 * paths, "tree wave rays"));
+    TRY(dalloc(c, &w.rays[1], sizeof(float4) * 2 * paths, "tree wave rays"));
+    TRY(dalloc(c, &w.hits, sizeof(float4) * paths, "tree wave hits"));
+    w.path_cap = (uint32_t)paths;
+    TRY(dalloc(c, &w.srays, sizeof(float4) * 2 * paths, "tree wave light segments"));
+    w.sray_cap = (uint32_t)paths;   // more segments than paths are traced in place
+    TRY(dalloc(c, &w.counters, sizeof(uint32_t) * kTreeWaveCounters, "tree wave counters"));
+    void* ps[9] = {w.vtx, w.acand, w.ps0, w.ps1, w.rays[0], w.rays[1], w.hits, w.srays, w.counters};
+    for (int k = 0; k < 9; ++k) V.tw_ptrs[k] = ps[k];
+    V.tw_paths = paths;
+    return TOF_OK;
+}
+
+// a direct gated render without the ellipsoidal connection or the shrink mapping runs its initial
+// stage as the bounce wavefront, except in the allocation-free form and beyond 16M (pixel, tree)
+// paths (~4 GB of scratch); batches (whose many small instances would pay for its 2 * depth + 1
+// launches each) and larger views keep the single kernel, which needs no scratch.  Both give the
+// same reservoirs.
+static bool use_tree_wave(const ViewH& V, int B, const tof_params* p, bool fixed) {
+    if (fixed || B > 0 || (p->flags & TOF_FLAG_ELLIPSOID) || p->shrink_k > 1.f) return false;
+    return (double)V.W * V.H * p->n_cand <= 16.0 * 1024.0 * 1024.0;
 }
 
 // the initial stage runs as the ellipsoidal wavefront: gated, ellipsoidal connection, not the
@@ -838,6 +884,15 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
         CK(launch_initial_ell_wave(ia, V.ell, V.tune.tile_h, eb, vb, s));
     } else if (g_rec) {
         g_rec->init.push_back(ia);   // staged batches hold gated views without those options only
+    } else if (!c->in_batch && use_tree_wave(V, B, params, fixed_wave != nullptr)) {
+        TRY(ensure_tree_wave(c, V, params->n_cand, params->depth));
+        TRY(persist_init(c));
+        int hb = c->hit_blocks, vb = c->vis_blocks;
+        if (V.tune.packet > 0) {
+            hb = std::min(hb, c->sms * V.tune.packet);
+            vb = std::min(vb, c->sms * V.tune.packet);
+        }
+        CK(launch_initial_tree_wave(ia, V.tw, V.tune.tile_h, hb, vb, s));
     } else {
         CK(launch_initial(ia, V.tune.tile_h, c->d_err, s));
     }

@@ -187,6 +187,26 @@ struct EllWaveDev {
     uint32_t* counters;     // requests, request fetch, segments, segment fetch
 };
 
+// wavefront of the gated initial stage without the ellipsoidal connection (tof_kernels.cu): the
+// path trees of all pixels advance one bounce per round -- a persistent closest-hit kernel with lane
+// refill traces the round's bounce rays, a shade kernel records each new vertex, queues its NEE
+// candidate's light segment for vis_kernel and samples the next bounce -- and the streaming RIS is
+// replayed per pixel in the trees' order.  Path p = pixel * nc + tree; slot (p, d) = p * depth + d - 1.
+constexpr int kTreeWaveCounters = 16;
+struct TreeWaveDev {
+    int nc, depth;
+    float4* vtx;            // per slot: (tri bits, b1, b2, area pdf) of vertex d
+    float2* acand;          // per slot: (f / p, tau) of the NEE candidate at vertex d (0: none; zeroed when occluded)
+    float4* ps0;            // per path: (throughput after the sampled bounce, prefix length, its pdf or -1 for a delta, 0)
+    float4* ps1;            // per path: (position of the vertex the bounce leaves, 0)
+    float4* rays[2];        // bounce rays towards vertex d in rays[d & 1]: (origin, tmax), (direction, path bits)
+    float4* hits;           // per ray of the round: (tri bits or kNoHit, b1, b2, t)
+    uint32_t path_cap;      // npix * nc: the most rays of a round
+    float4* srays;          // light segments of the NEE candidates (VisQ; target 2 * slot, the candidate's weight)
+    uint32_t sray_cap;
+    uint32_t* counters;     // [d]: rays towards vertex d, [8 + d]: their fetch counter, [14] light segments, [15] their fetch
+};
+
 // one instance's reuse pass in a batched launch (tof_render_batch): its arguments, its wavefront
 // scratch and its pixel range
 struct ReuseJob {

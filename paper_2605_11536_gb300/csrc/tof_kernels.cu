@@ -1,7 +1,8 @@
 // tof_kernels.cu -- per-frame kernels of the ToF ReSTIR hot path (sm_103a).
 //
 //   gbuffer_kernel   primary visibility, one jittered ray per pixel            (Sec. 3.2 setup)
-//   initial_kernel   path trees with NEE, streaming RIS into per-bin reservoirs (stage (1), Sec. 4.5)
+//   initial_kernel   path trees with NEE, streaming RIS into per-bin reservoirs (stage (1), Sec. 4.5);
+//                    direct gated renders run it as a bounce wavefront (tw_*_kernel)
 //   (temporal and spatial reuse, stages (2) and (3), are in tof_reuse.cu)
 //   splat_kernel     transient histogram H[px, b] = f(y_b) W_b                  (stage (4), Sec. 4.5)
 //   pt_kernel        plain gated / transient path tracing (the comparison of Sec. 6)
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(128, kEll ? 4 : 6) initial_kernel(const __grid
 //   ell_place_kernel   one thread per request: the walk, the ellipse clip, the candidate's weight;
 //                      its two visibility segments queued for vis_kernel (which zeroes the weight of
 //                      an occluded one)
-//   ell_select_kernel  the streaming RIS per pixel in the trees' order (tree-major; at vertex d the
+//   tree_select_kernel<true>  the streaming RIS per pixel in the trees' order (tree-major; at vertex d the
 //                      NEE candidate, then the ellipsoidal one), then the winner's record alone
 // --------------------------------------------------------------------------------------------
 struct RecordSink {
@@ -434,7 +435,9 @@ __global__ void __launch_bounds__(128, 6) ell_place_kernel(const __grid_constant
     }
 }
 
-__global__ void __launch_bounds__(128) ell_select_kernel(const __grid_constant__ InitArgs a, const EllWaveDev w) {
+// kEll = false: the tree wavefront (TreeWaveDev), whose trees are the only candidates
+template <bool kEll, class Wave>
+__global__ void __launch_bounds__(128) tree_select_kernel(const __grid_constant__ InitArgs a, const Wave w) {
     const FrameDev& F = a.F;
     int ix, iy;
     tile_pixel(a.tile_w, ix, iy);
@@ -464,7 +467,7 @@ __global__ void __launch_bounds__(128) ell_select_kernel(const __grid_constant__
                         if (u01(u.x) * S < wv) { sel_t = t; sel_k = d; sel_s = 0; sel_tau = ac.y; }
                     }
                 }
-                if (d < P.depth) {
+                if constexpr (kEll) if (d < P.depth) {
                     const float wv = invN * w.bw[base + d - 1];
                     if (wv > 0.f) {
                         uint4 u = philox((uint32_t)pix, F.frame, ((uint32_t)t << 8) | (uint32_t)(d + 1), P_ELL_RIS, P.seed);
@@ -489,7 +492,7 @@ __global__ void __launch_bounds__(128) ell_select_kernel(const __grid_constant__
                 T.cls[j] = mat_class(load_mat(g, T.v[j].mat));
                 T.pdfA[j] = v.w;
             }
-            if (sel_s) {
+            if constexpr (kEll) if (sel_s) {
                 float4 zb = w.bz[base + sel_k - 2];
                 T.v[sel_k] = surf_at(g, __float_as_int(zb.x), zb.y, zb.z);
                 T.cls[sel_k] = mat_class(load_mat(g, T.v[sel_k].mat));
@@ -507,6 +510,202 @@ __global__ void __launch_bounds__(128) ell_select_kernel(const __grid_constant__
         }
     }
     if (a.out) a.out[pix] = outv;
+}
+
+// --------------------------------------------------------------------------------------------
+// gated initial candidates as a bounce wavefront (TreeWaveDev): the same trees, candidates,
+// uniforms and order as initial_gated_kernel<false>, so the same reservoirs, with every lane of a
+// warp on the same step.  In the single kernel a warp's 32 path trees diverge in depth, in
+// traversal length and in whether a candidate needs a light segment, and most lanes idle:
+//   tw_start_kernel   one thread per path: vertex 1 (the G-buffer hit), its NEE candidate, the
+//                     first bounce
+//   tw_hit_kernel     per round, the closest hits of the round's bounce rays (persistent, each lane
+//                     refilled with the next ray between rounds of kHitSteps node visits)
+//   tw_shade_kernel   per round, one thread per hit: the vertex record, the NEE candidate (its light
+//                     segment queued for vis_kernel) and the next bounce
+//   vis_kernel        the light segments; an occluded one zeroes its candidate's weight
+//   tree_select_kernel<false>  the streaming RIS per pixel in the trees' order, then the winner's record
+// --------------------------------------------------------------------------------------------
+// vertex d of path p (tree t of pixel pix) at x, entered from direction wi with prefix throughput
+// beta and length len: its NEE candidate and, below the depth, the bounce towards vertex d + 1
+__device__ __forceinline__ void tw_vertex(const InitArgs& a, const TreeWaveDev& w, const Domain& D, uint32_t p, int pix, int t,
+                                          int d, const Surf& x, float3 wi, float beta, float len, VisQ& q) {
+    const FrameDev& F = a.F;
+    const ParamsDev& P = a.P;
+    const GeomDev& g = F.g;
+    const size_t slot = (size_t)p * (size_t)w.depth + (size_t)(d - 1);
+    Mat m = load_mat(g, x.mat);
+    const int kmin = (P.flags & 1u) ? 1 : 2;
+    if (d >= kmin && mat_class(m) != C_DELTA) {
+        float3 wl; float seg;
+        float lt = light_term(D, x, wl, seg);
+        float fs = lt > 0.f ? bsdf_f(m, x.n, wi, wl) : 0.f;
+        if (fs > 0.f) {
+            float tau = len + seg - D.o;
+            if (tau >= F.L0 && tau < F.L0 + F.dL) {
+                q.target = (uint32_t)(2 * slot);   // the float index of the candidate's weight
+                if (light_visible(D, g, x, P.ray_eps, &q)) w.acand[slot] = make_float2(beta * fs * lt, tau);
+            }
+        }
+    }
+    if (d >= P.depth) return;
+    uint4 u = philox((uint32_t)pix, F.frame, ((uint32_t)t << 8) | (uint32_t)d, P_BSDF, P.seed);
+    float3 wo; float pdf, thr; bool delta;
+    if (!bsdf_sample(m, x.n, wi, u01(u.x), u01(u.y), wo, pdf, thr, delta)) return;
+    const float3 o = offset_point(x.p, x.n, wo, P.ray_eps);
+    // each path sends at most one ray per round, so a round's rays never exceed the paths
+    const uint32_t i = reserve_coalesced(&w.counters[d + 1], 1u);
+    if (i >= w.path_cap) return;
+    float4* r = w.rays[(d + 1) & 1];
+    r[2 * (size_t)i] = make_float4(o.x, o.y, o.z, 3.0e38f);
+    r[2 * (size_t)i + 1] = make_float4(wo.x, wo.y, wo.z, __uint_as_float(p));
+    w.ps0[p] = make_float4(beta * thr, len, delta ? -1.0f : pdf, 0.f);
+    w.ps1[p] = make_float4(x.p.x, x.p.y, x.p.z, 0.f);
+}
+
+__global__ void __launch_bounds__(128) tw_start_kernel(const __grid_constant__ InitArgs a, const TreeWaveDev w) {
+    const FrameDev& F = a.F;
+    const uint32_t npath = (uint32_t)F.W * (uint32_t)F.H * (uint32_t)w.nc;
+    VisQ q;
+    q.rays = w.srays; q.counter = &w.counters[14]; q.cap = w.sray_cap; q.target = 0u;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < npath; p += gridDim.x * blockDim.x) {
+        const int pix = (int)(p / (uint32_t)w.nc), t = (int)(p % (uint32_t)w.nc);
+        float2* ac = w.acand + (size_t)p * w.depth;
+        for (int d = 0; d < w.depth; ++d) ac[d] = make_float2(0.f, 0.f);
+        float4 gb = F.gb[pix];
+        uint32_t tri = __float_as_uint(gb.x);
+        if (tri == kNoHit) continue;
+        Domain D = make_domain_hit(&F, true, (int)tri, gb.y, gb.z, gb.w, F.L0, F.dL);
+        tw_vertex(a, w, D, p, pix, t, 1, D.y1, dir_to(D.y1.p, D.x0), 1.0f, len3(D.x0 - D.y1.p), q);
+    }
+}
+
+// closest hits of the rays of one round: the loop of traverse<false> with the vis_kernel's lane
+// refill; hits[i] = (tri, b1, b2, t) of ray i, or kNoHit
+constexpr int kHitSteps = 32;
+__global__ void __launch_bounds__(128, 8) tw_hit_kernel(const GeomDev gref, const float4* __restrict__ rays, const uint32_t* counter,
+                                                     uint32_t cap, uint32_t* fetch, float4* __restrict__ hits) {
+    GeomDev g;
+    g.nodes = gref.nodes; g.leaf = gref.leaf; g.nt = gref.nt; g.err = gref.err;
+    const uint32_t n = min(*counter, cap);
+    const int lane = threadIdx.x & 31;
+    unsigned fault = 0u;
+    bool has = false, done = false, found = false;
+    float3 o = f3(0.f, 0.f, 0.f), d = o, id = o, ood = o;
+    float tmax = 0.f, best = 0.f, bb1 = 0.f, bb2 = 0.f;
+    int btri = 0;
+    uint32_t cur = 0;
+    int node = 0, sp = 0, budget = 0;
+    int stack[kStack];
+    while (true) {
+        const bool need = !has && !done;
+        const uint32_t want = __ballot_sync(0xFFFFFFFFu, need);
+        if (want) {
+            const int leader = __ffs(want) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(fetch, (uint32_t)__popc(want));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            if (need) {
+                const uint32_t i = base + (uint32_t)__popc(want & ((1u << lane) - 1u));
+                if (i < n) {
+                    float4 ra = rays[2 * (size_t)i], rb = rays[2 * (size_t)i + 1];
+                    o = f3(ra.x, ra.y, ra.z); d = f3(rb.x, rb.y, rb.z); tmax = ra.w;
+                    id = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+                    ood = f3(o.x * id.x, o.y * id.y, o.z * id.z);
+                    cur = i; found = false; best = tmax;
+                    node = 0; sp = 0; budget = g.nt + 64;
+                    has = true;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (__all_sync(0xFFFFFFFFu, done)) break;
+        bool fin = false;
+        for (int step = 0; step < kHitSteps && has; ++step) {
+            if (g.nt <= 1) {
+                float t, u, v; int orig;
+                if (g.nt == 1 && tri_test(g.leaf, 0, o, d, best, t, u, v, orig) && t < tmax) {
+                    found = true; best = t; btri = orig; bb1 = u; bb2 = v;
+                }
+                has = false; fin = true;
+                break;
+            }
+            if (--budget < 0) {
+                fault |= kErrVisitBudget;
+                has = false; fin = true;
+                break;
+            }
+            const float4* N = g.nodes + 4 * node;
+            float4 n0 = __ldg(N), n1 = __ldg(N + 1), n2 = __ldg(N + 2), n3 = __ldg(N + 3);
+            float a0 = n0.x * id.x - ood.x, a1 = n0.y * id.x - ood.x;
+            float b0 = n0.z * id.y - ood.y, c1y = n0.w * id.y - ood.y;
+            float c0 = n2.x * id.z - ood.z, c1 = n2.y * id.z - ood.z;
+            float lo0 = fmaxf(fmaxf(fminf(a0, a1), fminf(b0, c1y)), fmaxf(fminf(c0, c1), 0.f));
+            float hi0 = fminf(fminf(fmaxf(a0, a1), fmaxf(b0, c1y)), fminf(fmaxf(c0, c1), best));
+            float d0 = n1.x * id.x - ood.x, d1 = n1.y * id.x - ood.x;
+            float e0 = n1.z * id.y - ood.y, e1 = n1.w * id.y - ood.y;
+            float f0 = n2.z * id.z - ood.z, f1 = n2.w * id.z - ood.z;
+            float lo1 = fmaxf(fmaxf(fminf(d0, d1), fminf(e0, e1)), fmaxf(fminf(f0, f1), 0.f));
+            float hi1 = fminf(fminf(fmaxf(d0, d1), fmaxf(e0, e1)), fminf(fmaxf(f0, f1), best));
+            bool h0 = lo0 <= hi0, h1 = lo1 <= hi1;
+            int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
+            if (h0 && ch0 < 0) {
+                float t, u, v; int orig;
+                if (tri_test(g.leaf, ~ch0, o, d, best, t, u, v, orig) && (found || t < tmax) && closer(found, t, orig, best, btri)) {
+                    best = t; btri = orig; bb1 = u; bb2 = v; found = true;
+                }
+                h0 = false;
+            }
+            if (h1 && ch1 < 0) {
+                float t, u, v; int orig;
+                if (tri_test(g.leaf, ~ch1, o, d, best, t, u, v, orig) && (found || t < tmax) && closer(found, t, orig, best, btri)) {
+                    best = t; btri = orig; bb1 = u; bb2 = v; found = true;
+                }
+                h1 = false;
+            }
+            if (h0 && h1) {
+                int nearc = lo0 <= lo1 ? ch0 : ch1, farc = lo0 <= lo1 ? ch1 : ch0;
+                if (sp < kStack) stack[sp++] = farc;
+                else fault |= kErrStackOverflow;   // the far subtree is skipped: reported after the loop
+                node = nearc;
+            } else if (h0) {
+                node = ch0;
+            } else if (h1) {
+                node = ch1;
+            } else {
+                if (sp == 0) { has = false; fin = true; break; }
+                node = stack[--sp];
+            }
+        }
+        if (fin) hits[cur] = found ? make_float4(__int_as_float(btri), bb1, bb2, best) : make_float4(__uint_as_float(kNoHit), 0.f, 0.f, 0.f);
+    }
+    if (fault && g.err) atomicOr(g.err, fault);
+}
+
+// the hits of the round towards vertex d: one thread per ray
+__global__ void __launch_bounds__(128) tw_shade_kernel(const __grid_constant__ InitArgs a, const TreeWaveDev w, int d) {
+    const FrameDev& F = a.F;
+    const uint32_t n = min(w.counters[d], w.path_cap);
+    const float4* __restrict__ rays = w.rays[d & 1];
+    VisQ q;
+    q.rays = w.srays; q.counter = &w.counters[14]; q.cap = w.sray_cap; q.target = 0u;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 h = w.hits[i];
+        if (__float_as_uint(h.x) == kNoHit) continue;
+        const float4 rd = rays[2 * (size_t)i + 1];
+        const uint32_t p = __float_as_uint(rd.w);
+        const int pix = (int)(p / (uint32_t)w.nc), t = (int)(p % (uint32_t)w.nc);
+        const float4 s0 = w.ps0[p], s1 = w.ps1[p];
+        const Surf x = surf_at(F.g, __float_as_int(h.x), h.y, h.z);
+        const float3 prev = f3(s1.x, s1.y, s1.z), wo = f3(rd.x, rd.y, rd.z);
+        const float seg = len3(x.p - prev);
+        const float pdfA = s0.z < 0.f ? 1.0f : s0.z * fabsf(dot3(x.n, wo)) / (seg * seg);
+        w.vtx[(size_t)p * w.depth + (size_t)(d - 1)] = make_float4(h.x, h.y, h.z, pdfA);
+        const float4 gb = F.gb[pix];
+        Domain D = make_domain_hit(&F, true, (int)__float_as_uint(gb.x), gb.y, gb.z, gb.w, F.L0, F.dL);
+        tw_vertex(a, w, D, p, pix, t, d, x, dir_to(x.p, prev), s0.x, s0.y + seg, q);
+    }
 }
 
 // --------------------------------------------------------------------------------------------
@@ -764,7 +963,39 @@ cudaError_t launch_initial_ell_wave(const InitArgs& a, const EllWaveDev& w, int 
     e = launch_vis_queue(a.F.g, w.rays, &w.counters[2], w.ray_cap, &w.counters[3], w.bw, vis_blocks, s);
     if (e != cudaSuccess) return e;
     note_launch();
-    ell_select_kernel<<<grid, threads, 0, s>>>(a, w);
+    tree_select_kernel<true><<<grid, threads, 0, s>>>(a, w);
+    return cudaGetLastError();
+}
+// resident blocks of tw_hit_kernel on every SM (its lanes pull rays until the round's queue is empty)
+cudaError_t tree_hit_blocks(int* out) {
+    int dev = 0, sms = 0, b = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tw_hit_kernel, 128, 0);
+    *out = sms * (b > 0 ? b : 1);
+    return cudaGetLastError();
+}
+
+// depth - 1 rounds of (closest hits, shading) after the start, then the light segments and the
+// selection: 2 * depth + 1 kernels and one counter reset
+cudaError_t launch_initial_tree_wave(const InitArgs& a, const TreeWaveDev& w, int tile_h, int hit_blocks, int vis_blocks,
+                                     cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(w.counters, 0, kTreeWaveCounters * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const unsigned npath = (unsigned)a.F.W * (unsigned)a.F.H * (unsigned)w.nc;
+    note_launch();
+    tw_start_kernel<<<(npath + 127) / 128, 128, 0, s>>>(a, w);
+    for (int d = 2; d <= a.P.depth; ++d) {
+        note_launch(2);
+        tw_hit_kernel<<<hit_blocks, 128, 0, s>>>(a.F.g, w.rays[d & 1], &w.counters[d], w.path_cap, &w.counters[8 + d], w.hits);
+        tw_shade_kernel<<<hit_blocks, 128, 0, s>>>(a, w, d);
+    }
+    e = launch_vis_queue(a.F.g, w.srays, &w.counters[14], w.sray_cap, &w.counters[15], reinterpret_cast<float*>(w.acand),
+                         vis_blocks, s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    tree_select_kernel<false><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, w);
     return cudaGetLastError();
 }
 cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s) {
