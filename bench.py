@@ -67,14 +67,20 @@ BYTES = {
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# kernel as it is now, on the dynamic gated workload; None for kernels whose launches vary too much
-# from frame to frame for one capture to stand for the mean launch (task counts grow over the
-# first frames).  Must be retaken whenever the kernel changes.
+# kernels as they are now, on the dynamic gated workload (frame 5: the reuse passes' task counts
+# still grow over the first frames, so later launches move somewhat more).  Retaken whenever a
+# kernel changes; the hash below ties the figures to the sources they were captured on.
 ELL_WAVE = "ell_trees_kernel + ell_place_kernel + ell_select_kernel"
-NCU_TRAFFIC_SRC = "6131501fa04a"   # _src_hash() of the sources the figures below were captured on
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch (profiles/*_dynamic_gated_512.md)
-NCU_TRAFFIC = {"initial_gated_kernel<0>": 32.488960e6 + 31.040256e6, "reuse_merge_kernel": 109.030912e6 + 7.375872e6,
-               "shift_inv_kernel<0>": 167.921408e6 + 331.290880e6}
+TREE_WAVE = "tw_start_kernel + 3 x (tw_hit_kernel + tw_shade_kernel) + vis_kernel + tree_select_kernel"
+NCU_TRAFFIC_SRC = "6b447b41ab41"   # _src_hash() of the sources the figures below were captured on
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch (one stage for the initial wavefront),
+# spatial pass of frame 5 (profiles/launches_dynamic_gated_512.md, profiles/tree_wavefront_dynamic_gated_512.md)
+NCU_TRAFFIC = {TREE_WAVE: 231.60e6, "shift_inv_kernel<0>": 168.60e6 + 330.04e6, "shift_fwd_kernel<0>": 139.09e6 + 195.72e6,
+               "vis_kernel (inverse segments)": 77.64e6 + 1.95e6, "reuse_merge_kernel": 109.17e6 + 7.07e6}
+# L1 / L2 sector hit rates (%) and active lanes per warp instruction of the traversal-bound kernels,
+# from the same capture (the initial wavefront's first closest-hit round)
+NCU_HIT = {"tw_hit_kernel": [87.7, 71.4, 12.1], "shift_fwd_kernel<0>": [42.4, 44.4, 20.0],
+           "shift_inv_kernel<0>": [46.7, 63.0, 22.0], "vis_kernel": [95.2, 66.0, 13.4]}
 
 
 def _peaks():
@@ -1124,7 +1130,7 @@ def main():
             "spatial_inv_vis": BYTES["spatial_inv_vis"] * pf["spatial_inv_rays"],
             "spatial_merge": BYTES["spatial_merge"] * r["npix"]}
     ell, walk = int(bool(args.flags & 256)), int(bool(args.flags & 64))
-    kernels = {"gbuffer": "gbuffer_kernel", "initial": ELL_WAVE if ell else "initial_gated_kernel<0>", "temporal": "temporal pass (8 kernels)",
+    kernels = {"gbuffer": "gbuffer_kernel", "initial": ELL_WAVE if ell else TREE_WAVE, "temporal": "temporal pass (8 kernels)",
                "spatial_setup": "reuse_slots_kernel + reuse_units_kernel", "spatial_fwd_shift": "shift_fwd_kernel<%d>" % walk,
                "spatial_fwd_vis": "vis_kernel (forward segments) + emit_inv_kernel", "spatial_inv_shift": "shift_inv_kernel<%d>" % walk,
                "spatial_inv_vis": "vis_kernel (inverse segments)", "spatial_merge": "reuse_merge_kernel"}
@@ -1173,6 +1179,8 @@ def main():
             "roofline": roofline(dom),
             "clocks": {k: r["clocks"].get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "throughput": {k: (round(v, 1) if v else v) for k, v in thr.items()}}
+    if traffic:
+        line["throughput"]["ncu_l1_l2_hit_pct_lanes"] = NCU_HIT
     detail = {"headline": dict(line), "stage_ms": st, "kernel_rooflines": per_kernel, "src_hash": src,
               "newton": {"calls": r["stats"]["newton_calls"], "mean_iters": r["stats"]["newton_iters"] / max(1, r["stats"]["newton_calls"]),
                          "newton_sr": r["stats"]["newton_ok"] / max(1, r["stats"]["newton_calls"]),
