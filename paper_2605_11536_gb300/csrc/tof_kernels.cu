@@ -46,6 +46,17 @@ static __device__ __noinline__ bool ell_connect(const Domain& D, const ParamsDev
     return true;
 }
 
+// NEE at surface vertex x entered from direction wi: the BSDF value towards the light (0 when the
+// light does not reach x) and, through lt / seg, the light factor and the light segment's length.
+// Out of line, so that every caller -- the path-tree loop of the single kernels and the start and
+// shade kernels of the bounce wavefront -- evaluates it with the same code, and a candidate's
+// weight does not depend on which of them drew it.
+static __device__ __noinline__ float nee_eval(const Domain& D, const Surf& x, const Mat& m, float3 wi, float& lt, float& seg) {
+    float3 wl;
+    lt = light_term(D, x, wl, seg);
+    return lt > 0.f ? bsdf_f(m, x.n, wi, wl) : 0.f;
+}
+
 // One path tree; Sink(k, c, tau, T, strategy) receives each NEE candidate of length k in
 // [kmin, depth] whose tau lies in [glo, ghi) and whose light segment is unoccluded (c = f / p, no
 // gate; strategy 0).  With kEll every rough vertex x_d (d < depth) also places a vertex z by the
@@ -73,9 +84,8 @@ __device__ void trace_tree(const Domain& D, const ParamsDev& P, uint32_t px, uin
         float3 wi = dir_to(x.p, d == 1 ? D.x0 : T.v[d - 1].p);
         if constexpr (kEll == 2) sink.vertex(d, T, beta, len);
         if (d >= kmin && mat_class(m) != C_DELTA) {
-            float3 wl; float seg;
-            float lt = light_term(D, x, wl, seg);
-            float fs = lt > 0.f ? bsdf_f(m, x.n, wi, wl) : 0.f;
+            float lt, seg;
+            const float fs = nee_eval(D, x, m, wi, lt, seg);
             if (fs > 0.f) {
                 float tau = len + seg - D.o;
                 if (tau >= glo && tau < ghi && light_visible(D, g, x, P.ray_eps)) {
@@ -537,9 +547,8 @@ __device__ __forceinline__ void tw_vertex(const InitArgs& a, const TreeWaveDev& 
     Mat m = load_mat(g, x.mat);
     const int kmin = (P.flags & 1u) ? 1 : 2;
     if (d >= kmin && mat_class(m) != C_DELTA) {
-        float3 wl; float seg;
-        float lt = light_term(D, x, wl, seg);
-        float fs = lt > 0.f ? bsdf_f(m, x.n, wi, wl) : 0.f;
+        float lt, seg;
+        const float fs = nee_eval(D, x, m, wi, lt, seg);
         if (fs > 0.f) {
             float tau = len + seg - D.o;
             if (tau >= F.L0 && tau < F.L0 + F.dL) {
