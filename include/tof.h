@@ -276,7 +276,10 @@ tof_status tof_render_batch(tof_ctx* ctx, const tof_job* jobs, uint32_t n, void*
  *     reuse kernels (the width of the task packets in flight per SM), 1..8; 0 = as many as fit.
  *     Fewer leave room for other instances of a batch to run beside this one.
  *   layout: TOF_LAYOUT_SOA (six 16-byte planes, the default) or TOF_LAYOUT_AOS (each reservoir's
- *     96 bytes contiguous). */
+ *     96 bytes contiguous).
+ * In a staged batch (tof_render_batch) the per-pixel stages run blocks of 128 threads, tiles of
+ * tile_w x (128 / tile_w) pixels, and the persistent stages run as many blocks as fit: there only
+ * tile_w and the layout of a view's tuning apply. */
 #define TOF_LAYOUT_SOA 0
 #define TOF_LAYOUT_AOS 1
 typedef struct {
