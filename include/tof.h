@@ -202,8 +202,8 @@ tof_status tof_view_destroy(tof_ctx* ctx, tof_view view);
  * `frame` keys the random streams together with `seed`.  Without the ellipsoidal connection and
  * the shrink mapping, views of up to 16M pixels x trees run the initial stage as a bounce
  * wavefront whose scratch (about 240 MB for 512 x 512 x 4 trees at depth 4) the first such render
- * allocates; it gives the same reservoirs as the single kernel that batches and the
- * allocation-free form run. */
+ * allocates; it gives the same reservoirs as the single kernel that small instances of a batch
+ * and the allocation-free form run. */
 tof_status tof_render_gated(tof_ctx* ctx, tof_scene scene, tof_view view, const tof_sensor* sensor,
                             const tof_emitter* emitter, const tof_gate* gate, const tof_params* params,
                             uint64_t seed, uint32_t frame, float* out_image_dev, void* stream);
@@ -262,6 +262,9 @@ typedef struct {
  * with one kernel launch per stage over all of its instances (per-pixel stages map each block to its
  * instance; persistent stages pull every instance's tasks), ~20 launches per group whatever the
  * number of instances; the stage arguments travel as tables copied at the head of the graph.
+ * A gated instance of 256 x 256 pixels or more runs its initial stage as the bounce wavefront on its
+ * group's branch (its scratch is allocated before capture, like every view's); smaller ones are
+ * blocks of the batched single kernel.
  * Otherwise every job's stage kernels form their own branch (16 concurrent branches).  Jobs must
  * use distinct views.  Results equal those of rendering each job on its own.  Scratch for every view
  * is allocated before the graph is captured (first use of a view). */

@@ -635,9 +635,16 @@ tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[10]) {
 static bool g_no_marks = false;   // set while a batch is being captured (no profiling events)
 
 // staged batches: while set, render() records each stage's arguments instead of launching them
+// a recorded initial stage that a staged batch runs as the bounce wavefront
+struct WaveRec {
+    InitArgs a;
+    TreeWaveDev w;
+    int tile_h, hit_blocks, vis_blocks;
+};
 struct BatchRec {
     std::vector<GbufArgs> gbuf;
     std::vector<InitArgs> init;
+    std::vector<WaveRec> wave;
     std::vector<std::vector<ReuseJob>> pass;   // pass[q]: every instance's q-th reuse pass
     size_t q = 0;                              // the current instance's next pass
 };
@@ -709,14 +716,26 @@ static tof_status ensure_tree_wave(tof_ctx* c, ViewH& V, int nc, int depth) {
     return TOF_OK;
 }
 
-// a direct gated render without the ellipsoidal connection or the shrink mapping runs its initial
-// stage as the bounce wavefront, except in the allocation-free form and beyond 16M (pixel, tree)
-// paths (~4 GB of scratch); batches (whose many small instances would pay for its 2 * depth + 1
-// launches each) and larger views keep the single kernel, which needs no scratch.  Both give the
-// same reservoirs.
+// a gated render without the ellipsoidal connection or the shrink mapping runs its initial stage as
+// the bounce wavefront, except in the allocation-free form and beyond 16M (pixel, tree) paths (~4 GB
+// of scratch); in a batch only views of kBatchWaveMinPix pixels and more do (small instances would
+// pay for its 2 * depth + 1 launches each).  The rest keep the single kernel, which needs no scratch.
+// Both give the same reservoirs.
 static bool use_tree_wave(const ViewH& V, int B, const tof_params* p, bool fixed) {
     if (fixed || B > 0 || (p->flags & TOF_FLAG_ELLIPSOID) || p->shrink_k > 1.f) return false;
     return (double)V.W * V.H * p->n_cand <= 16.0 * 1024.0 * 1024.0;
+}
+
+// batches run a gated instance's initial stage as the bounce wavefront from this many pixels on:
+// smaller ones are cheaper as blocks of the batched single kernel than as 2 * depth + 1 launches
+constexpr size_t kBatchWaveMinPix = 256 * 256;
+static bool batch_tree_wave(const ViewH& V, const tof_job& J) {
+    return !J.transient && (size_t)V.W * V.H >= kBatchWaveMinPix && use_tree_wave(V, 0, &J.params, false);
+}
+// the view's wavefront scratch is allocated for these parameters (by prepare_job before a batch)
+static bool tree_wave_ready(const ViewH& V, const tof_params* p) {
+    return (size_t)V.W * V.H >= kBatchWaveMinPix && V.tw_paths >= (size_t)V.W * V.H * (size_t)p->n_cand &&
+           V.tw.nc == p->n_cand && V.tw.depth == p->depth;
 }
 
 // the initial stage runs as the ellipsoidal wavefront: gated, ellipsoidal connection, not the
@@ -868,6 +887,7 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
     auto out_of = [&](int st) { return bufs[(st + off) % 2]; };
     int stage = 0;
     InitArgs ia;
+    ia.wave = 0;
     ia.F = F; ia.dst = V.res[out_of(stage)].dev(); ia.P = P;
     ia.out = (stage == stages - 1 && B == 0) ? out : nullptr;
     ia.tile_w = V.tune.tile_w;
@@ -882,9 +902,9 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
             eb = std::min(eb, c->sms * V.tune.packet);
         }
         CK(launch_initial_ell_wave(ia, V.ell, V.tune.tile_h, eb, vb, s));
-    } else if (g_rec) {
-        g_rec->init.push_back(ia);   // staged batches hold gated views without those options only
-    } else if (!c->in_batch && use_tree_wave(V, B, params, fixed_wave != nullptr)) {
+    } else if (use_tree_wave(V, B, params, fixed_wave != nullptr) &&
+               (!(c->in_batch || g_rec) || tree_wave_ready(V, params))) {
+        // a batch uses the wavefront only where prepare_job allocated its scratch (large views)
         TRY(ensure_tree_wave(c, V, params->n_cand, params->depth));
         TRY(persist_init(c));
         int hb = c->hit_blocks, vb = c->vis_blocks;
@@ -892,7 +912,15 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
             hb = std::min(hb, c->sms * V.tune.packet);
             vb = std::min(vb, c->sms * V.tune.packet);
         }
-        CK(launch_initial_tree_wave(ia, V.tw, V.tune.tile_h, hb, vb, s));
+        if (g_rec) {
+            ia.wave = 1;
+            g_rec->init.push_back(ia);
+            g_rec->wave.push_back(WaveRec{ia, V.tw, V.tune.tile_h, hb, vb});
+        } else {
+            CK(launch_initial_tree_wave(ia, V.tw, V.tune.tile_h, hb, vb, s));
+        }
+    } else if (g_rec) {
+        g_rec->init.push_back(ia);   // staged batches hold gated views without those options only
     } else {
         CK(launch_initial(ia, V.tune.tile_h, c->d_err, s));
     }
@@ -1062,6 +1090,7 @@ static tof_status prepare_job(tof_ctx* c, const tof_job& J, uint32_t i) {
     if (J.transient && (J.params.flags & TOF_FLAG_BIN_REUSE) && S < 3) S = 3;
     TRY(ensure_wave(c, V, S, (int)cap));
     if (use_ell_wave(V, J.transient ? V.B : 0, &J.params, false)) TRY(ensure_ell_wave(c, V, J.params.n_cand, J.params.depth));
+    if (batch_tree_wave(V, J)) TRY(ensure_tree_wave(c, V, J.params.n_cand, J.params.depth));
     return TOF_OK;
 }
 
@@ -1166,6 +1195,10 @@ static cudaError_t staged_launch(tof_ctx* c, const StagedGroup& G, unsigned char
     if (nj == 0) return cudaSuccess;
     cudaError_t e = launch_gbuffer_batch((const GbufArgs*)(d + G.o_g), (const int*)(d + G.o_b), nj, G.bpix[nj], q);
     if (e == cudaSuccess) e = launch_initial_batch((const InitArgs*)(d + G.o_i), (const int*)(d + G.o_b), nj, G.bpix[nj], q);
+    for (size_t k = 0; k < G.rec.wave.size() && e == cudaSuccess; ++k) {
+        const WaveRec& w = G.rec.wave[k];
+        e = launch_initial_tree_wave(w.a, w.w, w.tile_h, w.hit_blocks, w.vis_blocks, q);
+    }
     for (size_t k = 0; k < G.rec.pass.size() && e == cudaSuccess; ++k)
         e = launch_reuse_batch((const ReuseJob*)(d + G.o_p[k]), (int)G.rec.pass[k].size(), (const int*)(d + G.o_s[k]),
                                G.bs[k].back(), (const int*)(d + G.o_u[k]), G.bu[k].back(), c->persist_blocks, c->vis_blocks, q);

@@ -130,6 +130,8 @@ struct InitArgs {
     ParamsDev P;
     float* out;              // gated image if this is the last stage (else null)
     int tile_w;
+    int wave;                // a staged batch runs this instance's initial stage as the bounce
+                             // wavefront: initial_gated_batch_kernel skips it
 };
 
 struct ReuseArgs {

@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(128, 6) initial_gated_batch_kernel(const InitA
     const int j = batch_job(blk0, n);
     block_copy(&s, &A[j]);
     __syncthreads();
+    if (s.wave) return;   // launched as the bounce wavefront after this kernel (the whole block)
     const int lb = (int)blockIdx.x - __ldg(&blk0[j]);
     const int tx = (s.F.W + s.tile_w - 1) / s.tile_w;
     initial_gated_body<false>(s, lb % tx, lb / tx);

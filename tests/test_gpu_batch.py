@@ -195,3 +195,52 @@ def test_full_size_instance_in_a_batch_matches_the_oracle():
         frac, relmse, _ = compare(imgs[f], o[f], oks[f])
         assert np.count_nonzero(o[f][oks[f]]) >= 30
         assert frac >= PARITY_FRAC and relmse <= PARITY_RELMSE, (f, frac, relmse)
+
+
+def test_large_instance_runs_the_wavefront_inside_a_batch_bit_for_bit():
+    """A 256x256 gated instance (large enough for its initial stage to run as the bounce wavefront
+    inside a staged batch) beside two small ones (the batched single kernel): over two frames, the
+    batched images equal the ones rendered one by one bit for bit."""
+    import torch
+    from paper_2605_11536_gb300 import tof
+    big = scenes.heightfield_spheres(W=256, H=256, frames=2, nx=60, ny=40, n_spheres=6)
+    box = scenes.box_icosphere(W=64, H=64, frames=2)
+    box.gates = [(5.0, 0.25)] * 2
+
+    def run(batched):
+        ctx = tof.tof_create(0)
+        imgs = []
+        try:
+            sb = tof.tof_scene_upload(ctx, big.verts, big.tris, big.tri_object, big.materials, big.object_material)
+            sx = tof.tof_scene_upload(ctx, box.verts, box.tris, box.tri_object, box.materials, box.object_material)
+            vb = tof.tof_view_create(ctx, sb, 256, 256, 0)
+            vx = [tof.tof_view_create(ctx, sx, 64, 64, 0) for _ in range(2)]
+            out = torch.zeros(256 * 256, device="cuda")
+            small = [torch.zeros(64 * 64, device="cuda") for _ in range(2)]
+            for f in range(2):
+                tof.tof_bvh_build(ctx, sb, big.xforms[f].reshape(-1), refit_only=0)
+                tof.tof_bvh_build(ctx, sx, box.xforms[f].reshape(-1), refit_only=0)
+                if batched:
+                    jobs = [tof.job(sb, vb, big.sensors[f], big.emitters[f], big.params, 7, f, out.data_ptr(),
+                                    gate=big.gates[f])]
+                    for k in range(2):
+                        jobs.append(tof.job(sx, vx[k], box.sensors[f], box.emitters[f], box.params, 40 + k, f,
+                                            small[k].data_ptr(), gate=box.gates[f]))
+                    tof.tof_render_batch(ctx, jobs)
+                else:
+                    tof.tof_render_gated(ctx, sb, vb, big.sensors[f], big.emitters[f], big.gates[f], big.params, 7, f,
+                                         out.data_ptr())
+                    for k in range(2):
+                        tof.tof_render_gated(ctx, sx, vx[k], box.sensors[f], box.emitters[f], box.gates[f], box.params,
+                                             40 + k, f, small[k].data_ptr())
+                tof.tof_sync(ctx)
+                imgs.append([out.cpu().numpy()] + [s.cpu().numpy() for s in small])
+        finally:
+            tof.tof_destroy(ctx)
+        return imgs
+
+    ind, bat = run(False), run(True)
+    for f in range(2):
+        for i in range(3):
+            assert np.count_nonzero(ind[f][i]) > 20, (f, i)
+            assert np.array_equal(ind[f][i], bat[f][i]), (f, i, int(np.count_nonzero(ind[f][i] != bat[f][i])))
