@@ -129,9 +129,9 @@ typedef struct { float t0, width; int32_t B; } tof_bins;
  * combined by the balance heuristic over the two densities of the last vertex (the paper's MIS
  * between direct and ellipsoidal connection), so the estimate stays unbiased.  Excludes the shrink
  * mapping.  Gated views run this stage as a wavefront whose scratch the first such render allocates
- * in the view (about 112 B per pixel x tree x vertex: 450 MB for 512 x 512, 4 trees, depth 4; views
- * above 32M such slots, transient views and tof_render_gated_noalloc use a single kernel that needs
- * none and gives the same result). */
+ * in the view (about 112 B per pixel x tree x vertex: 450 MB for 512 x 512, 4 trees, depth 4, plus
+ * the bounce wavefront's for its path trees; views above 32M such slots, transient views and
+ * tof_render_gated_noalloc use a single kernel that needs none and gives the same result). */
 #define TOF_FLAG_ELLIPSOID 256u
 
 /* reuse / sampling parameters (Sec. 6: path depth, candidates, neighbours, radius, M-cap;

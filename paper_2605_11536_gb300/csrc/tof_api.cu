@@ -25,6 +25,8 @@ cudaError_t launch_initial_ell_wave(const InitArgs& a, const EllWaveDev& w, int 
 cudaError_t launch_initial_tree_wave(const InitArgs& a, const TreeWaveDev& w, int tile_h, int hit_blocks, int vis_blocks,
                                      cudaStream_t s);
 cudaError_t tree_hit_blocks(int* out);
+cudaError_t launch_initial_ell_tree_wave(const InitArgs& a, const TreeWaveDev& tw, const EllWaveDev& ell, int tile_h, int hit_blocks,
+                                         int place_blocks, int vis_blocks, cudaStream_t s);
 cudaError_t ell_place_blocks(int* out);
 cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s);
 cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, int vis_blocks,
@@ -729,8 +731,10 @@ static bool use_tree_wave(const ViewH& V, int B, const tof_params* p, bool fixed
 // batches run a gated instance's initial stage as the bounce wavefront from this many pixels on:
 // smaller ones are cheaper as blocks of the batched single kernel than as 2 * depth + 1 launches
 constexpr size_t kBatchWaveMinPix = 256 * 256;
+static bool use_ell_wave(const ViewH& V, int B, const tof_params* p, bool fixed);
 static bool batch_tree_wave(const ViewH& V, const tof_job& J) {
-    return !J.transient && (size_t)V.W * V.H >= kBatchWaveMinPix && use_tree_wave(V, 0, &J.params, false);
+    return !J.transient && (size_t)V.W * V.H >= kBatchWaveMinPix &&
+           (use_tree_wave(V, 0, &J.params, false) || use_ell_wave(V, 0, &J.params, false));
 }
 // the view's wavefront scratch is allocated for these parameters (by prepare_job before a batch)
 static bool tree_wave_ready(const ViewH& V, const tof_params* p) {
@@ -901,7 +905,15 @@ static tof_status render(tof_ctx* c, tof_scene scene, tof_view vid, const tof_se
             vb = std::min(vb, c->sms * V.tune.packet);
             eb = std::min(eb, c->sms * V.tune.packet);
         }
-        CK(launch_initial_ell_wave(ia, V.ell, V.tune.tile_h, eb, vb, s));
+        if (!(c->in_batch || g_rec) || tree_wave_ready(V, params)) {
+            // its path trees as bounce rounds (a batch: where prepare_job allocated that scratch)
+            TRY(ensure_tree_wave(c, V, params->n_cand, params->depth));
+            int hb = c->hit_blocks;
+            if (V.tune.packet > 0) hb = std::min(hb, c->sms * V.tune.packet);
+            CK(launch_initial_ell_tree_wave(ia, V.tw, V.ell, V.tune.tile_h, hb, eb, vb, s));
+        } else {
+            CK(launch_initial_ell_wave(ia, V.ell, V.tune.tile_h, eb, vb, s));
+        }
     } else if (use_tree_wave(V, B, params, fixed_wave != nullptr) &&
                (!(c->in_batch || g_rec) || tree_wave_ready(V, params))) {
         // a batch uses the wavefront only where prepare_job allocated its scratch (large views)

@@ -538,14 +538,22 @@ __global__ void __launch_bounds__(128) tree_select_kernel(const __grid_constant_
 //   tree_select_kernel<false>  the streaming RIS per pixel in the trees' order, then the winner's record
 // --------------------------------------------------------------------------------------------
 // vertex d of path p (tree t of pixel pix) at x, entered from direction wi with prefix throughput
-// beta and length len: its NEE candidate and, below the depth, the bounce towards vertex d + 1
-__device__ __forceinline__ void tw_vertex(const InitArgs& a, const TreeWaveDev& w, const Domain& D, uint32_t p, int pix, int t,
-                                          int d, const Surf& x, float3 wi, float beta, float len, VisQ& q) {
+// beta and length len (area density pdfA, prefix length len_prev at vertex d - 1): its NEE candidate
+// and, below the depth, the bounce towards vertex d + 1.  kEll (the ellipsoidal connection, the tree
+// part of its wavefront; w.vtx / w.acand are then the EllWaveDev tables): the vertex's throughput
+// and length are recorded, the NEE candidate takes the balance-heuristic factor against the
+// ellipsoidal vertex placed from x_{d-1}, and a vertex that can place one is queued as a request --
+// the steps of trace_tree<2> with its recording sink.
+template <bool kEll>
+__device__ __forceinline__ void tw_vertex(const InitArgs& a, const TreeWaveDev& w, const EllWaveDev& e, const Domain& D, uint32_t p,
+                                          int pix, int t, int d, const Surf& x, float3 wi, float beta, float len, float pdfA,
+                                          float len_prev, VisQ& q) {
     const FrameDev& F = a.F;
     const ParamsDev& P = a.P;
     const GeomDev& g = F.g;
     const size_t slot = (size_t)p * (size_t)w.depth + (size_t)(d - 1);
     Mat m = load_mat(g, x.mat);
+    if constexpr (kEll) e.vtx2[slot] = make_float2(beta, len);
     const int kmin = (P.flags & 1u) ? 1 : 2;
     if (d >= kmin && mat_class(m) != C_DELTA) {
         float lt, seg;
@@ -553,9 +561,27 @@ __device__ __forceinline__ void tw_vertex(const InitArgs& a, const TreeWaveDev& 
         if (fs > 0.f) {
             float tau = len + seg - D.o;
             if (tau >= F.L0 && tau < F.L0 + F.dL) {
+                float c = beta * fs * lt;
+                if constexpr (kEll) {
+                    if (d > 1) {
+                        // the ellipsoidal connection was available at x_{d-1} when that vertex was rough
+                        const float4 pv = w.vtx[slot - 1];
+                        const Surf xp = surf_at(g, __float_as_int(pv.x), pv.y, pv.z);
+                        if (mat_class(load_mat(g, xp.mat)) != C_DELTA && D.light.kind != 0) {
+                            const float pe = ell_pdf(D, xp, len_prev, F.L0, F.L0 + F.dL, x);
+                            c *= pdfA / (pdfA + pe);
+                        }
+                    }
+                }
                 q.target = (uint32_t)(2 * slot);   // the float index of the candidate's weight
-                if (light_visible(D, g, x, P.ray_eps, &q)) w.acand[slot] = make_float2(beta * fs * lt, tau);
+                if (light_visible(D, g, x, P.ray_eps, &q)) w.acand[slot] = make_float2(c, tau);
             }
+        }
+    }
+    if constexpr (kEll) {
+        if (d < P.depth && mat_class(m) != C_DELTA && D.light.kind != 0) {
+            const uint32_t i = reserve_coalesced(&e.counters[0], 1u);
+            if (i < e.req_cap) e.req[i] = (uint32_t)slot;
         }
     }
     if (d >= P.depth) return;
@@ -573,7 +599,8 @@ __device__ __forceinline__ void tw_vertex(const InitArgs& a, const TreeWaveDev& 
     w.ps1[p] = make_float4(x.p.x, x.p.y, x.p.z, 0.f);
 }
 
-__global__ void __launch_bounds__(128) tw_start_kernel(const __grid_constant__ InitArgs a, const TreeWaveDev w) {
+template <bool kEll>
+__global__ void __launch_bounds__(128) tw_start_kernel(const __grid_constant__ InitArgs a, const TreeWaveDev w, const EllWaveDev e) {
     const FrameDev& F = a.F;
     const uint32_t npath = (uint32_t)F.W * (uint32_t)F.H * (uint32_t)w.nc;
     VisQ q;
@@ -582,11 +609,14 @@ __global__ void __launch_bounds__(128) tw_start_kernel(const __grid_constant__ I
         const int pix = (int)(p / (uint32_t)w.nc), t = (int)(p % (uint32_t)w.nc);
         float2* ac = w.acand + (size_t)p * w.depth;
         for (int d = 0; d < w.depth; ++d) ac[d] = make_float2(0.f, 0.f);
+        if constexpr (kEll)
+            for (int d = 0; d < w.depth; ++d) e.bw[(size_t)p * w.depth + d] = 0.f;
         float4 gb = F.gb[pix];
         uint32_t tri = __float_as_uint(gb.x);
         if (tri == kNoHit) continue;
         Domain D = make_domain_hit(&F, true, (int)tri, gb.y, gb.z, gb.w, F.L0, F.dL);
-        tw_vertex(a, w, D, p, pix, t, 1, D.y1, dir_to(D.y1.p, D.x0), 1.0f, len3(D.x0 - D.y1.p), q);
+        if constexpr (kEll) w.vtx[(size_t)p * w.depth] = make_float4(__int_as_float(D.y1.tri), D.y1.b1, D.y1.b2, 1.0f);
+        tw_vertex<kEll>(a, w, e, D, p, pix, t, 1, D.y1, dir_to(D.y1.p, D.x0), 1.0f, len3(D.x0 - D.y1.p), 1.0f, 0.f, q);
     }
 }
 
@@ -694,7 +724,9 @@ __global__ void __launch_bounds__(128, 8) tw_hit_kernel(const GeomDev gref, cons
 }
 
 // the hits of the round towards vertex d: one thread per ray
-__global__ void __launch_bounds__(128) tw_shade_kernel(const __grid_constant__ InitArgs a, const TreeWaveDev w, int d) {
+template <bool kEll>
+__global__ void __launch_bounds__(128) tw_shade_kernel(const __grid_constant__ InitArgs a, const TreeWaveDev w, const EllWaveDev e,
+                                                       int d) {
     const FrameDev& F = a.F;
     const uint32_t n = min(w.counters[d], w.path_cap);
     const float4* __restrict__ rays = w.rays[d & 1];
@@ -714,7 +746,7 @@ __global__ void __launch_bounds__(128) tw_shade_kernel(const __grid_constant__ I
         w.vtx[(size_t)p * w.depth + (size_t)(d - 1)] = make_float4(h.x, h.y, h.z, pdfA);
         const float4 gb = F.gb[pix];
         Domain D = make_domain_hit(&F, true, (int)__float_as_uint(gb.x), gb.y, gb.z, gb.w, F.L0, F.dL);
-        tw_vertex(a, w, D, p, pix, t, d, x, dir_to(x.p, prev), s0.x, s0.y + seg, q);
+        tw_vertex<kEll>(a, w, e, D, p, pix, t, d, x, dir_to(x.p, prev), s0.x, s0.y + seg, pdfA, s0.y, q);
     }
 }
 
@@ -994,18 +1026,51 @@ cudaError_t launch_initial_tree_wave(const InitArgs& a, const TreeWaveDev& w, in
     cudaError_t e = cudaMemsetAsync(w.counters, 0, kTreeWaveCounters * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const unsigned npath = (unsigned)a.F.W * (unsigned)a.F.H * (unsigned)w.nc;
+    const EllWaveDev none = {};
     note_launch();
-    tw_start_kernel<<<(npath + 127) / 128, 128, 0, s>>>(a, w);
+    tw_start_kernel<false><<<(npath + 127) / 128, 128, 0, s>>>(a, w, none);
     for (int d = 2; d <= a.P.depth; ++d) {
         note_launch(2);
         tw_hit_kernel<<<hit_blocks, 128, 0, s>>>(a.F.g, w.rays[d & 1], &w.counters[d], w.path_cap, &w.counters[8 + d], w.hits);
-        tw_shade_kernel<<<hit_blocks, 128, 0, s>>>(a, w, d);
+        tw_shade_kernel<false><<<hit_blocks, 128, 0, s>>>(a, w, none, d);
     }
     e = launch_vis_queue(a.F.g, w.srays, &w.counters[14], w.sray_cap, &w.counters[15], reinterpret_cast<float*>(w.acand),
                          vis_blocks, s);
     if (e != cudaSuccess) return e;
     note_launch();
     tree_select_kernel<false><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, w);
+    return cudaGetLastError();
+}
+
+// the ellipsoidal connection's initial wavefront with its path trees as bounce rounds: the tree
+// kernels write the EllWaveDev vertex, throughput, candidate and request tables (the same slots
+// as ell_trees_kernel), then placement, the two visibility queues and the selection as in
+// launch_initial_ell_wave
+cudaError_t launch_initial_ell_tree_wave(const InitArgs& a, const TreeWaveDev& tw, const EllWaveDev& ell, int tile_h, int hit_blocks,
+                                         int place_blocks, int vis_blocks, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(tw.counters, 0, kTreeWaveCounters * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ell.counters, 0, 4 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    TreeWaveDev w = tw;
+    w.vtx = ell.vtx;
+    w.acand = ell.acand;
+    const unsigned npath = (unsigned)a.F.W * (unsigned)a.F.H * (unsigned)w.nc;
+    note_launch();
+    tw_start_kernel<true><<<(npath + 127) / 128, 128, 0, s>>>(a, w, ell);
+    for (int d = 2; d <= a.P.depth; ++d) {
+        note_launch(2);
+        tw_hit_kernel<<<hit_blocks, 128, 0, s>>>(a.F.g, w.rays[d & 1], &w.counters[d], w.path_cap, &w.counters[8 + d], w.hits);
+        tw_shade_kernel<true><<<hit_blocks, 128, 0, s>>>(a, w, ell, d);
+    }
+    e = launch_vis_queue(a.F.g, w.srays, &w.counters[14], w.sray_cap, &w.counters[15], reinterpret_cast<float*>(w.acand),
+                         vis_blocks, s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    ell_place_kernel<<<place_blocks, 128, 0, s>>>(a, ell);
+    e = launch_vis_queue(a.F.g, ell.rays, &ell.counters[2], ell.ray_cap, &ell.counters[3], ell.bw, vis_blocks, s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    tree_select_kernel<true><<<tile_grid(a.F.W, a.F.H, a.tile_w, tile_h), a.tile_w * tile_h, 0, s>>>(a, ell);
     return cudaGetLastError();
 }
 cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s) {
