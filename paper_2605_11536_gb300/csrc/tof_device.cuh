@@ -333,6 +333,19 @@ static __device__ __forceinline__ uint32_t reserve_coalesced(uint32_t* counter, 
     return base + prefix;
 }
 
+// one slot for each lane converged here: a ballot, one atomic by the lowest lane, and each lane's
+// rank among the converged ones -- the slots reserve_coalesced(counter, 1) gives, in the same order,
+// without its loop over the warp
+static __device__ __forceinline__ uint32_t reserve_one(uint32_t* counter) {
+    const uint32_t mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
+}
+
 // visible(), or the same segment queued for vis_kernel (returns true: not known to be occluded)
 static __device__ bool visible_q(const VisQ* q, const GeomDev& g, float3 a, float3 an, float3 b, const float3* bn, float eps) {
     if (!q) return visible(g, a, an, b, bn, eps);
@@ -342,7 +355,7 @@ static __device__ bool visible_q(const VisQ* q, const GeomDev& g, float3 a, floa
     float dist = len3(d);
     if (!(dist > 0.f)) return true;
     d = d * (1.0f / dist);
-    uint32_t i = reserve_coalesced(q->counter, 1u);
+    uint32_t i = reserve_one(q->counter);
     if (i >= q->cap) {
         int tri; float b1, b2, t;
         return !traverse<true>(g, ao, d, dist, tri, b1, b2, t);

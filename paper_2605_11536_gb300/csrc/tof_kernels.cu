@@ -382,7 +382,7 @@ struct RecordSink {
         w->vtx2[base + d - 1] = make_float2(beta, len);
     }
     __device__ void request(int d) {
-        const uint32_t i = reserve_coalesced(&w->counters[0], 1u);
+        const uint32_t i = reserve_one(&w->counters[0]);
         if (i < w->req_cap) w->req[i] = (uint32_t)(base + d - 1);
     }
 };
@@ -580,7 +580,7 @@ __device__ __forceinline__ void tw_vertex(const InitArgs& a, const TreeWaveDev& 
     }
     if constexpr (kEll) {
         if (d < P.depth && mat_class(m) != C_DELTA && D.light.kind != 0) {
-            const uint32_t i = reserve_coalesced(&e.counters[0], 1u);
+            const uint32_t i = reserve_one(&e.counters[0]);
             if (i < e.req_cap) e.req[i] = (uint32_t)slot;
         }
     }
@@ -590,7 +590,7 @@ __device__ __forceinline__ void tw_vertex(const InitArgs& a, const TreeWaveDev& 
     if (!bsdf_sample(m, x.n, wi, u01(u.x), u01(u.y), wo, pdf, thr, delta)) return;
     const float3 o = offset_point(x.p, x.n, wo, P.ray_eps);
     // each path sends at most one ray per round, so a round's rays never exceed the paths
-    const uint32_t i = reserve_coalesced(&w.counters[d + 1], 1u);
+    const uint32_t i = reserve_one(&w.counters[d + 1]);
     if (i >= w.path_cap) return;
     float4* r = w.rays[(d + 1) & 1];
     r[2 * (size_t)i] = make_float4(o.x, o.y, o.z, 3.0e38f);
