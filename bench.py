@@ -72,15 +72,15 @@ BYTES = {
 # kernel changes; the hash below ties the figures to the sources they were captured on.
 ELL_WAVE = "ell_trees_kernel + ell_place_kernel + ell_select_kernel"
 TREE_WAVE = "tw_start_kernel + 3 x (tw_hit_kernel + tw_shade_kernel) + vis_kernel + tree_select_kernel"
-NCU_TRAFFIC_SRC = "7c6389051302"   # _src_hash() of the sources the figures below were captured on
+NCU_TRAFFIC_SRC = "c98ca3479467"   # _src_hash() of the sources the figures below were captured on
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (one stage for the initial wavefront),
 # spatial pass of frame 5 (profiles/launches_dynamic_gated_512.md, profiles/tree_wavefront_dynamic_gated_512.md)
-NCU_TRAFFIC = {TREE_WAVE: 304.53e6, "shift_inv_kernel<0>": 168.69e6 + 330.64e6, "shift_fwd_kernel<0>": 138.11e6 + 195.12e6,
-               "vis_kernel (inverse segments)": 77.65e6 + 1.73e6, "reuse_merge_kernel": 109.08e6 + 7.03e6}
+NCU_TRAFFIC = {TREE_WAVE: 306.13e6, "shift_inv_kernel<0>": 171.21e6 + 327.69e6, "shift_fwd_kernel<0>": 140.50e6 + 195.46e6,
+               "vis_kernel (inverse segments)": 77.65e6 + 1.75e6, "reuse_merge_kernel": 109.27e6 + 6.98e6}
 # L1 / L2 sector hit rates (%) and active lanes per warp instruction of the traversal-bound kernels,
 # from the same capture (the initial wavefront's first closest-hit round)
-NCU_HIT = {"tw_hit_kernel": [87.7, 71.4, 12.1], "shift_fwd_kernel<0>": [42.4, 44.4, 20.0],
-           "shift_inv_kernel<0>": [46.7, 63.0, 22.0], "vis_kernel": [95.2, 65.8, 13.4]}
+NCU_HIT = {"tw_hit_kernel": [87.7, 71.5, 12.1], "shift_fwd_kernel<0>": [42.2, 44.4, 20.4],
+           "shift_inv_kernel<0>": [46.6, 63.2, 22.5], "vis_kernel": [95.2, 65.8, 13.4]}
 
 
 def _peaks():
