@@ -30,7 +30,7 @@ cudaError_t launch_initial_ell_tree_wave(const InitArgs& a, const TreeWaveDev& t
 cudaError_t ell_place_blocks(int* out);
 cudaError_t launch_initial_shrink(const InitArgs& a, int tile_h, cudaStream_t s);
 cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, int vis_blocks,
-                              cudaEvent_t* ev, cudaStream_t s);
+                              cudaEvent_t* ev, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join);
 cudaError_t reuse_persist_blocks(int* out, int* vis_out);
 cudaError_t launch_splat(const SplatArgs& a, cudaStream_t s);
 cudaError_t launch_pt(const PtArgs& a, cudaStream_t s);
@@ -121,6 +121,12 @@ struct ViewH {
     std::vector<cudaEvent_t> kev;   // kReuseEvents events per timed spatial launch group
     size_t kev_used = 0;
     void* wave_ptrs[12] = {nullptr};
+    // direct renders: the second visibility queue, stream and fork / join events that let the
+    // canonical inverse shifts run beside the forward shifts (created on first use)
+    float4* rays2 = nullptr;
+    uint32_t ray2_cap = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     // the ellipsoidal connection's initial wavefront (gated views; sized on first use)
     EllWaveDev ell;
     size_t ell_slots = 0;        // pixels x trees x depth it holds
@@ -381,6 +387,8 @@ static tof_status noalloc_wave(tof_ctx* c, WaveDev* w) {
     w->terms = (float*)(b + kNA_terms);
     w->rays = (float4*)(b + kNA_rays);
     w->ray_cap = (uint32_t)kNoAllocRays;
+    w->rays2 = nullptr;
+    w->ray2_cap = 0;
     w->counters = (uint32_t*)(b + kNA_counters);
     return TOF_OK;
 }
@@ -605,6 +613,10 @@ tof_status tof_view_destroy(tof_ctx* c, tof_view id) {
     for (void* p : V.wave_ptrs) dfree(c, p);
     for (void* p : V.ell_ptrs) dfree(c, p);
     for (void* p : V.tw_ptrs) dfree(c, p);
+    dfree(c, V.rays2);
+    if (V.side) cudaStreamDestroy(V.side);
+    if (V.side_fork) cudaEventDestroy(V.side_fork);
+    if (V.side_join) cudaEventDestroy(V.side_join);
     dfree(c, V.stats);
     for (int k = 0; k < 7; ++k)
         if (V.ev[k]) cudaEventDestroy(V.ev[k]);
@@ -636,7 +648,6 @@ tof_status tof_view_stats(tof_ctx* c, tof_view id, double out[10]) {
 
 static bool g_no_marks = false;   // set while a batch is being captured (no profiling events)
 
-// staged batches: while set, render() records each stage's arguments instead of launching them
 // a recorded initial stage that a staged batch runs as the bounce wavefront
 struct WaveRec {
     InitArgs a;
@@ -650,6 +661,7 @@ struct BatchRec {
     std::vector<std::vector<ReuseJob>> pass;   // pass[q]: every instance's q-th reuse pass
     size_t q = 0;                              // the current instance's next pass
 };
+// staged batches: while set, render() records each stage's arguments instead of launching them
 static BatchRec* g_rec = nullptr;
 constexpr int kReuseEvents = 7;   // events around the kernels of one reuse launch group
 
@@ -784,6 +796,20 @@ static tof_status ensure_wave(tof_ctx* c, ViewH& V, int S, int cap) {
     return TOF_OK;
 }
 
+// the second visibility queue of a view's direct renders (the temporal pass's canonical inverse
+// shifts, at most one per pixel and bin: 4 segments per pixel, beyond which they are traced in
+// place), its stream and events
+static tof_status ensure_side(tof_ctx* c, ViewH& V) {
+    if (V.rays2) return TOF_OK;
+    const size_t cap = (size_t)V.W * V.H * 4 + ((size_t)1 << 20);
+    if (!V.side) CK(cudaStreamCreateWithFlags(&V.side, cudaStreamNonBlocking));
+    if (!V.side_fork) CK(cudaEventCreateWithFlags(&V.side_fork, cudaEventDisableTiming));
+    if (!V.side_join) CK(cudaEventCreateWithFlags(&V.side_join, cudaEventDisableTiming));
+    TRY(dalloc(c, &V.rays2, sizeof(float4) * 2 * cap, "second visibility queue"));
+    V.ray2_cap = (uint32_t)cap;
+    return TOF_OK;
+}
+
 // one reuse pass as a wavefront; transient passes run in pixel chunks so that a chunk's merge
 // units (at most B per pixel) never exceed the scratch capacity
 static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const WaveDev* fixed, cudaStream_t s) {
@@ -797,6 +823,13 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
     TRY(persist_init(c));
     WaveDev w = fixed ? *fixed : V.wave;
     w.slots = S;
+    // the temporal pass of a direct render runs the canonical inverse shifts beside the forward
+    // shifts: both are small there and wait on a few long chains (0.52 -> 0.39 ms per 512 x 512
+    // frame); in a spatial pass both fill the GPU and beside each other they were slower
+    const bool beside = ra.temporal && !fixed && !g_rec && !c->in_batch;
+    if (beside) TRY(ensure_side(c, V));
+    w.rays2 = beside ? V.rays2 : nullptr;
+    w.ray2_cap = beside ? V.ray2_cap : 0u;
     if (!fixed) w.cap_units = V.wave_cap;
     size_t chunk = V.B > 0 ? (size_t)V.wave_cap / Bn : npix;
     if (chunk < 1) chunk = 1;
@@ -824,7 +857,7 @@ static tof_status reuse_pass(tof_ctx* c, ViewH& V, const ReuseArgs& ra, const Wa
             pb = std::min(pb, c->sms * V.tune.packet);
             vb = std::min(vb, c->sms * V.tune.packet);
         }
-        CK(launch_reuse_wave(ra, w, (int)p0, (int)p1, pb, vb, ev, s));
+        CK(launch_reuse_wave(ra, w, (int)p0, (int)p1, pb, vb, ev, s, beside ? V.side : nullptr, V.side_fork, V.side_join));
     }
     if (g_rec) ++g_rec->q;
     return TOF_OK;

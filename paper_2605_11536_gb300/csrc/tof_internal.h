@@ -164,10 +164,13 @@ struct WaveDev {
     float* terms;           // cap_units * S * S
     float4* rays;           // 2 * ray_cap: queued visibility segments of the shifts (VisQ)
     uint32_t ray_cap;
+    float4* rays2;          // 2 * ray2_cap: the segments of the canonical samples' inverse shifts when
+    uint32_t ray2_cap;      // those run beside the forward shifts (null: one queue, one sequence)
     uint32_t* counters;     // units, forward tasks, inverse tasks, overflow, forward rays, inverse rays,
-                            // forward rays fetched, inverse rays fetched
+                            // forward rays fetched, inverse rays fetched, [8] canonical inverse tasks
+                            // (the task count after the units kernel), [9] / [10] their rays / fetched
 };
-constexpr int kWaveCounters = 8;
+constexpr int kWaveCounters = 12;
 
 // wavefront of the gated initial stage with the ellipsoidal connection (tof_kernels.cu): the path
 // trees record their vertices, their NEE candidates and the ellipsoidal requests; the vertices are

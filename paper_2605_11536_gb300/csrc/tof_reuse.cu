@@ -444,14 +444,14 @@ __global__ void __launch_bounds__(128) emit_inv_kernel(const __grid_constant__ R
 // --------------------------------------------------------------------------------------------
 // inverse shifts: candidate s's offset path (in the unit's domain) into domain j
 // --------------------------------------------------------------------------------------------
+// tasks [t0, t1) of the list; their visibility segments go to `rays` (counter rcount, capacity rcap)
 template <bool kWalk>
-__device__ __forceinline__ void shift_inv_body(const ReuseArgs& a, const WaveDev& w) {
-    const uint32_t cap = (uint32_t)w.cap_units * (uint32_t)w.slots * (uint32_t)(w.slots - 1);
-    const uint32_t ntask = min(w.counters[2], cap);
+__device__ __forceinline__ void shift_inv_body(const ReuseArgs& a, const WaveDev& w, uint32_t t0, uint32_t t1, float4* rays,
+                                               uint32_t* rcount, uint32_t rcap) {
     const int S = w.slots;
     const int Bn = a.cur.B > 0 ? a.cur.B : 1;
     unsigned long long ninv = 0;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
+    for (uint32_t t = t0 + blockIdx.x * blockDim.x + threadIdx.x; t < t1; t += gridDim.x * blockDim.x) {
         ++ninv;
         uint32_t task = w.inv[t];
         uint32_t u = task >> 8;
@@ -475,7 +475,7 @@ __device__ __forceinline__ void shift_inv_body(const ReuseArgs& a, const WaveDev
         float term = 0.f;
         const size_t ti = ((size_t)u * S + s) * S + j;
         VisQ vq;
-        vq.rays = w.rays; vq.counter = &w.counters[5]; vq.cap = w.ray_cap; vq.target = (uint32_t)ti;
+        vq.rays = rays; vq.counter = rcount; vq.cap = rcap; vq.target = (uint32_t)ti;
         if (slot_present(a, j, b) && shift_rec<false, kWalk>(y, D0, Dj, a.P, geom_static, tmp, pj, Jj, nullptr, &vq))
             term = w.slot_M[(size_t)pix * S + j] * pj * Jj;
         w.terms[ti] = term;
@@ -489,9 +489,16 @@ __device__ __forceinline__ void shift_inv_body(const ReuseArgs& a, const WaveDev
         }
     }
 }
+__device__ __forceinline__ uint32_t inv_task_cap(const WaveDev& w) {
+    return (uint32_t)w.cap_units * (uint32_t)w.slots * (uint32_t)(w.slots - 1);
+}
+// tasks [*lo, *hi) (lo null: from 0), read when the kernel starts
 template <bool kWalk>
-__global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w) {
-    shift_inv_body<kWalk>(a, w);
+__global__ void __launch_bounds__(128, 8) shift_inv_kernel(const __grid_constant__ ReuseArgs a, const __grid_constant__ WaveDev w,
+                                                          const uint32_t* lo, const uint32_t* hi, float4* rays, uint32_t* rcount,
+                                                          uint32_t rcap) {
+    const uint32_t cap = inv_task_cap(w);
+    shift_inv_body<kWalk>(a, w, lo ? min(*lo, cap) : 0u, min(*hi, cap), rays, rcount, rcap);
 }
 
 // --------------------------------------------------------------------------------------------
@@ -701,7 +708,8 @@ __global__ void __launch_bounds__(128, 8) reuse_persist_batch_kernel(const Reuse
         else if constexpr (kStage == 1)
             vis_body(a.cur.g, w.rays, &w.counters[4], w.ray_cap, &w.counters[6], w.py, a.stats, 4, a.temporal ? -1 : 8);
         else if constexpr (kStage == 2) emit_inv_body(a, w);
-        else if constexpr (kStage == 3) shift_inv_body<false>(a, w);
+        else if constexpr (kStage == 3)
+            shift_inv_body<false>(a, w, 0u, min(w.counters[2], inv_task_cap(w)), w.rays, &w.counters[5], w.ray_cap);
         else if constexpr (kStage == 4)
             vis_body(a.temporal ? a.prev.g : a.cur.g, w.rays, &w.counters[5], w.ray_cap, &w.counters[7], w.terms, a.stats, -1,
                      a.temporal ? -1 : 9);
@@ -726,12 +734,21 @@ cudaError_t launch_reuse_batch(const ReuseJob* J, int n, const int* blk_slots, i
 
 // ev (optional): 7 events recorded around the stages (setup | forward shifts | their visibility and
 // the inverse-task emission | inverse shifts | their visibility | merge) for per-stage timing
+// One reuse pass.  With a second queue (w.rays2) and a second stream s2, the canonical samples'
+// inverse shifts -- listed by the units kernel, independent of the forward shifts -- and their
+// visibility run on s2 beside the forward shifts, their visibility and the inverse-task emission
+// (fork / join events); the emitted inverse shifts follow after the join.  The shifts and
+// segments are the same ones, so the results are those of the single sequence, which runs without
+// rays2 (spatial passes, batches, the allocation-free form).  Small passes gain: their persistent
+// kernels wait on a few long dependent chains while most of the GPU idles.
 cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int p1, int persist_blocks, int vis_blocks,
-                              cudaEvent_t* ev, cudaStream_t s) {
+                              cudaEvent_t* ev, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
     cudaError_t e = cudaMemsetAsync(w.counters, 0, kWaveCounters * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     int np = p1 - p0;
     if (np <= 0) return cudaSuccess;
+    const bool beside = w.rays2 && s2 && fork && join;
+    const GeomDev ginv = a.temporal ? a.prev.g : a.cur.g;   // inverse shifts land in the reused domain
     if (ev) cudaEventRecord(ev[0], s);
     note_launch();
     reuse_slots_kernel<<<(np + 127) / 128, 128, 0, s>>>(a, w, p0, p1);
@@ -740,6 +757,20 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
     reuse_units_kernel<<<(unsigned)((nw + 127) / 128), 128, 0, s>>>(a, w, p0, p1);
     if (ev) cudaEventRecord(ev[1], s);
     const bool walk = (a.P.flags & kFlagTriangleWalk) != 0u;
+    if (beside) {
+        // the canonical inverse tasks are those listed so far
+        e = cudaMemcpyAsync(&w.counters[8], &w.counters[2], sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, fork, 0);
+        if (e != cudaSuccess) return e;
+        note_launch(2);
+        if (walk) shift_inv_kernel<true><<<persist_blocks, 128, 0, s2>>>(a, w, nullptr, &w.counters[8], w.rays2, &w.counters[9], w.ray2_cap);
+        else shift_inv_kernel<false><<<persist_blocks, 128, 0, s2>>>(a, w, nullptr, &w.counters[8], w.rays2, &w.counters[9], w.ray2_cap);
+        vis_kernel<<<vis_blocks, 128, 0, s2>>>(ginv, w.rays2, &w.counters[9], w.ray2_cap, &w.counters[10], w.terms, a.stats, -1,
+                                               a.temporal ? -1 : 9);
+        e = cudaEventRecord(join, s2);
+        if (e != cudaSuccess) return e;
+    }
     if (walk) { note_launch(); shift_fwd_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w); }
     else { note_launch(); shift_fwd_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w); }
     if (ev) cudaEventRecord(ev[2], s);
@@ -750,14 +781,17 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
     note_launch();
     emit_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
     if (ev) cudaEventRecord(ev[3], s);
-    if (walk) { note_launch(); shift_inv_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w); }
-    else { note_launch(); shift_inv_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w); }
+    if (beside) {
+        e = cudaStreamWaitEvent(s, join, 0);
+        if (e != cudaSuccess) return e;
+    }
+    const uint32_t* lo = beside ? &w.counters[8] : nullptr;
+    if (walk) { note_launch(); shift_inv_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w, lo, &w.counters[2], w.rays, &w.counters[5], w.ray_cap); }
+    else { note_launch(); shift_inv_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w, lo, &w.counters[2], w.rays, &w.counters[5], w.ray_cap); }
     if (ev) cudaEventRecord(ev[4], s);
-    // inverse shifts land in the reused domain: the previous frame for the temporal pass (its one
-    // reused slot), the current frame for spatial passes
     note_launch();
-    vis_kernel<<<vis_blocks, 128, 0, s>>>(a.temporal ? a.prev.g : a.cur.g, w.rays, &w.counters[5], w.ray_cap, &w.counters[7],
-                                          w.terms, a.stats, -1, a.temporal ? -1 : 9);
+    vis_kernel<<<vis_blocks, 128, 0, s>>>(ginv, w.rays, &w.counters[5], w.ray_cap, &w.counters[7], w.terms, a.stats, -1,
+                                          a.temporal ? -1 : 9);
     if (ev) cudaEventRecord(ev[5], s);
     note_launch();
     reuse_merge_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
