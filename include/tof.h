@@ -203,7 +203,10 @@ tof_status tof_view_destroy(tof_ctx* ctx, tof_view view);
  * the shrink mapping, views of up to 16M pixels x trees run the initial stage as a bounce
  * wavefront whose scratch (about 240 MB for 512 x 512 x 4 trees at depth 4) the first such render
  * allocates; it gives the same reservoirs as the single kernel that small instances of a batch
- * and the allocation-free form run. */
+ * and the allocation-free form run.  The temporal pass runs part of its work on a stream of the view
+ * (created with the view's first such render), forked from `stream` by an event and joined back
+ * into it before the spatial passes, so the frame completes in `stream` order as before, and a
+ * capture of `stream` into a CUDA graph takes that branch in. */
 tof_status tof_render_gated(tof_ctx* ctx, tof_scene scene, tof_view view, const tof_sensor* sensor,
                             const tof_emitter* emitter, const tof_gate* gate, const tof_params* params,
                             uint64_t seed, uint32_t frame, float* out_image_dev, void* stream);
