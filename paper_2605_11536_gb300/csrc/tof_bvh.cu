@@ -12,6 +12,8 @@
 //                   areas, bottom-up: 8 levels per block in shared memory, then one block)
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "tof_internal.h"
 
 namespace tof {
@@ -164,6 +166,78 @@ __global__ void __launch_bounds__(256) radix_scatter_kernel(const uint32_t* __re
     }
 }
 
+// The same four passes in one cooperative launch of one block per tile (all resident): per pass
+// the tile histograms, a grid-wide sync, each block's digit offsets -- the digit totals' exclusive
+// scan plus the digit's count in the earlier tiles, the global scan above restated per block --
+// the same stable scatter, and a grid-wide sync.  Sorted keys and values are those of the
+// separate launches (after four passes back in k0 / v0).
+__global__ void __launch_bounds__(256) radix_sort_coop_kernel(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int n,
+                                                              uint32_t* __restrict__ hist, int ntiles) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    __shared__ uint32_t h[256];
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wc[8][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    for (int shift = 0; shift < 32; shift += 8) {
+        h[tid] = 0u;
+        __syncthreads();
+        const int t0 = blockIdx.x * kTile;
+        for (int i = tid; i < kTile; i += 256) {
+            const int g = t0 + i;
+            if (g < n) atomicAdd(&h[(__ldcg(&ki[g]) >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        hist[tid * ntiles + blockIdx.x] = h[tid];
+        __threadfence();
+        grid.sync();
+        uint32_t tot = 0u, before = 0u;
+        for (int t = 0; t < ntiles; ++t) {
+            const uint32_t c = __ldcg(&hist[tid * ntiles + t]);
+            tot += c;
+            if (t < (int)blockIdx.x) before += c;
+        }
+        h[tid] = tot;
+        __syncthreads();
+        for (int off = 1; off < 256; off <<= 1) {   // inclusive scan of the digit totals
+            const uint32_t v = tid >= off ? h[tid - off] : 0u;
+            __syncthreads();
+            h[tid] += v;
+            __syncthreads();
+        }
+        base[tid] = h[tid] - tot + before;
+        for (int r = 0; r < kTile / 256; ++r) {
+            for (int k = 0; k < 8; ++k) wc[k][tid] = 0u;
+            __syncthreads();
+            const int i = t0 + r * 256 + tid;
+            const bool valid = i < n;
+            const uint32_t key = valid ? __ldcg(&ki[i]) : 0u;
+            const uint32_t dg = (key >> shift) & 255u;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, valid ? dg : 256u + (uint32_t)lane);
+            const uint32_t rank = __popc(peers & lt);
+            if (valid && rank == 0) wc[warp][dg] = __popc(peers);
+            __syncthreads();
+            if (valid) {
+                uint32_t off = base[dg] + rank;
+                for (int w = 0; w < warp; ++w) off += wc[w][dg];
+                ko[off] = key;
+                vo[off] = __ldcg(&vi[i]);
+            }
+            __syncthreads();
+            uint32_t add = 0;
+            for (int w = 0; w < 8; ++w) add += wc[w][tid];
+            base[tid] += add;
+            __syncthreads();
+        }
+        __threadfence();
+        grid.sync();
+        uint32_t* t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+}
+
 // ---- Karras 2012 hierarchy --------------------------------------------------------------------
 __device__ __forceinline__ int delta(const uint32_t* __restrict__ k, int n, int i, int j) {
     if (j < 0 || j >= n) return -1;
@@ -226,6 +300,14 @@ __device__ __forceinline__ Box node_box(const float4* N) {
     return b;
 }
 
+// arrival counter of a node: acquire-release at device scope, so that the second arrival sees the
+// node the first arrival wrote below it (release of its writes, acquire of the sibling's)
+__device__ __forceinline__ uint32_t arrive_acq_rel(uint32_t* p) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
+
 __global__ void refit_kernel(int n, const uint32_t* __restrict__ prim, const float4* __restrict__ tri, float4* __restrict__ leaf,
                              float4* nodes, const int* __restrict__ child, const int* __restrict__ parent_int,
                              const int* __restrict__ parent_leaf, uint32_t* __restrict__ counter) {
@@ -238,11 +320,9 @@ __global__ void refit_kernel(int n, const uint32_t* __restrict__ prim, const flo
     leaf[3 * (size_t)L + 2] = tri[3 * (size_t)t + 2];
     if (n == 1) return;
     int p = parent_leaf[L];
-    __threadfence();
     int guard = n;   // depth of a valid hierarchy is below n
     while (p >= 0 && --guard >= 0) {
-        if (atomicAdd(&counter[p], 1u) == 0u) return;   // first arrival: the sibling finishes p
-        __threadfence();
+        if (arrive_acq_rel(&counter[p]) == 0u) return;   // first arrival: the sibling finishes p
         int c[2] = {child[2 * p], child[2 * p + 1]};
         Box b[2];
         for (int k = 0; k < 2; ++k) b[k] = c[k] < 0 ? tri_box(tri, (int)prim[~c[k]]) : node_box(nodes + 4 * (size_t)c[k]);
@@ -251,7 +331,6 @@ __global__ void refit_kernel(int n, const uint32_t* __restrict__ prim, const flo
         N[1] = make_float4(b[1].lo[0], b[1].hi[0], b[1].lo[1], b[1].hi[1]);
         N[2] = make_float4(b[0].lo[2], b[0].hi[2], b[1].lo[2], b[1].hi[2]);
         N[3] = make_float4(__int_as_float(c[0]), __int_as_float(c[1]), 0.f, 0.f);
-        __threadfence();
         p = parent_int[p];
     }
 }
@@ -340,6 +419,35 @@ cudaError_t launch_build_topology(int n, const float4* cent, uint32_t* bb, uint3
     morton_kernel<<<blocks(n, 256), 256, 0, s>>>(n, cent, bb, keys, vals);
     int ntiles = (n + kTile - 1) / kTile;
     uint32_t *ki = keys, *vi = vals, *ko = keys2, *vo = vals2;
+    // one cooperative launch when every tile's block can be resident at once
+    // resident blocks of the cooperative sort on each device (found once per device and process)
+    static std::atomic<int> coop_blocks[64];
+    static std::atomic<bool> coop_known[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int coop_cap = 0;
+    if (dev >= 0 && dev < 64) {
+        if (!coop_known[dev].load()) {
+            int sms = 0, per = 0, coop = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, radix_sort_coop_kernel, 256, 0);
+            cudaGetLastError();
+            coop_blocks[dev].store(coop ? sms * per : 0);
+            coop_known[dev].store(true);
+        }
+        coop_cap = coop_blocks[dev].load();
+    }
+    if (ntiles <= coop_cap) {
+        int nn = n, nt = ntiles;
+        void* args[] = {&ki, &vi, &ko, &vo, &nn, &hist, &nt};
+        note_launch();
+        e = cudaLaunchCooperativeKernel((const void*)radix_sort_coop_kernel, dim3(ntiles), dim3(256), args, 0, s);
+        if (e != cudaSuccess) return e;
+        if (n > 1) { note_launch(); karras_kernel<<<blocks(n - 1, 256), 256, 0, s>>>(n, ki, child, parent_int, parent_leaf); }
+        *prim_out = vi;
+        return cudaGetLastError();
+    }
     for (int shift = 0; shift < 32; shift += 8) {
         note_launch();
         radix_hist_kernel<<<ntiles, 256, 0, s>>>(ki, n, shift, hist, ntiles);
