@@ -749,6 +749,9 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
     if (np <= 0) return cudaSuccess;
     const bool beside = w.rays2 && s2 && fork && join;
     const GeomDev ginv = a.temporal ? a.prev.g : a.cur.g;   // inverse shifts land in the reused domain
+    // only the generalized balance heuristic over three or more slots emits inverse shifts for the
+    // shifted candidates (emit_inv_body); otherwise every inverse shift is a canonical one
+    const bool emits = w.slots > 2 && !(a.P.flags & kFlagPairwiseMis);
     if (ev) cudaEventRecord(ev[0], s);
     note_launch();
     reuse_slots_kernel<<<(np + 127) / 128, 128, 0, s>>>(a, w, p0, p1);
@@ -778,20 +781,26 @@ cudaError_t launch_reuse_wave(const ReuseArgs& a, const WaveDev& w, int p0, int 
     note_launch();
     vis_kernel<<<vis_blocks, 128, 0, s>>>(a.cur.g, w.rays, &w.counters[4], w.ray_cap, &w.counters[6], w.py, a.stats, 4,
                                           a.temporal ? -1 : 8);
-    note_launch();
-    emit_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    if (emits) {
+        note_launch();
+        emit_inv_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
+    }
     if (ev) cudaEventRecord(ev[3], s);
     if (beside) {
         e = cudaStreamWaitEvent(s, join, 0);
         if (e != cudaSuccess) return e;
     }
-    const uint32_t* lo = beside ? &w.counters[8] : nullptr;
-    if (walk) { note_launch(); shift_inv_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w, lo, &w.counters[2], w.rays, &w.counters[5], w.ray_cap); }
-    else { note_launch(); shift_inv_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w, lo, &w.counters[2], w.rays, &w.counters[5], w.ray_cap); }
+    if (emits || !beside) {   // beside with nothing emitted: the second stream did every inverse shift
+        const uint32_t* lo = beside ? &w.counters[8] : nullptr;
+        if (walk) { note_launch(); shift_inv_kernel<true><<<persist_blocks, 128, 0, s>>>(a, w, lo, &w.counters[2], w.rays, &w.counters[5], w.ray_cap); }
+        else { note_launch(); shift_inv_kernel<false><<<persist_blocks, 128, 0, s>>>(a, w, lo, &w.counters[2], w.rays, &w.counters[5], w.ray_cap); }
+    }
     if (ev) cudaEventRecord(ev[4], s);
-    note_launch();
-    vis_kernel<<<vis_blocks, 128, 0, s>>>(ginv, w.rays, &w.counters[5], w.ray_cap, &w.counters[7], w.terms, a.stats, -1,
-                                          a.temporal ? -1 : 9);
+    if (emits || !beside) {
+        note_launch();
+        vis_kernel<<<vis_blocks, 128, 0, s>>>(ginv, w.rays, &w.counters[5], w.ray_cap, &w.counters[7], w.terms, a.stats, -1,
+                                              a.temporal ? -1 : 9);
+    }
     if (ev) cudaEventRecord(ev[5], s);
     note_launch();
     reuse_merge_kernel<<<persist_blocks, 128, 0, s>>>(a, w);
