@@ -72,15 +72,15 @@ BYTES = {
 # kernel changes; the hash below ties the figures to the sources they were captured on.
 ELL_WAVE = "ell_trees_kernel + ell_place_kernel + ell_select_kernel"
 TREE_WAVE = "tw_start_kernel + 3 x (tw_hit_kernel + tw_shade_kernel) + vis_kernel + tree_select_kernel"
-NCU_TRAFFIC_SRC = "57795d6fa060"   # _src_hash() of the sources the figures below were captured on
+NCU_TRAFFIC_SRC = "ac8af494847f"   # _src_hash() of the sources the figures below were captured on
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (one stage for the initial wavefront),
 # frame 5 (profiles/launches_dynamic_gated_512.md, profiles/tree_wavefront_dynamic_gated_512.md)
-NCU_TRAFFIC = {TREE_WAVE: 306.16e6, "shift_inv_kernel<0>": 184.94e6 + 378.70e6, "shift_fwd_kernel<0>": 163.96e6 + 239.84e6,
-               "vis_kernel (inverse segments)": 87.55e6 + 2.90e6, "reuse_merge_kernel": 115.75e6 + 7.47e6}
+NCU_TRAFFIC = {TREE_WAVE: 306.09e6, "shift_inv_kernel<0>": 185.79e6 + 380.14e6, "shift_fwd_kernel<0>": 166.26e6 + 240.34e6,
+               "vis_kernel (inverse segments)": 87.57e6 + 2.90e6, "reuse_merge_kernel": 115.84e6 + 7.45e6}
 # L1 / L2 sector hit rates (%) and active lanes per warp instruction of the traversal-bound kernels,
 # from the same capture (the initial wavefront's first closest-hit round)
-NCU_HIT = {"tw_hit_kernel": [87.5, 71.8, 12.1], "shift_fwd_kernel<0>": [41.9, 45.4, 20.4],
-           "shift_inv_kernel<0>": [47.0, 64.9, 22.1], "vis_kernel": [94.9, 67.1, 13.5]}
+NCU_HIT = {"tw_hit_kernel": [87.5, 72.0, 12.1], "shift_fwd_kernel<0>": [42.0, 45.1, 20.4],
+           "shift_inv_kernel<0>": [46.9, 64.8, 22.1], "vis_kernel": [94.8, 67.2, 13.5]}
 
 
 def _peaks():
